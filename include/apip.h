@@ -1,0 +1,178 @@
+/*
+ * apip.h -- C ABI of libapip, the GB300 (sm_103a) force evaluation of the
+ * conservative adaptive-precision (AP) EAM+ACE potential of arxiv 2512.07693
+ * ("Conservative adaptive-precision interatomic potentials").
+ *
+ *   E   = sum_i [ lam_i E_i^prec + (1 - lam_i) E_i^EAM ]           (Eq. 4)
+ *   F_i = -grad_i E, including the (E^prec - E^EAM) grad lam terms  (Eq. 5)
+ *
+ * lam is the weight of the PRECISE model (lam = 1: precise, lam = 0: fast EAM);
+ * the paper's lambda (Eq. 2) is the weight of the fast model, lambda = 1 - lam.
+ * The precise model is ACE, optionally on top of the EAM
+ * (apip_params.precise_adds_eam: E^prec = E^ACE + E^EAM).
+ *
+ * Conventions for every call:
+ *  - Units: Angstrom, eV, ps; inv_mass in (A/ps^2)/(eV/A), i.e. 1/(m[amu] * 1.0364269e-4).
+ *  - Vectors are AoS [n][3] float64, row-major, contiguous.  Every array
+ *    argument is a DEVICE pointer owned by the caller, except where a comment
+ *    says "host".  The library never frees caller memory.
+ *  - box: host array of the three edge lengths of an orthorhombic periodic
+ *    cell.  Each edge must be >= 3 * (cutoff + skin).  Positions may lie
+ *    outside [0, L); they are treated periodically.
+ *  - id: int32 atom identifiers, unique, in [0, n_atoms_max).  The CSP pair
+ *    list stores partner IDs, so atoms may be reordered between calls.
+ *  - type: int32, single species; must be 0.
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are asynchronous: the returned status covers argument checks and
+ *    launch errors.  Errors detected on the device (neighbour overflow,
+ *    non-finite input) are latched in the context and returned by the next
+ *    apip_sync() (which synchronises the stream).
+ *  - Not thread-safe for one context; distinct contexts are independent.
+ */
+#ifndef APIP_H
+#define APIP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct apip_ctx apip_ctx;
+
+typedef enum {
+  APIP_OK = 0,
+  APIP_ERR_ARG = 1,          /* invalid argument: NULL pointer, size, parameter, box too small */
+  APIP_ERR_CUDA = 2,         /* a CUDA runtime call failed (apip_last_error has the text) */
+  APIP_ERR_NB_OVERFLOW = 3,  /* an atom had more neighbours than max_nb, or a cell more atoms
+                                than cell_cap; apip_last_error reports the size needed */
+  APIP_ERR_BAD_INPUT = 4,    /* non-finite position, id out of range, or a CSP partner ID
+                                that is not present */
+  APIP_ERR_STATE = 5         /* call order: apip_init_csp_pairs must precede calls that use
+                                the paper's switch */
+} apip_status;
+
+enum { APIP_FP64 = 0, APIP_FP32 = 1 };
+
+/* How lam is obtained.
+ * APIP_LAM_PAPER : lam_i = 1 - f_trans(d_i, d_lo, d_hi), d_i the locally averaged
+ *                  CSP^list descriptor (Eq. 2, Eq. 6, Eq. B3).
+ * APIP_LAM_CONST0: lam = 0 for all atoms (pure fast model).
+ * APIP_LAM_CONST1: lam = 1 for all atoms (pure precise model). */
+enum { APIP_LAM_PAPER = 0, APIP_LAM_CONST0 = 1, APIP_LAM_CONST1 = 2 };
+
+/* Model and run parameters; copied by apip_create.  Field order is ABI. */
+typedef struct apip_params {
+  int32_t precision;         /* APIP_FP64 (all arithmetic in float64) or APIP_FP32 (pair
+                                arithmetic in float32 with compensated sums; positions,
+                                velocities, force output and energy reductions float64) */
+  int32_t lam_mode;          /* APIP_LAM_* */
+  int32_t grad_lambda;       /* 1: include F^(grad lambda) (conservative, Eq. S15-S27);
+                                0: drop it (the non-conservative ablation of Fig. 3b) */
+  int32_t precise_adds_eam;  /* 1: E^prec = E^ACE + E^EAM; 0: E^prec = E^ACE */
+  /* fast model, Eq. B1: rho(r) = A exp(-beta (r - re)) fc(r),
+     Phi(r) = D [exp(-2 alpha (r - r0)) - 2 exp(-alpha (r - r0))] fc(r),
+     xi(z) = -sqrt(z), fc(r) = f_trans(r, rc - rc_width, rc) */
+  double eam_A, eam_beta, eam_re, eam_D, eam_alpha, eam_r0, eam_rc, eam_rc_width;
+  /* precise model: ACE with Chebyshev radial basis R_n = T_{n-1}(1 - 2r/rc) fc(r),
+     real Y_lm, A_nlm = a_scale sum_j R_n Y_lm, canonical product basis of body
+     order <= nu_max, E = c1.B + (( c2.B )^2 + eps^2)^(1/4) - sqrt(eps).
+     n_max in [1, 8], l_max in [0, 4], nu_max in [1, 4], n_max (l_max+1)^2 <= 254. */
+  int32_t ace_n_max, ace_l_max, ace_nu_max, ace_pad;
+  double ace_rc, ace_rc_width, ace_eps, ace_a_scale;
+  const double* ace_c1;      /* host, ace_n_basis entries (copied) */
+  const double* ace_c2;      /* host, ace_n_basis entries (copied) */
+  int64_t ace_n_basis;       /* must equal apip_ace_basis_size(n_max, l_max, nu_max) */
+  /* switch (Eq. 2, Eq. 6, Appendix B): w(r) = f_trans(r, r_w - r_w_width, r_w) */
+  double sw_r_w, sw_r_w_width, sw_d_lo, sw_d_hi, sw_d0;
+  /* CSP^list pair detection (Eq. B3): csp_nnb nearest neighbours within csp_rcut */
+  double csp_rcut;
+  int32_t csp_nnb;           /* even, <= 8 */
+  int32_t nb_pad;
+  /* neighbour list: cutoff = max(eam_rc, ace_rc, sw_r_w) + skin */
+  double skin;
+  int32_t max_nb;            /* neighbour capacity per atom (<= 256) */
+  int32_t cell_cap;          /* atom capacity per cell (<= 256) */
+} apip_params;
+
+/* Number of product-basis functions of the canonical ACE basis (the length of
+ * ace_c1 / ace_c2), or -1 for out-of-range arguments.  Enumeration order: nu = 1
+ * (n, 0); nu = 2 pairs p1 <= p2 with equal l; nu = 3 triples p1 <= p2 <= p3 with
+ * even l-sum and the triangle rule; nu = 4 quadruples p1 <= ... <= p4 with an
+ * intermediate L coupling (12)(34); p = (n-1)(l_max+1) + l. */
+int64_t apip_ace_basis_size(int32_t n_max, int32_t l_max, int32_t nu_max);
+
+/* Create a context for up to n_atoms_max atoms.  Allocates all scratch (cells,
+ * neighbour list, per-atom switch arrays, ACE tables) on the current device.
+ * Errors: APIP_ERR_ARG (bad parameters), APIP_ERR_CUDA (allocation). */
+apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** out);
+
+/* Free a context and its device memory (synchronises the device). NULL is ok. */
+apip_status apip_destroy(apip_ctx* ctx);
+
+/* Build the cell-binned neighbour list (cutoff + skin) for the n atoms at pos.
+ * Normally not needed: the force calls rebuild on their own when an atom has
+ * moved more than skin/2 since the last build.  Paper: distances only (main text
+ * after Eq. 5); the list itself is an implementation device. */
+apip_status apip_build_neighbors(apip_ctx* ctx, const double* pos, const double box[3],
+                                 const int32_t* id, int64_t n, void* stream);
+
+/* Detect the CSP^list opposite-neighbour pairs once (t = 0, Appendix B, Eq. B3):
+ * for each atom the csp_nnb nearest neighbours within csp_rcut (ties by ID) are
+ * paired greedily by ascending |r_ia + r_ib|^2.  Partner IDs are kept for the
+ * rest of the context's life. */
+apip_status apip_init_csp_pairs(apip_ctx* ctx, const double* pos, const double box[3],
+                                const int32_t* id, int64_t n, void* stream);
+
+/* Switch only (Eq. 2, Eq. 6): writes lam (ACE weight) and dlam = d lam/d d_i for
+ * every atom (float64, optional, may be NULL) and the number of atoms with lam > 0
+ * (the compacted precise + transition set) to *n_ace_out (device int64, may be NULL). */
+apip_status apip_switch(apip_ctx* ctx, const double* pos, const double box[3],
+                        const int32_t* type, const int32_t* id, int64_t n,
+                        double* lam_out, double* dlam_out, int64_t* n_ace_out, void* stream);
+
+/* Energy and forces (Eq. 4, Eq. 5).  force_out [n][3] is overwritten with F = -grad E.
+ * e_atom_out [n] (optional) receives lam_i E_i^prec + (1 - lam_i) E_i^EAM.
+ * e_total_out (device scalar, optional) receives E, reduced in float64. */
+apip_status apip_energy_forces(apip_ctx* ctx, const double* pos, const double box[3],
+                               const int32_t* type, const int32_t* id, int64_t n,
+                               double* force_out, double* e_atom_out, double* e_total_out,
+                               void* stream);
+
+/* n_steps velocity-Verlet NVE steps (float64 state).  On entry force holds F(pos)
+ * (from apip_energy_forces); on exit pos, vel, force are advanced and wrapped into
+ * the box.  thermo_out (device, optional) receives per step s = 0..n_steps-1 five
+ * float64 values: E_pot, E_kin = sum v^2 / (2 inv_mass), and the total momentum
+ * sum v / inv_mass (x, y, z), all after the step. */
+apip_status apip_verlet_step(apip_ctx* ctx, double* pos, double* vel, double* force,
+                             const double* inv_mass, const double box[3],
+                             const int32_t* type, const int32_t* id, int64_t n, double dt,
+                             int32_t n_steps, double* thermo_out, void* stream);
+
+/* Synchronise the stream and return the first device-side error latched since
+ * the last apip_sync (APIP_OK if none); clears the latch. */
+apip_status apip_sync(apip_ctx* ctx, void* stream);
+
+/* Text of the last error of this context ("" if none). Never NULL. */
+const char* apip_last_error(apip_ctx* ctx);
+
+/* Internal per-atom arrays of the last force/switch call, for inspection and
+ * testing.  Copies n entries as float64 into dst (device) unless stated:
+ *   APIP_FIELD_G, _D, _WBAR, _LAM, _DLAM, _E_EAM, _E_ACE (0 unless lam > 0), _ZETA
+ *   APIP_FIELD_ACE_LIST : int64 dst, the compacted atom indices with lam > 0
+ *                         (unordered; only the first count entries are defined)
+ *   APIP_FIELD_NNB      : int64 dst, neighbours per atom (within cutoff + skin)
+ *   APIP_FIELD_NBLIST   : int64 dst [n][max_nb], neighbour indices (-1 padded)
+ *   APIP_FIELD_CSP      : int64 dst [n][csp_nnb], partner IDs (-1 = none) */
+enum {
+  APIP_FIELD_G = 0, APIP_FIELD_D = 1, APIP_FIELD_WBAR = 2, APIP_FIELD_LAM = 3,
+  APIP_FIELD_DLAM = 4, APIP_FIELD_E_EAM = 5, APIP_FIELD_E_ACE = 6, APIP_FIELD_ZETA = 7,
+  APIP_FIELD_ACE_LIST = 8, APIP_FIELD_NNB = 9, APIP_FIELD_NBLIST = 10, APIP_FIELD_CSP = 11
+};
+apip_status apip_get_field(apip_ctx* ctx, int32_t field, void* dst, int64_t n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APIP_H */

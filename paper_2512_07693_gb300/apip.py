@@ -1,0 +1,239 @@
+"""Python binding of libapip (ctypes over the C ABI of include/apip.h).
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels.  Functions carry the C names; tensors are torch CUDA tensors
+(float64 for positions/velocities/forces/energies, int32 for ids and types)
+and are passed by device pointer.  ``stream`` defaults to torch's current
+stream.  Importing this module fails loudly if the library has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libapip.so")
+
+APIP_OK, APIP_ERR_ARG, APIP_ERR_CUDA, APIP_ERR_NB_OVERFLOW, APIP_ERR_BAD_INPUT, APIP_ERR_STATE = range(6)
+STATUS_NAMES = {0: "APIP_OK", 1: "APIP_ERR_ARG", 2: "APIP_ERR_CUDA", 3: "APIP_ERR_NB_OVERFLOW",
+                4: "APIP_ERR_BAD_INPUT", 5: "APIP_ERR_STATE"}
+APIP_FP64, APIP_FP32 = 0, 1
+APIP_LAM_PAPER, APIP_LAM_CONST0, APIP_LAM_CONST1 = 0, 1, 2
+FIELDS = dict(g=0, d=1, wbar=2, lam=3, dlam=4, e_eam=5, e_ace=6, zeta=7, ace_list=8, nnb=9, nblist=10, csp=11)
+MVV2E = 1.0364269e-4   # amu A^2 / ps^2 -> eV
+
+_c_int32, _c_int64, _c_double, _vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+
+class ApipParams(ctypes.Structure):
+    """Mirror of struct apip_params (field order is ABI)."""
+    _fields_ = [
+        ("precision", _c_int32), ("lam_mode", _c_int32), ("grad_lambda", _c_int32), ("precise_adds_eam", _c_int32),
+        ("eam_A", _c_double), ("eam_beta", _c_double), ("eam_re", _c_double), ("eam_D", _c_double),
+        ("eam_alpha", _c_double), ("eam_r0", _c_double), ("eam_rc", _c_double), ("eam_rc_width", _c_double),
+        ("ace_n_max", _c_int32), ("ace_l_max", _c_int32), ("ace_nu_max", _c_int32), ("ace_pad", _c_int32),
+        ("ace_rc", _c_double), ("ace_rc_width", _c_double), ("ace_eps", _c_double), ("ace_a_scale", _c_double),
+        ("ace_c1", ctypes.POINTER(_c_double)), ("ace_c2", ctypes.POINTER(_c_double)), ("ace_n_basis", _c_int64),
+        ("sw_r_w", _c_double), ("sw_r_w_width", _c_double), ("sw_d_lo", _c_double), ("sw_d_hi", _c_double),
+        ("sw_d0", _c_double),
+        ("csp_rcut", _c_double), ("csp_nnb", _c_int32), ("nb_pad", _c_int32),
+        ("skin", _c_double), ("max_nb", _c_int32), ("cell_cap", _c_int32),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2512_07693_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    sig = {
+        "apip_ace_basis_size": (_c_int64, [_c_int32, _c_int32, _c_int32]),
+        "apip_create": (ctypes.c_int, [P(ApipParams), _c_int64, P(_vp)]),
+        "apip_destroy": (ctypes.c_int, [_vp]),
+        "apip_build_neighbors": (ctypes.c_int, [_vp, _vp, P(_c_double), _vp, _c_int64, _vp]),
+        "apip_init_csp_pairs": (ctypes.c_int, [_vp, _vp, P(_c_double), _vp, _c_int64, _vp]),
+        "apip_switch": (ctypes.c_int, [_vp, _vp, P(_c_double), _vp, _vp, _c_int64, _vp, _vp, _vp, _vp]),
+        "apip_energy_forces": (ctypes.c_int, [_vp, _vp, P(_c_double), _vp, _vp, _c_int64, _vp, _vp, _vp, _vp]),
+        "apip_verlet_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, P(_c_double), _vp, _vp, _c_int64, _c_double,
+                                            _c_int32, _vp, _vp]),
+        "apip_sync": (ctypes.c_int, [_vp, _vp]),
+        "apip_last_error": (ctypes.c_char_p, [_vp]),
+        "apip_get_field": (ctypes.c_int, [_vp, _c_int32, _vp, _c_int64, _vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class ApipError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _box(box):
+    return (_c_double * 3)(*[float(x) for x in box])
+
+
+def _check(ctx, st):
+    if st != APIP_OK:
+        raise ApipError(st, lib.apip_last_error(ctx).decode() if ctx else "")
+
+
+# ------------------------------------------------------------ C-named calls
+def apip_ace_basis_size(n_max, l_max, nu_max):
+    return int(lib.apip_ace_basis_size(n_max, l_max, nu_max))
+
+
+def apip_create(params, n_atoms_max):
+    ctx = _vp()
+    st = lib.apip_create(ctypes.byref(params), int(n_atoms_max), ctypes.byref(ctx))
+    if st != APIP_OK:
+        raise ApipError(st, "apip_create rejected the parameters or could not allocate")
+    return ctx
+
+
+def apip_destroy(ctx):
+    return lib.apip_destroy(ctx)
+
+
+def apip_build_neighbors(ctx, pos, box, id, n, stream=None):
+    _check(ctx, lib.apip_build_neighbors(ctx, _ptr(pos), _box(box), _ptr(id), int(n), _stream(stream)))
+
+
+def apip_init_csp_pairs(ctx, pos, box, id, n, stream=None):
+    _check(ctx, lib.apip_init_csp_pairs(ctx, _ptr(pos), _box(box), _ptr(id), int(n), _stream(stream)))
+
+
+def apip_switch(ctx, pos, box, type, id, n, lam_out=None, dlam_out=None, n_ace_out=None, stream=None):
+    _check(ctx, lib.apip_switch(ctx, _ptr(pos), _box(box), _ptr(type), _ptr(id), int(n), _ptr(lam_out),
+                                _ptr(dlam_out), _ptr(n_ace_out), _stream(stream)))
+
+
+def apip_energy_forces(ctx, pos, box, type, id, n, force_out, e_atom_out=None, e_total_out=None, stream=None):
+    _check(ctx, lib.apip_energy_forces(ctx, _ptr(pos), _box(box), _ptr(type), _ptr(id), int(n), _ptr(force_out),
+                                       _ptr(e_atom_out), _ptr(e_total_out), _stream(stream)))
+
+
+def apip_verlet_step(ctx, pos, vel, force, inv_mass, box, type, id, n, dt, n_steps, thermo_out=None, stream=None):
+    _check(ctx, lib.apip_verlet_step(ctx, _ptr(pos), _ptr(vel), _ptr(force), _ptr(inv_mass), _box(box), _ptr(type),
+                                     _ptr(id), int(n), float(dt), int(n_steps), _ptr(thermo_out), _stream(stream)))
+
+
+def apip_sync(ctx, stream=None):
+    _check(ctx, lib.apip_sync(ctx, _stream(stream)))
+
+
+def apip_last_error(ctx):
+    return lib.apip_last_error(ctx).decode()
+
+
+def apip_get_field(ctx, field, dst, n, stream=None):
+    f = FIELDS[field] if isinstance(field, str) else int(field)
+    _check(ctx, lib.apip_get_field(ctx, f, _ptr(dst), int(n), _stream(stream)))
+
+
+# ---------------------------------------------------------------- helpers
+def make_params(prm, precision="fp64", lam_mode="paper", grad_lambda=True, skin=0.5, max_nb=96, cell_cap=64):
+    """apip_params from a parameter dict (keys eam, ace, switch, csp,
+    precise_adds_eam).  The returned structure keeps the coefficient arrays
+    alive through its ``_keep`` attribute."""
+    e, a, s, c = prm["eam"], prm["ace"], prm["switch"], prm["csp"]
+    c1 = np.ascontiguousarray(a["c1"], dtype=np.float64)
+    c2 = np.ascontiguousarray(a["c2"], dtype=np.float64)
+    p = ApipParams()
+    p.precision = {"fp64": APIP_FP64, "fp32": APIP_FP32}[precision]
+    p.lam_mode = {"paper": APIP_LAM_PAPER, "const0": APIP_LAM_CONST0, "const1": APIP_LAM_CONST1}[lam_mode]
+    p.grad_lambda = int(bool(grad_lambda))
+    p.precise_adds_eam = int(bool(prm.get("precise_adds_eam", False)))
+    p.eam_A, p.eam_beta, p.eam_re = e["A"], e["beta"], e["r_e"]
+    p.eam_D, p.eam_alpha, p.eam_r0 = e["D"], e["alpha"], e["r_0"]
+    p.eam_rc, p.eam_rc_width = e["rc"], e["rc_width"]
+    p.ace_n_max, p.ace_l_max, p.ace_nu_max = a["n_max"], a["l_max"], a["nu_max"]
+    p.ace_rc, p.ace_rc_width, p.ace_eps, p.ace_a_scale = a["rc"], a["rc_width"], a["eps"], a["a_scale"]
+    nb = apip_ace_basis_size(a["n_max"], a["l_max"], a["nu_max"])
+    assert len(c1) >= nb and len(c2) >= nb
+    c1, c2 = np.ascontiguousarray(c1[:nb]), np.ascontiguousarray(c2[:nb])
+    p.ace_c1 = c1.ctypes.data_as(ctypes.POINTER(_c_double))
+    p.ace_c2 = c2.ctypes.data_as(ctypes.POINTER(_c_double))
+    p.ace_n_basis = nb
+    p.sw_r_w, p.sw_r_w_width = s["r_w"], s["r_w_width"]
+    p.sw_d_lo, p.sw_d_hi, p.sw_d0 = s["d_lo"], s["d_hi"], s["d0"]
+    p.csp_rcut, p.csp_nnb = c["rcut"], c["nnb"]
+    p.skin, p.max_nb, p.cell_cap = skin, max_nb, cell_cap
+    p._keep = (c1, c2)
+    return p
+
+
+class Apip:
+    """One library context with its parameters; thin convenience over the C calls."""
+
+    def __init__(self, prm, n_atoms_max, **kw):
+        self.params = make_params(prm, **kw)
+        self.ctx = apip_create(self.params, n_atoms_max)
+        self.n_atoms_max = int(n_atoms_max)
+        self.max_nb = self.params.max_nb
+        self.csp_nnb = self.params.csp_nnb
+
+    def close(self):
+        if self.ctx:
+            apip_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_csp_pairs(self, pos, box, ids, stream=None):
+        apip_init_csp_pairs(self.ctx, pos, box, ids, pos.shape[0], stream)
+
+    def build_neighbors(self, pos, box, ids, stream=None):
+        apip_build_neighbors(self.ctx, pos, box, ids, pos.shape[0], stream)
+
+    def switch(self, pos, box, types, ids, lam_out=None, dlam_out=None, n_ace_out=None, stream=None):
+        apip_switch(self.ctx, pos, box, types, ids, pos.shape[0], lam_out, dlam_out, n_ace_out, stream)
+
+    def energy_forces(self, pos, box, types, ids, force_out, e_atom_out=None, e_total_out=None, stream=None):
+        apip_energy_forces(self.ctx, pos, box, types, ids, pos.shape[0], force_out, e_atom_out, e_total_out, stream)
+
+    def verlet_step(self, pos, vel, force, inv_mass, box, types, ids, dt, n_steps, thermo_out=None, stream=None):
+        apip_verlet_step(self.ctx, pos, vel, force, inv_mass, box, types, ids, pos.shape[0], dt, n_steps,
+                         thermo_out, stream)
+
+    def sync(self, stream=None):
+        apip_sync(self.ctx, stream)
+
+    def field(self, name, n):
+        """Copy an internal per-atom array into a new torch tensor."""
+        import torch
+        dev = torch.device("cuda")
+        if name == "nblist":
+            out = torch.empty((n, self.max_nb), dtype=torch.int64, device=dev)
+        elif name == "csp":
+            out = torch.empty((n, self.csp_nnb), dtype=torch.int64, device=dev)
+        elif name in ("ace_list", "nnb"):
+            out = torch.empty(n, dtype=torch.int64, device=dev)
+        else:
+            out = torch.empty(n, dtype=torch.float64, device=dev)
+        apip_get_field(self.ctx, name, out, n)
+        return out

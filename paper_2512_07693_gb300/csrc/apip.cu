@@ -1,0 +1,496 @@
+// C ABI of libapip: context management and the host-side orchestration of the
+// adaptive-precision force pipeline (one stream, no host synchronisation):
+//
+//   prep -> [neighbour rebuild, skipped on the device unless an atom moved more
+//   than skin/2] -> pass 1 (EAM density, g) -> pass 2 (switch, EAM force,
+//   compaction of lam > 0) -> ACE on the compacted atoms -> CSP part of
+//   grad-lambda -> float64 energy reduction.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "kernels.h"
+
+using namespace apip;
+
+namespace {
+
+apip_status fail(apip_ctx* c, apip_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define APIP_CK(expr)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(ctx, APIP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int nblk(int64_t n) { return (int)std::max<int64_t>(1, (n + kBlock - 1) / kBlock); }
+
+size_t esize(const apip_ctx* c) { return c->p.precision == APIP_FP32 ? sizeof(float) : sizeof(double); }
+
+template <typename T> T* as(void* p) { return reinterpret_cast<T*>(p); }
+
+void free_all(apip_ctx* c) {
+  void* ptrs[] = {c->cell_count, c->cell_atoms, c->nnb, c->nbl, c->pos_ref, c->posh, c->posl, c->id2idx,
+                  c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
+                  c->cvec, c->ace_list, c->counts, c->flags, c->status, c->partials, c->thermo_part,
+                  c->e_scratch, c->key3, c->k3a, c->k3b, c->key4, c->k4a, c->k4b};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+apip_status check_params(const apip_params* p, std::string* why) {
+  auto bad = [&](const char* m) { *why = m; return APIP_ERR_ARG; };
+  if (p->precision != APIP_FP64 && p->precision != APIP_FP32) return bad("precision must be APIP_FP64 or APIP_FP32");
+  if (p->lam_mode < APIP_LAM_PAPER || p->lam_mode > APIP_LAM_CONST1) return bad("unknown lam_mode");
+  if (p->ace_n_max < 1 || p->ace_n_max > kNmaxCap) return bad("ace_n_max must be in [1, 8]");
+  if (p->ace_l_max < 0 || p->ace_l_max > kLmaxCap) return bad("ace_l_max must be in [0, 4]");
+  if (p->ace_nu_max < 1 || p->ace_nu_max > 4) return bad("ace_nu_max must be in [1, 4]");
+  if (p->ace_n_max * (p->ace_l_max + 1) * (p->ace_l_max + 1) > 254) return bad("n_max (l_max+1)^2 must be <= 254");
+  if (!p->ace_c1 || !p->ace_c2) return bad("ace_c1 / ace_c2 must not be NULL");
+  if (!(p->ace_rc > 0 && p->ace_rc_width > 0 && p->ace_rc_width <= p->ace_rc)) return bad("bad ACE cutoff");
+  if (!(p->ace_eps > 0)) return bad("ace_eps must be > 0");
+  if (!(p->eam_rc > 0 && p->eam_rc_width > 0 && p->eam_rc_width <= p->eam_rc)) return bad("bad EAM cutoff");
+  if (!(p->sw_r_w > 0 && p->sw_r_w_width > 0 && p->sw_r_w_width <= p->sw_r_w)) return bad("bad switch cutoff");
+  if (!(p->sw_d_hi > p->sw_d_lo)) return bad("sw_d_hi must exceed sw_d_lo");
+  if (p->csp_nnb < 2 || p->csp_nnb > kCspCap || p->csp_nnb % 2) return bad("csp_nnb must be even, 2..8");
+  if (!(p->csp_rcut > 0)) return bad("csp_rcut must be > 0");
+  if (!(p->skin >= 0)) return bad("skin must be >= 0");
+  if (p->max_nb < 1 || p->max_nb > 1024) return bad("max_nb must be in [1, 1024]");
+  if (p->cell_cap < 1 || p->cell_cap > 1024) return bad("cell_cap must be in [1, 1024]");
+  const double cut = std::max(std::max(p->eam_rc, p->ace_rc), p->sw_r_w);
+  if (p->csp_rcut > cut + p->skin) return bad("csp_rcut must not exceed the neighbour cutoff + skin");
+  return APIP_OK;
+}
+
+// Cell grid for a new box; marks the neighbour list for rebuild.
+apip_status set_geometry(apip_ctx* ctx, const double* box, cudaStream_t s) {
+  if (!box) return fail(ctx, APIP_ERR_ARG, "box must not be NULL");
+  for (int k = 0; k < 3; ++k)
+    if (!(std::isfinite(box[k]) && box[k] > 0)) return fail(ctx, APIP_ERR_ARG, "box edges must be finite and > 0");
+  if (ctx->geo_set && box[0] == ctx->geo.L[0] && box[1] == ctx->geo.L[1] && box[2] == ctx->geo.L[2]) return APIP_OK;
+  Geo g{};
+  int ncell = 1;
+  for (int k = 0; k < 3; ++k) {
+    g.L[k] = box[k];
+    g.nc[k] = (int)std::floor(box[k] / ctx->r_list);
+    if (g.nc[k] < 3)
+      return fail(ctx, APIP_ERR_ARG, "each box edge must be >= 3 * (cutoff + skin) = " + std::to_string(3 * ctx->r_list));
+    g.cs[k] = box[k] / g.nc[k];
+    g.Lh[k] = (float)box[k];
+    g.Ll[k] = (float)(box[k] - (double)g.Lh[k]);
+    ncell *= g.nc[k];
+  }
+  if (ncell > ctx->ncell_alloc) {
+    if (ctx->cell_count) cudaFree(ctx->cell_count);
+    if (ctx->cell_atoms) cudaFree(ctx->cell_atoms);
+    ctx->cell_count = nullptr;
+    ctx->cell_atoms = nullptr;
+    APIP_CK(cudaMalloc(&ctx->cell_count, sizeof(int) * ncell));
+    APIP_CK(cudaMalloc(&ctx->cell_atoms, sizeof(int) * (size_t)ncell * ctx->p.cell_cap));
+    ctx->ncell_alloc = ncell;
+  }
+  ctx->ncell = ncell;
+  ctx->geo = g;
+  ctx->geo_set = true;
+  APIP_CK(cudaMemsetAsync(ctx->flags, 0xff, sizeof(int), s));
+  return APIP_OK;
+}
+
+}  // namespace
+
+namespace apip {
+
+template <typename T>
+Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* force, double* e_atom) {
+  Args<T> a{};
+  const apip_params& p = c->p;
+  a.n = n;
+  a.nmax = (int)c->nmax;
+  a.max_nb = p.max_nb;
+  a.cell_cap = p.cell_cap;
+  a.csp_nnb = p.csp_nnb;
+  a.lam_mode = p.lam_mode;
+  a.precise_adds_eam = p.precise_adds_eam;
+  a.grad_lambda = p.grad_lambda;
+  a.eam_force = 1;
+  a.geo = c->geo;
+  a.eam = {p.eam_A, p.eam_beta, p.eam_re, p.eam_D, p.eam_alpha, p.eam_r0, p.eam_rc, p.eam_rc - p.eam_rc_width};
+  a.sw = {p.sw_r_w, p.sw_r_w - p.sw_r_w_width, p.sw_d_lo, p.sw_d_hi, p.sw_d0};
+  a.r_list2 = c->r_list * c->r_list;
+  a.skin_half2 = 0.25 * p.skin * p.skin;
+  a.csp_rcut2 = p.csp_rcut * p.csp_rcut;
+  a.pos = pos;
+  a.id = id;
+  a.nnb = c->nnb; a.nbl = c->nbl; a.pos_ref = c->pos_ref; a.posh = c->posh; a.posl = c->posl;
+  a.id2idx = c->id2idx; a.csp = c->csp; a.cell_count = c->cell_count; a.cell_atoms = c->cell_atoms;
+  a.zeta = as<T>(c->zeta); a.xi_p = as<T>(c->xi_p); a.e_eam = as<T>(c->e_eam); a.g = as<T>(c->g);
+  a.wbar = as<T>(c->wbar); a.dd = as<T>(c->dd); a.lam = as<T>(c->lam); a.dlam = as<T>(c->dlam);
+  a.e_ace = as<T>(c->e_ace);
+  a.cvec = c->cvec; a.ace_list = c->ace_list; a.counts = c->counts; a.flags = c->flags; a.status = c->status;
+  a.partials = c->partials;
+  a.n_part_p1 = nblk(n);
+  a.force = force;
+  a.e_atom = e_atom;
+  return a;
+}
+
+}  // namespace apip
+
+namespace {
+
+template <typename T> void set_view(Args<T>& a, apip_ctx* c);
+template <> void set_view<double>(Args<double>& a, apip_ctx* c) {
+  a.pv.pos = a.pos;
+  for (int k = 0; k < 3; ++k) { a.pv.L[k] = c->geo.L[k]; a.pv.invL[k] = 1.0 / c->geo.L[k]; }
+}
+template <> void set_view<float>(Args<float>& a, apip_ctx* c) {
+  a.pv.hi = c->posh;
+  a.pv.lo = c->posl;
+  for (int k = 0; k < 3; ++k) {
+    a.pv.Lh[k] = c->geo.Lh[k];
+    a.pv.Ll[k] = c->geo.Ll[k];
+    a.pv.half[k] = (float)(0.5 * c->geo.L[k]);
+  }
+}
+
+template <typename T>
+AceDev<T> ace_dev(apip_ctx* c) {
+  AceDev<T> t{};
+  const apip_params& p = c->p;
+  t.n_max = p.ace_n_max;
+  t.l_max = p.ace_l_max;
+  t.nA = p.ace_n_max * (p.ace_l_max + 1) * (p.ace_l_max + 1);
+  t.rc = T(p.ace_rc);
+  t.rc_lo = T(p.ace_rc - p.ace_rc_width);
+  t.eps = T(p.ace_eps);
+  t.sqrt_eps = T(std::sqrt(p.ace_eps));
+  t.a_scale = T(p.ace_a_scale);
+  t.key3 = c->key3; t.k3a = as<T>(c->k3a); t.k3b = as<T>(c->k3b); t.n3 = c->n3;
+  t.key4 = c->key4; t.k4a = as<T>(c->k4a); t.k4b = as<T>(c->k4b); t.n4 = c->n4;
+  return t;
+}
+
+apip_status check_call(apip_ctx* ctx, const double* pos, const int32_t* id, int64_t n) {
+  if (!ctx) return APIP_ERR_ARG;
+  if (n < 0 || n > ctx->nmax) return fail(ctx, APIP_ERR_ARG, "n must be in [0, n_atoms_max]");
+  if (n > 0 && (!pos || !id)) return fail(ctx, APIP_ERR_ARG, "pos and id must not be NULL");
+  return APIP_OK;
+}
+
+apip_status launch_status(apip_ctx* ctx) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, APIP_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return APIP_OK;
+}
+
+// The force pipeline after prep (or after the drift of a Verlet step).
+template <typename T>
+void force_pipeline(apip_ctx* c, Args<T>& a, cudaStream_t s) {
+  launch_neighbors<T>(a, c->ncell, s);
+  launch_pass1<T>(a, s);
+  launch_pass2<T>(a, s);
+  launch_ace<T>(a, ace_dev<T>(c), c->ace_blocks, s);
+  if (a.lam_mode == APIP_LAM_PAPER && a.grad_lambda) launch_csp_force<T>(a, s);
+}
+
+template <typename T>
+apip_status energy_forces_t(apip_ctx* c, const double* pos, const int32_t* id, int n, double* force,
+                            double* e_atom, double* e_total, cudaStream_t s) {
+  Args<T> a = make_args<T>(c, pos, id, n, force, e_atom);
+  set_view<T>(a, c);
+  launch_prep<T>(a, s);
+  force_pipeline<T>(c, a, s);
+  launch_final(c->partials, a.n_part_p1 + c->ace_blocks * kAceWarps, e_total, nullptr, nullptr, 0, nullptr,
+               c->flags, c->counts, nullptr, s);
+  return launch_status(c);
+}
+
+template <typename T>
+apip_status switch_t(apip_ctx* c, const double* pos, const int32_t* id, int n, double* lam_out,
+                     double* dlam_out, int64_t* n_ace_out, cudaStream_t s) {
+  Args<T> a = make_args<T>(c, pos, id, n, nullptr, nullptr);
+  set_view<T>(a, c);
+  a.eam_force = 0;
+  launch_prep<T>(a, s);
+  launch_neighbors<T>(a, c->ncell, s);
+  launch_pass1<T>(a, s);
+  launch_pass2<T>(a, s);
+  if (lam_out) launch_get_field<T>(a, APIP_FIELD_LAM, lam_out, s);
+  if (dlam_out) launch_get_field<T>(a, APIP_FIELD_DLAM, dlam_out, s);
+  launch_final(c->partials, 0, nullptr, nullptr, nullptr, 0, nullptr, c->flags, c->counts, n_ace_out, s);
+  return launch_status(c);
+}
+
+template <typename T>
+apip_status neighbors_t(apip_ctx* c, const double* pos, const int32_t* id, int n, cudaStream_t s) {
+  Args<T> a = make_args<T>(c, pos, id, n, nullptr, nullptr);
+  set_view<T>(a, c);
+  launch_prep<T>(a, s);
+  cudaMemsetAsync(c->flags, 0xff, sizeof(int), s);
+  launch_neighbors<T>(a, c->ncell, s);
+  cudaMemsetAsync(c->flags, 0, sizeof(int), s);
+  return launch_status(c);
+}
+
+template <typename T>
+apip_status verlet_t(apip_ctx* c, double* pos, double* vel, double* force, const double* inv_mass,
+                     const int32_t* id, int n, double dt, int steps, double* thermo, cudaStream_t s) {
+  Args<T> a = make_args<T>(c, pos, id, n, force, nullptr);
+  set_view<T>(a, c);
+  const int ntb = nblk(n);
+  const int n_part = a.n_part_p1 + c->ace_blocks * kAceWarps;
+  for (int k = 0; k < steps; ++k) {
+    launch_verlet<T>(a, k == 0 ? 0 : 1, pos, vel, force, inv_mass, dt, c->thermo_part, s);
+    force_pipeline<T>(c, a, s);
+    launch_final(c->partials, n_part, nullptr, thermo ? thermo + 5 * k : nullptr,
+                 (thermo && k > 0) ? c->thermo_part : nullptr, ntb, thermo ? thermo + 5 * (k - 1) : nullptr,
+                 c->flags, c->counts, nullptr, s);
+  }
+  launch_verlet<T>(a, 2, pos, vel, force, inv_mass, dt, c->thermo_part, s);
+  if (thermo) launch_thermo_final(c->thermo_part, ntb, thermo + 5 * (steps - 1), s);
+  return launch_status(c);
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+int64_t apip_ace_basis_size(int32_t n_max, int32_t l_max, int32_t nu_max) {
+  return basis_size(n_max, l_max, nu_max);
+}
+
+apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** out) {
+  if (!p || !out) return APIP_ERR_ARG;
+  *out = nullptr;
+  std::string why;
+  if (check_params(p, &why) != APIP_OK) return APIP_ERR_ARG;
+  if (n_atoms_max < 1 || n_atoms_max > (int64_t)1 << 30 || n_atoms_max * (int64_t)p->max_nb > ((int64_t)1 << 40))
+    return APIP_ERR_ARG;
+  const int64_t nb = basis_size(p->ace_n_max, p->ace_l_max, p->ace_nu_max);
+  if (nb != p->ace_n_basis) return APIP_ERR_ARG;
+  apip_ctx* ctx = new (std::nothrow) apip_ctx();
+  if (!ctx) return APIP_ERR_ARG;
+  ctx->p = *p;
+  ctx->ace_c1.assign(p->ace_c1, p->ace_c1 + nb);
+  ctx->ace_c2.assign(p->ace_c2, p->ace_c2 + nb);
+  ctx->p.ace_c1 = nullptr;
+  ctx->p.ace_c2 = nullptr;
+  ctx->nmax = n_atoms_max;
+  ctx->r_list = std::max(std::max(p->eam_rc, p->ace_rc), p->sw_r_w) + p->skin;
+  HostTerms terms;
+  if (!build_terms(p->ace_n_max, p->ace_l_max, p->ace_nu_max, ctx->ace_c1.data(), ctx->ace_c2.data(), nb, &terms,
+                   &why)) {
+    delete ctx;
+    return APIP_ERR_ARG;
+  }
+  auto fail_create = [&](cudaError_t e) {
+    free_all(ctx);
+    delete ctx;
+    (void)e;
+    return APIP_ERR_CUDA;
+  };
+#define APIP_ALLOC(ptr, bytes)                                 \
+  do {                                                         \
+    cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));      \
+    if (e_ != cudaSuccess) return fail_create(e_);             \
+  } while (0)
+  cudaGetDevice(&ctx->dev);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->dev);
+  ctx->ace_blocks = std::max(1, sms) * 8;
+  const size_t N = (size_t)n_atoms_max;
+  const size_t es = esize(ctx);
+  APIP_ALLOC(ctx->nnb, sizeof(int) * N);
+  APIP_ALLOC(ctx->nbl, sizeof(int) * N * p->max_nb);
+  APIP_ALLOC(ctx->pos_ref, sizeof(double) * 3 * N);
+  if (p->precision == APIP_FP32) {
+    APIP_ALLOC(ctx->posh, sizeof(float4) * N);
+    APIP_ALLOC(ctx->posl, sizeof(float4) * N);
+  }
+  APIP_ALLOC(ctx->id2idx, sizeof(int) * N);
+  APIP_ALLOC(ctx->csp, sizeof(int) * N * kCspCap);
+  void** per_atom[] = {&ctx->zeta, &ctx->xi_p, &ctx->e_eam, &ctx->g, &ctx->wbar, &ctx->dd, &ctx->lam, &ctx->dlam, &ctx->e_ace};
+  for (void** q : per_atom) APIP_ALLOC(*q, es * N);
+  APIP_ALLOC(ctx->cvec, sizeof(double) * N);
+  APIP_ALLOC(ctx->ace_list, sizeof(int) * N);
+  APIP_ALLOC(ctx->counts, sizeof(int) * 4);
+  APIP_ALLOC(ctx->flags, sizeof(int) * 4);
+  APIP_ALLOC(ctx->status, sizeof(int) * ST_COUNT);
+  const int p1 = nblk(n_atoms_max);
+  APIP_ALLOC(ctx->partials, sizeof(double) * (p1 + ctx->ace_blocks * kAceWarps));
+  APIP_ALLOC(ctx->thermo_part, sizeof(double) * 4 * p1);
+  APIP_ALLOC(ctx->e_scratch, sizeof(double) * 2);
+  ctx->n3 = (int)terms.key3.size();
+  ctx->n4 = (int)terms.key4.size();
+  APIP_ALLOC(ctx->key3, sizeof(uint32_t) * std::max(1, ctx->n3));
+  APIP_ALLOC(ctx->k3a, es * std::max(1, ctx->n3));
+  APIP_ALLOC(ctx->k3b, es * std::max(1, ctx->n3));
+  APIP_ALLOC(ctx->key4, sizeof(uint32_t) * std::max(1, ctx->n4));
+  APIP_ALLOC(ctx->k4a, es * std::max(1, ctx->n4));
+  APIP_ALLOC(ctx->k4b, es * std::max(1, ctx->n4));
+#undef APIP_ALLOC
+  auto upload = [&](void* dst, const std::vector<double>& v) -> cudaError_t {
+    if (v.empty()) return cudaSuccess;
+    if (p->precision == APIP_FP64) return cudaMemcpy(dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice);
+    std::vector<float> f(v.begin(), v.end());
+    return cudaMemcpy(dst, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice);
+  };
+  cudaError_t e = cudaSuccess;
+  if (ctx->n3) e = cudaMemcpy(ctx->key3, terms.key3.data(), sizeof(uint32_t) * ctx->n3, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && ctx->n4)
+    e = cudaMemcpy(ctx->key4, terms.key4.data(), sizeof(uint32_t) * ctx->n4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = upload(ctx->k3a, terms.k3a);
+  if (e == cudaSuccess) e = upload(ctx->k3b, terms.k3b);
+  if (e == cudaSuccess) e = upload(ctx->k4a, terms.k4a);
+  if (e == cudaSuccess) e = upload(ctx->k4b, terms.k4b);
+  if (e == cudaSuccess) e = cudaMemset(ctx->id2idx, 0xff, sizeof(int) * N);
+  if (e == cudaSuccess) e = cudaMemset(ctx->csp, 0xff, sizeof(int) * N * kCspCap);
+  if (e == cudaSuccess) e = cudaMemset(ctx->cvec, 0, sizeof(double) * N);
+  if (e == cudaSuccess) e = cudaMemset(ctx->counts, 0, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(ctx->flags, 0xff, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(int) * ST_COUNT);
+  if (e == cudaSuccess) e = cudaMemset(ctx->pos_ref, 0, sizeof(double) * 3 * N);
+  if (e == cudaSuccess) e = cudaMemset(ctx->nnb, 0, sizeof(int) * N);
+  if (e != cudaSuccess) return fail_create(e);
+  double norms[(kLmaxCap + 1) * (kLmaxCap + 1)];
+  ylm_norms(kLmaxCap, norms);
+  if (p->precision == APIP_FP64) ace_set_norms<double>(norms, (kLmaxCap + 1) * (kLmaxCap + 1));
+  else ace_set_norms<float>(norms, (kLmaxCap + 1) * (kLmaxCap + 1));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_create(e);
+  *out = ctx;
+  return APIP_OK;
+}
+
+apip_status apip_destroy(apip_ctx* ctx) {
+  if (!ctx) return APIP_OK;
+  cudaDeviceSynchronize();
+  free_all(ctx);
+  delete ctx;
+  return APIP_OK;
+}
+
+const char* apip_last_error(apip_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+apip_status apip_build_neighbors(apip_ctx* ctx, const double* pos, const double box[3], const int32_t* id,
+                                 int64_t n, void* stream) {
+  apip_status st = check_call(ctx, pos, id, n);
+  if (st != APIP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = set_geometry(ctx, box, s)) != APIP_OK) return st;
+  if (n == 0) return APIP_OK;
+  return ctx->p.precision == APIP_FP32 ? neighbors_t<float>(ctx, pos, id, (int)n, s)
+                                       : neighbors_t<double>(ctx, pos, id, (int)n, s);
+}
+
+apip_status apip_init_csp_pairs(apip_ctx* ctx, const double* pos, const double box[3], const int32_t* id,
+                                int64_t n, void* stream) {
+  apip_status st = apip_build_neighbors(ctx, pos, box, id, n, stream);
+  if (st != APIP_OK) return st;
+  if (n == 0) { ctx->csp_ready = true; return APIP_OK; }
+  Args<double> a = make_args<double>(ctx, pos, id, (int)n, nullptr, nullptr);
+  launch_csp_init(a, (cudaStream_t)stream);
+  st = launch_status(ctx);
+  if (st == APIP_OK) ctx->csp_ready = true;
+  return st;
+}
+
+apip_status apip_switch(apip_ctx* ctx, const double* pos, const double box[3], const int32_t* type,
+                        const int32_t* id, int64_t n, double* lam_out, double* dlam_out, int64_t* n_ace_out,
+                        void* stream) {
+  (void)type;
+  apip_status st = check_call(ctx, pos, id, n);
+  if (st != APIP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = set_geometry(ctx, box, s)) != APIP_OK) return st;
+  if (ctx->p.lam_mode == APIP_LAM_PAPER && !ctx->csp_ready)
+    return fail(ctx, APIP_ERR_STATE, "apip_init_csp_pairs must be called before the paper's switch is used");
+  if (n == 0) {
+    if (n_ace_out) cudaMemsetAsync(n_ace_out, 0, sizeof(int64_t), s);
+    return launch_status(ctx);
+  }
+  return ctx->p.precision == APIP_FP32 ? switch_t<float>(ctx, pos, id, (int)n, lam_out, dlam_out, n_ace_out, s)
+                                       : switch_t<double>(ctx, pos, id, (int)n, lam_out, dlam_out, n_ace_out, s);
+}
+
+apip_status apip_energy_forces(apip_ctx* ctx, const double* pos, const double box[3], const int32_t* type,
+                               const int32_t* id, int64_t n, double* force_out, double* e_atom_out,
+                               double* e_total_out, void* stream) {
+  (void)type;
+  apip_status st = check_call(ctx, pos, id, n);
+  if (st != APIP_OK) return st;
+  if (n > 0 && !force_out) return fail(ctx, APIP_ERR_ARG, "force_out must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = set_geometry(ctx, box, s)) != APIP_OK) return st;
+  if (ctx->p.lam_mode == APIP_LAM_PAPER && !ctx->csp_ready)
+    return fail(ctx, APIP_ERR_STATE, "apip_init_csp_pairs must be called before the paper's switch is used");
+  if (n == 0) {
+    if (e_total_out) cudaMemsetAsync(e_total_out, 0, sizeof(double), s);
+    return launch_status(ctx);
+  }
+  return ctx->p.precision == APIP_FP32
+             ? energy_forces_t<float>(ctx, pos, id, (int)n, force_out, e_atom_out, e_total_out, s)
+             : energy_forces_t<double>(ctx, pos, id, (int)n, force_out, e_atom_out, e_total_out, s);
+}
+
+apip_status apip_verlet_step(apip_ctx* ctx, double* pos, double* vel, double* force, const double* inv_mass,
+                             const double box[3], const int32_t* type, const int32_t* id, int64_t n, double dt,
+                             int32_t n_steps, double* thermo_out, void* stream) {
+  (void)type;
+  apip_status st = check_call(ctx, pos, id, n);
+  if (st != APIP_OK) return st;
+  if (n > 0 && (!vel || !force || !inv_mass)) return fail(ctx, APIP_ERR_ARG, "vel, force, inv_mass must not be NULL");
+  if (n_steps < 0 || !std::isfinite(dt)) return fail(ctx, APIP_ERR_ARG, "n_steps must be >= 0 and dt finite");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = set_geometry(ctx, box, s)) != APIP_OK) return st;
+  if (ctx->p.lam_mode == APIP_LAM_PAPER && !ctx->csp_ready)
+    return fail(ctx, APIP_ERR_STATE, "apip_init_csp_pairs must be called before the paper's switch is used");
+  if (n == 0 || n_steps == 0) return launch_status(ctx);
+  return ctx->p.precision == APIP_FP32
+             ? verlet_t<float>(ctx, pos, vel, force, inv_mass, id, (int)n, dt, n_steps, thermo_out, s)
+             : verlet_t<double>(ctx, pos, vel, force, inv_mass, id, (int)n, dt, n_steps, thermo_out, s);
+}
+
+apip_status apip_sync(apip_ctx* ctx, void* stream) {
+  if (!ctx) return APIP_ERR_ARG;
+  APIP_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  int st[ST_COUNT];
+  APIP_CK(cudaMemcpy(st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost));
+  APIP_CK(cudaMemset(ctx->status, 0, sizeof(st)));
+  if (st[ST_NB_OVERFLOW])
+    return fail(ctx, APIP_ERR_NB_OVERFLOW, "neighbour list overflow: an atom has " + std::to_string(st[ST_MAX_NNB]) +
+                                              " neighbours, max_nb = " + std::to_string(ctx->p.max_nb));
+  if (st[ST_CELL_OVERFLOW])
+    return fail(ctx, APIP_ERR_NB_OVERFLOW, "cell overflow: a cell holds " + std::to_string(st[ST_MAX_CELL]) +
+                                              " atoms, cell_cap = " + std::to_string(ctx->p.cell_cap));
+  if (st[ST_BAD_INPUT]) return fail(ctx, APIP_ERR_BAD_INPUT, "non-finite position or atom id out of range");
+  if (st[ST_BAD_PARTNER]) return fail(ctx, APIP_ERR_BAD_INPUT, "a CSP partner id is not present");
+  return APIP_OK;
+}
+
+apip_status apip_get_field(apip_ctx* ctx, int32_t field, void* dst, int64_t n, void* stream) {
+  if (!ctx) return APIP_ERR_ARG;
+  if (!dst || n < 0 || n > ctx->nmax) return fail(ctx, APIP_ERR_ARG, "bad dst or n");
+  if (field < APIP_FIELD_G || field > APIP_FIELD_CSP) return fail(ctx, APIP_ERR_ARG, "unknown field");
+  if (n == 0) return APIP_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ctx->p.precision == APIP_FP32) {
+    Args<float> a = make_args<float>(ctx, nullptr, nullptr, (int)n, nullptr, nullptr);
+    launch_get_field<float>(a, field, dst, s);
+  } else {
+    Args<double> a = make_args<double>(ctx, nullptr, nullptr, (int)n, nullptr, nullptr);
+    launch_get_field<double>(a, field, dst, s);
+  }
+  return launch_status(ctx);
+}
+
+}  // extern "C"

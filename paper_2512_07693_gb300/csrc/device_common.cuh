@@ -1,0 +1,111 @@
+// Device helpers shared by the libapip kernels: the transition function,
+// minimum-image pair vectors for both precisions, compensated sums and warp
+// reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "apip_internal.h"
+
+namespace apip {
+
+template <typename T> struct V3 { T x, y, z; };
+
+template <typename T>
+__device__ __forceinline__ T dot3(const V3<T>& a, const V3<T>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// f_trans(x, lo, hi) of Eq. S1 and its derivative: 1 below lo, 0 above hi,
+// in between 1/2 + t (15/16 + t^2 (-5/8 + 3/16 t^2)) with t = (hi + lo - 2x)/(hi - lo).
+template <typename T>
+__device__ __forceinline__ T ftrans(T x, T lo, T hi, T inv_w, T* deriv) {
+  if (x <= lo) { *deriv = T(0); return T(1); }
+  if (x >= hi) { *deriv = T(0); return T(0); }
+  const T t = (hi + lo - T(2) * x) * inv_w;
+  const T t2 = t * t;
+  *deriv = (T(0.9375) + t2 * (T(-1.875) + T(0.9375) * t2)) * (T(-2) * inv_w);
+  return T(0.5) + t * (T(0.9375) + t2 * (T(-0.625) + T(0.1875) * t2));
+}
+
+// Running sum with Kahan compensation in FP32; plain in FP64.
+template <typename T> struct Acc {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T v) {
+    const T y = v - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ T value() const { return s; }
+};
+template <> struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// Positions.  FP64 path: the caller's float64 array, minimum image with rint.
+// FP32 path: each wrapped coordinate split as hi + lo floats; the pair vector is
+// formed as (hi_j - hi_i) + (lo_j - lo_i) after moving whichever coordinate lies
+// in the upper half of the box down by L (hi and lo separately).  Both hi
+// differences are then exact (Sterbenz) or rounded at the scale of the pair
+// distance, so r_ij carries ~1e-7 A error instead of the ~1e-5 A of plain floats.
+template <typename T> struct PosView;
+
+template <> struct PosView<double> {
+  const double* pos;
+  double L[3], invL[3];
+  struct Self { double x, y, z; };
+  __device__ __forceinline__ Self self(int i) const { return {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]}; }
+  __device__ __forceinline__ V3<double> vec(const Self& s, int j) const {
+    double dx = pos[3 * j] - s.x, dy = pos[3 * j + 1] - s.y, dz = pos[3 * j + 2] - s.z;
+    dx -= L[0] * rint(dx * invL[0]);
+    dy -= L[1] * rint(dy * invL[1]);
+    dz -= L[2] * rint(dz * invL[2]);
+    return {dx, dy, dz};
+  }
+};
+
+__device__ __forceinline__ float split_diff(float a, float al, float b, float bl, float Lh, float Ll, float half) {
+  const float dd = a - b;
+  if (dd > half) { a -= Lh; al -= Ll; }
+  else if (dd < -half) { b -= Lh; bl -= Ll; }
+  return (a - b) + (al - bl);
+}
+
+template <> struct PosView<float> {
+  const float4* hi;
+  const float4* lo;
+  float Lh[3], Ll[3], half[3];
+  struct Self { float4 h, l; };
+  __device__ __forceinline__ Self self(int i) const { return {hi[i], lo[i]}; }
+  __device__ __forceinline__ V3<float> vec(const Self& s, int j) const {
+    const float4 h = hi[j], l = lo[j];
+    return {split_diff(h.x, l.x, s.h.x, s.l.x, Lh[0], Ll[0], half[0]),
+            split_diff(h.y, l.y, s.h.y, s.l.y, Lh[1], Ll[1], half[1]),
+            split_diff(h.z, l.z, s.h.z, s.l.z, Lh[2], Ll[2], half[2])};
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide float64 sum (result valid in thread 0); blockDim.x <= 1024.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (w == 0) v = warp_sum(v);
+  __syncthreads();
+  return v;
+}
+
+}  // namespace apip

@@ -1,0 +1,562 @@
+// All-atom passes of the adaptive-precision force pipeline: position
+// preparation, the cell-binned neighbour list, the one-off CSP pair detection,
+// pass 1 (EAM density and CSP^list g), pass 2 (switch, unweighted EAM force and
+// stream compaction of lam > 0), the CSP part of the grad-lambda force, the
+// float64 reductions and the velocity-Verlet kernels.
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace apip {
+
+namespace {
+
+__device__ __forceinline__ double wrap1(double x, double L, double invL) {
+  double w = x - L * floor(x * invL);
+  if (w >= L) w -= L;
+  if (w < 0.0) w += L;
+  return w;
+}
+
+__device__ __forceinline__ int cell_of(double xw, double L, int nc) {
+  int c = (int)(xw * ((double)nc / L));
+  return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+// Duties shared by k_prep and the drift of the Verlet kernels for atom i at
+// position (x, y, z): finiteness and id checks, the id -> index map, the hi/lo
+// split of the wrapped position (FP32 path) and the neighbour-list trigger
+// (displacement since the last build > skin / 2).
+template <typename T>
+__device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, double y, double z) {
+  if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicOr(&a.status[ST_BAD_INPUT], 1);
+  const int idv = a.id[i];
+  if (idv < 0 || idv >= a.nmax) atomicOr(&a.status[ST_BAD_INPUT], 1);
+  else a.id2idx[idv] = i;
+  if (sizeof(T) == 4) {
+    const double xs[3] = {x, y, z};
+    float h[3], l[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double w = wrap1(xs[k], a.geo.L[k], 1.0 / a.geo.L[k]);
+      h[k] = (float)w;
+      l[k] = (float)(w - (double)h[k]);
+    }
+    a.posh[i] = make_float4(h[0], h[1], h[2], 0.f);
+    a.posl[i] = make_float4(l[0], l[1], l[2], 0.f);
+  }
+  double dx = x - a.pos_ref[3 * i], dy = y - a.pos_ref[3 * i + 1], dz = z - a.pos_ref[3 * i + 2];
+  dx -= a.geo.L[0] * rint(dx / a.geo.L[0]);
+  dy -= a.geo.L[1] * rint(dy / a.geo.L[1]);
+  dz -= a.geo.L[2] * rint(dz / a.geo.L[2]);
+  if (dx * dx + dy * dy + dz * dz > a.skin_half2) atomicOr(&a.flags[0], 1);
+}
+
+template <typename T>
+__global__ void k_prep(Args<T> a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) a.counts[0] = 0;
+  if (i >= a.n) return;
+  prep_atom(a, i, a.pos[3 * i], a.pos[3 * i + 1], a.pos[3 * i + 2]);
+}
+
+// ------------------------------------------------------------ neighbour list
+__global__ void k_cell_clear(const int* flags, int* cell_count, int ncell) {
+  if (!flags[0]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ncell) cell_count[c] = 0;
+}
+
+template <typename T>
+__global__ void k_bin(Args<T> a) {
+  if (!a.flags[0]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  int c[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    c[k] = cell_of(wrap1(a.pos[3 * i + k], a.geo.L[k], 1.0 / a.geo.L[k]), a.geo.L[k], a.geo.nc[k]);
+  const int cell = (c[2] * a.geo.nc[1] + c[1]) * a.geo.nc[0] + c[0];
+  const int slot = atomicAdd(&a.cell_count[cell], 1);
+  if (slot < a.cell_cap) {
+    a.cell_atoms[cell * a.cell_cap + slot] = i;
+  } else {
+    atomicOr(&a.status[ST_CELL_OVERFLOW], 1);
+    atomicMax(&a.status[ST_MAX_CELL], slot + 1);
+  }
+}
+
+// Order each cell by atom index so that neighbour order (and thus every sum
+// over neighbours) does not depend on the order of the binning atomics.
+__global__ void k_cell_sort(const int* flags, const int* cell_count, int* cell_atoms, int ncell, int cap) {
+  if (!flags[0]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int cnt = min(cell_count[c], cap);
+  int* v = cell_atoms + (size_t)c * cap;
+  for (int k = 1; k < cnt; ++k) {
+    const int x = v[k];
+    int m = k - 1;
+    while (m >= 0 && v[m] > x) { v[m + 1] = v[m]; --m; }
+    v[m + 1] = x;
+  }
+}
+
+template <typename T>
+__global__ void k_nbfill(Args<T> a) {
+  if (!a.flags[0]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  int c[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    c[k] = cell_of(wrap1(a.pos[3 * i + k], a.geo.L[k], 1.0 / a.geo.L[k]), a.geo.L[k], a.geo.nc[k]);
+  const auto si = a.pv.self(i);
+  int cnt = 0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int cz = (c[2] + dz + a.geo.nc[2]) % a.geo.nc[2];
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int cy = (c[1] + dy + a.geo.nc[1]) % a.geo.nc[1];
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int cx = (c[0] + dx + a.geo.nc[0]) % a.geo.nc[0];
+        const int cell = (cz * a.geo.nc[1] + cy) * a.geo.nc[0] + cx;
+        const int m = min(a.cell_count[cell], a.cell_cap);
+        const int* v = a.cell_atoms + (size_t)cell * a.cell_cap;
+        for (int k = 0; k < m; ++k) {
+          const int j = v[k];
+          if (j == i) continue;
+          const auto d = a.pv.vec(si, j);
+          if ((double)dot3(d, d) < a.r_list2) {
+            if (cnt < a.max_nb) a.nbl[(size_t)cnt * a.nmax + i] = j;
+            ++cnt;
+          }
+        }
+      }
+    }
+  }
+  if (cnt > a.max_nb) {
+    atomicOr(&a.status[ST_NB_OVERFLOW], 1);
+    atomicMax(&a.status[ST_MAX_NNB], cnt);
+  }
+  a.nnb[i] = min(cnt, a.max_nb);
+  a.pos_ref[3 * i] = a.pos[3 * i];
+  a.pos_ref[3 * i + 1] = a.pos[3 * i + 1];
+  a.pos_ref[3 * i + 2] = a.pos[3 * i + 2];
+}
+
+// -------------------------------------------------------------- CSP pairs
+// Detection at t = 0 (Eq. B3): the csp_nnb nearest neighbours within
+// csp_rcut (ordered by squared distance, ties by id) are paired greedily by
+// ascending |r_ia + r_ib|^2 (ties by rank).  All float64 operations are
+// explicitly rounded (no contraction) so the pairing is reproducible.
+__device__ __forceinline__ double sq_rn(double x, double y, double z) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+}
+
+__device__ __forceinline__ double minimg_rn(double d, double L) {
+  return __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
+}
+
+__global__ void k_csp_init(Args<double> a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  double r2s[kCspCap], rv[kCspCap][3];
+  int ids[kCspCap];
+  int m = 0;
+  const int K = a.csp_nnb;
+  const double xi = a.pos[3 * i], yi = a.pos[3 * i + 1], zi = a.pos[3 * i + 2];
+  const int cnt = a.nnb[i];
+  for (int s = 0; s < cnt; ++s) {
+    const int j = a.nbl[(size_t)s * a.nmax + i];
+    const double dx = minimg_rn(__dsub_rn(a.pos[3 * j], xi), a.geo.L[0]);
+    const double dy = minimg_rn(__dsub_rn(a.pos[3 * j + 1], yi), a.geo.L[1]);
+    const double dz = minimg_rn(__dsub_rn(a.pos[3 * j + 2], zi), a.geo.L[2]);
+    const double r2 = sq_rn(dx, dy, dz);
+    if (!(r2 < a.csp_rcut2)) continue;
+    const int idj = a.id[j];
+    // insert into the sorted list of the K best (r2, id)
+    if (m == K && !(r2 < r2s[K - 1] || (r2 == r2s[K - 1] && idj < ids[K - 1]))) continue;
+    if (m < K) ++m;
+    int p = m - 1;
+    while (p > 0 && (r2 < r2s[p - 1] || (r2 == r2s[p - 1] && idj < ids[p - 1]))) {
+      r2s[p] = r2s[p - 1]; ids[p] = ids[p - 1];
+      rv[p][0] = rv[p - 1][0]; rv[p][1] = rv[p - 1][1]; rv[p][2] = rv[p - 1][2];
+      --p;
+    }
+    r2s[p] = r2; ids[p] = idj; rv[p][0] = dx; rv[p][1] = dy; rv[p][2] = dz;
+  }
+  int* out = a.csp + (size_t)i * kCspCap;
+  for (int k = 0; k < kCspCap; ++k) out[k] = -1;
+  bool used[kCspCap];
+  for (int k = 0; k < kCspCap; ++k) used[k] = false;
+  for (int k = 0; 2 * k < K; ++k) {
+    double best = 0.0;
+    int bp = -1, bq = -1;
+    for (int p = 0; p < m; ++p) {
+      if (used[p]) continue;
+      for (int q = p + 1; q < m; ++q) {
+        if (used[q]) continue;
+        const double s2 = sq_rn(__dadd_rn(rv[p][0], rv[q][0]), __dadd_rn(rv[p][1], rv[q][1]),
+                                __dadd_rn(rv[p][2], rv[q][2]));
+        if (bp < 0 || s2 < best) { best = s2; bp = p; bq = q; }
+      }
+    }
+    if (bp < 0) break;
+    used[bp] = used[bq] = true;
+    out[2 * k] = ids[bp];
+    out[2 * k + 1] = ids[bq];
+  }
+}
+
+// ------------------------------------------------------------------ pass 1
+// zeta_i and E_i^EAM (Eq. B1, S8), xi'(zeta_i), and g_i = CSP^list_i (Eq. B3).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_pass1(Args<T> a) {
+  __shared__ double sh[32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double e_out = 0.0;
+  if (i < a.n) {
+    const auto si = a.pv.self(i);
+    const T rc2 = T(a.eam.rc * a.eam.rc), rc = T(a.eam.rc), rlo = T(a.eam.rc_lo);
+    const T inv_w = T(1.0 / (a.eam.rc - a.eam.rc_lo));
+    const T A = T(a.eam.A), beta = T(a.eam.beta), re = T(a.eam.re), D = T(a.eam.D),
+            alpha = T(a.eam.alpha), r0 = T(a.eam.r0);
+    Acc<T> zeta, pair;
+    const int cnt = a.nnb[i];
+    for (int s = 0; s < cnt; ++s) {
+      const int j = a.nbl[(size_t)s * a.nmax + i];
+      const auto d = a.pv.vec(si, j);
+      const T r2 = dot3(d, d);
+      if (r2 < rc2) {
+        const T r = sqrt(r2);
+        T dfc;
+        const T fc = ftrans(r, rlo, rc, inv_w, &dfc);
+        const T x = exp(-alpha * (r - r0));
+        zeta.add(A * exp(-beta * (r - re)) * fc);
+        pair.add(D * (x * x - T(2) * x) * fc);
+      }
+    }
+    const T z = zeta.value();
+    const T sz = z > T(0) ? sqrt(z) : T(0);
+    const T e = -sz + T(0.5) * pair.value();
+    a.zeta[i] = z;
+    a.xi_p[i] = z > T(0) ? T(-0.5) / sz : T(0);
+    a.e_eam[i] = e;
+    if (a.e_atom) a.e_atom[i] = (double)e;
+    e_out = (double)e;
+    T g = T(0);
+    if (a.lam_mode == APIP_LAM_PAPER) {
+      Acc<T> gs;
+      const int* pr = a.csp + (size_t)i * kCspCap;
+      for (int k = 0; 2 * k + 1 < a.csp_nnb; ++k) {
+        const int ia_id = pr[2 * k], ib_id = pr[2 * k + 1];
+        if (ia_id < 0 || ib_id < 0) continue;
+        if (ia_id >= a.nmax || ib_id >= a.nmax) { atomicOr(&a.status[ST_BAD_PARTNER], 1); continue; }
+        const int ia = a.id2idx[ia_id], ib = a.id2idx[ib_id];
+        if (ia < 0 || ib < 0 || ia >= a.n || ib >= a.n) { atomicOr(&a.status[ST_BAD_PARTNER], 1); continue; }
+        const auto u1 = a.pv.vec(si, ia);
+        const auto u2 = a.pv.vec(si, ib);
+        const V3<T> u{u1.x + u2.x, u1.y + u2.y, u1.z + u2.z};
+        gs.add(dot3(u, u));
+      }
+      g = gs.value();
+    }
+    a.g[i] = g;
+  }
+  const double tot = block_sum(e_out, sh);
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = tot;
+}
+
+// ------------------------------------------------------------------ pass 2
+// Switch (Eq. 6, Eq. 2 with lam = 1 - f_trans), the EAM force with unit weights
+// F_i = sum_k [(xi'_i + xi'_k) rho'(r_ik) + Phi'(r_ik)] e_ik  (S13; the lam-
+// dependent part of S12 is added by the ACE kernel for the atoms with lam > 0),
+// and warp-ballot compaction of {i : lam_i > 0} into ace_list.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = i < a.n;
+  T lam = T(0);
+  if (active) {
+    const auto si = a.pv.self(i);
+    const bool paper = a.lam_mode == APIP_LAM_PAPER;
+    const T rw2 = T(a.sw.r_w * a.sw.r_w), rw = T(a.sw.r_w), rwlo = T(a.sw.r_w_lo);
+    const T rw_inv = T(1.0 / (a.sw.r_w - a.sw.r_w_lo));
+    const T rc2 = T(a.eam.rc * a.eam.rc), rc = T(a.eam.rc), rlo = T(a.eam.rc_lo);
+    const T inv_w = T(1.0 / (a.eam.rc - a.eam.rc_lo));
+    const T A = T(a.eam.A), beta = T(a.eam.beta), re = T(a.eam.re), D = T(a.eam.D),
+            alpha = T(a.eam.alpha), r0 = T(a.eam.r0);
+    const T xi_i = a.xi_p[i];
+    Acc<T> wbar, S, fx, fy, fz;
+    wbar.add(T(1));
+    if (paper) S.add(a.g[i]);
+    const int cnt = a.nnb[i];
+    for (int s = 0; s < cnt; ++s) {
+      const int j = a.nbl[(size_t)s * a.nmax + i];
+      const auto d = a.pv.vec(si, j);
+      const T r2 = dot3(d, d);
+      const bool in_w = paper && r2 < rw2;
+      const bool in_e = a.eam_force && r2 < rc2;
+      if (!(in_w || in_e)) continue;
+      const T r = sqrt(r2);
+      if (in_w) {
+        T dw;
+        const T w = ftrans(r, rwlo, rw, rw_inv, &dw);
+        wbar.add(w);
+        S.add(a.g[j] * w);
+      }
+      if (in_e) {
+        T dfc;
+        const T fc = ftrans(r, rlo, rc, inv_w, &dfc);
+        const T er = A * exp(-beta * (r - re));
+        const T drho = er * (dfc - beta * fc);
+        const T x = exp(-alpha * (r - r0));
+        const T dphi = D * (T(2) * alpha * (x - x * x) * fc + (x * x - T(2) * x) * dfc);
+        const T sc = ((xi_i + a.xi_p[j]) * drho + dphi) / r;
+        fx.add(sc * d.x);
+        fy.add(sc * d.y);
+        fz.add(sc * d.z);
+      }
+    }
+    T dv = T(0), dl = T(0), wb = T(1);
+    if (paper) {
+      wb = wbar.value();
+      dv = S.value() / wb - T(a.sw.d0);
+      T df;
+      const T f = ftrans(dv, T(a.sw.d_lo), T(a.sw.d_hi), T(1.0 / (a.sw.d_hi - a.sw.d_lo)), &df);
+      lam = T(1) - f;
+      dl = -df;
+    } else {
+      lam = a.lam_mode == APIP_LAM_CONST1 ? T(1) : T(0);
+    }
+    a.lam[i] = lam;
+    a.dlam[i] = dl;
+    a.wbar[i] = wb;
+    a.dd[i] = dv;
+    if (a.force) {
+      a.force[3 * i] = (double)fx.value();
+      a.force[3 * i + 1] = (double)fy.value();
+      a.force[3 * i + 2] = (double)fz.value();
+    }
+  }
+  const bool pred = active && lam > T(0);
+  const unsigned mask = __ballot_sync(0xffffffffu, pred);
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0 && mask) base = atomicAdd(&a.counts[0], __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (pred) a.ace_list[base + __popc(mask & ((1u << lane) - 1u))] = i;
+}
+
+// -------------------------------------------- grad-lambda force, CSP part
+// F -= grad sum_j c_j g_j (Eq. S25-S27) for the atoms with c_j != 0, where
+// c_j = sum_k Et_k w(r_kj) was accumulated by the ACE kernel; resets c_j.
+template <typename T>
+__global__ void k_csp_force(Args<T> a) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.n) return;
+  const double c = a.cvec[j];
+  if (c == 0.0) return;
+  a.cvec[j] = 0.0;
+  const auto sj = a.pv.self(j);
+  const int* pr = a.csp + (size_t)j * kCspCap;
+  double fj[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; 2 * k + 1 < a.csp_nnb; ++k) {
+    const int ia_id = pr[2 * k], ib_id = pr[2 * k + 1];
+    if (ia_id < 0 || ib_id < 0 || ia_id >= a.nmax || ib_id >= a.nmax) continue;
+    const int ia = a.id2idx[ia_id], ib = a.id2idx[ib_id];
+    if (ia < 0 || ib < 0 || ia >= a.n || ib >= a.n) continue;
+    const auto u1 = a.pv.vec(sj, ia);
+    const auto u2 = a.pv.vec(sj, ib);
+    const double u[3] = {(double)(u1.x + u2.x), (double)(u1.y + u2.y), (double)(u1.z + u2.z)};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      atomicAdd(&a.force[3 * ia + q], -2.0 * c * u[q]);
+      atomicAdd(&a.force[3 * ib + q], -2.0 * c * u[q]);
+      fj[q] += 4.0 * c * u[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) atomicAdd(&a.force[3 * j + q], fj[q]);
+}
+
+// ------------------------------------------------------------- reductions
+__device__ __forceinline__ void neumaier(double& s, double& c, double v) {
+  const double t = s + v;
+  c += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
+  s = t;
+}
+
+__global__ void k_final(const double* partials, int n_part, double* e_total, double* e_pot_slot,
+                        const double* thermo_part, int n_tb, double* thermo_slot, int* flags,
+                        const int* counts, int64_t* n_ace_out) {
+  __shared__ double sh[32];
+  double s = 0.0, c = 0.0;
+  for (int k = threadIdx.x; k < n_part; k += blockDim.x) neumaier(s, c, partials[k]);
+  const double tot = block_sum(s, sh) + block_sum(c, sh);
+  if (threadIdx.x == 0) {
+    if (e_total) *e_total = tot;
+    if (e_pot_slot) *e_pot_slot = tot;
+    flags[0] = 0;
+    if (n_ace_out) *n_ace_out = (int64_t)counts[0];
+  }
+  if (thermo_part) {
+    for (int q = 0; q < 4; ++q) {
+      double ts = 0.0, tc = 0.0;
+      for (int k = threadIdx.x; k < n_tb; k += blockDim.x) neumaier(ts, tc, thermo_part[4 * k + q]);
+      const double tt = block_sum(ts, sh) + block_sum(tc, sh);
+      if (threadIdx.x == 0) thermo_slot[1 + q] = tt;
+    }
+  }
+}
+
+__global__ void k_thermo_final(const double* thermo_part, int n_tb, double* thermo_slot) {
+  __shared__ double sh[32];
+  for (int q = 0; q < 4; ++q) {
+    double ts = 0.0, tc = 0.0;
+    for (int k = threadIdx.x; k < n_tb; k += blockDim.x) neumaier(ts, tc, thermo_part[4 * k + q]);
+    const double tt = block_sum(ts, sh) + block_sum(tc, sh);
+    if (threadIdx.x == 0) thermo_slot[1 + q] = tt;
+  }
+}
+
+// ----------------------------------------------------------------- Verlet
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* pos, double* vel,
+                                                   const double* force, const double* inv_mass,
+                                                   double dt, double* thermo_part) {
+  __shared__ double sh[32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && mode != 2) a.counts[0] = 0;
+  double ke = 0.0, p[3] = {0.0, 0.0, 0.0};
+  if (i < a.n) {
+    const double im = inv_mass[i];
+    const double h = 0.5 * dt * im;
+    double v[3], x[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v[q] = vel[3 * i + q] + h * force[3 * i + q];
+    if (mode != 0) {
+      ke = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / im;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) p[q] = v[q] / im;
+    }
+    if (mode == 1) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) v[q] += h * force[3 * i + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) vel[3 * i + q] = v[q];
+    if (mode != 2) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        x[q] = wrap1(pos[3 * i + q] + dt * v[q], a.geo.L[q], 1.0 / a.geo.L[q]);
+        pos[3 * i + q] = x[q];
+      }
+      prep_atom(a, i, x[0], x[1], x[2]);
+    }
+  }
+  if (mode != 0) {
+    const double vals[4] = {ke, p[0], p[1], p[2]};
+    for (int q = 0; q < 4; ++q) {
+      const double t = block_sum(vals[q], sh);
+      if (threadIdx.x == 0) thermo_part[4 * blockIdx.x + q] = t;
+    }
+  }
+}
+
+// ------------------------------------------------------------ inspection
+template <typename T>
+__global__ void k_get_field(Args<T> a, int field, void* dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  double* dd = (double*)dst;
+  long long* di = (long long*)dst;
+  switch (field) {
+    case APIP_FIELD_G: dd[i] = (double)a.g[i]; break;
+    case APIP_FIELD_D: dd[i] = (double)a.dd[i]; break;
+    case APIP_FIELD_WBAR: dd[i] = (double)a.wbar[i]; break;
+    case APIP_FIELD_LAM: dd[i] = (double)a.lam[i]; break;
+    case APIP_FIELD_DLAM: dd[i] = (double)a.dlam[i]; break;
+    case APIP_FIELD_E_EAM: dd[i] = (double)a.e_eam[i]; break;
+    case APIP_FIELD_E_ACE: dd[i] = a.lam[i] > T(0) ? (double)a.e_ace[i] : 0.0; break;
+    case APIP_FIELD_ZETA: dd[i] = (double)a.zeta[i]; break;
+    case APIP_FIELD_ACE_LIST: di[i] = i < a.counts[0] ? (long long)a.ace_list[i] : -1; break;
+    case APIP_FIELD_NNB: di[i] = a.nnb[i]; break;
+    case APIP_FIELD_NBLIST:
+      for (int s = 0; s < a.max_nb; ++s)
+        di[(size_t)i * a.max_nb + s] = s < a.nnb[i] ? (long long)a.nbl[(size_t)s * a.nmax + i] : -1;
+      break;
+    case APIP_FIELD_CSP:
+      for (int s = 0; s < a.csp_nnb; ++s) di[(size_t)i * a.csp_nnb + s] = a.csp[(size_t)i * kCspCap + s];
+      break;
+    default: break;
+  }
+}
+
+inline int nblocks(int n, int b = kBlock) { return (n + b - 1) / b > 0 ? (n + b - 1) / b : 1; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+template <typename T> void launch_prep(const Args<T>& a, cudaStream_t s) {
+  k_prep<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+}
+
+template <typename T> void launch_neighbors(const Args<T>& a, int ncell, cudaStream_t s) {
+  k_cell_clear<<<nblocks(ncell), kBlock, 0, s>>>(a.flags, a.cell_count, ncell);
+  k_bin<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+  k_cell_sort<<<nblocks(ncell), kBlock, 0, s>>>(a.flags, a.cell_count, a.cell_atoms, ncell, a.cell_cap);
+  k_nbfill<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+}
+
+void launch_csp_init(const Args<double>& a, cudaStream_t s) {
+  k_csp_init<<<nblocks(a.n, 128), 128, 0, s>>>(a);
+}
+
+template <typename T> void launch_pass1(const Args<T>& a, cudaStream_t s) {
+  k_pass1<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+}
+
+template <typename T> void launch_pass2(const Args<T>& a, cudaStream_t s) {
+  k_pass2<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+}
+
+template <typename T> void launch_csp_force(const Args<T>& a, cudaStream_t s) {
+  k_csp_force<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+}
+
+void launch_final(double* partials, int n_part, double* e_total, double* e_pot_slot,
+                  const double* thermo_part, int n_tblocks, double* thermo_slot, int* flags,
+                  const int* counts, int64_t* n_ace_out, cudaStream_t s) {
+  k_final<<<1, 256, 0, s>>>(partials, n_part, e_total, e_pot_slot, thermo_part, n_tblocks, thermo_slot,
+                            flags, counts, n_ace_out);
+}
+
+void launch_thermo_final(const double* thermo_part, int n_tblocks, double* thermo_slot, cudaStream_t s) {
+  k_thermo_final<<<1, 256, 0, s>>>(thermo_part, n_tblocks, thermo_slot);
+}
+
+template <typename T> void launch_verlet(const Args<T>& a, int mode, double* pos, double* vel,
+                                         const double* force, const double* inv_mass, double dt,
+                                         double* thermo_part, cudaStream_t s) {
+  k_verlet<T><<<nblocks(a.n), kBlock, 0, s>>>(a, mode, pos, vel, force, inv_mass, dt, thermo_part);
+}
+
+template <typename T> void launch_get_field(const Args<T>& a, int field, void* dst, cudaStream_t s) {
+  k_get_field<T><<<nblocks(a.n), kBlock, 0, s>>>(a, field, dst);
+}
+
+#define APIP_INST(T)                                                                              \
+  template void launch_prep<T>(const Args<T>&, cudaStream_t);                                     \
+  template void launch_neighbors<T>(const Args<T>&, int, cudaStream_t);                           \
+  template void launch_pass1<T>(const Args<T>&, cudaStream_t);                                    \
+  template void launch_pass2<T>(const Args<T>&, cudaStream_t);                                    \
+  template void launch_csp_force<T>(const Args<T>&, cudaStream_t);                                \
+  template void launch_verlet<T>(const Args<T>&, int, double*, double*, const double*,            \
+                                 const double*, double, double*, cudaStream_t);                   \
+  template void launch_get_field<T>(const Args<T>&, int, void*, cudaStream_t);
+APIP_INST(double)
+APIP_INST(float)
+#undef APIP_INST
+
+}  // namespace apip

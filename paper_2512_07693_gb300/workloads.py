@@ -131,11 +131,15 @@ def config(name, n_basis_fn, scale=None):
       crack2m   : 200 x 100 x 50 cell slab with a wedge crack (~2.0 M atoms);
                   ACE n_max 8, l_max 4, nu <= 4; FP32
     """
+    switch = {}
     if name == "vacancy2k":
         cells = 10 if scale is None else scale
         s = vacancy_crystal(cells=cells)
         nm, lm, nu, seed = 6, 3, 3, 2
         s.update(dt=0.001, steps=100, precision="fp64")
+        # sigma = 0.05 A makes a few bulk CSP pair lists detect second-shell
+        # partners; d_lo/d_hi are raised so that ~5 % of the atoms use ACE
+        switch = dict(d_lo=1.2, d_hi=2.2)
     elif name == "void250k":
         cells = 50 if scale is None else scale
         radius = 15.0 if scale is None else 15.0 * cells / 50.0
@@ -151,7 +155,7 @@ def config(name, n_basis_fn, scale=None):
         s.update(dt=0.001, steps=100, precision="fp32")
     else:
         raise KeyError(name)
-    prm = dict(precise_adds_eam=True, eam=dict(EAM), switch=dict(SWITCH), csp=dict(CSP),
+    prm = dict(precise_adds_eam=True, eam=dict(EAM), switch=dict(SWITCH, **switch), csp=dict(CSP),
                ace=ace_params(nm, lm, nu, seed, n_basis_fn(nm, lm, nu)))
     s.update(name=name, prm=prm)
     return s
