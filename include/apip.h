@@ -171,6 +171,20 @@ enum {
 };
 apip_status apip_get_field(apip_ctx* ctx, int32_t field, void* dst, int64_t n, void* stream);
 
+/* Per-phase device timing (tracing).  While enabled, every call records CUDA
+ * events around its phases on the call's stream; apip_profile_read synchronises,
+ * writes the accumulated device milliseconds and launch counts per phase since
+ * the last read into the host arrays ms[APIP_PHASE_COUNT] and
+ * launches[APIP_PHASE_COUNT], and resets them.  Phases: PREP (position
+ * preparation or Verlet kernels), NEIGHBOR (the four conditional neighbour-list
+ * kernels), PASS1, PASS2, ACE, CSP (CSP part of grad-lambda), REDUCE. */
+enum {
+  APIP_PHASE_PREP = 0, APIP_PHASE_NEIGHBOR = 1, APIP_PHASE_PASS1 = 2, APIP_PHASE_PASS2 = 3,
+  APIP_PHASE_ACE = 4, APIP_PHASE_CSP = 5, APIP_PHASE_REDUCE = 6, APIP_PHASE_COUNT = 7
+};
+apip_status apip_profile(apip_ctx* ctx, int32_t enable);
+apip_status apip_profile_read(apip_ctx* ctx, double* ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,7 @@ STATUS_NAMES = {0: "APIP_OK", 1: "APIP_ERR_ARG", 2: "APIP_ERR_CUDA", 3: "APIP_ER
                 4: "APIP_ERR_BAD_INPUT", 5: "APIP_ERR_STATE"}
 APIP_FP64, APIP_FP32 = 0, 1
 APIP_LAM_PAPER, APIP_LAM_CONST0, APIP_LAM_CONST1 = 0, 1, 2
+PHASES = ("prep", "neighbor", "pass1", "pass2", "ace", "csp", "reduce")
 FIELDS = dict(g=0, d=1, wbar=2, lam=3, dlam=4, e_eam=5, e_ace=6, zeta=7, ace_list=8, nnb=9, nblist=10, csp=11)
 MVV2E = 1.0364269e-4   # amu A^2 / ps^2 -> eV
 
@@ -59,6 +60,8 @@ def _load():
         "apip_sync": (ctypes.c_int, [_vp, _vp]),
         "apip_last_error": (ctypes.c_char_p, [_vp]),
         "apip_get_field": (ctypes.c_int, [_vp, _c_int32, _vp, _c_int64, _vp]),
+        "apip_profile": (ctypes.c_int, [_vp, _c_int32]),
+        "apip_profile_read": (ctypes.c_int, [_vp, P(_c_double), P(_c_int64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -149,6 +152,18 @@ def apip_last_error(ctx):
 def apip_get_field(ctx, field, dst, n, stream=None):
     f = FIELDS[field] if isinstance(field, str) else int(field)
     _check(ctx, lib.apip_get_field(ctx, f, _ptr(dst), int(n), _stream(stream)))
+
+
+def apip_profile(ctx, enable):
+    _check(ctx, lib.apip_profile(ctx, int(bool(enable))))
+
+
+def apip_profile_read(ctx):
+    """{phase: (milliseconds, launches)} accumulated since the last read."""
+    ms = (_c_double * len(PHASES))()
+    nl = (_c_int64 * len(PHASES))()
+    _check(ctx, lib.apip_profile_read(ctx, ms, nl))
+    return {name: (ms[k], nl[k]) for k, name in enumerate(PHASES)}
 
 
 # ---------------------------------------------------------------- helpers

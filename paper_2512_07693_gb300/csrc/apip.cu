@@ -37,7 +37,42 @@ size_t esize(const apip_ctx* c) { return c->p.precision == APIP_FP32 ? sizeof(fl
 
 template <typename T> T* as(void* p) { return reinterpret_cast<T*>(p); }
 
+cudaEvent_t take_event(apip_ctx* c) {
+  if (!c->prof_pool.empty()) {
+    cudaEvent_t e = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Records CUDA events around one phase of a call when profiling is enabled.
+struct Phase {
+  apip_ctx* c;
+  int phase, launches;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  Phase(apip_ctx* c_, int ph, int nl, cudaStream_t s_) : c(c_), phase(ph), launches(nl), s(s_) {
+    if (c->prof) {
+      a = take_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~Phase() {
+    if (!c->prof) return;
+    cudaEvent_t b = take_event(c);
+    cudaEventRecord(b, s);
+    c->prof_pending.push_back({phase, launches, a, b});
+  }
+};
+
 void free_all(apip_ctx* c) {
+  for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+  c->prof_pending.clear();
+  c->prof_pool.clear();
   void* ptrs[] = {c->cell_count, c->cell_atoms, c->nnb, c->nbl, c->pos_ref, c->posh, c->posl, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->counts, c->flags, c->status, c->partials, c->thermo_part,
@@ -194,11 +229,14 @@ apip_status launch_status(apip_ctx* ctx) {
 // The force pipeline after prep (or after the drift of a Verlet step).
 template <typename T>
 void force_pipeline(apip_ctx* c, Args<T>& a, cudaStream_t s) {
-  launch_neighbors<T>(a, c->ncell, s);
-  launch_pass1<T>(a, s);
-  launch_pass2<T>(a, s);
-  launch_ace<T>(a, ace_dev<T>(c), c->ace_blocks, s);
-  if (a.lam_mode == APIP_LAM_PAPER && a.grad_lambda) launch_csp_force<T>(a, s);
+  { Phase ph(c, APIP_PHASE_NEIGHBOR, 4, s); launch_neighbors<T>(a, c->ncell, s); }
+  { Phase ph(c, APIP_PHASE_PASS1, 1, s); launch_pass1<T>(a, s); }
+  { Phase ph(c, APIP_PHASE_PASS2, 1, s); launch_pass2<T>(a, s); }
+  { Phase ph(c, APIP_PHASE_ACE, 1, s); launch_ace<T>(a, ace_dev<T>(c), c->ace_blocks, s); }
+  if (a.lam_mode == APIP_LAM_PAPER && a.grad_lambda) {
+    Phase ph(c, APIP_PHASE_CSP, 1, s);
+    launch_csp_force<T>(a, s);
+  }
 }
 
 template <typename T>
@@ -206,8 +244,9 @@ apip_status energy_forces_t(apip_ctx* c, const double* pos, const int32_t* id, i
                             double* e_atom, double* e_total, cudaStream_t s) {
   Args<T> a = make_args<T>(c, pos, id, n, force, e_atom);
   set_view<T>(a, c);
-  launch_prep<T>(a, s);
+  { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_prep<T>(a, s); }
   force_pipeline<T>(c, a, s);
+  Phase ph(c, APIP_PHASE_REDUCE, 1, s);
   launch_final(c->partials, a.n_part_p1 + c->ace_blocks * kAceWarps, e_total, nullptr, nullptr, 0, nullptr,
                c->flags, c->counts, nullptr, s);
   return launch_status(c);
@@ -248,14 +287,18 @@ apip_status verlet_t(apip_ctx* c, double* pos, double* vel, double* force, const
   const int ntb = nblk(n);
   const int n_part = a.n_part_p1 + c->ace_blocks * kAceWarps;
   for (int k = 0; k < steps; ++k) {
-    launch_verlet<T>(a, k == 0 ? 0 : 1, pos, vel, force, inv_mass, dt, c->thermo_part, s);
+    { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, k == 0 ? 0 : 1, pos, vel, force, inv_mass, dt, c->thermo_part, s); }
     force_pipeline<T>(c, a, s);
+    Phase ph(c, APIP_PHASE_REDUCE, 1, s);
     launch_final(c->partials, n_part, nullptr, thermo ? thermo + 5 * k : nullptr,
                  (thermo && k > 0) ? c->thermo_part : nullptr, ntb, thermo ? thermo + 5 * (k - 1) : nullptr,
                  c->flags, c->counts, nullptr, s);
   }
-  launch_verlet<T>(a, 2, pos, vel, force, inv_mass, dt, c->thermo_part, s);
-  if (thermo) launch_thermo_final(c->thermo_part, ntb, thermo + 5 * (steps - 1), s);
+  { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, 2, pos, vel, force, inv_mass, dt, c->thermo_part, s); }
+  if (thermo) {
+    Phase ph(c, APIP_PHASE_REDUCE, 1, s);
+    launch_thermo_final(c->thermo_part, ntb, thermo + 5 * (steps - 1), s);
+  }
   return launch_status(c);
 }
 
@@ -474,6 +517,33 @@ apip_status apip_sync(apip_ctx* ctx, void* stream) {
                                               " atoms, cell_cap = " + std::to_string(ctx->p.cell_cap));
   if (st[ST_BAD_INPUT]) return fail(ctx, APIP_ERR_BAD_INPUT, "non-finite position or atom id out of range");
   if (st[ST_BAD_PARTNER]) return fail(ctx, APIP_ERR_BAD_INPUT, "a CSP partner id is not present");
+  return APIP_OK;
+}
+
+apip_status apip_profile(apip_ctx* ctx, int32_t enable) {
+  if (!ctx) return APIP_ERR_ARG;
+  ctx->prof = enable != 0;
+  return APIP_OK;
+}
+
+apip_status apip_profile_read(apip_ctx* ctx, double* ms, int64_t* launches) {
+  if (!ctx || !ms || !launches) return APIP_ERR_ARG;
+  for (auto& r : ctx->prof_pending) {
+    APIP_CK(cudaEventSynchronize(r.b));
+    float t = 0.f;
+    APIP_CK(cudaEventElapsedTime(&t, r.a, r.b));
+    ctx->prof_ms[r.phase] += t;
+    ctx->prof_n[r.phase] += r.launches;
+    ctx->prof_pool.push_back(r.a);
+    ctx->prof_pool.push_back(r.b);
+  }
+  ctx->prof_pending.clear();
+  for (int k = 0; k < APIP_PHASE_COUNT; ++k) {
+    ms[k] = ctx->prof_ms[k];
+    launches[k] = ctx->prof_n[k];
+    ctx->prof_ms[k] = 0.0;
+    ctx->prof_n[k] = 0;
+  }
   return APIP_OK;
 }
 

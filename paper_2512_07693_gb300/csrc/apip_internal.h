@@ -6,7 +6,7 @@
 #include <string>
 #include <vector>
 
-#include <vector_types.h>
+#include <cuda_runtime.h>
 
 #include "apip.h"
 
@@ -105,6 +105,14 @@ struct apip_ctx {
   double* e_scratch = nullptr;    // [2] total energy scratch
   int n_part = 0;
   int ace_blocks = 0;
+
+  // phase timing (apip_profile)
+  bool prof = false;
+  struct ProfRec { int phase; int launches; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[APIP_PHASE_COUNT] = {};
+  int64_t prof_n[APIP_PHASE_COUNT] = {};
 
   // ACE tables (element size = precision)
   uint32_t* key3 = nullptr; void* k3a = nullptr; void* k3b = nullptr; int n3 = 0;

@@ -17,15 +17,33 @@ template <typename T>
 __device__ __forceinline__ T dot3(const V3<T>& a, const V3<T>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
 // f_trans(x, lo, hi) of Eq. S1 and its derivative: 1 below lo, 0 above hi,
-// in between 1/2 + t (15/16 + t^2 (-5/8 + 3/16 t^2)) with t = (hi + lo - 2x)/(hi - lo).
+// in between the quintic 1/2 + 15/16 t - 5/8 t^3 + 3/16 t^5 of
+// t = (hi + lo - 2x)/(hi - lo).  It is evaluated in the factored forms
+//   f = (1 + t)^3 (8 - 9t + 3t^2) / 16,   1 - f = (1 - t)^3 (8 + 9t + 3t^2) / 16,
+//   df/dt = 15/16 (1 - t^2)^2,
+// which keep full relative precision near both ends (in FP32 the expanded
+// polynomial loses every digit of 1 - f close to x = lo).
 template <typename T>
 __device__ __forceinline__ T ftrans(T x, T lo, T hi, T inv_w, T* deriv) {
   if (x <= lo) { *deriv = T(0); return T(1); }
   if (x >= hi) { *deriv = T(0); return T(0); }
   const T t = (hi + lo - T(2) * x) * inv_w;
-  const T t2 = t * t;
-  *deriv = (T(0.9375) + t2 * (T(-1.875) + T(0.9375) * t2)) * (T(-2) * inv_w);
-  return T(0.5) + t * (T(0.9375) + t2 * (T(-0.625) + T(0.1875) * t2));
+  const T u = T(1) - t * t;
+  *deriv = T(0.9375) * u * u * (T(-2) * inv_w);
+  const T p = T(1) + t;
+  return T(0.0625) * p * p * p * (T(8) + t * (T(-9) + T(3) * t));
+}
+
+// 1 - f_trans(x, lo, hi) and d(1 - f_trans)/dx.
+template <typename T>
+__device__ __forceinline__ T ftrans_c(T x, T lo, T hi, T inv_w, T* deriv) {
+  if (x <= lo) { *deriv = T(0); return T(0); }
+  if (x >= hi) { *deriv = T(0); return T(1); }
+  const T t = (hi + lo - T(2) * x) * inv_w;
+  const T u = T(1) - t * t;
+  *deriv = T(0.9375) * u * u * (T(2) * inv_w);
+  const T q = T(1) - t;
+  return T(0.0625) * q * q * q * (T(8) + t * (T(9) + T(3) * t));
 }
 
 // Running sum with Kahan compensation in FP32; plain in FP64.

@@ -180,21 +180,21 @@ __global__ void __launch_bounds__(kAceWarps * 32) k_ace(Args<T> a, AceDev<T> t) 
     __syncwarp();
 
     // 2. embedding channels
-    T p1 = T(0), p2 = T(0);
+    Acc<T> s1, s2;     // compensated in FP32
     for (int q = lane; q < t.n3; q += 32) {
       const uint32_t k = t.key3[q];
       const T x = A[k & 255u] * A[(k >> 8) & 255u] * A[(k >> 16) & 255u];
-      p1 += t.k3a[q] * x;
-      p2 += t.k3b[q] * x;
+      s1.add(t.k3a[q] * x);
+      s2.add(t.k3b[q] * x);
     }
     for (int q = lane; q < t.n4; q += 32) {
       const uint32_t k = t.key4[q];
       const T x = A[k & 255u] * A[(k >> 8) & 255u] * A[(k >> 16) & 255u] * A[k >> 24];
-      p1 += t.k4a[q] * x;
-      p2 += t.k4b[q] * x;
+      s1.add(t.k4a[q] * x);
+      s2.add(t.k4b[q] * x);
     }
-    p1 = warp_sum(p1);
-    p2 = warp_sum(p2);
+    const T p1 = warp_sum(s1.value());
+    const T p2 = warp_sum(s2.value());
     const T q2 = sqrt(p2 * p2 + t.eps * t.eps);
     const T e_ace = p1 + sqrt(q2) - t.sqrt_eps;
     const T dfs = T(0.5) * p2 / (q2 * sqrt(q2));

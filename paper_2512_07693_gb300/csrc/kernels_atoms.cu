@@ -322,10 +322,7 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
     if (paper) {
       wb = wbar.value();
       dv = S.value() / wb - T(a.sw.d0);
-      T df;
-      const T f = ftrans(dv, T(a.sw.d_lo), T(a.sw.d_hi), T(1.0 / (a.sw.d_hi - a.sw.d_lo)), &df);
-      lam = T(1) - f;
-      dl = -df;
+      lam = ftrans_c(dv, T(a.sw.d_lo), T(a.sw.d_hi), T(1.0 / (a.sw.d_hi - a.sw.d_lo)), &dl);
     } else {
       lam = a.lam_mode == APIP_LAM_CONST1 ? T(1) : T(0);
     }

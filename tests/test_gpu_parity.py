@@ -46,8 +46,10 @@ def compare(g, o, prec, check_sets=True):
         if prec == "fp64":
             assert np.array_equal(Pg, np.sort(P))
         else:
+            # float32 may only disagree where d is within its rounding of d_lo
+            # (there lam ~ (d - d_lo)^3 is negligible)
             diff = np.setxor1d(Pg, P)
-            assert np.all(np.abs(o["d"][diff] - o["switch_dlo"]) < 1e-4), diff
+            assert np.all((np.abs(o["d"][diff] - o["switch_dlo"]) < 1e-5) | (lam[diff] < 1e-12)), diff
     np.testing.assert_allclose(g["e_eam"], o["e_eam"], atol=tol["e"])
     both = np.intersect1d(Pg, P)
     np.testing.assert_allclose(g["e_ace"][both], o["e_ace"][both], atol=tol["e"])
