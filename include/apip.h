@@ -48,8 +48,9 @@ typedef enum {
                                 than cell_cap; apip_last_error reports the size needed */
   APIP_ERR_BAD_INPUT = 4,    /* non-finite position, id out of range, or a CSP partner ID
                                 that is not present */
-  APIP_ERR_STATE = 5         /* call order: apip_init_csp_pairs must precede calls that use
+  APIP_ERR_STATE = 5,        /* call order: apip_init_csp_pairs must precede calls that use
                                 the paper's switch */
+  APIP_ERR_SIZE = 6          /* input larger than a fixed-capacity entry point can hold */
 } apip_status;
 
 enum { APIP_FP64 = 0, APIP_FP32 = 1 };
@@ -184,6 +185,31 @@ enum {
 };
 apip_status apip_profile(apip_ctx* ctx, int32_t enable);
 apip_status apip_profile_read(apip_ctx* ctx, double* ms, int64_t* launches);
+
+/* Allocation-free total energy.  The paper has no counterpart: this is a service
+ * for callers that cannot call cudaMalloc, such as a host program whose device
+ * memory is entirely owned by its own pool allocator, or a latency-critical loop
+ * that must never enter the allocator.  It needs no context.
+ *
+ * Sums the caller's per-atom energies e_atom[0..n) (device, float64) into
+ * *e_total (device scalar) with the same compensated two-stage float64 reduction
+ * that apip_energy_forces uses for e_total_out.  Its block partials are kept in
+ * one fixed file-scope device array of APIP_STATIC_MAX_BLOCKS doubles (32 KiB),
+ * which every GPU that loads the library holds until the process exits, so n is
+ * limited to APIP_STATIC_MAX_ATOMS; larger n returns APIP_ERR_SIZE without any
+ * GPU work.  The call allocates nothing: no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *  - The first call on each device looks up the array's device address (with that
+ *    device current) and caches it; make that first call before any stream capture.
+ *  - All calls share the one array.  Each call writes every partial it reads, so
+ *    nothing needs clearing between calls, but calls that overlap on the GPU (on
+ *    different streams, or from different host threads) race on the partials and
+ *    may return wrong sums: serialise them.
+ * Errors: APIP_ERR_ARG (NULL pointer, n < 0), APIP_ERR_SIZE, APIP_ERR_CUDA. */
+#define APIP_STATIC_ATOMS_PER_BLOCK 4096
+#define APIP_STATIC_MAX_BLOCKS 4096
+#define APIP_STATIC_MAX_ATOMS ((int64_t)APIP_STATIC_ATOMS_PER_BLOCK * APIP_STATIC_MAX_BLOCKS)
+apip_status apip_reduce_energy_static(const double* e_atom, int64_t n, double* e_total, void* stream);
 
 #ifdef __cplusplus
 }

@@ -14,9 +14,10 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libapip.so")
 
-APIP_OK, APIP_ERR_ARG, APIP_ERR_CUDA, APIP_ERR_NB_OVERFLOW, APIP_ERR_BAD_INPUT, APIP_ERR_STATE = range(6)
+APIP_OK, APIP_ERR_ARG, APIP_ERR_CUDA, APIP_ERR_NB_OVERFLOW, APIP_ERR_BAD_INPUT, APIP_ERR_STATE, APIP_ERR_SIZE = range(7)
 STATUS_NAMES = {0: "APIP_OK", 1: "APIP_ERR_ARG", 2: "APIP_ERR_CUDA", 3: "APIP_ERR_NB_OVERFLOW",
-                4: "APIP_ERR_BAD_INPUT", 5: "APIP_ERR_STATE"}
+                4: "APIP_ERR_BAD_INPUT", 5: "APIP_ERR_STATE", 6: "APIP_ERR_SIZE"}
+APIP_STATIC_MAX_ATOMS = 4096 * 4096
 APIP_FP64, APIP_FP32 = 0, 1
 APIP_LAM_PAPER, APIP_LAM_CONST0, APIP_LAM_CONST1 = 0, 1, 2
 PHASES = ("prep", "neighbor", "pass1", "pass2", "ace", "csp", "reduce")
@@ -62,6 +63,7 @@ def _load():
         "apip_get_field": (ctypes.c_int, [_vp, _c_int32, _vp, _c_int64, _vp]),
         "apip_profile": (ctypes.c_int, [_vp, _c_int32]),
         "apip_profile_read": (ctypes.c_int, [_vp, P(_c_double), P(_c_int64)]),
+        "apip_reduce_energy_static": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -164,6 +166,17 @@ def apip_profile_read(ctx):
     nl = (_c_int64 * len(PHASES))()
     _check(ctx, lib.apip_profile_read(ctx, ms, nl))
     return {name: (ms[k], nl[k]) for k, name in enumerate(PHASES)}
+
+
+def apip_reduce_energy_static(e_atom, n, e_total, stream=None):
+    """Total of e_atom[0..n) into e_total[0] without any device allocation (for
+    callers that cannot call cudaMalloc); n <= APIP_STATIC_MAX_ATOMS.  Calls that
+    overlap on the GPU share one scratch array and race; serialise them."""
+    st = lib.apip_reduce_energy_static(_ptr(e_atom), int(n), _ptr(e_total), _stream(stream))
+    if st != APIP_OK:
+        why = {APIP_ERR_SIZE: f"n = {n} exceeds APIP_STATIC_MAX_ATOMS = {APIP_STATIC_MAX_ATOMS}",
+               APIP_ERR_ARG: "NULL pointer or negative n"}.get(st, "CUDA error")
+        raise ApipError(st, why)
 
 
 # ---------------------------------------------------------------- helpers

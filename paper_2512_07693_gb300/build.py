@@ -13,7 +13,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libapip.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["apip.cu", "kernels_atoms.cu", "kernels_ace.cu", "ace_tables.cpp"]
+SOURCES = ["apip.cu", "kernels_atoms.cu", "kernels_ace.cu", "ace_tables.cpp", "apip_static.cu"]
 HEADERS = ["apip_internal.h", "device_common.cuh", "kernels.h"]
 
 
