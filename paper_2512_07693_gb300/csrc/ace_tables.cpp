@@ -253,6 +253,44 @@ bool build_terms(int n_max, int l_max, int nu_max, const double* c1, const doubl
     out->k4a.push_back(kv.second.a);
     out->k4b.push_back(kv.second.b);
   }
+  // Derivative entries: d phi_c / dA[tgt] = sum_e K_c[e] A[a] A[b] A[c] over the
+  // entries e with target tgt, one per (term, position of tgt) and merged when the
+  // remaining index triple coincides.  Key = tgt << 24 | a | b << 8 | c << 16 with
+  // a <= b <= c (index nA = the constant 1), so the list is sorted by target.
+  std::map<uint32_t, Coef> td;
+  auto add_d = [&](int tgt, int a, int b, int c, const Coef& k) {
+    if (tgt == one) return;
+    int v[3] = {a, b, c};
+    std::sort(v, v + 3);
+    const uint32_t key = ((uint32_t)tgt << 24) | (uint32_t)v[0] | ((uint32_t)v[1] << 8) | ((uint32_t)v[2] << 16);
+    Coef& e = td[key];
+    e.a += k.a;
+    e.b += k.b;
+  };
+  for (size_t q = 0; q < out->key3.size(); ++q) {
+    const uint32_t k = out->key3[q];
+    const int i0 = k & 255u, i1 = (k >> 8) & 255u, i2 = (k >> 16) & 255u;
+    const Coef c{out->k3a[q], out->k3b[q]};
+    add_d(i0, i1, i2, one, c);
+    add_d(i1, i0, i2, one, c);
+    add_d(i2, i0, i1, one, c);
+  }
+  for (size_t q = 0; q < out->key4.size(); ++q) {
+    const uint32_t k = out->key4[q];
+    const int i0 = k & 255u, i1 = (k >> 8) & 255u, i2 = (k >> 16) & 255u, i3 = k >> 24;
+    const Coef c{out->k4a[q], out->k4b[q]};
+    add_d(i0, i1, i2, i3, c);
+    add_d(i1, i0, i2, i3, c);
+    add_d(i2, i0, i1, i3, c);
+    add_d(i3, i0, i1, i2, c);
+  }
+  out->keyd.clear(); out->kda.clear(); out->kdb.clear();
+  for (const auto& kv : td) {
+    if (kv.second.a == 0.0 && kv.second.b == 0.0) continue;
+    out->keyd.push_back(kv.first);
+    out->kda.push_back(kv.second.a);
+    out->kdb.push_back(kv.second.b);
+  }
   return true;
 }
 

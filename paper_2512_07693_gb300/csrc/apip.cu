@@ -76,7 +76,7 @@ void free_all(apip_ctx* c) {
   void* ptrs[] = {c->cell_count, c->cell_atoms, c->nnb, c->nbl, c->pos_ref, c->posh, c->posl, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->counts, c->flags, c->status, c->partials, c->thermo_part,
-                  c->e_scratch, c->key3, c->k3a, c->k3b, c->key4, c->k4a, c->k4b};
+                  c->e_scratch, c->key3, c->k3a, c->k3b, c->key4, c->k4a, c->k4b, c->keyd, c->kda, c->kdb};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -119,6 +119,7 @@ apip_status set_geometry(apip_ctx* ctx, const double* box, cudaStream_t s) {
     if (g.nc[k] < 3)
       return fail(ctx, APIP_ERR_ARG, "each box edge must be >= 3 * (cutoff + skin) = " + std::to_string(3 * ctx->r_list));
     g.cs[k] = box[k] / g.nc[k];
+    g.invL[k] = 1.0 / box[k];
     g.Lh[k] = (float)box[k];
     g.Ll[k] = (float)(box[k] - (double)g.Lh[k]);
     ncell *= g.nc[k];
@@ -157,8 +158,10 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.grad_lambda = p.grad_lambda;
   a.eam_force = 1;
   a.geo = c->geo;
-  a.eam = {p.eam_A, p.eam_beta, p.eam_re, p.eam_D, p.eam_alpha, p.eam_r0, p.eam_rc, p.eam_rc - p.eam_rc_width};
-  a.sw = {p.sw_r_w, p.sw_r_w - p.sw_r_w_width, p.sw_d_lo, p.sw_d_hi, p.sw_d0};
+  a.eam = {p.eam_A, p.eam_beta, p.eam_re, p.eam_D, p.eam_alpha, p.eam_r0, p.eam_rc, p.eam_rc - p.eam_rc_width,
+           1.0 / p.eam_rc_width};
+  a.sw = {p.sw_r_w, p.sw_r_w - p.sw_r_w_width, p.sw_d_lo, p.sw_d_hi, p.sw_d0, 1.0 / p.sw_r_w_width,
+          1.0 / (p.sw_d_hi - p.sw_d_lo)};
   a.r_list2 = c->r_list * c->r_list;
   a.skin_half2 = 0.25 * p.skin * p.skin;
   a.csp_rcut2 = p.csp_rcut * p.csp_rcut;
@@ -210,6 +213,7 @@ AceDev<T> ace_dev(apip_ctx* c) {
   t.a_scale = T(p.ace_a_scale);
   t.key3 = c->key3; t.k3a = as<T>(c->k3a); t.k3b = as<T>(c->k3b); t.n3 = c->n3;
   t.key4 = c->key4; t.k4a = as<T>(c->k4a); t.k4b = as<T>(c->k4b); t.n4 = c->n4;
+  t.keyd = c->keyd; t.kda = as<T>(c->kda); t.kdb = as<T>(c->kdb); t.nd = c->nd;
   return t;
 }
 
@@ -374,12 +378,16 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->e_scratch, sizeof(double) * 2);
   ctx->n3 = (int)terms.key3.size();
   ctx->n4 = (int)terms.key4.size();
+  ctx->nd = (int)terms.keyd.size();
   APIP_ALLOC(ctx->key3, sizeof(uint32_t) * std::max(1, ctx->n3));
   APIP_ALLOC(ctx->k3a, es * std::max(1, ctx->n3));
   APIP_ALLOC(ctx->k3b, es * std::max(1, ctx->n3));
   APIP_ALLOC(ctx->key4, sizeof(uint32_t) * std::max(1, ctx->n4));
   APIP_ALLOC(ctx->k4a, es * std::max(1, ctx->n4));
   APIP_ALLOC(ctx->k4b, es * std::max(1, ctx->n4));
+  APIP_ALLOC(ctx->keyd, sizeof(uint32_t) * std::max(1, ctx->nd));
+  APIP_ALLOC(ctx->kda, es * std::max(1, ctx->nd));
+  APIP_ALLOC(ctx->kdb, es * std::max(1, ctx->nd));
 #undef APIP_ALLOC
   auto upload = [&](void* dst, const std::vector<double>& v) -> cudaError_t {
     if (v.empty()) return cudaSuccess;
@@ -391,6 +399,10 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   if (ctx->n3) e = cudaMemcpy(ctx->key3, terms.key3.data(), sizeof(uint32_t) * ctx->n3, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && ctx->n4)
     e = cudaMemcpy(ctx->key4, terms.key4.data(), sizeof(uint32_t) * ctx->n4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && ctx->nd)
+    e = cudaMemcpy(ctx->keyd, terms.keyd.data(), sizeof(uint32_t) * ctx->nd, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = upload(ctx->kda, terms.kda);
+  if (e == cudaSuccess) e = upload(ctx->kdb, terms.kdb);
   if (e == cudaSuccess) e = upload(ctx->k3a, terms.k3a);
   if (e == cudaSuccess) e = upload(ctx->k3b, terms.k3b);
   if (e == cudaSuccess) e = upload(ctx->k4a, terms.k4a);

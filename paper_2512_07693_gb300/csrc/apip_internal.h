@@ -33,12 +33,13 @@ enum {
 struct Geo {
   double L[3];          // box edges
   double cs[3];         // cell edges (>= r_list)
+  double invL[3];       // 1 / L
   int nc[3];            // cells per axis (>= 3)
   float Lh[3], Ll[3];   // L split as float hi + lo (FP32 path)
 };
 
-struct EamP { double A, beta, re, D, alpha, r0, rc, rc_lo; };
-struct SwP { double r_w, r_w_lo, d_lo, d_hi, d0; };
+struct EamP { double A, beta, re, D, alpha, r0, rc, rc_lo, inv_w; };   // inv_w = 1/(rc - rc_lo)
+struct SwP { double r_w, r_w_lo, d_lo, d_hi, d0, inv_w, inv_d; };  // 1/(r_w - r_w_lo), 1/(d_hi - d_lo)
 
 // ACE tables on the device: terms of the folded product basis,
 //   phi_c = sum_t K_c[t] prod_{q} A[idx_q(t)],  c = 1, 2,
@@ -49,11 +50,12 @@ struct AceDev {
   T rc, rc_lo, eps, sqrt_eps, a_scale;
   const uint32_t* key3; const T* k3a; const T* k3b; int n3;   // 3-index terms
   const uint32_t* key4; const T* k4a; const T* k4b; int n4;   // 4-index terms
+  const uint32_t* keyd; const T* kda; const T* kdb; int nd;   // derivative entries, sorted by target
 };
 
 struct HostTerms {
-  std::vector<uint32_t> key3, key4;
-  std::vector<double> k3a, k3b, k4a, k4b;
+  std::vector<uint32_t> key3, key4, keyd;
+  std::vector<double> k3a, k3b, k4a, k4b, kda, kdb;
 };
 
 // ace_tables.cpp
@@ -117,4 +119,5 @@ struct apip_ctx {
   // ACE tables (element size = precision)
   uint32_t* key3 = nullptr; void* k3a = nullptr; void* k3b = nullptr; int n3 = 0;
   uint32_t* key4 = nullptr; void* k4a = nullptr; void* k4b = nullptr; int n4 = 0;
+  uint32_t* keyd = nullptr; void* kda = nullptr; void* kdb = nullptr; int nd = 0;
 };

@@ -7,8 +7,9 @@
 //     neighbours at a time into shared memory, then lanes own components of A.
 //  2. phi_c = sum_t K_c[t] prod_q A[idx_q(t)] over the folded term lists (lanes
 //     stride the terms); E_i^ACE = phi_1 + (phi_2^2 + eps^2)^(1/4) - sqrt(eps).
-//  3. omega = dE_i/dA by reverse accumulation over the same terms (shared-memory
-//     atomics), scaled by a_scale lam_i.
+//  3. omega = dE_i/dA from the derivative entries of the terms, sorted by target
+//     A index: a segmented warp scan per 32 entries, no atomics; then scaled by
+//     a_scale lam_i.
 //  4. Lane = neighbour j: f_ij = sum_nlm omega_nlm grad(R_n Y_lm)(r_ij) (Eq. S14 /
 //     A1 force contribution); plus, for the fast-model weights (1 - lam), the part
 //     -lam_i a_ij e_ij of S12 that pass 2 left out; plus, when dlam_i != 0, the
@@ -120,9 +121,9 @@ __global__ void __launch_bounds__(kAceWarps * 32) k_ace(Args<T> a, AceDev<T> t) 
   const int nw = gridDim.x * kAceWarps;
   const T rc2 = t.rc * t.rc;
   const T rcE2 = T(a.eam.rc * a.eam.rc), rcE = T(a.eam.rc), rcE_lo = T(a.eam.rc_lo);
-  const T rcE_inv = T(1.0 / (a.eam.rc - a.eam.rc_lo));
+  const T rcE_inv = T(a.eam.inv_w);
   const T rw2 = T(a.sw.r_w * a.sw.r_w), rw = T(a.sw.r_w), rw_lo = T(a.sw.r_w_lo);
-  const T rw_inv = T(1.0 / (a.sw.r_w - a.sw.r_w_lo));
+  const T rw_inv = T(a.sw.inv_w);
   const bool eam_corr = !a.precise_adds_eam && a.eam_force;
   const int n_max = t.n_max;
   double e_part = 0.0;
@@ -199,27 +200,28 @@ __global__ void __launch_bounds__(kAceWarps * 32) k_ace(Args<T> a, AceDev<T> t) 
     const T e_ace = p1 + sqrt(q2) - t.sqrt_eps;
     const T dfs = T(0.5) * p2 / (q2 * sqrt(q2));
 
-    // 3. omega = dE/dA (reverse accumulation)
-    for (int q = lane; q < t.n3; q += 32) {
-      const uint32_t k = t.key3[q];
-      const int i0 = k & 255u, i1 = (k >> 8) & 255u, i2 = (k >> 16) & 255u;
-      const T x0 = A[i0], x1 = A[i1], x2 = A[i2];
-      const T kap = t.k3a[q] + dfs * t.k3b[q];
-      atomicAdd(&W[i0], kap * x1 * x2);
-      atomicAdd(&W[i1], kap * x0 * x2);
-      atomicAdd(&W[i2], kap * x0 * x1);
+    // 3. omega = dE/dA from the derivative entries (sorted by target): 32
+    //    consecutive entries per step, a segmented warp scan over equal targets,
+    //    and one plain shared-memory update per distinct target.
+    for (int base = 0; base < t.nd; base += 32) {
+      const int q = base + lane;
+      int tgt = -1 - lane;
+      T v = T(0);
+      if (q < t.nd) {
+        const uint32_t k = t.keyd[q];
+        tgt = (int)(k >> 24);
+        v = (t.kda[q] + dfs * t.kdb[q]) * A[k & 255u] * A[(k >> 8) & 255u] * A[(k >> 16) & 255u];
+      }
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const T vo = __shfl_up_sync(0xffffffffu, v, o);
+        const int to = __shfl_up_sync(0xffffffffu, tgt, o);
+        if (lane >= o && to == tgt) v += vo;
+      }
+      const int tn = __shfl_down_sync(0xffffffffu, tgt, 1);
+      if (q < t.nd && (lane == 31 || tn != tgt)) W[tgt] += v;
+      __syncwarp();
     }
-    for (int q = lane; q < t.n4; q += 32) {
-      const uint32_t k = t.key4[q];
-      const int i0 = k & 255u, i1 = (k >> 8) & 255u, i2 = (k >> 16) & 255u, i3 = k >> 24;
-      const T x0 = A[i0], x1 = A[i1], x2 = A[i2], x3 = A[i3];
-      const T kap = t.k4a[q] + dfs * t.k4b[q];
-      atomicAdd(&W[i0], kap * x1 * x2 * x3);
-      atomicAdd(&W[i1], kap * x0 * x2 * x3);
-      atomicAdd(&W[i2], kap * x0 * x1 * x3);
-      atomicAdd(&W[i3], kap * x0 * x1 * x2);
-    }
-    __syncwarp();
 
     const T lam_i = a.lam[i];
     const T e_eam_i = a.e_eam[i];

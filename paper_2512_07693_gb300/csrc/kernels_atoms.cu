@@ -38,7 +38,7 @@ __device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, dou
     float h[3], l[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const double w = wrap1(xs[k], a.geo.L[k], 1.0 / a.geo.L[k]);
+      const double w = wrap1(xs[k], a.geo.L[k], a.geo.invL[k]);
       h[k] = (float)w;
       l[k] = (float)(w - (double)h[k]);
     }
@@ -46,9 +46,9 @@ __device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, dou
     a.posl[i] = make_float4(l[0], l[1], l[2], 0.f);
   }
   double dx = x - a.pos_ref[3 * i], dy = y - a.pos_ref[3 * i + 1], dz = z - a.pos_ref[3 * i + 2];
-  dx -= a.geo.L[0] * rint(dx / a.geo.L[0]);
-  dy -= a.geo.L[1] * rint(dy / a.geo.L[1]);
-  dz -= a.geo.L[2] * rint(dz / a.geo.L[2]);
+  dx -= a.geo.L[0] * rint(dx * a.geo.invL[0]);
+  dy -= a.geo.L[1] * rint(dy * a.geo.invL[1]);
+  dz -= a.geo.L[2] * rint(dz * a.geo.invL[2]);
   if (dx * dx + dy * dy + dz * dz > a.skin_half2) atomicOr(&a.flags[0], 1);
 }
 
@@ -75,7 +75,7 @@ __global__ void k_bin(Args<T> a) {
   int c[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
-    c[k] = cell_of(wrap1(a.pos[3 * i + k], a.geo.L[k], 1.0 / a.geo.L[k]), a.geo.L[k], a.geo.nc[k]);
+    c[k] = cell_of(wrap1(a.pos[3 * i + k], a.geo.L[k], a.geo.invL[k]), a.geo.L[k], a.geo.nc[k]);
   const int cell = (c[2] * a.geo.nc[1] + c[1]) * a.geo.nc[0] + c[0];
   const int slot = atomicAdd(&a.cell_count[cell], 1);
   if (slot < a.cell_cap) {
@@ -110,7 +110,7 @@ __global__ void k_nbfill(Args<T> a) {
   int c[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
-    c[k] = cell_of(wrap1(a.pos[3 * i + k], a.geo.L[k], 1.0 / a.geo.L[k]), a.geo.L[k], a.geo.nc[k]);
+    c[k] = cell_of(wrap1(a.pos[3 * i + k], a.geo.L[k], a.geo.invL[k]), a.geo.L[k], a.geo.nc[k]);
   const auto si = a.pv.self(i);
   int cnt = 0;
   for (int dz = -1; dz <= 1; ++dz) {
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kBlock) k_pass1(Args<T> a) {
   if (i < a.n) {
     const auto si = a.pv.self(i);
     const T rc2 = T(a.eam.rc * a.eam.rc), rc = T(a.eam.rc), rlo = T(a.eam.rc_lo);
-    const T inv_w = T(1.0 / (a.eam.rc - a.eam.rc_lo));
+    const T inv_w = T(a.eam.inv_w);
     const T A = T(a.eam.A), beta = T(a.eam.beta), re = T(a.eam.re), D = T(a.eam.D),
             alpha = T(a.eam.alpha), r0 = T(a.eam.r0);
     Acc<T> zeta, pair;
@@ -281,9 +281,9 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
     const auto si = a.pv.self(i);
     const bool paper = a.lam_mode == APIP_LAM_PAPER;
     const T rw2 = T(a.sw.r_w * a.sw.r_w), rw = T(a.sw.r_w), rwlo = T(a.sw.r_w_lo);
-    const T rw_inv = T(1.0 / (a.sw.r_w - a.sw.r_w_lo));
+    const T rw_inv = T(a.sw.inv_w);
     const T rc2 = T(a.eam.rc * a.eam.rc), rc = T(a.eam.rc), rlo = T(a.eam.rc_lo);
-    const T inv_w = T(1.0 / (a.eam.rc - a.eam.rc_lo));
+    const T inv_w = T(a.eam.inv_w);
     const T A = T(a.eam.A), beta = T(a.eam.beta), re = T(a.eam.re), D = T(a.eam.D),
             alpha = T(a.eam.alpha), r0 = T(a.eam.r0);
     const T xi_i = a.xi_p[i];
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
     if (paper) {
       wb = wbar.value();
       dv = S.value() / wb - T(a.sw.d0);
-      lam = ftrans_c(dv, T(a.sw.d_lo), T(a.sw.d_hi), T(1.0 / (a.sw.d_hi - a.sw.d_lo)), &dl);
+      lam = ftrans_c(dv, T(a.sw.d_lo), T(a.sw.d_hi), T(a.sw.inv_d), &dl);
     } else {
       lam = a.lam_mode == APIP_LAM_CONST1 ? T(1) : T(0);
     }
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* 
     if (mode != 2) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        x[q] = wrap1(pos[3 * i + q] + dt * v[q], a.geo.L[q], 1.0 / a.geo.L[q]);
+        x[q] = wrap1(pos[3 * i + q] + dt * v[q], a.geo.L[q], a.geo.invL[q]);
         pos[3 * i + q] = x[q];
       }
       prep_atom(a, i, x[0], x[1], x[2]);
