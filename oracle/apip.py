@@ -8,6 +8,8 @@ Oracle: test infrastructure only.
 
 lam is the ACE weight (the paper's lambda is 1 - lam).  ``lam_mode``:
   "paper"  lam_i = 1 - f_trans(d_i, d_lo, d_hi) from the CSP descriptor (Eq. 2, 6)
+  "learned" the same switch with g_k = MLP(radial descriptors) (oracle/mlp.py,
+           weights in prm["mlp"])
   "const0" lam = 0 everywhere (pure EAM)
   "const1" lam = 1 everywhere (pure ACE)
 and ``lam_const`` (float array, NaN = follow Eq. 2) fixes lam on a subset
@@ -19,6 +21,7 @@ import math
 import numpy as np
 
 from . import ace as ace_mod
+from . import mlp
 from .csp import csp_g
 from .eam import eam_energies, eam_forces
 from .neighbors import pairs
@@ -39,8 +42,12 @@ def energy_forces(pos, box, ids, partners, prm, model=None, lam_mode="paper",
     i, j, rvec, r = pairs(pos, box, cutoff(prm))
     e_eam, zeta = eam_energies(n, i, j, r, prm["eam"])
     sw = prm["switch"]
+    rc_a, w_a = prm["ace"]["rc"], prm["ace"]["rc_width"]
     if lam_mode == "paper":
         g = csp_g(pos, box, ids, partners)
+        wbar, d, lam, dlam = descriptor(n, i, j, r, g, sw, lam_const)
+    elif lam_mode == "learned":
+        g, _, _ = mlp.learned_g(n, i, r, prm["mlp"], rc_a, w_a)
         wbar, d, lam, dlam = descriptor(n, i, j, r, g, sw, lam_const)
     else:
         val = {"const0": 0.0, "const1": 1.0}[lam_mode]
@@ -65,9 +72,13 @@ def energy_forces(pos, box, ids, partners, prm, model=None, lam_mode="paper",
         return out
     F += eam_forces(n, i, j, rvec, r, zeta, 1.0 - lam + beta * lam, prm["eam"])
     F += ace_f
-    if grad_lambda and lam_mode == "paper":
+    if grad_lambda and lam_mode in ("paper", "learned"):
         delta = e_prec - e_eam
+        g_force = None
+        if lam_mode == "learned":
+            def g_force(c):
+                return mlp.learned_force(n, i, j, rvec, r, prm["mlp"], c, rc_a, w_a)
         F += grad_lambda_force(n, i, j, rvec, r, g, d, wbar, dlam, delta, sw,
-                               pos, box, ids, partners)
+                               pos, box, ids, partners, g_force=g_force)
     out["F"] = F
     return out

@@ -47,9 +47,10 @@ def descriptor(n, i, j, r, g, p, lam_const=None):
     return wbar, d, lam, dlam
 
 
-def grad_lambda_force(n, i, j, rvec, r, g, d, wbar, dlam, delta, p, pos, box, ids, partners):
+def grad_lambda_force(n, i, j, rvec, r, g, d, wbar, dlam, delta, p, pos, box, ids, partners, g_force=None):
     """F^(grad lambda) = -grad sum_k lam_k Delta_k with Delta_k = E_k^ACE - E_k^EAM
-    held fixed (Eq. S15, written for lam = ACE weight).
+    held fixed (Eq. S15, written for lam = ACE weight).  ``g_force(c)`` returns
+    -grad sum_j c_j g_j for the atomic quantity in use (default: CSP^list).
 
     Chain rule through Eq. 6: with Et_k = Delta_k (dlam/dd)_k / wbar_k (Eq. S17 up
     to the sign convention of lam) and D_k = d_k + d0,
@@ -72,5 +73,5 @@ def grad_lambda_force(n, i, j, rvec, r, g, d, wbar, dlam, delta, p, pos, box, id
         F[:, comp] += np.bincount(kk, weights=f[:, comp], minlength=n)
         F[:, comp] -= np.bincount(jj, weights=f[:, comp], minlength=n)
     c = Et + np.bincount(jj, weights=Et[kk] * w(rr, p), minlength=n)
-    F += csp_force(pos, box, ids, partners, c)
+    F += csp_force(pos, box, ids, partners, c) if g_force is None else g_force(c)
     return F

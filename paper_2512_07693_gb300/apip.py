@@ -33,7 +33,7 @@ class ApipParams(ctypes.Structure):
         ("precision", _c_int32), ("lam_mode", _c_int32), ("grad_lambda", _c_int32), ("precise_adds_eam", _c_int32),
         ("eam_A", _c_double), ("eam_beta", _c_double), ("eam_re", _c_double), ("eam_D", _c_double),
         ("eam_alpha", _c_double), ("eam_r0", _c_double), ("eam_rc", _c_double), ("eam_rc_width", _c_double),
-        ("ace_n_max", _c_int32), ("ace_l_max", _c_int32), ("ace_nu_max", _c_int32), ("ace_pad", _c_int32),
+        ("ace_n_max", _c_int32), ("ace_l_max", _c_int32), ("ace_nu_max", _c_int32), ("ace_group", _c_int32),
         ("ace_rc", _c_double), ("ace_rc_width", _c_double), ("ace_eps", _c_double), ("ace_a_scale", _c_double),
         ("ace_c1", ctypes.POINTER(_c_double)), ("ace_c2", ctypes.POINTER(_c_double)), ("ace_n_basis", _c_int64),
         ("sw_r_w", _c_double), ("sw_r_w_width", _c_double), ("sw_d_lo", _c_double), ("sw_d_hi", _c_double),
@@ -180,7 +180,8 @@ def apip_reduce_energy_static(e_atom, n, e_total, stream=None):
 
 
 # ---------------------------------------------------------------- helpers
-def make_params(prm, precision="fp64", lam_mode="paper", grad_lambda=True, skin=0.5, max_nb=96, cell_cap=64):
+def make_params(prm, precision="fp64", lam_mode="paper", grad_lambda=True, skin=0.5, max_nb=96, cell_cap=64,
+                ace_group=0):
     """apip_params from a parameter dict (keys eam, ace, switch, csp,
     precise_adds_eam).  The returned structure keeps the coefficient arrays
     alive through its ``_keep`` attribute."""
@@ -197,6 +198,7 @@ def make_params(prm, precision="fp64", lam_mode="paper", grad_lambda=True, skin=
     p.eam_rc, p.eam_rc_width = e["rc"], e["rc_width"]
     p.ace_n_max, p.ace_l_max, p.ace_nu_max = a["n_max"], a["l_max"], a["nu_max"]
     p.ace_rc, p.ace_rc_width, p.ace_eps, p.ace_a_scale = a["rc"], a["rc_width"], a["eps"], a["a_scale"]
+    p.ace_group = int(ace_group)
     nb = apip_ace_basis_size(a["n_max"], a["l_max"], a["nu_max"])
     assert len(c1) >= nb and len(c2) >= nb
     c1, c2 = np.ascontiguousarray(c1[:nb]), np.ascontiguousarray(c2[:nb])

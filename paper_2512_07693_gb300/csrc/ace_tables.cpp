@@ -284,13 +284,45 @@ bool build_terms(int n_max, int l_max, int nu_max, const double* c1, const doubl
     add_d(i2, i0, i1, i3, c);
     add_d(i3, i0, i1, i2, c);
   }
-  out->keyd.clear(); out->kda.clear(); out->kdb.clear();
+  // Group the entries by target and hand whole targets to kAceAdjWarps warps,
+  // largest first to the least-loaded warp, so that each target is reduced by
+  // exactly one warp (no two warps write the same omega component).
+  std::vector<std::vector<std::pair<uint32_t, Coef>>> by_tgt(nA);
   for (const auto& kv : td) {
     if (kv.second.a == 0.0 && kv.second.b == 0.0) continue;
-    out->keyd.push_back(kv.first);
-    out->kda.push_back(kv.second.a);
-    out->kdb.push_back(kv.second.b);
+    by_tgt[kv.first >> 24].push_back(kv);
   }
+  std::vector<int> order(nA);
+  for (int t = 0; t < nA; ++t) order[t] = t;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return by_tgt[x].size() > by_tgt[y].size(); });
+  std::vector<std::vector<int>> bins(kAceAdjWarps);
+  std::vector<size_t> load(kAceAdjWarps, 0);
+  for (int t : order) {
+    if (by_tgt[t].empty()) continue;
+    const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    bins[b].push_back(t);
+    load[b] += by_tgt[t].size();
+  }
+  out->keyd.clear(); out->kda.clear(); out->kdb.clear(); out->sched.clear();
+  std::vector<int> triples;
+  out->sched.assign(kAceAdjWarps + 1, 0);
+  for (int b = 0; b < kAceAdjWarps; ++b) {
+    out->sched[b] = (int)(triples.size() / 3);
+    for (int t : bins[b]) {
+      const int start = (int)out->keyd.size();
+      for (const auto& kv : by_tgt[t]) {
+        out->keyd.push_back(kv.first);
+        out->kda.push_back(kv.second.a);
+        out->kdb.push_back(kv.second.b);
+      }
+      triples.push_back(t);
+      triples.push_back(start);
+      triples.push_back((int)out->keyd.size());
+    }
+  }
+  out->sched[kAceAdjWarps] = (int)(triples.size() / 3);
+  out->sched.insert(out->sched.end(), triples.begin(), triples.end());
   return true;
 }
 

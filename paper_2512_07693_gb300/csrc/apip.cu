@@ -76,7 +76,7 @@ void free_all(apip_ctx* c) {
   void* ptrs[] = {c->cell_count, c->cell_atoms, c->nnb, c->nbl, c->pos_ref, c->posh, c->posl, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->counts, c->flags, c->status, c->partials, c->thermo_part,
-                  c->e_scratch, c->key3, c->k3a, c->k3b, c->key4, c->k4a, c->k4b, c->keyd, c->kda, c->kdb};
+                  c->e_scratch, c->key3, c->k3a, c->k3b, c->key4, c->k4a, c->k4b, c->keyd, c->kda, c->kdb, c->sched};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -89,6 +89,7 @@ apip_status check_params(const apip_params* p, std::string* why) {
   if (p->ace_l_max < 0 || p->ace_l_max > kLmaxCap) return bad("ace_l_max must be in [0, 4]");
   if (p->ace_nu_max < 1 || p->ace_nu_max > 4) return bad("ace_nu_max must be in [1, 4]");
   if (p->ace_n_max * (p->ace_l_max + 1) * (p->ace_l_max + 1) > 254) return bad("n_max (l_max+1)^2 must be <= 254");
+  if (p->ace_group != 0 && p->ace_group != 1 && p->ace_group != 8) return bad("ace_group must be 0, 1 or 8");
   if (!p->ace_c1 || !p->ace_c2) return bad("ace_c1 / ace_c2 must not be NULL");
   if (!(p->ace_rc > 0 && p->ace_rc_width > 0 && p->ace_rc_width <= p->ace_rc)) return bad("bad ACE cutoff");
   if (!(p->ace_eps > 0)) return bad("ace_eps must be > 0");
@@ -214,6 +215,8 @@ AceDev<T> ace_dev(apip_ctx* c) {
   t.key3 = c->key3; t.k3a = as<T>(c->k3a); t.k3b = as<T>(c->k3b); t.n3 = c->n3;
   t.key4 = c->key4; t.k4a = as<T>(c->k4a); t.k4b = as<T>(c->k4b); t.n4 = c->n4;
   t.keyd = c->keyd; t.kda = as<T>(c->kda); t.kdb = as<T>(c->kdb); t.nd = c->nd;
+  t.sched = c->sched;
+  t.group = p.ace_group != 0 ? p.ace_group : (p.lam_mode == APIP_LAM_PAPER ? 1 : 8);
   return t;
 }
 
@@ -251,7 +254,7 @@ apip_status energy_forces_t(apip_ctx* c, const double* pos, const int32_t* id, i
   { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_prep<T>(a, s); }
   force_pipeline<T>(c, a, s);
   Phase ph(c, APIP_PHASE_REDUCE, 1, s);
-  launch_final(c->partials, a.n_part_p1 + c->ace_blocks * kAceWarps, e_total, nullptr, nullptr, 0, nullptr,
+  launch_final(c->partials, a.n_part_p1 + c->ace_blocks, e_total, nullptr, nullptr, 0, nullptr,
                c->flags, c->counts, nullptr, s);
   return launch_status(c);
 }
@@ -289,7 +292,7 @@ apip_status verlet_t(apip_ctx* c, double* pos, double* vel, double* force, const
   Args<T> a = make_args<T>(c, pos, id, n, force, nullptr);
   set_view<T>(a, c);
   const int ntb = nblk(n);
-  const int n_part = a.n_part_p1 + c->ace_blocks * kAceWarps;
+  const int n_part = a.n_part_p1 + c->ace_blocks;
   for (int k = 0; k < steps; ++k) {
     { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, k == 0 ? 0 : 1, pos, vel, force, inv_mass, dt, c->thermo_part, s); }
     force_pipeline<T>(c, a, s);
@@ -373,7 +376,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->flags, sizeof(int) * 4);
   APIP_ALLOC(ctx->status, sizeof(int) * ST_COUNT);
   const int p1 = nblk(n_atoms_max);
-  APIP_ALLOC(ctx->partials, sizeof(double) * (p1 + ctx->ace_blocks * kAceWarps));
+  APIP_ALLOC(ctx->partials, sizeof(double) * (p1 + ctx->ace_blocks));
   APIP_ALLOC(ctx->thermo_part, sizeof(double) * 4 * p1);
   APIP_ALLOC(ctx->e_scratch, sizeof(double) * 2);
   ctx->n3 = (int)terms.key3.size();
@@ -388,6 +391,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->keyd, sizeof(uint32_t) * std::max(1, ctx->nd));
   APIP_ALLOC(ctx->kda, es * std::max(1, ctx->nd));
   APIP_ALLOC(ctx->kdb, es * std::max(1, ctx->nd));
+  APIP_ALLOC(ctx->sched, sizeof(int) * terms.sched.size());
 #undef APIP_ALLOC
   auto upload = [&](void* dst, const std::vector<double>& v) -> cudaError_t {
     if (v.empty()) return cudaSuccess;
@@ -403,6 +407,8 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
     e = cudaMemcpy(ctx->keyd, terms.keyd.data(), sizeof(uint32_t) * ctx->nd, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = upload(ctx->kda, terms.kda);
   if (e == cudaSuccess) e = upload(ctx->kdb, terms.kdb);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->sched, terms.sched.data(), sizeof(int) * terms.sched.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = upload(ctx->k3a, terms.k3a);
   if (e == cudaSuccess) e = upload(ctx->k3b, terms.k3b);
   if (e == cudaSuccess) e = upload(ctx->k4a, terms.k4a);

@@ -16,7 +16,8 @@ constexpr int kNmaxCap = 8;    // largest n_max
 constexpr int kLmaxCap = 4;    // largest l_max
 constexpr int kCspCap = 8;     // largest csp_nnb
 constexpr int kBlock = 256;    // threads per block of the all-atom passes
-constexpr int kAceWarps = 4;   // warps (= atoms in flight) per ACE block
+constexpr int kAceAdjWarps = 8;            // warps per ACE block
+constexpr int kAceThreads = 32 * kAceAdjWarps;
 
 // Device status words (apip_ctx::status)
 enum {
@@ -50,12 +51,18 @@ struct AceDev {
   T rc, rc_lo, eps, sqrt_eps, a_scale;
   const uint32_t* key3; const T* k3a; const T* k3b; int n3;   // 3-index terms
   const uint32_t* key4; const T* k4a; const T* k4b; int n4;   // 4-index terms
-  const uint32_t* keyd; const T* kda; const T* kdb; int nd;   // derivative entries, sorted by target
+  const uint32_t* keyd; const T* kda; const T* kdb; int nd;   // derivative entries, grouped by target
+  const int* sched;             // adjoint schedule (HostTerms::sched)
+  int group;                    // compacted atoms per thread block (1 or 8)
 };
 
 struct HostTerms {
   std::vector<uint32_t> key3, key4, keyd;
   std::vector<double> k3a, k3b, k4a, k4b, kda, kdb;
+  // adjoint schedule: sched[w], w = 0..kAceAdjWarps, are offsets (in triples) of
+  // warp w's targets; triples (target, start, end) into keyd follow at
+  // sched[kAceAdjWarps + 1 + 3 * t]
+  std::vector<int> sched;
 };
 
 // ace_tables.cpp
@@ -120,4 +127,5 @@ struct apip_ctx {
   uint32_t* key3 = nullptr; void* k3a = nullptr; void* k3b = nullptr; int n3 = 0;
   uint32_t* key4 = nullptr; void* k4a = nullptr; void* k4b = nullptr; int n4 = 0;
   uint32_t* keyd = nullptr; void* kda = nullptr; void* kdb = nullptr; int nd = 0;
+  int* sched = nullptr;
 };

@@ -41,6 +41,22 @@ def ace_params(n_max, l_max, nu_max, seed, n_basis, a_scale=0.25):
                 eps=1e-2, a_scale=a_scale, c1=c[:, 0].copy(), c2=c[:, 1].copy())
 
 
+def mlp_params(seed, n_in=32, width=64):
+    """Seeded initial weights of the 32 -> 64 -> 64 -> 64 -> 1 indicator network:
+    uniform on [-1/sqrt(fan_in), 1/sqrt(fan_in)] (float64; keys W1 b1 W2 b2 W3 b3 w4 b4)."""
+    rng = np.random.default_rng(seed)
+
+    def lin(fan_out, fan_in):
+        b = 1.0 / np.sqrt(fan_in)
+        return rng.uniform(-b, b, (fan_out, fan_in)), rng.uniform(-b, b, fan_out)
+
+    W1, b1 = lin(width, n_in)
+    W2, b2 = lin(width, width)
+    W3, b3 = lin(width, width)
+    w4, b4 = lin(1, width)
+    return dict(W1=W1, b1=b1, W2=W2, b2=b2, W3=W3, b3=b3, w4=w4[0].copy(), b4=float(b4[0]))
+
+
 def bcc(nx, ny, nz, a=LATTICE_A):
     """Perfect bcc lattice, two atoms per cubic cell, x fastest within a cell row."""
     g = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz),

@@ -20,12 +20,13 @@ def to_dev(torch, s):
                 inv_mass=torch.tensor(1.0 / (s["mass"] * 1.0364269e-4), dtype=torch.float64, device=dev))
 
 
-def run_gpu(s, precision="fp64", lam_mode="paper", grad_lambda=True, max_nb=96, fields=True, prm=None):
+def run_gpu(s, precision="fp64", lam_mode="paper", grad_lambda=True, max_nb=96, fields=True, prm=None, ace_group=0):
     torch = torch_cuda()
     from paper_2512_07693_gb300 import apip
     prm = prm or s["prm"]
     n = len(s["pos"])
-    m = apip.Apip(prm, n, precision=precision, lam_mode=lam_mode, grad_lambda=grad_lambda, max_nb=max_nb)
+    m = apip.Apip(prm, n, precision=precision, lam_mode=lam_mode, grad_lambda=grad_lambda, max_nb=max_nb,
+                  ace_group=ace_group)
     t = to_dev(torch, s)
     box = [float(x) for x in s["box"]]
     if lam_mode == "paper":

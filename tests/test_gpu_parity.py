@@ -67,10 +67,11 @@ def _check(s, prec="fp64", **kw):
     return g, o
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_mixed_system_parity(prec):
+@pytest.mark.parametrize("prec,group", [("fp64", 0), ("fp32", 0), ("fp64", 8), ("fp32", 8)])
+def test_mixed_system_parity(prec, group):
+    """group = compacted atoms per ACE thread block (0: automatic, 1 here)."""
     s = small()
-    g, o = _check(s, prec)
+    g, o = _check(s, prec, ace_group=group)
     # every regime is exercised
     assert np.any(o["lam"] == 1.0) and np.any(o["lam"] == 0.0) and np.count_nonzero(o["dlam"]) > 10
 
