@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ace-steps", type=int, default=5, help="steps of the all-ACE comparison run")
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--ace-group", type=int, default=0, choices=[0, 1, 8],
+                    help="compacted atoms per ACE thread block (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -152,11 +154,14 @@ def clocks_stop(handle, gpu_index):
 
 
 # ---------------------------------------------------------------------- ours
+ACE_GROUP = 0
+
+
 def setup(torch, prm, s, lam_mode, precision="fp32"):
     from paper_2512_07693_gb300 import apip
     n = len(s["pos"])
     dev = torch.device("cuda")
-    m = apip.Apip(prm, n, precision=precision, lam_mode=lam_mode, max_nb=80, cell_cap=48)
+    m = apip.Apip(prm, n, precision=precision, lam_mode=lam_mode, max_nb=80, cell_cap=48, ace_group=ACE_GROUP)
     t = dict(pos=torch.tensor(s["pos"], dtype=torch.float64, device=dev),
              vel=torch.tensor(s["vel"], dtype=torch.float64, device=dev),
              ids=torch.tensor(s["ids"], dtype=torch.int32, device=dev),
@@ -202,6 +207,8 @@ def ace_flops_per_atom(s, nnb_rc):
 def run_ours(args):
     import numpy as np
     import torch
+    global ACE_GROUP
+    ACE_GROUP = args.ace_group
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist

@@ -59,8 +59,23 @@ enum { APIP_FP64 = 0, APIP_FP32 = 1 };
  * APIP_LAM_PAPER : lam_i = 1 - f_trans(d_i, d_lo, d_hi), d_i the locally averaged
  *                  CSP^list descriptor (Eq. 2, Eq. 6, Eq. B3).
  * APIP_LAM_CONST0: lam = 0 for all atoms (pure fast model).
- * APIP_LAM_CONST1: lam = 1 for all atoms (pure precise model). */
-enum { APIP_LAM_PAPER = 0, APIP_LAM_CONST0 = 1, APIP_LAM_CONST1 = 2 };
+ * APIP_LAM_CONST1: lam = 1 for all atoms (pure precise model).
+ * APIP_LAM_LEARNED: the paper's switch (Eq. 2, Eq. 6) with the atomic quantity g_k
+ *                  given by a small MLP on radial descriptors instead of CSP^list
+ *                  (any differentiable, distance-only g_k is allowed by the paper,
+ *                  main text after Eq. 5); weights from apip_set_mlp. */
+enum { APIP_LAM_PAPER = 0, APIP_LAM_CONST0 = 1, APIP_LAM_CONST1 = 2, APIP_LAM_LEARNED = 3 };
+
+/* Learned indicator network: radial descriptors
+ *   G_im = sum_{j, r_ij < ace_rc} exp(-eta (r_ij - mu_m)^2) fc(r_ij),  m = 0..31,
+ *   mu_m = 1.5 + m (5.0 - 1.5)/31 A, eta = 1/(2 * 0.15^2) A^-2, fc the ACE cutoff function,
+ * then g = w4 . h3 + b4 with h_k = silu(W_k h_{k-1} + b_k), h_0 = 0.25 G, widths
+ * 32 -> 64 -> 64 -> 64 -> 1, silu(x) = x / (1 + exp(-x)).  Parameters are one flat
+ * float32 array of APIP_MLP_NPARAM values in the order W1 [64][32], b1 [64],
+ * W2 [64][64], b2 [64], W3 [64][64], b3 [64], w4 [64], b4 [1] (row-major). */
+#define APIP_MLP_IN 32
+#define APIP_MLP_WIDTH 64
+#define APIP_MLP_NPARAM 10497
 
 /* Model and run parameters; copied by apip_create.  Field order is ABI. */
 typedef struct apip_params {
@@ -79,7 +94,9 @@ typedef struct apip_params {
      real Y_lm, A_nlm = a_scale sum_j R_n Y_lm, canonical product basis of body
      order <= nu_max, E = c1.B + (( c2.B )^2 + eps^2)^(1/4) - sqrt(eps).
      n_max in [1, 8], l_max in [0, 4], nu_max in [1, 4], n_max (l_max+1)^2 <= 254. */
-  int32_t ace_n_max, ace_l_max, ace_nu_max, ace_pad;
+  int32_t ace_n_max, ace_l_max, ace_nu_max;
+  int32_t ace_group;         /* compacted atoms per ACE thread block: 0 = automatic (1 for the
+                                paper's switch, 8 for constant lam), or 1 or 8 */
   double ace_rc, ace_rc_width, ace_eps, ace_a_scale;
   const double* ace_c1;      /* host, ace_n_basis entries (copied) */
   const double* ace_c2;      /* host, ace_n_basis entries (copied) */
@@ -185,6 +202,28 @@ enum {
 };
 apip_status apip_profile(apip_ctx* ctx, int32_t enable);
 apip_status apip_profile_read(apip_ctx* ctx, double* ms, int64_t* launches);
+
+/* Learned indicator (workload row: MLP on radial descriptors trained on per-atom
+ * |E^prec - E^EAM|; no counterpart in the paper beyond its allowance of any
+ * differentiable distance-only g_k).
+ *
+ * apip_set_mlp: copy the network parameters (device, float32, APIP_MLP_NPARAM)
+ *   into the context; required before APIP_LAM_LEARNED calls (APIP_ERR_STATE otherwise).
+ * apip_descriptors: the 32 radial descriptors of every atom as bfloat16 (round to
+ *   nearest even), desc_bf16 device [n][32] (training inputs).
+ * apip_mlp_loss_grad: for a batch of descriptors (bfloat16 [batch][32]) and labels
+ *   y (float32 [batch]): *loss_out = mean (g - y)^2 and grad_out[APIP_MLP_NPARAM]
+ *   its gradient with respect to params (all device, float32 accumulation).  The
+ *   context keeps a workspace of 1.5 KiB per sample, grown on demand.
+ * apip_mlp_adam: one Adam update (beta1 0.9, beta2 0.999, eps 1e-8, bias
+ *   corrected, step t >= 1) of params with grad; m and v are the moment arrays. */
+apip_status apip_set_mlp(apip_ctx* ctx, const float* params, void* stream);
+apip_status apip_descriptors(apip_ctx* ctx, const double* pos, const double box[3], const int32_t* id,
+                             int64_t n, uint16_t* desc_bf16, void* stream);
+apip_status apip_mlp_loss_grad(apip_ctx* ctx, const uint16_t* desc_bf16, const float* y, int64_t batch,
+                               const float* params, float* grad_out, float* loss_out, void* stream);
+apip_status apip_mlp_adam(apip_ctx* ctx, float* params, const float* grad, float* m, float* v, int32_t t,
+                          float lr, void* stream);
 
 /* Allocation-free total energy.  The paper has no counterpart: this is a service
  * for callers that cannot call cudaMalloc, such as a host program whose device

@@ -19,7 +19,12 @@ STATUS_NAMES = {0: "APIP_OK", 1: "APIP_ERR_ARG", 2: "APIP_ERR_CUDA", 3: "APIP_ER
                 4: "APIP_ERR_BAD_INPUT", 5: "APIP_ERR_STATE", 6: "APIP_ERR_SIZE"}
 APIP_STATIC_MAX_ATOMS = 4096 * 4096
 APIP_FP64, APIP_FP32 = 0, 1
-APIP_LAM_PAPER, APIP_LAM_CONST0, APIP_LAM_CONST1 = 0, 1, 2
+APIP_LAM_PAPER, APIP_LAM_CONST0, APIP_LAM_CONST1, APIP_LAM_LEARNED = 0, 1, 2, 3
+LAM_MODES = {"paper": APIP_LAM_PAPER, "const0": APIP_LAM_CONST0, "const1": APIP_LAM_CONST1,
+             "learned": APIP_LAM_LEARNED}
+APIP_MLP_NPARAM = 10497
+MLP_LAYOUT = (("W1", (64, 32)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (64, 64)), ("b3", (64,)),
+              ("w4", (64,)), ("b4", ()))
 PHASES = ("prep", "neighbor", "pass1", "pass2", "ace", "csp", "reduce")
 FIELDS = dict(g=0, d=1, wbar=2, lam=3, dlam=4, e_eam=5, e_ace=6, zeta=7, ace_list=8, nnb=9, nblist=10, csp=11)
 MVV2E = 1.0364269e-4   # amu A^2 / ps^2 -> eV
@@ -64,6 +69,10 @@ def _load():
         "apip_profile": (ctypes.c_int, [_vp, _c_int32]),
         "apip_profile_read": (ctypes.c_int, [_vp, P(_c_double), P(_c_int64)]),
         "apip_reduce_energy_static": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
+        "apip_set_mlp": (ctypes.c_int, [_vp, _vp, _vp]),
+        "apip_descriptors": (ctypes.c_int, [_vp, _vp, P(_c_double), _vp, _c_int64, _vp, _vp]),
+        "apip_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, _c_int64, _vp, _vp, _vp, _vp]),
+        "apip_mlp_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _c_int32, ctypes.c_float, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -179,6 +188,43 @@ def apip_reduce_energy_static(e_atom, n, e_total, stream=None):
         raise ApipError(st, why)
 
 
+def apip_set_mlp(ctx, params, stream=None):
+    _check(ctx, lib.apip_set_mlp(ctx, _ptr(params), _stream(stream)))
+
+
+def apip_descriptors(ctx, pos, box, id, n, desc_bf16, stream=None):
+    _check(ctx, lib.apip_descriptors(ctx, _ptr(pos), _box(box), _ptr(id), int(n), _ptr(desc_bf16), _stream(stream)))
+
+
+def apip_mlp_loss_grad(ctx, desc_bf16, y, batch, params, grad_out, loss_out, stream=None):
+    _check(ctx, lib.apip_mlp_loss_grad(ctx, _ptr(desc_bf16), _ptr(y), int(batch), _ptr(params), _ptr(grad_out),
+                                       _ptr(loss_out), _stream(stream)))
+
+
+def apip_mlp_adam(ctx, params, grad, m, v, t, lr, stream=None):
+    _check(ctx, lib.apip_mlp_adam(ctx, _ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(t), float(lr),
+                                  _stream(stream)))
+
+
+def mlp_flat(weights):
+    """Flat float32 parameter vector (apip.h layout) from a dict of arrays."""
+    parts = [np.asarray(weights[k], dtype=np.float32).reshape(-1) for k, _ in MLP_LAYOUT]
+    out = np.concatenate(parts)
+    assert out.size == APIP_MLP_NPARAM
+    return out
+
+
+def mlp_unflat(flat):
+    """Inverse of mlp_flat (float64 arrays; b4 a float)."""
+    flat = np.asarray(flat, dtype=np.float64).reshape(-1)
+    out, k = {}, 0
+    for name, shape in MLP_LAYOUT:
+        size = int(np.prod(shape)) if shape else 1
+        out[name] = flat[k:k + size].reshape(shape) if shape else float(flat[k])
+        k += size
+    return out
+
+
 # ---------------------------------------------------------------- helpers
 def make_params(prm, precision="fp64", lam_mode="paper", grad_lambda=True, skin=0.5, max_nb=96, cell_cap=64,
                 ace_group=0):
@@ -190,7 +236,7 @@ def make_params(prm, precision="fp64", lam_mode="paper", grad_lambda=True, skin=
     c2 = np.ascontiguousarray(a["c2"], dtype=np.float64)
     p = ApipParams()
     p.precision = {"fp64": APIP_FP64, "fp32": APIP_FP32}[precision]
-    p.lam_mode = {"paper": APIP_LAM_PAPER, "const0": APIP_LAM_CONST0, "const1": APIP_LAM_CONST1}[lam_mode]
+    p.lam_mode = LAM_MODES[lam_mode]
     p.grad_lambda = int(bool(grad_lambda))
     p.precise_adds_eam = int(bool(prm.get("precise_adds_eam", False)))
     p.eam_A, p.eam_beta, p.eam_re = e["A"], e["beta"], e["r_e"]
@@ -252,6 +298,12 @@ class Apip:
 
     def sync(self, stream=None):
         apip_sync(self.ctx, stream)
+
+    def set_mlp(self, params, stream=None):
+        apip_set_mlp(self.ctx, params, stream)
+
+    def descriptors(self, pos, box, ids, desc_bf16, stream=None):
+        apip_descriptors(self.ctx, pos, box, ids, pos.shape[0], desc_bf16, stream)
 
     def field(self, name, n):
         """Copy an internal per-atom array into a new torch tensor."""

@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
       Acc<T> f1[KA], f2[KA];
       const int per3 = (t.n3 + kAceAdjWarps - 1) / kAceAdjWarps;
       const int e3 = min(t.n3, (warp + 1) * per3);
+#pragma unroll 4
       for (int q = warp * per3 + lane; q < e3; q += 32) {
         const uint32_t key = t.key3[q];
         const T K1 = t.k3a[q], K2 = t.k3b[q];
@@ -220,6 +221,7 @@ __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
       }
       const int per4 = (t.n4 + kAceAdjWarps - 1) / kAceAdjWarps;
       const int e4 = min(t.n4, (warp + 1) * per4);
+#pragma unroll 4
       for (int q = warp * per4 + lane; q < e4; q += 32) {
         const uint32_t key = t.key4[q];
         const T K1 = t.k4a[q], K2 = t.k4b[q];
@@ -262,7 +264,8 @@ __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
         const T e_eam = a.e_eam[i];
         delta = e_ace + (a.precise_adds_eam ? e_eam : T(0)) - e_eam;
         const T dl = a.dlam[i];
-        trans = (a.grad_lambda && a.lam_mode == APIP_LAM_PAPER && dl != T(0)) ? 1 : 0;
+        trans = (a.grad_lambda && (a.lam_mode == APIP_LAM_PAPER || a.lam_mode == APIP_LAM_LEARNED) &&
+                 dl != T(0)) ? 1 : 0;
         et = trans ? delta * dl / a.wbar[i] : T(0);
         D = a.dd[i] + T(a.sw.d0);
         xi = a.xi_p[i];
@@ -286,6 +289,7 @@ __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
         T acc[KA];
 #pragma unroll
         for (int k = 0; k < KA; ++k) acc[k] = T(0);
+#pragma unroll 4
         for (int q = st + lane; q < en; q += 32) {
           const uint32_t key = t.keyd[q];
           const T K1 = t.kda[q], K2 = t.kdb[q];

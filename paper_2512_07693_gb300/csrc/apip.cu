@@ -73,10 +73,10 @@ void free_all(apip_ctx* c) {
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   c->prof_pending.clear();
   c->prof_pool.clear();
-  void* ptrs[] = {c->cell_count, c->cell_atoms, c->nnb, c->nbl, c->pos_ref, c->posh, c->posl, c->id2idx,
+  void* ptrs[] = {c->cell_count, c->cell_atoms, c->nnb, c->nbl, c->pos_ref, c->posq, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->counts, c->flags, c->status, c->partials, c->thermo_part,
-                  c->e_scratch, c->key3, c->k3a, c->k3b, c->key4, c->k4a, c->k4b, c->keyd, c->kda, c->kdb, c->sched};
+                  c->e_scratch, c->key3, c->k3a, c->k3b, c->key4, c->k4a, c->k4b, c->keyd, c->kda, c->kdb, c->sched, c->mlp_w, c->mlp_ws};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -84,7 +84,7 @@ void free_all(apip_ctx* c) {
 apip_status check_params(const apip_params* p, std::string* why) {
   auto bad = [&](const char* m) { *why = m; return APIP_ERR_ARG; };
   if (p->precision != APIP_FP64 && p->precision != APIP_FP32) return bad("precision must be APIP_FP64 or APIP_FP32");
-  if (p->lam_mode < APIP_LAM_PAPER || p->lam_mode > APIP_LAM_CONST1) return bad("unknown lam_mode");
+  if (p->lam_mode < APIP_LAM_PAPER || p->lam_mode > APIP_LAM_LEARNED) return bad("unknown lam_mode");
   if (p->ace_n_max < 1 || p->ace_n_max > kNmaxCap) return bad("ace_n_max must be in [1, 8]");
   if (p->ace_l_max < 0 || p->ace_l_max > kLmaxCap) return bad("ace_l_max must be in [0, 4]");
   if (p->ace_nu_max < 1 || p->ace_nu_max > 4) return bad("ace_nu_max must be in [1, 4]");
@@ -121,8 +121,8 @@ apip_status set_geometry(apip_ctx* ctx, const double* box, cudaStream_t s) {
       return fail(ctx, APIP_ERR_ARG, "each box edge must be >= 3 * (cutoff + skin) = " + std::to_string(3 * ctx->r_list));
     g.cs[k] = box[k] / g.nc[k];
     g.invL[k] = 1.0 / box[k];
-    g.Lh[k] = (float)box[k];
-    g.Ll[k] = (float)(box[k] - (double)g.Lh[k]);
+    g.inv_unit[k] = 4294967296.0 / box[k];
+    g.unit[k] = (float)(box[k] / 4294967296.0);
     ncell *= g.nc[k];
   }
   if (ncell > ctx->ncell_alloc) {
@@ -168,7 +168,7 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.csp_rcut2 = p.csp_rcut * p.csp_rcut;
   a.pos = pos;
   a.id = id;
-  a.nnb = c->nnb; a.nbl = c->nbl; a.pos_ref = c->pos_ref; a.posh = c->posh; a.posl = c->posl;
+  a.nnb = c->nnb; a.nbl = c->nbl; a.pos_ref = c->pos_ref; a.posq = c->posq;
   a.id2idx = c->id2idx; a.csp = c->csp; a.cell_count = c->cell_count; a.cell_atoms = c->cell_atoms;
   a.zeta = as<T>(c->zeta); a.xi_p = as<T>(c->xi_p); a.e_eam = as<T>(c->e_eam); a.g = as<T>(c->g);
   a.wbar = as<T>(c->wbar); a.dd = as<T>(c->dd); a.lam = as<T>(c->lam); a.dlam = as<T>(c->dlam);
@@ -178,6 +178,9 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.n_part_p1 = nblk(n);
   a.force = force;
   a.e_atom = e_atom;
+  a.mlp_w = as<T>(c->mlp_w);
+  a.ace_rc = T(p.ace_rc);
+  a.ace_rc_lo = T(p.ace_rc - p.ace_rc_width);
   return a;
 }
 
@@ -191,13 +194,8 @@ template <> void set_view<double>(Args<double>& a, apip_ctx* c) {
   for (int k = 0; k < 3; ++k) { a.pv.L[k] = c->geo.L[k]; a.pv.invL[k] = 1.0 / c->geo.L[k]; }
 }
 template <> void set_view<float>(Args<float>& a, apip_ctx* c) {
-  a.pv.hi = c->posh;
-  a.pv.lo = c->posl;
-  for (int k = 0; k < 3; ++k) {
-    a.pv.Lh[k] = c->geo.Lh[k];
-    a.pv.Ll[k] = c->geo.Ll[k];
-    a.pv.half[k] = (float)(0.5 * c->geo.L[k]);
-  }
+  a.pv.q = c->posq;
+  for (int k = 0; k < 3; ++k) a.pv.unit[k] = c->geo.unit[k];
 }
 
 template <typename T>
@@ -216,7 +214,8 @@ AceDev<T> ace_dev(apip_ctx* c) {
   t.key4 = c->key4; t.k4a = as<T>(c->k4a); t.k4b = as<T>(c->k4b); t.n4 = c->n4;
   t.keyd = c->keyd; t.kda = as<T>(c->kda); t.kdb = as<T>(c->kdb); t.nd = c->nd;
   t.sched = c->sched;
-  t.group = p.ace_group != 0 ? p.ace_group : (p.lam_mode == APIP_LAM_PAPER ? 1 : 8);
+  t.group = p.ace_group != 0 ? p.ace_group
+                             : ((p.lam_mode == APIP_LAM_PAPER || p.lam_mode == APIP_LAM_LEARNED) ? 1 : 8);
   return t;
 }
 
@@ -227,22 +226,41 @@ apip_status check_call(apip_ctx* ctx, const double* pos, const int32_t* id, int6
   return APIP_OK;
 }
 
+// Call-order state: the switch needs its inputs set up first.
+apip_status ready(apip_ctx* ctx) {
+  if (ctx->p.lam_mode == APIP_LAM_PAPER && !ctx->csp_ready)
+    return fail(ctx, APIP_ERR_STATE, "apip_init_csp_pairs must be called before the paper's switch is used");
+  if (ctx->p.lam_mode == APIP_LAM_LEARNED && !ctx->mlp_ready)
+    return fail(ctx, APIP_ERR_STATE, "apip_set_mlp must be called before the learned switch is used");
+  return APIP_OK;
+}
+
 apip_status launch_status(apip_ctx* ctx) {
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, APIP_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return APIP_OK;
 }
 
+// Pass 1 for the switch in use: CSP^list g, or the learned g = MLP(G).
+template <typename T>
+void pass1(const Args<T>& a, cudaStream_t s) {
+  if (a.lam_mode == APIP_LAM_LEARNED) launch_pass1_learned<T>(a, s);
+  else launch_pass1<T>(a, s);
+}
+
 // The force pipeline after prep (or after the drift of a Verlet step).
 template <typename T>
 void force_pipeline(apip_ctx* c, Args<T>& a, cudaStream_t s) {
   { Phase ph(c, APIP_PHASE_NEIGHBOR, 4, s); launch_neighbors<T>(a, c->ncell, s); }
-  { Phase ph(c, APIP_PHASE_PASS1, 1, s); launch_pass1<T>(a, s); }
+  { Phase ph(c, APIP_PHASE_PASS1, 1, s); pass1<T>(a, s); }
   { Phase ph(c, APIP_PHASE_PASS2, 1, s); launch_pass2<T>(a, s); }
   { Phase ph(c, APIP_PHASE_ACE, 1, s); launch_ace<T>(a, ace_dev<T>(c), c->ace_blocks, s); }
   if (a.lam_mode == APIP_LAM_PAPER && a.grad_lambda) {
     Phase ph(c, APIP_PHASE_CSP, 1, s);
     launch_csp_force<T>(a, s);
+  } else if (a.lam_mode == APIP_LAM_LEARNED && a.grad_lambda) {
+    Phase ph(c, APIP_PHASE_CSP, 1, s);
+    launch_mlp_force<T>(a, s);
   }
 }
 
@@ -267,7 +285,7 @@ apip_status switch_t(apip_ctx* c, const double* pos, const int32_t* id, int n, d
   a.eam_force = 0;
   launch_prep<T>(a, s);
   launch_neighbors<T>(a, c->ncell, s);
-  launch_pass1<T>(a, s);
+  pass1<T>(a, s);
   launch_pass2<T>(a, s);
   if (lam_out) launch_get_field<T>(a, APIP_FIELD_LAM, lam_out, s);
   if (dlam_out) launch_get_field<T>(a, APIP_FIELD_DLAM, dlam_out, s);
@@ -363,8 +381,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->nbl, sizeof(int) * N * p->max_nb);
   APIP_ALLOC(ctx->pos_ref, sizeof(double) * 3 * N);
   if (p->precision == APIP_FP32) {
-    APIP_ALLOC(ctx->posh, sizeof(float4) * N);
-    APIP_ALLOC(ctx->posl, sizeof(float4) * N);
+    APIP_ALLOC(ctx->posq, sizeof(uint4) * N);
   }
   APIP_ALLOC(ctx->id2idx, sizeof(int) * N);
   APIP_ALLOC(ctx->csp, sizeof(int) * N * kCspCap);
@@ -379,6 +396,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->partials, sizeof(double) * (p1 + ctx->ace_blocks));
   APIP_ALLOC(ctx->thermo_part, sizeof(double) * 4 * p1);
   APIP_ALLOC(ctx->e_scratch, sizeof(double) * 2);
+  APIP_ALLOC(ctx->mlp_w, es * APIP_MLP_NPARAM);
   ctx->n3 = (int)terms.key3.size();
   ctx->n4 = (int)terms.key4.size();
   ctx->nd = (int)terms.keyd.size();
@@ -473,8 +491,7 @@ apip_status apip_switch(apip_ctx* ctx, const double* pos, const double box[3], c
   if (st != APIP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = set_geometry(ctx, box, s)) != APIP_OK) return st;
-  if (ctx->p.lam_mode == APIP_LAM_PAPER && !ctx->csp_ready)
-    return fail(ctx, APIP_ERR_STATE, "apip_init_csp_pairs must be called before the paper's switch is used");
+  if ((st = ready(ctx)) != APIP_OK) return st;
   if (n == 0) {
     if (n_ace_out) cudaMemsetAsync(n_ace_out, 0, sizeof(int64_t), s);
     return launch_status(ctx);
@@ -492,8 +509,7 @@ apip_status apip_energy_forces(apip_ctx* ctx, const double* pos, const double bo
   if (n > 0 && !force_out) return fail(ctx, APIP_ERR_ARG, "force_out must not be NULL");
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = set_geometry(ctx, box, s)) != APIP_OK) return st;
-  if (ctx->p.lam_mode == APIP_LAM_PAPER && !ctx->csp_ready)
-    return fail(ctx, APIP_ERR_STATE, "apip_init_csp_pairs must be called before the paper's switch is used");
+  if ((st = ready(ctx)) != APIP_OK) return st;
   if (n == 0) {
     if (e_total_out) cudaMemsetAsync(e_total_out, 0, sizeof(double), s);
     return launch_status(ctx);
@@ -513,8 +529,7 @@ apip_status apip_verlet_step(apip_ctx* ctx, double* pos, double* vel, double* fo
   if (n_steps < 0 || !std::isfinite(dt)) return fail(ctx, APIP_ERR_ARG, "n_steps must be >= 0 and dt finite");
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = set_geometry(ctx, box, s)) != APIP_OK) return st;
-  if (ctx->p.lam_mode == APIP_LAM_PAPER && !ctx->csp_ready)
-    return fail(ctx, APIP_ERR_STATE, "apip_init_csp_pairs must be called before the paper's switch is used");
+  if ((st = ready(ctx)) != APIP_OK) return st;
   if (n == 0 || n_steps == 0) return launch_status(ctx);
   return ctx->p.precision == APIP_FP32
              ? verlet_t<float>(ctx, pos, vel, force, inv_mass, id, (int)n, dt, n_steps, thermo_out, s)
@@ -536,6 +551,67 @@ apip_status apip_sync(apip_ctx* ctx, void* stream) {
   if (st[ST_BAD_INPUT]) return fail(ctx, APIP_ERR_BAD_INPUT, "non-finite position or atom id out of range");
   if (st[ST_BAD_PARTNER]) return fail(ctx, APIP_ERR_BAD_INPUT, "a CSP partner id is not present");
   return APIP_OK;
+}
+
+apip_status apip_set_mlp(apip_ctx* ctx, const float* params, void* stream) {
+  if (!ctx) return APIP_ERR_ARG;
+  if (!params) return fail(ctx, APIP_ERR_ARG, "params must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ctx->p.precision == APIP_FP32) launch_cast_params<float>(params, as<float>(ctx->mlp_w), s);
+  else launch_cast_params<double>(params, as<double>(ctx->mlp_w), s);
+  const apip_status st = launch_status(ctx);
+  if (st == APIP_OK) ctx->mlp_ready = true;
+  return st;
+}
+
+apip_status apip_descriptors(apip_ctx* ctx, const double* pos, const double box[3], const int32_t* id,
+                             int64_t n, uint16_t* desc_bf16, void* stream) {
+  apip_status st = check_call(ctx, pos, id, n);
+  if (st != APIP_OK) return st;
+  if (n > 0 && !desc_bf16) return fail(ctx, APIP_ERR_ARG, "desc_bf16 must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = set_geometry(ctx, box, s)) != APIP_OK) return st;
+  if (n == 0) return APIP_OK;
+  if (ctx->p.precision == APIP_FP32) {
+    Args<float> a = make_args<float>(ctx, pos, id, (int)n, nullptr, nullptr);
+    set_view<float>(a, ctx);
+    launch_prep<float>(a, s);
+    launch_neighbors<float>(a, ctx->ncell, s);
+    launch_descriptors<float>(a, desc_bf16, s);
+  } else {
+    Args<double> a = make_args<double>(ctx, pos, id, (int)n, nullptr, nullptr);
+    set_view<double>(a, ctx);
+    launch_prep<double>(a, s);
+    launch_neighbors<double>(a, ctx->ncell, s);
+    launch_descriptors<double>(a, desc_bf16, s);
+  }
+  APIP_CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int), s));
+  return launch_status(ctx);
+}
+
+apip_status apip_mlp_loss_grad(apip_ctx* ctx, const uint16_t* desc_bf16, const float* y, int64_t batch,
+                               const float* params, float* grad_out, float* loss_out, void* stream) {
+  if (!ctx) return APIP_ERR_ARG;
+  if (batch < 1 || batch > (1 << 26) || !desc_bf16 || !y || !params || !grad_out || !loss_out)
+    return fail(ctx, APIP_ERR_ARG, "bad batch or NULL pointer");
+  const size_t need = mlp_workspace_floats((int)batch);
+  if (need > ctx->mlp_ws_cap) {
+    if (ctx->mlp_ws) cudaFree(ctx->mlp_ws);
+    ctx->mlp_ws = nullptr;
+    ctx->mlp_ws_cap = 0;
+    APIP_CK(cudaMalloc(&ctx->mlp_ws, sizeof(float) * need));
+    ctx->mlp_ws_cap = need;
+  }
+  launch_mlp_loss_grad(desc_bf16, y, (int)batch, params, grad_out, loss_out, ctx->mlp_ws, (cudaStream_t)stream);
+  return launch_status(ctx);
+}
+
+apip_status apip_mlp_adam(apip_ctx* ctx, float* params, const float* grad, float* m, float* v, int32_t t,
+                          float lr, void* stream) {
+  if (!ctx) return APIP_ERR_ARG;
+  if (!params || !grad || !m || !v || t < 1) return fail(ctx, APIP_ERR_ARG, "NULL pointer or t < 1");
+  launch_mlp_adam(params, grad, m, v, t, lr, (cudaStream_t)stream);
+  return launch_status(ctx);
 }
 
 apip_status apip_profile(apip_ctx* ctx, int32_t enable) {

@@ -36,7 +36,8 @@ struct Geo {
   double cs[3];         // cell edges (>= r_list)
   double invL[3];       // 1 / L
   int nc[3];            // cells per axis (>= 3)
-  float Lh[3], Ll[3];   // L split as float hi + lo (FP32 path)
+  double inv_unit[3];   // 2^32 / L (FP32 path fixed-point coordinates)
+  float unit[3];        // L / 2^32
 };
 
 struct EamP { double A, beta, re, D, alpha, r0, rc, rc_lo, inv_w; };   // inv_w = 1/(rc - rc_lo)
@@ -95,8 +96,7 @@ struct apip_ctx {
   int* nnb = nullptr;
   int* nbl = nullptr;          // column-major [max_nb][nmax]
   double* pos_ref = nullptr;   // [nmax][3]
-  float4* posh = nullptr;      // FP32 path: wrapped position, float hi part
-  float4* posl = nullptr;      //            and float lo part
+  uint4* posq = nullptr;       // FP32 path: fixed-point wrapped position (x, y, z, 0)
   int* id2idx = nullptr;       // [nmax]
   int* csp = nullptr;          // [nmax][kCspCap] partner ids
 
@@ -128,4 +128,10 @@ struct apip_ctx {
   uint32_t* key4 = nullptr; void* k4a = nullptr; void* k4b = nullptr; int n4 = 0;
   uint32_t* keyd = nullptr; void* kda = nullptr; void* kdb = nullptr; int nd = 0;
   int* sched = nullptr;
+
+  // learned indicator
+  void* mlp_w = nullptr;       // APIP_MLP_NPARAM weights (element size = precision)
+  bool mlp_ready = false;
+  float* mlp_ws = nullptr;     // training workspace
+  size_t mlp_ws_cap = 0;       // floats
 };

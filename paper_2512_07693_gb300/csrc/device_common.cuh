@@ -64,11 +64,11 @@ template <> struct Acc<double> {
 };
 
 // Positions.  FP64 path: the caller's float64 array, minimum image with rint.
-// FP32 path: each wrapped coordinate split as hi + lo floats; the pair vector is
-// formed as (hi_j - hi_i) + (lo_j - lo_i) after moving whichever coordinate lies
-// in the upper half of the box down by L (hi and lo separately).  Both hi
-// differences are then exact (Sterbenz) or rounded at the scale of the pair
-// distance, so r_ij carries ~1e-7 A error instead of the ~1e-5 A of plain floats.
+// FP32 path: each coordinate as a 32-bit fixed-point fraction of the box,
+// q = floor(x_wrapped / L * 2^32).  The unsigned difference q_j - q_i read as a
+// signed integer is the minimum-image separation in units of L / 2^32
+// (3.3e-8 A for L = 143 A), exact; converting it to float rounds at the scale of
+// the pair distance (~1e-7 A), where plain float coordinates would carry ~1e-5 A.
 template <typename T> struct PosView;
 
 template <> struct PosView<double> {
@@ -85,26 +85,23 @@ template <> struct PosView<double> {
   }
 };
 
-__device__ __forceinline__ float split_diff(float a, float al, float b, float bl, float Lh, float Ll, float half) {
-  const float dd = a - b;
-  if (dd > half) { a -= Lh; al -= Ll; }
-  else if (dd < -half) { b -= Lh; bl -= Ll; }
-  return (a - b) + (al - bl);
-}
-
 template <> struct PosView<float> {
-  const float4* hi;
-  const float4* lo;
-  float Lh[3], Ll[3], half[3];
-  struct Self { float4 h, l; };
-  __device__ __forceinline__ Self self(int i) const { return {hi[i], lo[i]}; }
+  const uint4* q;
+  float unit[3];                 // L / 2^32
+  struct Self { uint4 q; };
+  __device__ __forceinline__ Self self(int i) const { return {q[i]}; }
   __device__ __forceinline__ V3<float> vec(const Self& s, int j) const {
-    const float4 h = hi[j], l = lo[j];
-    return {split_diff(h.x, l.x, s.h.x, s.l.x, Lh[0], Ll[0], half[0]),
-            split_diff(h.y, l.y, s.h.y, s.l.y, Lh[1], Ll[1], half[1]),
-            split_diff(h.z, l.z, s.h.z, s.l.z, Lh[2], Ll[2], half[2])};
+    const uint4 o = q[j];
+    return {(float)(int)(o.x - s.q.x) * unit[0], (float)(int)(o.y - s.q.y) * unit[1],
+            (float)(int)(o.z - s.q.z) * unit[2]};
   }
 };
+
+// Fixed-point coordinate of a wrapped position w in [0, L): floor(w / L * 2^32),
+// with w = L (a rounding edge) mapping to 0, its periodic image.
+__device__ __forceinline__ unsigned int fixed_coord(double w, double inv_unit) {
+  return (unsigned int)((unsigned long long)(w * inv_unit) & 0xffffffffull);
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

@@ -22,14 +22,27 @@ struct Args {
 
   const double* pos;      // caller positions [n][3]
   const int* id;          // caller ids [n]
-  int* nnb; int* nbl; double* pos_ref; float4* posh; float4* posl; int* id2idx; int* csp;
+  int* nnb; int* nbl; double* pos_ref; uint4* posq; int* id2idx; int* csp;
   int* cell_count; int* cell_atoms;
   T* zeta; T* xi_p; T* e_eam; T* g; T* wbar; T* dd; T* lam; T* dlam; T* e_ace;
   double* cvec; int* ace_list; int* counts; int* flags; int* status;
   double* partials; int n_part_p1;
   double* force;          // caller force [n][3]
   double* e_atom;         // caller per-atom energy [n] or null
+  const T* mlp_w;         // learned indicator weights (APIP_MLP_NPARAM, layout of apip.h)
+  T ace_rc, ace_rc_lo;    // cutoff of the radial descriptors (the ACE cutoff)
 };
+
+// EAM density and pair terms of one neighbour at distance r < rc (Eq. B1, S7-S8):
+// rho(r) = A exp(-beta (r - r_e)) fc(r), Phi(r) = D [x^2 - 2x] fc(r), x = exp(-alpha (r - r_0)).
+template <typename T>
+__device__ __forceinline__ void eam_terms(const EamP& e, T r, T* rho, T* phi) {
+  T dfc;
+  const T fc = ftrans(r, T(e.rc_lo), T(e.rc), T(e.inv_w), &dfc);
+  const T x = exp(-T(e.alpha) * (r - T(e.r0)));
+  *rho = T(e.A) * exp(-T(e.beta) * (r - T(e.re))) * fc;
+  *phi = T(e.D) * (x * x - T(2) * x) * fc;
+}
 
 template <typename T> Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n,
                                         double* force, double* e_atom);
@@ -54,7 +67,17 @@ template <typename T> void launch_verlet(const Args<T>& a, int mode, double* pos
                                          double* thermo_part, cudaStream_t s);
 void launch_thermo_final(const double* thermo_part, int n_tblocks, double* thermo_slot, cudaStream_t s);
 
-// ACE (kernels_ace.cu)
+// learned indicator (kernels_mlp.cu)
+template <typename T> void launch_pass1_learned(const Args<T>& a, cudaStream_t s);
+template <typename T> void launch_mlp_force(const Args<T>& a, cudaStream_t s);
+template <typename T> void launch_descriptors(const Args<T>& a, uint16_t* out, cudaStream_t s);
+template <typename T> void launch_cast_params(const float* src, T* dst, cudaStream_t s);
+void launch_mlp_loss_grad(const uint16_t* desc, const float* y, int batch, const float* params, float* grad,
+                          float* loss, float* ws, cudaStream_t s);
+size_t mlp_workspace_floats(int batch);
+void launch_mlp_adam(float* p, const float* g, float* m, float* v, int t, float lr, cudaStream_t s);
+
+// ACE (kernels_ace_f32.cu, kernels_ace_f64.cu)
 template <typename T> void ace_set_norms(const double* norms, int count);
 template <typename T> void launch_ace(const Args<T>& a, const AceDev<T>& ace, int blocks, cudaStream_t s);
 

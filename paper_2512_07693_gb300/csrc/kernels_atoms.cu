@@ -35,15 +35,10 @@ __device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, dou
   else a.id2idx[idv] = i;
   if (sizeof(T) == 4) {
     const double xs[3] = {x, y, z};
-    float h[3], l[3];
+    unsigned int q[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const double w = wrap1(xs[k], a.geo.L[k], a.geo.invL[k]);
-      h[k] = (float)w;
-      l[k] = (float)(w - (double)h[k]);
-    }
-    a.posh[i] = make_float4(h[0], h[1], h[2], 0.f);
-    a.posl[i] = make_float4(l[0], l[1], l[2], 0.f);
+    for (int k = 0; k < 3; ++k) q[k] = fixed_coord(wrap1(xs[k], a.geo.L[k], a.geo.invL[k]), a.geo.inv_unit[k]);
+    a.posq[i] = make_uint4(q[0], q[1], q[2], 0u);
   }
   double dx = x - a.pos_ref[3 * i], dy = y - a.pos_ref[3 * i + 1], dz = z - a.pos_ref[3 * i + 2];
   dx -= a.geo.L[0] * rint(dx * a.geo.invL[0]);
@@ -279,7 +274,7 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
   T lam = T(0);
   if (active) {
     const auto si = a.pv.self(i);
-    const bool paper = a.lam_mode == APIP_LAM_PAPER;
+    const bool paper = a.lam_mode == APIP_LAM_PAPER || a.lam_mode == APIP_LAM_LEARNED;
     const T rw2 = T(a.sw.r_w * a.sw.r_w), rw = T(a.sw.r_w), rwlo = T(a.sw.r_w_lo);
     const T rw_inv = T(a.sw.inv_w);
     const T rc2 = T(a.eam.rc * a.eam.rc), rc = T(a.eam.rc), rlo = T(a.eam.rc_lo);
@@ -433,9 +428,13 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* 
 #pragma unroll
     for (int q = 0; q < 3; ++q) v[q] = vel[3 * i + q] + h * force[3 * i + q];
     if (mode != 0) {
-      ke = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / im;
+      // mass = 1/inv_mass: exact in the float64 path; a float reciprocal (relative
+      // error ~1e-7 on each atom's E_kin and momentum) in the float32 path, where
+      // a float64 division per atom would cost more than the rest of the kernel
+      const double mass = sizeof(T) == 8 ? 1.0 / im : (double)(1.0f / (float)im);
+      ke = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * mass;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) p[q] = v[q] / im;
+      for (int q = 0; q < 3; ++q) p[q] = v[q] * mass;
     }
     if (mode == 1) {
 #pragma unroll

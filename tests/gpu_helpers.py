@@ -31,6 +31,9 @@ def run_gpu(s, precision="fp64", lam_mode="paper", grad_lambda=True, max_nb=96, 
     box = [float(x) for x in s["box"]]
     if lam_mode == "paper":
         m.init_csp_pairs(t["pos"], box, t["ids"])
+    if lam_mode == "learned":
+        flat = torch.tensor(apip.mlp_flat(prm["mlp"]), device="cuda")
+        m.set_mlp(flat)
     F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     ea = torch.empty(n, dtype=torch.float64, device="cuda")
     E = torch.zeros(1, dtype=torch.float64, device="cuda")
