@@ -50,7 +50,9 @@ typedef enum {
                                 that is not present */
   APIP_ERR_STATE = 5,        /* call order: apip_init_csp_pairs must precede calls that use
                                 the paper's switch */
-  APIP_ERR_SIZE = 6          /* input larger than a fixed-capacity entry point can hold */
+  APIP_ERR_SIZE = 6,         /* input larger than a fixed-capacity entry point can hold */
+  APIP_ERR_TIMEOUT = 7       /* a device-side wait (asynchronous table copy) exceeded its
+                                iteration limit; the results of that call are invalid */
 } apip_status;
 
 enum { APIP_FP64 = 0, APIP_FP32 = 1 };

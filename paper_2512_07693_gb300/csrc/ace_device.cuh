@@ -107,6 +107,86 @@ __device__ __forceinline__ void radial(T r, const AceDev<T>& t, T* R, T* dR) {
   }
 }
 
+// ---- 1-D bulk asynchronous copies (TMA) of table chunks into shared memory,
+// completed on an mbarrier; every wait is bounded.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(b)) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+constexpr int kWaitLimit = 1 << 22;
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Streams the n records of src through the two shared buffers, kAceChunk at a
+// time (the copy of chunk c+1 overlaps the processing of chunk c); all threads
+// call fn(records, count, chunk) for every chunk.  phase holds the parity of the
+// two barriers and cur the buffer to use next; both persist across calls.
+// Returns false (on every thread) if a copy did not arrive within the wait limit.
+template <typename T, typename Fn>
+__device__ __forceinline__ bool stream_table(const Rec<T>* src, int n, Rec<T>* bufs, uint64_t* bars,
+                                             uint32_t& phase, int& cur, Fn&& fn) {
+  const int nch = (n + kAceChunk - 1) / kAceChunk;
+  if (nch == 0) return true;
+  if (threadIdx.x == 0)
+    bulk_load(bufs + (size_t)cur * kAceChunk, src, min(kAceChunk, n) * (uint32_t)sizeof(Rec<T>), bars + cur);
+  for (int c = 0; c < nch; ++c) {
+    const int b = (cur + c) & 1;
+    if (threadIdx.x == 0 && c + 1 < nch) {
+      const int cnt = min(kAceChunk, n - (c + 1) * kAceChunk);
+      bulk_load(bufs + (size_t)(b ^ 1) * kAceChunk, src + (size_t)(c + 1) * kAceChunk,
+                cnt * (uint32_t)sizeof(Rec<T>), bars + (b ^ 1));
+    }
+    const bool ok = mbar_wait(bars + b, (phase >> b) & 1u);
+    phase ^= 1u << b;
+    if (__syncthreads_or(!ok)) {
+      // let a copy still in flight land before the block exits (bounded)
+      if (threadIdx.x == 0 && c + 1 < nch) mbar_wait(bars + (b ^ 1), (phase >> (b ^ 1)) & 1u);
+      return false;
+    }
+    fn(bufs + (size_t)b * kAceChunk, min(kAceChunk, n - c * kAceChunk), c);
+    __syncthreads();
+  }
+  cur = (cur + nch) & 1;
+  return true;
+}
+
+// n elements of T rounded up to a multiple of 16 bytes.
+template <typename T>
+__host__ __device__ __forceinline__ int aw_elems(int n) {
+  return (int)(((size_t)n * sizeof(T) + 15) / 16 * 16 / sizeof(T));
+}
+
+// Elements of T in the staging area: the per-pair R, Y rows of steps 1 and 4, or
+// two table chunks in steps 2 and 3, whichever is larger (16-byte multiple).
+template <typename T, int LMAX>
+__host__ __device__ constexpr size_t stage_elems() {
+  constexpr size_t ry = (size_t)kAceThreads * (kNmaxCap + (LMAX + 1) * (LMAX + 1)) * sizeof(T);
+  constexpr size_t tb = (size_t)2 * kAceChunk * sizeof(Rec<T>);
+  return ((ry > tb ? ry : tb) + 15) / 16 * 16 / sizeof(T);
+}
+
 template <int KA>
 __device__ __forceinline__ int atom_of_pair(int p, const int* off) {
   int k = 0;
@@ -126,10 +206,21 @@ __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nA = t.nA, nA1 = nA + 1;
+  const int aw = aw_elems<T>(nA1 * KA);   // A and W rounded up to 16 bytes
   T* A = reinterpret_cast<T*>(smem_raw);
-  T* W = A + nA1 * KA;
-  T* RY = W + nA1 * KA;
-  T* red = RY + kAceThreads * RYS;
+  T* W = A + aw;
+  T* RY = W + aw;
+  T* red = RY + stage_elems<T, LMAX>();
+  Rec<T>* stage = reinterpret_cast<Rec<T>*>(RY);   // table chunks share the pair staging area
+  __shared__ uint64_t s_bar[2];
+  uint32_t phase = 0;
+  int cur = 0;
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0]);
+    mbar_init(&s_bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
 
   const int count = a.counts[0];
   const int ngroups = (count + KA - 1) / KA;
@@ -200,41 +291,48 @@ __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
     for (int item = tid; item < nA * KA; item += kAceThreads) A[item] *= t.a_scale;
     __syncthreads();
 
-    // 2. embedding channels
+    // 2. embedding channels, the term tables streamed through shared memory
     {
       Acc<T> f1[KA], f2[KA];
-      const int per3 = (t.n3 + kAceAdjWarps - 1) / kAceAdjWarps;
-      const int e3 = min(t.n3, (warp + 1) * per3);
+      auto fwd3 = [&](const Rec<T>* r, int cnt, int) {
+        const int per = (cnt + kAceAdjWarps - 1) / kAceAdjWarps;
+        const int e = min(cnt, (warp + 1) * per);
 #pragma unroll 4
-      for (int q = warp * per3 + lane; q < e3; q += 32) {
-        const uint32_t key = t.key3[q];
-        const T K1 = t.k3a[q], K2 = t.k3b[q];
-        const T* a0 = A + (key & 255u) * KA;
-        const T* a1 = A + ((key >> 8) & 255u) * KA;
-        const T* a2 = A + ((key >> 16) & 255u) * KA;
+        for (int q = warp * per + lane; q < e; q += 32) {
+          const Rec<T> rc = r[q];
+          const T* a0 = A + (rc.key & 255u) * KA;
+          const T* a1 = A + ((rc.key >> 8) & 255u) * KA;
+          const T* a2 = A + ((rc.key >> 16) & 255u) * KA;
 #pragma unroll
-        for (int k = 0; k < KA; ++k) {
-          const T x = a0[k] * a1[k] * a2[k];
-          f1[k].add(K1 * x);
-          f2[k].add(K2 * x);
+          for (int k = 0; k < KA; ++k) {
+            const T x = a0[k] * a1[k] * a2[k];
+            f1[k].add(rc.k1 * x);
+            f2[k].add(rc.k2 * x);
+          }
         }
-      }
-      const int per4 = (t.n4 + kAceAdjWarps - 1) / kAceAdjWarps;
-      const int e4 = min(t.n4, (warp + 1) * per4);
+      };
+      auto fwd4 = [&](const Rec<T>* r, int cnt, int) {
+        const int per = (cnt + kAceAdjWarps - 1) / kAceAdjWarps;
+        const int e = min(cnt, (warp + 1) * per);
 #pragma unroll 4
-      for (int q = warp * per4 + lane; q < e4; q += 32) {
-        const uint32_t key = t.key4[q];
-        const T K1 = t.k4a[q], K2 = t.k4b[q];
-        const T* a0 = A + (key & 255u) * KA;
-        const T* a1 = A + ((key >> 8) & 255u) * KA;
-        const T* a2 = A + ((key >> 16) & 255u) * KA;
-        const T* a3 = A + (key >> 24) * KA;
+        for (int q = warp * per + lane; q < e; q += 32) {
+          const Rec<T> rc = r[q];
+          const T* a0 = A + (rc.key & 255u) * KA;
+          const T* a1 = A + ((rc.key >> 8) & 255u) * KA;
+          const T* a2 = A + ((rc.key >> 16) & 255u) * KA;
+          const T* a3 = A + (rc.key >> 24) * KA;
 #pragma unroll
-        for (int k = 0; k < KA; ++k) {
-          const T x = a0[k] * a1[k] * a2[k] * a3[k];
-          f1[k].add(K1 * x);
-          f2[k].add(K2 * x);
+          for (int k = 0; k < KA; ++k) {
+            const T x = a0[k] * a1[k] * a2[k] * a3[k];
+            f1[k].add(rc.k1 * x);
+            f2[k].add(rc.k2 * x);
+          }
         }
+      };
+      if (!stream_table<T>(t.rec3, t.n3, stage, s_bar, phase, cur, fwd3) ||
+          !stream_table<T>(t.rec4, t.n4, stage, s_bar, phase, cur, fwd4)) {
+        if (tid == 0) atomicOr(&a.status[ST_TIMEOUT], 1);
+        return;
       }
 #pragma unroll
       for (int k = 0; k < KA; ++k) {
@@ -274,38 +372,44 @@ __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
     }
     __syncthreads();
 
-    // 3. omega = dE/dA, whole targets per warp
+    // 3. omega = dE/dA: derivative entries streamed through shared memory; in
+    //    each chunk every target piece belongs to one warp (host schedule)
     {
-      T dfs[KA], ws[KA];
+      T dfs[KA];
 #pragma unroll
-      for (int k = 0; k < KA; ++k) {
-        dfs[k] = s_dfs[k];
-        ws[k] = t.a_scale * s_lam[k];
-      }
-      const int* tri = t.sched + kAceAdjWarps + 1;
-      const int u1 = t.sched[warp + 1];
-      for (int u = t.sched[warp]; u < u1; ++u) {
-        const int tgt = tri[3 * u], st = tri[3 * u + 1], en = tri[3 * u + 2];
-        T acc[KA];
+      for (int k = 0; k < KA; ++k) dfs[k] = s_dfs[k];
+      const int nch = t.sched[0];
+      const int* woff = t.sched + 1 + nch + 1;
+      const int* tri = woff + nch * kAceAdjWarps + 1;
+      auto adj = [&](const Rec<T>* r, int, int c) {
+        const int u1 = woff[c * kAceAdjWarps + warp + 1];
+        for (int u = woff[c * kAceAdjWarps + warp]; u < u1; ++u) {
+          const int tgt = tri[3 * u], st = tri[3 * u + 1], en = tri[3 * u + 2];
+          T acc[KA];
 #pragma unroll
-        for (int k = 0; k < KA; ++k) acc[k] = T(0);
+          for (int k = 0; k < KA; ++k) acc[k] = T(0);
 #pragma unroll 4
-        for (int q = st + lane; q < en; q += 32) {
-          const uint32_t key = t.keyd[q];
-          const T K1 = t.kda[q], K2 = t.kdb[q];
-          const T* a0 = A + (key & 255u) * KA;
-          const T* a1 = A + ((key >> 8) & 255u) * KA;
-          const T* a2 = A + ((key >> 16) & 255u) * KA;
+          for (int q = st + lane; q < en; q += 32) {
+            const Rec<T> rc = r[q];
+            const T* a0 = A + (rc.key & 255u) * KA;
+            const T* a1 = A + ((rc.key >> 8) & 255u) * KA;
+            const T* a2 = A + ((rc.key >> 16) & 255u) * KA;
 #pragma unroll
-          for (int k = 0; k < KA; ++k) acc[k] += (K1 + dfs[k] * K2) * a0[k] * a1[k] * a2[k];
-        }
+            for (int k = 0; k < KA; ++k) acc[k] += (rc.k1 + dfs[k] * rc.k2) * a0[k] * a1[k] * a2[k];
+          }
 #pragma unroll
-        for (int k = 0; k < KA; ++k) {
-          const T v = warp_sum(acc[k]);
-          if (lane == 0) W[tgt * KA + k] = v * ws[k];
+          for (int k = 0; k < KA; ++k) {
+            const T v = warp_sum(acc[k]);
+            if (lane == 0) W[tgt * KA + k] += v;
+          }
         }
+      };
+      if (!stream_table<T>(t.recd, t.nd, stage, s_bar, phase, cur, adj)) {
+        if (tid == 0) atomicOr(&a.status[ST_TIMEOUT], 1);
+        return;
       }
     }
+    for (int item = tid; item < nA * KA; item += kAceThreads) W[item] *= t.a_scale * s_lam[item % KA];
     __syncthreads();
 
     // 4. pair forces
@@ -398,7 +502,8 @@ __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
 template <typename T, int LMAX, int KA>
 void launch_lk(const Args<T>& a, const AceDev<T>& t, int blocks, cudaStream_t s) {
   constexpr int NLM = (LMAX + 1) * (LMAX + 1);
-  const size_t bytes = sizeof(T) * ((size_t)2 * (t.nA + 1) * KA + (size_t)kAceThreads * (kNmaxCap + NLM) +
+  (void)NLM;
+  const size_t bytes = sizeof(T) * ((size_t)2 * aw_elems<T>((t.nA + 1) * KA) + stage_elems<T, LMAX>() +
                                     (size_t)2 * kAceAdjWarps * KA);
   cudaFuncSetAttribute(k_ace<T, LMAX, KA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   k_ace<T, LMAX, KA><<<blocks, kAceThreads, bytes, s>>>(a, t);

@@ -17,6 +17,7 @@
 // which matches the real harmonics of the kernels (no Condon-Shortley phase
 // in the real functions).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <map>
@@ -284,44 +285,49 @@ bool build_terms(int n_max, int l_max, int nu_max, const double* c1, const doubl
     add_d(i2, i0, i1, i3, c);
     add_d(i3, i0, i1, i2, c);
   }
-  // Group the entries by target and hand whole targets to kAceAdjWarps warps,
-  // largest first to the least-loaded warp, so that each target is reduced by
-  // exactly one warp (no two warps write the same omega component).
-  std::vector<std::vector<std::pair<uint32_t, Coef>>> by_tgt(nA);
+  // The entries, sorted by target (the map order), are cut into chunks of
+  // kAceChunk that the kernel streams through shared memory.  Inside a chunk each
+  // target forms one contiguous piece; pieces go to the kAceAdjWarps warps,
+  // largest first to the least-loaded warp, so no two warps of a chunk write the
+  // same omega component (a target split across chunks is summed chunk by chunk).
+  out->keyd.clear(); out->kda.clear(); out->kdb.clear(); out->sched.clear();
   for (const auto& kv : td) {
     if (kv.second.a == 0.0 && kv.second.b == 0.0) continue;
-    by_tgt[kv.first >> 24].push_back(kv);
+    out->keyd.push_back(kv.first);
+    out->kda.push_back(kv.second.a);
+    out->kdb.push_back(kv.second.b);
   }
-  std::vector<int> order(nA);
-  for (int t = 0; t < nA; ++t) order[t] = t;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int x, int y) { return by_tgt[x].size() > by_tgt[y].size(); });
-  std::vector<std::vector<int>> bins(kAceAdjWarps);
-  std::vector<size_t> load(kAceAdjWarps, 0);
-  for (int t : order) {
-    if (by_tgt[t].empty()) continue;
-    const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    bins[b].push_back(t);
-    load[b] += by_tgt[t].size();
-  }
-  out->keyd.clear(); out->kda.clear(); out->kdb.clear(); out->sched.clear();
-  std::vector<int> triples;
-  out->sched.assign(kAceAdjWarps + 1, 0);
-  for (int b = 0; b < kAceAdjWarps; ++b) {
-    out->sched[b] = (int)(triples.size() / 3);
-    for (int t : bins[b]) {
-      const int start = (int)out->keyd.size();
-      for (const auto& kv : by_tgt[t]) {
-        out->keyd.push_back(kv.first);
-        out->kda.push_back(kv.second.a);
-        out->kdb.push_back(kv.second.b);
-      }
-      triples.push_back(t);
-      triples.push_back(start);
-      triples.push_back((int)out->keyd.size());
+  const int ne = (int)out->keyd.size();
+  const int nch = (ne + kAceChunk - 1) / kAceChunk;
+  std::vector<int> choff(nch + 1), woff, triples;
+  for (int c = 0; c <= nch; ++c) choff[c] = std::min(ne, c * kAceChunk);
+  woff.push_back(0);
+  for (int c = 0; c < nch; ++c) {
+    std::vector<std::array<int, 3>> pieces;  // (target, rel start, rel end)
+    for (int q = choff[c]; q < choff[c + 1];) {
+      const int t = (int)(out->keyd[q] >> 24);
+      int e = q;
+      while (e < choff[c + 1] && (int)(out->keyd[e] >> 24) == t) ++e;
+      pieces.push_back({t, q - choff[c], e - choff[c]});
+      q = e;
+    }
+    std::stable_sort(pieces.begin(), pieces.end(),
+                     [](const auto& x, const auto& y) { return x[2] - x[1] > y[2] - y[1]; });
+    std::vector<std::vector<std::array<int, 3>>> bins(kAceAdjWarps);
+    std::vector<int> load(kAceAdjWarps, 0);
+    for (const auto& pc : pieces) {
+      const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      bins[b].push_back(pc);
+      load[b] += pc[2] - pc[1];
+    }
+    for (int b = 0; b < kAceAdjWarps; ++b) {
+      for (const auto& pc : bins[b]) triples.insert(triples.end(), pc.begin(), pc.end());
+      woff.push_back((int)(triples.size() / 3));
     }
   }
-  out->sched[kAceAdjWarps] = (int)(triples.size() / 3);
+  out->sched.push_back(nch);
+  out->sched.insert(out->sched.end(), choff.begin(), choff.end());
+  out->sched.insert(out->sched.end(), woff.begin(), woff.end());
   out->sched.insert(out->sched.end(), triples.begin(), triples.end());
   return true;
 }

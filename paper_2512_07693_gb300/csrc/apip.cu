@@ -73,10 +73,10 @@ void free_all(apip_ctx* c) {
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   c->prof_pending.clear();
   c->prof_pool.clear();
-  void* ptrs[] = {c->cell_count, c->cell_atoms, c->nnb, c->nbl, c->pos_ref, c->posq, c->id2idx,
+  void* ptrs[] = {c->cell_count, c->cell_atoms, c->nnb, c->nbl, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->counts, c->flags, c->status, c->partials, c->thermo_part,
-                  c->e_scratch, c->key3, c->k3a, c->k3b, c->key4, c->k4a, c->k4b, c->keyd, c->kda, c->kdb, c->sched, c->mlp_w, c->mlp_ws};
+                  c->e_scratch, c->rec3, c->rec4, c->recd, c->sched, c->mlp_w, c->mlp_ws};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -168,7 +168,7 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.csp_rcut2 = p.csp_rcut * p.csp_rcut;
   a.pos = pos;
   a.id = id;
-  a.nnb = c->nnb; a.nbl = c->nbl; a.pos_ref = c->pos_ref; a.posq = c->posq;
+  a.nnb = c->nnb; a.nbl = c->nbl; a.pos_ref = c->pos_ref; a.posq = c->posq; a.posq_ref = c->posq_ref;
   a.id2idx = c->id2idx; a.csp = c->csp; a.cell_count = c->cell_count; a.cell_atoms = c->cell_atoms;
   a.zeta = as<T>(c->zeta); a.xi_p = as<T>(c->xi_p); a.e_eam = as<T>(c->e_eam); a.g = as<T>(c->g);
   a.wbar = as<T>(c->wbar); a.dd = as<T>(c->dd); a.lam = as<T>(c->lam); a.dlam = as<T>(c->dlam);
@@ -210,9 +210,9 @@ AceDev<T> ace_dev(apip_ctx* c) {
   t.eps = T(p.ace_eps);
   t.sqrt_eps = T(std::sqrt(p.ace_eps));
   t.a_scale = T(p.ace_a_scale);
-  t.key3 = c->key3; t.k3a = as<T>(c->k3a); t.k3b = as<T>(c->k3b); t.n3 = c->n3;
-  t.key4 = c->key4; t.k4a = as<T>(c->k4a); t.k4b = as<T>(c->k4b); t.n4 = c->n4;
-  t.keyd = c->keyd; t.kda = as<T>(c->kda); t.kdb = as<T>(c->kdb); t.nd = c->nd;
+  t.rec3 = as<Rec<T>>(c->rec3); t.n3 = c->n3;
+  t.rec4 = as<Rec<T>>(c->rec4); t.n4 = c->n4;
+  t.recd = as<Rec<T>>(c->recd); t.nd = c->nd;
   t.sched = c->sched;
   t.group = p.ace_group != 0 ? p.ace_group
                              : ((p.lam_mode == APIP_LAM_PAPER || p.lam_mode == APIP_LAM_LEARNED) ? 1 : 8);
@@ -382,6 +382,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->pos_ref, sizeof(double) * 3 * N);
   if (p->precision == APIP_FP32) {
     APIP_ALLOC(ctx->posq, sizeof(uint4) * N);
+    APIP_ALLOC(ctx->posq_ref, sizeof(uint4) * N);
   }
   APIP_ALLOC(ctx->id2idx, sizeof(int) * N);
   APIP_ALLOC(ctx->csp, sizeof(int) * N * kCspCap);
@@ -400,37 +401,29 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   ctx->n3 = (int)terms.key3.size();
   ctx->n4 = (int)terms.key4.size();
   ctx->nd = (int)terms.keyd.size();
-  APIP_ALLOC(ctx->key3, sizeof(uint32_t) * std::max(1, ctx->n3));
-  APIP_ALLOC(ctx->k3a, es * std::max(1, ctx->n3));
-  APIP_ALLOC(ctx->k3b, es * std::max(1, ctx->n3));
-  APIP_ALLOC(ctx->key4, sizeof(uint32_t) * std::max(1, ctx->n4));
-  APIP_ALLOC(ctx->k4a, es * std::max(1, ctx->n4));
-  APIP_ALLOC(ctx->k4b, es * std::max(1, ctx->n4));
-  APIP_ALLOC(ctx->keyd, sizeof(uint32_t) * std::max(1, ctx->nd));
-  APIP_ALLOC(ctx->kda, es * std::max(1, ctx->nd));
-  APIP_ALLOC(ctx->kdb, es * std::max(1, ctx->nd));
+  const size_t rs = p->precision == APIP_FP32 ? sizeof(Rec<float>) : sizeof(Rec<double>);
+  APIP_ALLOC(ctx->rec3, rs * std::max(1, ctx->n3));
+  APIP_ALLOC(ctx->rec4, rs * std::max(1, ctx->n4));
+  APIP_ALLOC(ctx->recd, rs * std::max(1, ctx->nd));
   APIP_ALLOC(ctx->sched, sizeof(int) * terms.sched.size());
 #undef APIP_ALLOC
-  auto upload = [&](void* dst, const std::vector<double>& v) -> cudaError_t {
-    if (v.empty()) return cudaSuccess;
-    if (p->precision == APIP_FP64) return cudaMemcpy(dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice);
-    std::vector<float> f(v.begin(), v.end());
-    return cudaMemcpy(dst, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice);
+  auto upload = [&](void* dst, const std::vector<uint32_t>& key, const std::vector<double>& a,
+                    const std::vector<double>& b) -> cudaError_t {
+    if (key.empty()) return cudaSuccess;
+    if (p->precision == APIP_FP64) {
+      std::vector<Rec<double>> r(key.size());
+      for (size_t q = 0; q < key.size(); ++q) r[q] = Rec<double>{key[q], 0u, a[q], b[q], 0ull};
+      return cudaMemcpy(dst, r.data(), sizeof(Rec<double>) * r.size(), cudaMemcpyHostToDevice);
+    }
+    std::vector<Rec<float>> r(key.size());
+    for (size_t q = 0; q < key.size(); ++q) r[q] = Rec<float>{key[q], (float)a[q], (float)b[q], 0u};
+    return cudaMemcpy(dst, r.data(), sizeof(Rec<float>) * r.size(), cudaMemcpyHostToDevice);
   };
-  cudaError_t e = cudaSuccess;
-  if (ctx->n3) e = cudaMemcpy(ctx->key3, terms.key3.data(), sizeof(uint32_t) * ctx->n3, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && ctx->n4)
-    e = cudaMemcpy(ctx->key4, terms.key4.data(), sizeof(uint32_t) * ctx->n4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && ctx->nd)
-    e = cudaMemcpy(ctx->keyd, terms.keyd.data(), sizeof(uint32_t) * ctx->nd, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = upload(ctx->kda, terms.kda);
-  if (e == cudaSuccess) e = upload(ctx->kdb, terms.kdb);
+  cudaError_t e = upload(ctx->rec3, terms.key3, terms.k3a, terms.k3b);
+  if (e == cudaSuccess) e = upload(ctx->rec4, terms.key4, terms.k4a, terms.k4b);
+  if (e == cudaSuccess) e = upload(ctx->recd, terms.keyd, terms.kda, terms.kdb);
   if (e == cudaSuccess)
     e = cudaMemcpy(ctx->sched, terms.sched.data(), sizeof(int) * terms.sched.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = upload(ctx->k3a, terms.k3a);
-  if (e == cudaSuccess) e = upload(ctx->k3b, terms.k3b);
-  if (e == cudaSuccess) e = upload(ctx->k4a, terms.k4a);
-  if (e == cudaSuccess) e = upload(ctx->k4b, terms.k4b);
   if (e == cudaSuccess) e = cudaMemset(ctx->id2idx, 0xff, sizeof(int) * N);
   if (e == cudaSuccess) e = cudaMemset(ctx->csp, 0xff, sizeof(int) * N * kCspCap);
   if (e == cudaSuccess) e = cudaMemset(ctx->cvec, 0, sizeof(double) * N);
@@ -438,6 +431,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   if (e == cudaSuccess) e = cudaMemset(ctx->flags, 0xff, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(int) * ST_COUNT);
   if (e == cudaSuccess) e = cudaMemset(ctx->pos_ref, 0, sizeof(double) * 3 * N);
+  if (e == cudaSuccess && ctx->posq_ref) e = cudaMemset(ctx->posq_ref, 0, sizeof(uint4) * N);
   if (e == cudaSuccess) e = cudaMemset(ctx->nnb, 0, sizeof(int) * N);
   if (e != cudaSuccess) return fail_create(e);
   double norms[(kLmaxCap + 1) * (kLmaxCap + 1)];
@@ -548,6 +542,7 @@ apip_status apip_sync(apip_ctx* ctx, void* stream) {
   if (st[ST_CELL_OVERFLOW])
     return fail(ctx, APIP_ERR_NB_OVERFLOW, "cell overflow: a cell holds " + std::to_string(st[ST_MAX_CELL]) +
                                               " atoms, cell_cap = " + std::to_string(ctx->p.cell_cap));
+  if (st[ST_TIMEOUT]) return fail(ctx, APIP_ERR_TIMEOUT, "an asynchronous table copy did not complete in time");
   if (st[ST_BAD_INPUT]) return fail(ctx, APIP_ERR_BAD_INPUT, "non-finite position or atom id out of range");
   if (st[ST_BAD_PARTNER]) return fail(ctx, APIP_ERR_BAD_INPUT, "a CSP partner id is not present");
   return APIP_OK;

@@ -17,6 +17,7 @@ constexpr int kLmaxCap = 4;    // largest l_max
 constexpr int kCspCap = 8;     // largest csp_nnb
 constexpr int kBlock = 256;    // threads per block of the all-atom passes
 constexpr int kAceAdjWarps = 8;            // warps per ACE block
+constexpr int kAceChunk = 1024;            // table records per shared-memory stage
 constexpr int kAceThreads = 32 * kAceAdjWarps;
 
 // Device status words (apip_ctx::status)
@@ -27,6 +28,7 @@ enum {
   ST_BAD_PARTNER = 3,   // CSP partner id not present
   ST_MAX_NNB = 4,       // largest neighbour count seen (for the error text)
   ST_MAX_CELL = 5,      // largest cell occupancy seen
+  ST_TIMEOUT = 6,       // a bounded device wait gave up
   ST_COUNT = 8
 };
 
@@ -43,6 +45,13 @@ struct Geo {
 struct EamP { double A, beta, re, D, alpha, r0, rc, rc_lo, inv_w; };   // inv_w = 1/(rc - rc_lo)
 struct SwP { double r_w, r_w_lo, d_lo, d_hi, d0, inv_w, inv_d; };  // 1/(r_w - r_w_lo), 1/(d_hi - d_lo)
 
+// One record of an ACE table: packed 8-bit A indices and the coefficients of the
+// two embedding channels; 16-byte aligned so that chunks of records can be
+// copied into shared memory by bulk asynchronous copies.
+template <typename T> struct Rec;
+template <> struct alignas(16) Rec<float> { uint32_t key; float k1, k2; uint32_t pad; };
+template <> struct alignas(16) Rec<double> { uint32_t key, pad; double k1, k2; uint64_t pad2; };
+
 // ACE tables on the device: terms of the folded product basis,
 //   phi_c = sum_t K_c[t] prod_{q} A[idx_q(t)],  c = 1, 2,
 // with A[nA] == 1 padding the lower body orders.  Keys hold 8-bit indices.
@@ -50,9 +59,9 @@ template <typename T>
 struct AceDev {
   int n_max, l_max, nA;         // nA = n_max (l_max+1)^2
   T rc, rc_lo, eps, sqrt_eps, a_scale;
-  const uint32_t* key3; const T* k3a; const T* k3b; int n3;   // 3-index terms
-  const uint32_t* key4; const T* k4a; const T* k4b; int n4;   // 4-index terms
-  const uint32_t* keyd; const T* kda; const T* kdb; int nd;   // derivative entries, grouped by target
+  const Rec<T>* rec3; int n3;   // 3-index terms
+  const Rec<T>* rec4; int n4;   // 4-index terms
+  const Rec<T>* recd; int nd;   // derivative entries, sorted by target
   const int* sched;             // adjoint schedule (HostTerms::sched)
   int group;                    // compacted atoms per thread block (1 or 8)
 };
@@ -60,9 +69,10 @@ struct AceDev {
 struct HostTerms {
   std::vector<uint32_t> key3, key4, keyd;
   std::vector<double> k3a, k3b, k4a, k4b, kda, kdb;
-  // adjoint schedule: sched[w], w = 0..kAceAdjWarps, are offsets (in triples) of
-  // warp w's targets; triples (target, start, end) into keyd follow at
-  // sched[kAceAdjWarps + 1 + 3 * t]
+  // adjoint schedule: sched[0] = number of chunks nch; then nch + 1 entry offsets
+  // of the chunks; then nch * kAceAdjWarps + 1 offsets (in pieces) of the pieces of
+  // chunk c, warp w at index c * kAceAdjWarps + w; then the pieces as (target,
+  // start, end) relative to their chunk
   std::vector<int> sched;
 };
 
@@ -97,6 +107,7 @@ struct apip_ctx {
   int* nbl = nullptr;          // column-major [max_nb][nmax]
   double* pos_ref = nullptr;   // [nmax][3]
   uint4* posq = nullptr;       // FP32 path: fixed-point wrapped position (x, y, z, 0)
+  uint4* posq_ref = nullptr;   // FP32 path: posq at the last neighbour-list build
   int* id2idx = nullptr;       // [nmax]
   int* csp = nullptr;          // [nmax][kCspCap] partner ids
 
@@ -124,9 +135,9 @@ struct apip_ctx {
   int64_t prof_n[APIP_PHASE_COUNT] = {};
 
   // ACE tables (element size = precision)
-  uint32_t* key3 = nullptr; void* k3a = nullptr; void* k3b = nullptr; int n3 = 0;
-  uint32_t* key4 = nullptr; void* k4a = nullptr; void* k4b = nullptr; int n4 = 0;
-  uint32_t* keyd = nullptr; void* kda = nullptr; void* kdb = nullptr; int nd = 0;
+  void* rec3 = nullptr; int n3 = 0;   // Rec<T> arrays
+  void* rec4 = nullptr; int n4 = 0;
+  void* recd = nullptr; int nd = 0;
   int* sched = nullptr;
 
   // learned indicator

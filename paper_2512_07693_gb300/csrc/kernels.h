@@ -22,7 +22,7 @@ struct Args {
 
   const double* pos;      // caller positions [n][3]
   const int* id;          // caller ids [n]
-  int* nnb; int* nbl; double* pos_ref; uint4* posq; int* id2idx; int* csp;
+  int* nnb; int* nbl; double* pos_ref; uint4* posq; uint4* posq_ref; int* id2idx; int* csp;
   int* cell_count; int* cell_atoms;
   T* zeta; T* xi_p; T* e_eam; T* g; T* wbar; T* dd; T* lam; T* dlam; T* e_ace;
   double* cvec; int* ace_list; int* counts; int* flags; int* status;

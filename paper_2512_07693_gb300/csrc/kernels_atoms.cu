@@ -24,11 +24,15 @@ __device__ __forceinline__ int cell_of(double xw, double L, int nc) {
 }
 
 // Duties shared by k_prep and the drift of the Verlet kernels for atom i at
-// position (x, y, z): finiteness and id checks, the id -> index map, the hi/lo
-// split of the wrapped position (FP32 path) and the neighbour-list trigger
-// (displacement since the last build > skin / 2).
+// position (x, y, z): finiteness and id checks, the id -> index map, the
+// fixed-point coordinates (FP32 path) and the neighbour-list trigger
+// (displacement since the last build > skin / 2).  In the FP32 path the
+// displacement is taken from the fixed-point coordinates (integer differences),
+// which keeps float64 arithmetic out of this per-atom work; ``wrapped`` says that
+// (x, y, z) already lie in [0, L).
 template <typename T>
-__device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, double y, double z) {
+__device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, double y, double z,
+                                          bool wrapped = false) {
   if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicOr(&a.status[ST_BAD_INPUT], 1);
   const int idv = a.id[i];
   if (idv < 0 || idv >= a.nmax) atomicOr(&a.status[ST_BAD_INPUT], 1);
@@ -37,8 +41,14 @@ __device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, dou
     const double xs[3] = {x, y, z};
     unsigned int q[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) q[k] = fixed_coord(wrap1(xs[k], a.geo.L[k], a.geo.invL[k]), a.geo.inv_unit[k]);
+    for (int k = 0; k < 3; ++k)
+      q[k] = fixed_coord(wrapped ? xs[k] : wrap1(xs[k], a.geo.L[k], a.geo.invL[k]), a.geo.inv_unit[k]);
     a.posq[i] = make_uint4(q[0], q[1], q[2], 0u);
+    const uint4 r = a.posq_ref[i];
+    const float ex = (float)(int)(q[0] - r.x) * a.geo.unit[0], ey = (float)(int)(q[1] - r.y) * a.geo.unit[1],
+                ez = (float)(int)(q[2] - r.z) * a.geo.unit[2];
+    if (ex * ex + ey * ey + ez * ez > (float)a.skin_half2) atomicOr(&a.flags[0], 1);
+    return;
   }
   double dx = x - a.pos_ref[3 * i], dy = y - a.pos_ref[3 * i + 1], dz = z - a.pos_ref[3 * i + 2];
   dx -= a.geo.L[0] * rint(dx * a.geo.invL[0]);
@@ -134,9 +144,13 @@ __global__ void k_nbfill(Args<T> a) {
     atomicMax(&a.status[ST_MAX_NNB], cnt);
   }
   a.nnb[i] = min(cnt, a.max_nb);
-  a.pos_ref[3 * i] = a.pos[3 * i];
-  a.pos_ref[3 * i + 1] = a.pos[3 * i + 1];
-  a.pos_ref[3 * i + 2] = a.pos[3 * i + 2];
+  if (sizeof(T) == 4) {
+    a.posq_ref[i] = a.posq[i];
+  } else {
+    a.pos_ref[3 * i] = a.pos[3 * i];
+    a.pos_ref[3 * i + 1] = a.pos[3 * i + 1];
+    a.pos_ref[3 * i + 2] = a.pos[3 * i + 2];
+  }
 }
 
 // -------------------------------------------------------------- CSP pairs
@@ -448,7 +462,7 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* 
         x[q] = wrap1(pos[3 * i + q] + dt * v[q], a.geo.L[q], a.geo.invL[q]);
         pos[3 * i + q] = x[q];
       }
-      prep_atom(a, i, x[0], x[1], x[2]);
+      prep_atom(a, i, x[0], x[1], x[2], true);
     }
   }
   if (mode != 0) {

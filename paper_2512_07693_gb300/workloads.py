@@ -135,6 +135,25 @@ def crack_slab(nx=200, ny=100, nz=50, opening=2.0, vacuum=15.0, sigma=0.03,
     return _finish(pos, vel, box)
 
 
+def training_config(k, cells=10, base_seed=5):
+    """Training configuration k of the learned-indicator data set: a bcc cells^3
+    crystal (2000 sites for cells = 10) with one to three random point defects
+    (vacancies, or interstitials at octahedral sites), temperature T ~ U[300, 1200] K
+    and Gaussian displacements of sigma(T) = 0.05 A sqrt(T / 300) (seed base_seed + k)."""
+    rng = np.random.default_rng(base_seed + k)
+    pos, box = bcc(cells, cells, cells)
+    temp = rng.uniform(300.0, 1200.0)
+    for _ in range(int(rng.integers(1, 4))):
+        if rng.random() < 0.5:
+            pos = np.delete(pos, rng.integers(len(pos)), axis=0)
+        else:
+            cell = rng.integers(cells, size=3).astype(np.float64)
+            face = (cell + np.array([0.5, 0.5, 0.0])) * LATTICE_A    # octahedral site of the cell
+            pos = np.vstack([pos, face])
+    pos = displace(pos, 0.05 * np.sqrt(temp / 300.0), base_seed + 100000 + k)
+    return _finish(pos, np.zeros_like(pos), box, temp=temp)
+
+
 def config(name, n_basis_fn, scale=None):
     """Named workloads.  ``n_basis_fn(n_max, l_max, nu_max)`` returns the
     product-basis size (each side computes it itself).  ``scale`` shrinks the

@@ -21,16 +21,22 @@ def f32(params):
 
 
 def learned_system(seed=31, cells=6):
+    """An untrained network with its output layer scaled by 30, so that g varies over
+    a range like a trained indicator's (an untrained one is nearly constant, and a
+    switch window inside its tiny spread would amplify float32 rounding by ~1e3);
+    the window spans the 5-95 % quantiles of the resulting d."""
     s = W.vacancy_crystal(cells=cells, sigma=0.08, seed=seed)
     nb = len(ace.enumerate_basis(6, 3, 3))
-    prm = dict(precise_adds_eam=True, eam=dict(W.EAM), csp=dict(W.CSP), mlp=f32(W.mlp_params(7)),
+    net = W.mlp_params(7)
+    net["w4"] = 30.0 * net["w4"]
+    prm = dict(precise_adds_eam=True, eam=dict(W.EAM), csp=dict(W.CSP), mlp=f32(net),
                switch=dict(W.SWITCH), ace=W.ace_params(6, 3, 3, 2, nb))
     n = len(s["pos"])
     i, j, rv, r = pairs(s["pos"], s["box"], 5.5)
     g, _, _ = mlp.learned_g(n, i, r, prm["mlp"], 5.0, 1.0)
     _, d, _, _ = descriptor(n, i, j, r, g, dict(prm["switch"], d_lo=-1e9, d_hi=1e9))
-    lo, hi = np.quantile(d, [0.3, 0.8])
-    prm["switch"].update(d_lo=float(lo), d_hi=float(hi))
+    lo = float(np.quantile(d, 0.2))
+    prm["switch"].update(d_lo=lo, d_hi=lo + 0.5 * float(g.max() - g.min()))
     s["prm"] = prm
     return s
 
@@ -41,15 +47,81 @@ def test_learned_switch_parity(prec, tolF, tolE):
     o = run_oracle(s, lam_mode="learned")
     assert np.count_nonzero(o["dlam"]) > 50
     g = run_gpu(s, precision=prec, lam_mode="learned")
+    err = np.abs(g["F"] - o["F"]).max()
+    assert err <= tolF, err
+    # float64: pair terms cancel to rounding; float32: both atoms of a gathered
+    # pair evaluate it separately in float32, so the sum is ~N eps |F|
+    assert np.abs(g["F"].sum(axis=0)).max() < (1e-8 if prec == "fp64" else 1e-4)
     if prec == "fp64":
         np.testing.assert_allclose(g["g"], o["g"], atol=1e-12)
         np.testing.assert_allclose(g["lam"], o["lam"], atol=1e-12)
+        np.testing.assert_allclose(g["e_atom"], o["e_atom"], atol=tolE)
     else:
-        np.testing.assert_allclose(g["g"], o["g"], atol=1e-5)
-    np.testing.assert_allclose(g["e_atom"], o["e_atom"], atol=tolE + 1e-6 * (prec == "fp32"))
-    err = np.abs(g["F"] - o["F"]).max()
-    assert err <= tolF, err
-    assert np.abs(g["F"].sum(axis=0)).max() < 1e-8
+        # float32 g carries ~1e-6 relative rounding from the 10 k multiply-adds of the
+        # network; through the switch it moves lam by |dlam/dd| * dg, and the energy
+        # by that times |E^prec - E^EAM|: the per-atom bar is 1e-5 eV plus that budget
+        dg = 1e-6 * np.abs(o["g"]).max()
+        np.testing.assert_allclose(g["g"], o["g"], atol=10 * dg)
+        budget = tolE + dg * np.abs(o["dlam"] * (o["e_ace"] - o["e_eam"]))
+        assert np.all(np.abs(g["e_atom"] - o["e_atom"]) <= budget)
+
+
+def _ap_energy_error(s, prm, lam_mode, params=None):
+    """x = |{lam > 0}| / N and the RMS over atoms of the adaptive energy error
+    relative to the precise model, the constant bulk offset removed:
+    err_i = E_i^AP - E_i^prec + (1 - lam_i) dE^(0) = -(1 - lam_i)(dE_i - dE^(0))."""
+    torch = torch_cuda()
+    from paper_2512_07693_gb300 import apip
+    n = len(s["pos"])
+    t = to_dev(torch, s)
+    box = [float(b) for b in s["box"]]
+    out = {}
+    for mode in ("const1", lam_mode):
+        m = apip.Apip(prm, n, precision="fp32", lam_mode=mode)
+        if mode == "paper":
+            m.init_csp_pairs(t["pos"], box, t["ids"])
+        if mode == "learned":
+            m.set_mlp(params)
+        F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        e = torch.empty(n, dtype=torch.float64, device="cuda")
+        m.energy_forces(t["pos"], box, t["types"], t["ids"], F, e_atom_out=e)
+        m.sync()
+        out[mode] = (e.cpu().numpy(), m.field("lam", n).cpu().numpy(), m.field("e_eam", n).cpu().numpy(),
+                     m.field("d", n).cpu().numpy())
+        m.close()
+    return out
+
+
+def test_trained_indicator_beats_csp_at_equal_ace_fraction():
+    """The network trained on the method's own |dE - dE^(0)| selects the atoms
+    whose fast-model energy is wrong better than CSP^list does: at the same ACE
+    fraction x it leaves a smaller energy error."""
+    torch_cuda()
+    from paper_2512_07693_gb300 import apip, train
+    prm = W.config("vacancy2k", apip.apip_ace_basis_size)["prm"]
+    G, y, ref = train.make_dataset(prm, n_configs=60, cells=10)
+    params, hist = train.train(G, y, epochs=20, batch=4096, lr=1e-3, prm=prm)
+    assert hist[-1] < 0.5 * hist[0]
+    rms = {"paper": [], "learned": []}
+    held_out = [k for k in range(1000, 1100) if W.training_config(k, cells=10)["temp"] < 700.0][:4]
+    for k in held_out:
+        s = W.training_config(k, cells=10)
+        paper = _ap_energy_error(s, prm, "paper")
+        e_prec, _, e_eam, _ = paper["const1"]
+        dE = e_prec - e_eam
+        e_ap, lam_p, _, _ = paper["paper"]
+        x = float((lam_p > 0).mean())
+        rms["paper"].append(np.sqrt(np.mean(((1 - lam_p) * (dE - ref)) ** 2)))
+        # learned switch with its window placed to give the same x
+        wide = dict(prm, switch=dict(prm["switch"], d_lo=-1e3, d_hi=1e3))
+        d = _ap_energy_error(s, wide, "learned", params)["learned"][3]
+        lo = float(np.quantile(d, 1.0 - x))
+        width = 0.25 * float(np.std(d))
+        tuned = dict(prm, switch=dict(prm["switch"], d_lo=lo, d_hi=lo + width))
+        lam_l = _ap_energy_error(s, tuned, "learned", params)["learned"][1]
+        assert abs((lam_l > 0).mean() - x) < 0.02
+        rms["learned"].append(np.sqrt(np.mean(((1 - lam_l) * (dE - ref)) ** 2)))
+    assert np.mean(rms["learned"]) < np.mean(rms["paper"]), rms
 
 
 def _bf16(x):
