@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ace-steps", type=int, default=5, help="steps of the all-ACE comparison run")
     ap.add_argument("--e2e-steps", type=int, default=50)
-    ap.add_argument("--ace-group", type=int, default=0, choices=[0, 1, 8],
+    ap.add_argument("--ace-group", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="compacted atoms per ACE thread block (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -192,16 +192,19 @@ def timed_steps(torch, m, t, box, steps, flush, thermo=None):
     return [a.elapsed_time(b) for a, b in zip(starts, ends)]
 
 
-def ace_flops_per_atom(s, nnb_rc):
-    """Algorithmic float32 operations of the ACE kernel per compacted atom:
-    A accumulation 2 n NLM per neighbour, force contraction (u, v) 4 n NLM + 8 NLM
-    per neighbour, forward 6 per 3-term (7 per 4-term), adjoint 11 per 3-term
-    (15 per 4-term).  Basis evaluation (R, Y) is not counted."""
-    from paper_2512_07693_gb300 import apip
+def ace_flops_per_atom(s, nnb_rc, info):
+    """Algorithmic float32 operations of the ACE kernel per compacted atom, a
+    multiply-add counted as 2: per neighbour within r_c, A accumulation 2 n NLM and
+    the force contraction (u, v) 4 n NLM + 8 NLM; per atom, the Gaunt couplings 3
+    per product, the basis dot products 2 per segment element + 4 per record (two
+    channels), the reverse rows 4 per row element, the C -> A entries 3 each.
+    Basis evaluation (R, Y) is not counted.  ``info`` = apip_ace_info."""
     a = s["prm"]["ace"]
     nlm = (a["l_max"] + 1) ** 2
     per_nb = 2 * a["n_max"] * nlm + 4 * a["n_max"] * nlm + 8 * nlm
-    return nnb_rc * per_nb, per_nb
+    per_atom = (3 * info["gaunt_products"] + 2 * info["record_len_sum"] + 4 * info["records"]
+                + 4 * info["row_len_sum"] + 3 * info["c_to_a_entries"])
+    return nnb_rc * per_nb + per_atom, per_nb
 
 
 def run_ours(args):
@@ -256,6 +259,16 @@ def run_ours(args):
     launches_per_step = sum(v[1] for v in prof.values()) / prof_steps
     nnb = m.field("nnb", n).cpu().numpy()
     P = m.field("ace_list", n).cpu().numpy()[: int((lam > 0).sum())]
+    ace_info = apip.apip_ace_info(m.ctx)
+    # neighbours within the ACE cutoff of the compacted atoms (the per-pair work)
+    nbl = m.field("nblist", n)[torch.as_tensor(P, device="cuda")].cpu().numpy()
+    pos_now = t["pos"].cpu().numpy()
+    jj = np.where(nbl >= 0, nbl, P[:, None])
+    dv = pos_now[jj] - pos_now[P][:, None, :]
+    dv -= np.asarray(box) * np.rint(dv / np.asarray(box))
+    r2 = np.sum(dv * dv, axis=2)
+    rc = s["prm"]["ace"]["rc"]
+    nb_rc_ace = float(np.mean(np.sum((nbl >= 0) & (r2 < rc * rc) & (jj != P[:, None]), axis=1))) if len(P) else 0.0
     del m
 
     # --- all-ACE run on the same GPU (lam = 1 everywhere)
@@ -311,8 +324,8 @@ def run_ours(args):
                 "frac": achieved / hbm, "traffic": None, "algorithmic_bytes_per_launch": traffic_alg,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}
     else:
-        nb_rc = mean_nnb
-        fl_atom, _ = ace_flops_per_atom(s, nb_rc)
+        nb_rc = nb_rc_ace
+        fl_atom, _ = ace_flops_per_atom(s, nb_rc, ace_info)
         fl = fl_atom * len(P)
         peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
         achieved = fl / (dom_ms * 1e-3) / 1e12
@@ -337,6 +350,7 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": int(round(launches_per_step * args.steps)),
+        "ace_tables": ace_info,
     }
     if rank == 0 and not args.no_cpu_baseline:
         cb = oracle_sample(None, 15.0)

@@ -97,8 +97,11 @@ typedef struct apip_params {
      order <= nu_max, E = c1.B + (( c2.B )^2 + eps^2)^(1/4) - sqrt(eps).
      n_max in [1, 8], l_max in [0, 4], nu_max in [1, 4], n_max (l_max+1)^2 <= 254. */
   int32_t ace_n_max, ace_l_max, ace_nu_max;
-  int32_t ace_group;         /* compacted atoms per ACE thread block: 0 = automatic (1 for the
-                                paper's switch, 8 for constant lam), or 1 or 8 */
+  int32_t ace_group;         /* compacted atoms per ACE thread block: 1, 2, 4 or 8, or 0 =
+                                automatic (the largest whose two per-atom pools of
+                                1 + n_max (l_max+1)^2 + couplings values leave room for two
+                                resident blocks per SM).  A group whose pools do not fit in
+                                shared memory is rejected by apip_create (APIP_ERR_ARG). */
   double ace_rc, ace_rc_width, ace_eps, ace_a_scale;
   const double* ace_c1;      /* host, ace_n_basis entries (copied) */
   const double* ace_c2;      /* host, ace_n_basis entries (copied) */
@@ -124,7 +127,8 @@ int64_t apip_ace_basis_size(int32_t n_max, int32_t l_max, int32_t nu_max);
 
 /* Create a context for up to n_atoms_max atoms.  Allocates all scratch (cells,
  * neighbour list, per-atom switch arrays, ACE tables) on the current device.
- * Errors: APIP_ERR_ARG (bad parameters), APIP_ERR_CUDA (allocation). */
+ * Errors: APIP_ERR_ARG (bad parameters, or an ACE group that does not fit in
+ * shared memory), APIP_ERR_CUDA (allocation). */
 apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** out);
 
 /* Free a context and its device memory (synchronises the device). NULL is ok. */
@@ -204,6 +208,21 @@ enum {
 };
 apip_status apip_profile(apip_ctx* ctx, int32_t enable);
 apip_status apip_profile_read(apip_ctx* ctx, double* ms, int64_t* launches);
+
+/* Sizes of the ACE evaluation that apip_create built, for work accounting
+ * (host call, no device work).  out (host, APIP_ACE_INFO_COUNT entries):
+ *   [0] pool values per atom: 1 + n_max (l_max+1)^2 + coupling components
+ *   [1] coupling components C_{(p1 p2) L M}
+ *   [2] Gaunt products summed over the components (one multiply-add pair each)
+ *   [3] basis records (one dot product of two pool segments each)
+ *   [4] sum over the records of their segment length
+ *   [5] sum over the pool values of the length of their reverse row
+ *   [6] C -> A back-propagation entries
+ *   [7] compacted atoms per ACE thread block
+ *   [8] ACE thread blocks per launch
+ * Errors: APIP_ERR_ARG (NULL argument). */
+#define APIP_ACE_INFO_COUNT 9
+apip_status apip_ace_info(apip_ctx* ctx, int64_t* out);
 
 /* Learned indicator (workload row: MLP on radial descriptors trained on per-atom
  * |E^prec - E^EAM|; no counterpart in the paper beyond its allowance of any

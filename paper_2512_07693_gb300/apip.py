@@ -68,6 +68,7 @@ def _load():
         "apip_get_field": (ctypes.c_int, [_vp, _c_int32, _vp, _c_int64, _vp]),
         "apip_profile": (ctypes.c_int, [_vp, _c_int32]),
         "apip_profile_read": (ctypes.c_int, [_vp, P(_c_double), P(_c_int64)]),
+        "apip_ace_info": (ctypes.c_int, [_vp, P(_c_int64)]),
         "apip_reduce_energy_static": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
         "apip_set_mlp": (ctypes.c_int, [_vp, _vp, _vp]),
         "apip_descriptors": (ctypes.c_int, [_vp, _vp, P(_c_double), _vp, _c_int64, _vp, _vp]),
@@ -175,6 +176,17 @@ def apip_profile_read(ctx):
     nl = (_c_int64 * len(PHASES))()
     _check(ctx, lib.apip_profile_read(ctx, ms, nl))
     return {name: (ms[k], nl[k]) for k, name in enumerate(PHASES)}
+
+
+ACE_INFO = ("pool", "couplings", "gaunt_products", "records", "record_len_sum", "row_len_sum",
+            "c_to_a_entries", "group", "blocks")
+
+
+def apip_ace_info(ctx):
+    """Sizes of the ACE evaluation built at creation, as a dict (see ACE_INFO)."""
+    out = (_c_int64 * len(ACE_INFO))()
+    _check(ctx, lib.apip_ace_info(ctx, out))
+    return {k: int(out[q]) for q, k in enumerate(ACE_INFO)}
 
 
 def apip_reduce_energy_static(e_atom, n, e_total, stream=None):

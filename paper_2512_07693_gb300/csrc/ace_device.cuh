@@ -4,18 +4,21 @@
 // translation unit per precision (kernels_ace_f32.cu, kernels_ace_f64.cu), each
 // of which defines ynorm<T> (the real Y_lm normalisation in constant memory).
 //
-// One thread block (8 warps) handles a group of KA compacted atoms at a time:
+// One thread block (8 warps) handles a group of KA compacted atoms at a time,
+// with the per-atom pool X = [1 | A | C] and its adjoint in shared memory
+// (layout [pool index][KA]):
 //  1. A_nlm = a_scale sum_j R_n(r_ij) Y_lm(rhat_ij): one thread per (atom,
 //     neighbour) pair evaluates R and Y into shared memory, then threads own
-//     (component, atom) entries of A (layout A[c][KA]).
-//  2. phi_c = sum_t K_c[t] prod_q A[idx_q(t)] over the folded term lists; warps
-//     take contiguous eighths of the list, lanes stride it (coalesced), every
-//     lane keeps one compensated sum per atom; then
+//     (component, atom) entries of A.
+//  2. C_{(p1 p2) L M} = sum G(l1 m1, l2 m2, L M) A_{p1 m1} A_{p2 m2} (a thread per
+//     component); then phi_c = sum_b c_cb X_{s1(b)} . X_{s2(b)} over the
+//     basis records (a thread per record, compensated sums per atom) and
 //     E_i^ACE = phi_1 + (phi_2^2 + eps^2)^(1/4) - sqrt(eps).
-//  3. omega = dE_i/dA: derivative entries grouped by target component, whole
-//     targets assigned to warps on the host (balanced by entry count); a warp
-//     sums a target's entries lane-strided and one lane writes omega once.  No
-//     atomics.  omega is scaled by a_scale lam_i.
+//  3. The adjoint dE/dX: a thread per pool value gathers its segment's reverse
+//     row (sum of k_b X_partner, k_b = c1_b + F'(phi_2) c2_b); then dE/dC goes
+//     back onto A through the Gaunt entries, grouped by target A component and
+//     cut into pieces whose partial sums are reduced per target.  No atomics.
+//     omega = dE/dA a_scale lam_i.
 //  4. One thread per pair: f_ij = sum_nlm omega_nlm grad(R_n Y_lm)(r_ij) (the ACE
 //     force contribution of Eq. S14 / A1); plus, when the fast weights are 1 - lam,
 //     the part -lam_i a_ij e_ij of S12 that pass 2 left out; plus, when
@@ -107,84 +110,19 @@ __device__ __forceinline__ void radial(T r, const AceDev<T>& t, T* R, T* dR) {
   }
 }
 
-// ---- 1-D bulk asynchronous copies (TMA) of table chunks into shared memory,
-// completed on an mbarrier; every wait is bounded.
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(b)) : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
-
-constexpr int kWaitLimit = 1 << 22;
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < kWaitLimit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-// Streams the n records of src through the two shared buffers, kAceChunk at a
-// time (the copy of chunk c+1 overlaps the processing of chunk c); all threads
-// call fn(records, count, chunk) for every chunk.  phase holds the parity of the
-// two barriers and cur the buffer to use next; both persist across calls.
-// Returns false (on every thread) if a copy did not arrive within the wait limit.
-template <typename T, typename Fn>
-__device__ __forceinline__ bool stream_table(const Rec<T>* src, int n, Rec<T>* bufs, uint64_t* bars,
-                                             uint32_t& phase, int& cur, Fn&& fn) {
-  const int nch = (n + kAceChunk - 1) / kAceChunk;
-  if (nch == 0) return true;
-  if (threadIdx.x == 0)
-    bulk_load(bufs + (size_t)cur * kAceChunk, src, min(kAceChunk, n) * (uint32_t)sizeof(Rec<T>), bars + cur);
-  for (int c = 0; c < nch; ++c) {
-    const int b = (cur + c) & 1;
-    if (threadIdx.x == 0 && c + 1 < nch) {
-      const int cnt = min(kAceChunk, n - (c + 1) * kAceChunk);
-      bulk_load(bufs + (size_t)(b ^ 1) * kAceChunk, src + (size_t)(c + 1) * kAceChunk,
-                cnt * (uint32_t)sizeof(Rec<T>), bars + (b ^ 1));
-    }
-    const bool ok = mbar_wait(bars + b, (phase >> b) & 1u);
-    phase ^= 1u << b;
-    if (__syncthreads_or(!ok)) {
-      // let a copy still in flight land before the block exits (bounded)
-      if (threadIdx.x == 0 && c + 1 < nch) mbar_wait(bars + (b ^ 1), (phase >> (b ^ 1)) & 1u);
-      return false;
-    }
-    fn(bufs + (size_t)b * kAceChunk, min(kAceChunk, n - c * kAceChunk), c);
-    __syncthreads();
-  }
-  cur = (cur + nch) & 1;
-  return true;
-}
-
-// n elements of T rounded up to a multiple of 16 bytes.
+// Elements of T in one pool of npool values for KA atoms, padded to 16 bytes.
 template <typename T>
-__host__ __device__ __forceinline__ int aw_elems(int n) {
-  return (int)(((size_t)n * sizeof(T) + 15) / 16 * 16 / sizeof(T));
+__host__ __device__ __forceinline__ int pool_elems(int npool, int KA) {
+  return (int)(((size_t)npool * KA * sizeof(T) + 15) / 16 * 16 / sizeof(T));
 }
 
-// Elements of T in the staging area: the per-pair R, Y rows of steps 1 and 4, or
-// two table chunks in steps 2 and 3, whichever is larger (16-byte multiple).
-template <typename T, int LMAX>
-__host__ __device__ constexpr size_t stage_elems() {
-  constexpr size_t ry = (size_t)kAceThreads * (kNmaxCap + (LMAX + 1) * (LMAX + 1)) * sizeof(T);
-  constexpr size_t tb = (size_t)2 * kAceChunk * sizeof(Rec<T>);
-  return ((ry > tb ? ry : tb) + 15) / 16 * 16 / sizeof(T);
+// Dynamic shared memory of k_ace: the pool X, its adjoint (which also holds the
+// per-pair R, Y rows of step 1), and the block reduction.
+template <typename T, int LMAX, int KA>
+__host__ __device__ inline size_t ace_smem_bytes(int npool) {
+  constexpr size_t ry = (size_t)kAceThreads * (kNmaxCap + (LMAX + 1) * (LMAX + 1));
+  const size_t px = (size_t)pool_elems<T>(npool, KA);
+  return sizeof(T) * (px + (px > ry ? px : ry) + (size_t)2 * kAceWarps * KA);
 }
 
 template <int KA>
@@ -199,28 +137,21 @@ template <typename T, int LMAX, int KA>
 __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
   constexpr int NLM = (LMAX + 1) * (LMAX + 1);
   constexpr int RYS = kNmaxCap + NLM;
+  constexpr int RY_ELEMS = kAceThreads * RYS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_atom[KA], s_off[KA + 1], s_trans[KA];
   __shared__ T s_dfs[KA], s_e[KA], s_lam[KA], s_delta[KA], s_et[KA], s_D[KA], s_xi[KA];
   __shared__ double s_ep[KA];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nA = t.nA, nA1 = nA + 1;
-  const int aw = aw_elems<T>(nA1 * KA);   // A and W rounded up to 16 bytes
-  T* A = reinterpret_cast<T*>(smem_raw);
-  T* W = A + aw;
-  T* RY = W + aw;
-  T* red = RY + stage_elems<T, LMAX>();
-  Rec<T>* stage = reinterpret_cast<Rec<T>*>(RY);   // table chunks share the pair staging area
-  __shared__ uint64_t s_bar[2];
-  uint32_t phase = 0;
-  int cur = 0;
-  if (threadIdx.x == 0) {
-    mbar_init(&s_bar[0]);
-    mbar_init(&s_bar[1]);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
+  const int nA = t.nA, npool = t.npool, c0 = 1 + nA;
+  const int px = pool_elems<T>(npool, KA);
+  T* X = reinterpret_cast<T*>(smem_raw);   // X[q * KA + k]
+  T* G = X + px;                           // dE/dX, same layout
+  T* RY = G;                               // step 1 staging
+  T* red = G + (px > RY_ELEMS ? px : RY_ELEMS);
+  T* A = X + KA;                           // A[c * KA + k] = X[(1 + c) * KA + k]
+  T* W = G + KA;                           // omega, same layout as A
 
   const int count = a.counts[0];
   const int ngroups = (count + KA - 1) / KA;
@@ -241,10 +172,7 @@ __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
       s_off[0] = 0;
       for (int k = 0; k < KA; ++k) s_off[k + 1] = s_off[k] + (s_atom[k] >= 0 ? a.nnb[s_atom[k]] : 0);
     }
-    for (int c = tid; c < nA1 * KA; c += kAceThreads) {
-      A[c] = (c >= nA * KA) ? T(1) : T(0);
-      W[c] = T(0);
-    }
+    for (int c = tid; c < c0 * KA; c += kAceThreads) X[c] = (c < KA) ? T(1) : T(0);
     __syncthreads();
     const int total = s_off[KA];
 
@@ -291,48 +219,46 @@ __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
     for (int item = tid; item < nA * KA; item += kAceThreads) A[item] *= t.a_scale;
     __syncthreads();
 
-    // 2. embedding channels, the term tables streamed through shared memory
+    // 2a. Gaunt couplings of pairs of A segments
+    for (int c = tid; c < t.nC; c += kAceThreads) {
+      const uint2 cp = t.comp[c];
+      const T* x1 = X + (cp.x & 0xffffu) * KA;
+      const T* x2 = X + (cp.x >> 16) * KA;
+      const int g0 = (int)(cp.y >> 8), g1 = g0 + (int)(cp.y & 255u);
+      T acc[KA];
+#pragma unroll
+      for (int k = 0; k < KA; ++k) acc[k] = T(0);
+      for (int e = g0; e < g1; ++e) {
+        const Ent<T> g = t.gent[e];
+        const T* u = x1 + (g.key & 255u) * KA;
+        const T* v = x2 + (g.key >> 8) * KA;
+#pragma unroll
+        for (int k = 0; k < KA; ++k) acc[k] += g.v * u[k] * v[k];
+      }
+#pragma unroll
+      for (int k = 0; k < KA; ++k) X[(c0 + c) * KA + k] = acc[k];
+    }
+    __syncthreads();
+
+    // 2b. embedding channels: one dot product of two pool segments per record
     {
       Acc<T> f1[KA], f2[KA];
-      auto fwd3 = [&](const Rec<T>* r, int cnt, int) {
-        const int per = (cnt + kAceAdjWarps - 1) / kAceAdjWarps;
-        const int e = min(cnt, (warp + 1) * per);
-#pragma unroll 4
-        for (int q = warp * per + lane; q < e; q += 32) {
-          const Rec<T> rc = r[q];
-          const T* a0 = A + (rc.key & 255u) * KA;
-          const T* a1 = A + ((rc.key >> 8) & 255u) * KA;
-          const T* a2 = A + ((rc.key >> 16) & 255u) * KA;
+      for (int r = tid; r < t.nf; r += kAceThreads) {
+        const Rec<T> rc = t.frec[r];
+        const T* u = X + (rc.key & 0xffffu) * KA;
+        const T* v = X + (rc.key >> 16) * KA;
+        T dot[KA];
 #pragma unroll
-          for (int k = 0; k < KA; ++k) {
-            const T x = a0[k] * a1[k] * a2[k];
-            f1[k].add(rc.k1 * x);
-            f2[k].add(rc.k2 * x);
-          }
-        }
-      };
-      auto fwd4 = [&](const Rec<T>* r, int cnt, int) {
-        const int per = (cnt + kAceAdjWarps - 1) / kAceAdjWarps;
-        const int e = min(cnt, (warp + 1) * per);
-#pragma unroll 4
-        for (int q = warp * per + lane; q < e; q += 32) {
-          const Rec<T> rc = r[q];
-          const T* a0 = A + (rc.key & 255u) * KA;
-          const T* a1 = A + ((rc.key >> 8) & 255u) * KA;
-          const T* a2 = A + ((rc.key >> 16) & 255u) * KA;
-          const T* a3 = A + (rc.key >> 24) * KA;
+        for (int k = 0; k < KA; ++k) dot[k] = T(0);
+        for (int m = 0; m < (int)rc.len; ++m) {
 #pragma unroll
-          for (int k = 0; k < KA; ++k) {
-            const T x = a0[k] * a1[k] * a2[k] * a3[k];
-            f1[k].add(rc.k1 * x);
-            f2[k].add(rc.k2 * x);
-          }
+          for (int k = 0; k < KA; ++k) dot[k] += u[m * KA + k] * v[m * KA + k];
         }
-      };
-      if (!stream_table<T>(t.rec3, t.n3, stage, s_bar, phase, cur, fwd3) ||
-          !stream_table<T>(t.rec4, t.n4, stage, s_bar, phase, cur, fwd4)) {
-        if (tid == 0) atomicOr(&a.status[ST_TIMEOUT], 1);
-        return;
+#pragma unroll
+        for (int k = 0; k < KA; ++k) {
+          f1[k].add(rc.k1 * dot[k]);
+          f2[k].add(rc.k2 * dot[k]);
+        }
       }
 #pragma unroll
       for (int k = 0; k < KA; ++k) {
@@ -346,7 +272,7 @@ __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
     __syncthreads();
     if (tid < KA) {
       T p1 = T(0), p2 = T(0);
-      for (int w = 0; w < kAceAdjWarps; ++w) {
+      for (int w = 0; w < kAceWarps; ++w) {
         p1 += red[(2 * w) * KA + tid];
         p2 += red[(2 * w + 1) * KA + tid];
       }
@@ -372,46 +298,54 @@ __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
     }
     __syncthreads();
 
-    // 3. omega = dE/dA: derivative entries streamed through shared memory; in
-    //    each chunk every target piece belongs to one warp (host schedule)
+    // 3a. dE/dX: each pool value gathers the reverse row of its segment
     {
       T dfs[KA];
 #pragma unroll
       for (int k = 0; k < KA; ++k) dfs[k] = s_dfs[k];
-      const int nch = t.sched[0];
-      const int* woff = t.sched + 1 + nch + 1;
-      const int* tri = woff + nch * kAceAdjWarps + 1;
-      auto adj = [&](const Rec<T>* r, int, int c) {
-        const int u1 = woff[c * kAceAdjWarps + warp + 1];
-        for (int u = woff[c * kAceAdjWarps + warp]; u < u1; ++u) {
-          const int tgt = tri[3 * u], st = tri[3 * u + 1], en = tri[3 * u + 2];
-          T acc[KA];
+      for (int q = 1 + tid; q < npool; q += kAceThreads) {
+        const int4 qr = t.qrow[q];
+        T acc[KA];
 #pragma unroll
-          for (int k = 0; k < KA; ++k) acc[k] = T(0);
-#pragma unroll 4
-          for (int q = st + lane; q < en; q += 32) {
-            const Rec<T> rc = r[q];
-            const T* a0 = A + (rc.key & 255u) * KA;
-            const T* a1 = A + ((rc.key >> 8) & 255u) * KA;
-            const T* a2 = A + ((rc.key >> 16) & 255u) * KA;
+        for (int k = 0; k < KA; ++k) acc[k] = T(0);
+        for (int e = qr.x; e < qr.y; ++e) {
+          const Rec<T> rc = t.arec[e];
+          const T* v = X + (rc.key + qr.z) * KA;
 #pragma unroll
-            for (int k = 0; k < KA; ++k) acc[k] += (rc.k1 + dfs[k] * rc.k2) * a0[k] * a1[k] * a2[k];
-          }
-#pragma unroll
-          for (int k = 0; k < KA; ++k) {
-            const T v = warp_sum(acc[k]);
-            if (lane == 0) W[tgt * KA + k] += v;
-          }
+          for (int k = 0; k < KA; ++k) acc[k] += (rc.k1 + dfs[k] * rc.k2) * v[k];
         }
-      };
-      if (!stream_table<T>(t.recd, t.nd, stage, s_bar, phase, cur, adj)) {
-        if (tid == 0) atomicOr(&a.status[ST_TIMEOUT], 1);
-        return;
+#pragma unroll
+        for (int k = 0; k < KA; ++k) G[q * KA + k] = acc[k];
       }
     }
-    for (int item = tid; item < nA * KA; item += kAceThreads) W[item] *= t.a_scale * s_lam[item % KA];
     __syncthreads();
 
+    // 3b. dE/dC back onto A: partial sums of the pieces, kept in the C part of X
+    //     (not read again for this group)
+    for (int pc = tid; pc < t.npc; pc += kAceThreads) {
+      T acc[KA];
+#pragma unroll
+      for (int k = 0; k < KA; ++k) acc[k] = T(0);
+      const int e1 = t.poff[pc + 1];
+      for (int e = t.poff[pc]; e < e1; ++e) {
+        const Ent<T> b = t.bent[e];
+        const T* gc = G + (b.key & 0xffffu) * KA;
+        const T* xo = X + (b.key >> 16) * KA;
+#pragma unroll
+        for (int k = 0; k < KA; ++k) acc[k] += b.v * gc[k] * xo[k];
+      }
+#pragma unroll
+      for (int k = 0; k < KA; ++k) X[(c0 + pc) * KA + k] = acc[k];
+    }
+    __syncthreads();
+    for (int item = tid; item < nA * KA; item += kAceThreads) {
+      const int c = item / KA, k = item - c * KA;
+      T s = W[item];
+      const int p1 = t.tpiece[c + 1];
+      for (int pc = t.tpiece[c]; pc < p1; ++pc) s += X[(c0 + pc) * KA + k];
+      W[item] = s * t.a_scale * s_lam[k];
+    }
+    __syncthreads();
     // 4. pair forces
     for (int base = 0; base < total; base += kAceThreads) {
       const int p = base + tid;
@@ -501,12 +435,26 @@ __global__ void __launch_bounds__(kAceThreads) k_ace(Args<T> a, AceDev<T> t) {
 
 template <typename T, int LMAX, int KA>
 void launch_lk(const Args<T>& a, const AceDev<T>& t, int blocks, cudaStream_t s) {
-  constexpr int NLM = (LMAX + 1) * (LMAX + 1);
-  (void)NLM;
-  const size_t bytes = sizeof(T) * ((size_t)2 * aw_elems<T>((t.nA + 1) * KA) + stage_elems<T, LMAX>() +
-                                    (size_t)2 * kAceAdjWarps * KA);
+  const size_t bytes = ace_smem_bytes<T, LMAX, KA>(t.npool);
   cudaFuncSetAttribute(k_ace<T, LMAX, KA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   k_ace<T, LMAX, KA><<<blocks, kAceThreads, bytes, s>>>(a, t);
+}
+
+// Resident blocks per SM of k_ace for this pool size (0 if it does not fit).
+template <typename T, int LMAX, int KA>
+int occupancy_lk(int npool, size_t* bytes) {
+  *bytes = ace_smem_bytes<T, LMAX, KA>(npool);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (*bytes + (size_t)1024 > (size_t)optin) return 0;
+  if (cudaFuncSetAttribute(k_ace<T, LMAX, KA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes) !=
+      cudaSuccess)
+    return 0;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ace<T, LMAX, KA>, kAceThreads, *bytes) != cudaSuccess)
+    return 0;
+  return occ;
 }
 
 template <typename T, int KA>
@@ -520,10 +468,35 @@ void launch_k(const Args<T>& a, const AceDev<T>& t, int blocks, cudaStream_t s) 
   }
 }
 
+template <typename T, int KA>
+int occupancy_k(int l_max, int npool, size_t* bytes) {
+  switch (l_max) {
+    case 0: return occupancy_lk<T, 0, KA>(npool, bytes);
+    case 1: return occupancy_lk<T, 1, KA>(npool, bytes);
+    case 2: return occupancy_lk<T, 2, KA>(npool, bytes);
+    case 3: return occupancy_lk<T, 3, KA>(npool, bytes);
+    default: return occupancy_lk<T, 4, KA>(npool, bytes);
+  }
+}
+
 template <typename T>
 void launch_ace_impl(const Args<T>& a, const AceDev<T>& t, int blocks, cudaStream_t s) {
-  if (t.group == 8) launch_k<T, 8>(a, t, blocks, s);
-  else launch_k<T, 1>(a, t, blocks, s);
+  switch (t.group) {
+    case 8: launch_k<T, 8>(a, t, blocks, s); break;
+    case 4: launch_k<T, 4>(a, t, blocks, s); break;
+    case 2: launch_k<T, 2>(a, t, blocks, s); break;
+    default: launch_k<T, 1>(a, t, blocks, s); break;
+  }
+}
+
+template <typename T>
+int ace_occupancy_impl(int l_max, int group, int npool, size_t* bytes) {
+  switch (group) {
+    case 8: return occupancy_k<T, 8>(l_max, npool, bytes);
+    case 4: return occupancy_k<T, 4>(l_max, npool, bytes);
+    case 2: return occupancy_k<T, 2>(l_max, npool, bytes);
+    default: return occupancy_k<T, 1>(l_max, npool, bytes);
+  }
 }
 
 }  // namespace apip

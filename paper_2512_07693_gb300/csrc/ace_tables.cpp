@@ -1,14 +1,12 @@
 // Host-side construction of the ACE tables: the canonical product basis, the
-// real Gaunt coefficients and the coefficient-folded term lists that the GPU
-// kernel evaluates.
+// real Gaunt coefficients and the coupled tables that the GPU kernel evaluates.
 //
 // The paper takes ACE from the literature (Appendix B; Eq. S14).  Here the
 // product basis B_b is the standard rotation-invariant coupling of the atomic
-// density A_nlm through real Gaunt coefficients, and the two embedding
-// channels phi_c = sum_b c_cb B_b are folded into one polynomial in A per
-// channel:  phi_c = sum_t K_c[t] prod_q A[idx_q(t)],  with one term per
-// distinct (sorted) index tuple.  A[nA] == 1 pads lower body orders so that
-// orders 1..3 share one 3-index list and order 4 has a 4-index list.
+// density A_nlm through real Gaunt coefficients, and the embedding channels are
+// phi_c = sum_b c_cb B_b.  The kernel evaluates every B_b as one dot product of
+// two segments of a per-atom pool of A and of pairwise Gaunt couplings of A
+// (build_coupled below).
 //
 // Real Gaunt coefficients are built from complex ones (Wigner 3j by Racah's
 // formula) through the unitary map from complex to real spherical harmonics:
@@ -22,7 +20,6 @@
 #include <complex>
 #include <map>
 #include <tuple>
-#include <unordered_map>
 
 #include "apip_internal.h"
 
@@ -112,10 +109,6 @@ std::vector<Basis> enumerate(int n_max, int l_max, int nu_max) {
   return out;
 }
 
-struct Coef { double a = 0.0, b = 0.0; };
-
-constexpr size_t kMaxTerms4 = size_t(1) << 22;
-
 }  // namespace
 
 double real_gaunt(int l1, int m1, int l2, int m2, int l3, int m3) {
@@ -149,186 +142,179 @@ int64_t basis_size(int n_max, int l_max, int nu_max) {
   return (int64_t)enumerate(n_max, l_max, nu_max).size();
 }
 
-bool build_terms(int n_max, int l_max, int nu_max, const double* c1, const double* c2,
-                 int64_t n_basis, HostTerms* out, std::string* err) {
+// The coupled evaluation.  Every basis function is one dot product of two
+// segments of a per-atom pool X = [1 | A | C]:
+//   nu = 1:  A_{n00} . 1
+//   nu = 2:  A_{p1} . A_{p2}                      (l1 = l2, length 2l + 1)
+//   nu = 3:  C_{(p1 p2) l3} . A_{p3}              (length 2 l3 + 1)
+//   nu = 4:  C_{(p1 p2) L} . C_{(p3 p4) L}        (length 2L + 1)
+// with A_p = (A_{n l m})_{m=-l..l} for p = (n, l) and the couplings
+//   C_{(p1 p2) L M} = sum_{m1 m2} G(l1 m1, l2 m2, L M) A_{p1 m1} A_{p2 m2}.
+// This is the same polynomial as the basis definition (the Gaunt sums are only
+// grouped differently), and the reverse pass follows the same structure:
+//   dE/dX_s = sum over the records touching segment s of k_b X_partner,
+//   k_b = c1_b + F'(phi_2) c2_b (a record with both sides on s counts twice),
+// then dE/dC is pushed back onto A through the Gaunt entries.
+bool build_coupled(int n_max, int l_max, int nu_max, const double* c1, const double* c2, int64_t n_basis,
+                   HostAce* out, std::string* err) {
   const int nlm = (l_max + 1) * (l_max + 1);
   const int nA = n_max * nlm;
-  if (nA > 254) { *err = "n_max (l_max+1)^2 must be <= 254"; return false; }
   const auto basis = enumerate(n_max, l_max, nu_max);
   if ((int64_t)basis.size() != n_basis) {
     *err = "ace_n_basis does not match the canonical basis size " + std::to_string(basis.size());
     return false;
   }
-  const int one = nA;
-  auto aidx = [&](int n, int l, int m) { return (n - 1) * nlm + l * l + l + m; };
-  // Gaunt cache for (l1, l2, l3) with m's.
-  std::map<std::tuple<int, int, int, int, int, int>, double> gcache;
-  auto G = [&](int l1, int m1, int l2, int m2, int l3, int m3) {
-    auto key = std::make_tuple(l1, m1, l2, m2, l3, m3);
-    auto it = gcache.find(key);
-    if (it != gcache.end()) return it->second;
-    const double v = real_gaunt(l1, m1, l2, m2, l3, m3);
-    gcache.emplace(key, v);
-    return v;
+  // pool offset of A_{n l m = -l}
+  auto aoff = [&](int n, int l) { return 1 + (n - 1) * nlm + l * l; };
+  struct Coupling { int n1, l1, n2, l2, L, off; };
+  std::vector<Coupling> coup;
+  std::map<std::tuple<int, int, int, int, int>, int> cidx;
+  int next = 1 + nA;
+  auto coupling = [&](int n1, int l1, int n2, int l2, int L) {
+    const auto key = std::make_tuple(n1, l1, n2, l2, L);
+    auto it = cidx.find(key);
+    if (it != cidx.end()) return coup[it->second].off;
+    cidx.emplace(key, (int)coup.size());
+    coup.push_back({n1, l1, n2, l2, L, next});
+    next += 2 * L + 1;
+    return coup.back().off;
   };
-  std::map<uint32_t, Coef> t3;
-  std::unordered_map<uint32_t, Coef> t4;
-  // nonzero G(l1 m1, l2 m2, L M) as (m1, m2, M, g), per (l1, l2, L)
-  std::map<std::tuple<int, int, int>, std::vector<std::tuple<int, int, int, double>>> glist;
-  auto GL = [&](int l1, int l2, int L) -> const std::vector<std::tuple<int, int, int, double>>& {
-    auto key = std::make_tuple(l1, l2, L);
-    auto it = glist.find(key);
-    if (it != glist.end()) return it->second;
-    std::vector<std::tuple<int, int, int, double>> v;
-    for (int M = -L; M <= L; ++M)
-      for (int m1 = -l1; m1 <= l1; ++m1)
-        for (int m2 = -l2; m2 <= l2; ++m2) {
-          const double g = G(l1, m1, l2, m2, L, M);
-          if (g != 0.0) v.emplace_back(m1, m2, M, g);
-        }
-    return glist.emplace(key, std::move(v)).first->second;
-  };
-  auto add3 = [&](int a, int b, int c, double w, double ca, double cb) {
-    int v[3] = {a, b, c};
-    std::sort(v, v + 3);
-    const uint32_t key = (uint32_t)v[0] | ((uint32_t)v[1] << 8) | ((uint32_t)v[2] << 16);
-    Coef& k = t3[key];
-    k.a += w * ca;
-    k.b += w * cb;
-  };
-  auto add4 = [&](int a, int b, int c, int d, double w, double ca, double cb) {
-    int v[4] = {a, b, c, d};
-    std::sort(v, v + 4);
-    const uint32_t key = (uint32_t)v[0] | ((uint32_t)v[1] << 8) | ((uint32_t)v[2] << 16) | ((uint32_t)v[3] << 24);
-    Coef& k = t4[key];
-    k.a += w * ca;
-    k.b += w * cb;
-  };
+  struct F { int o1, o2, len; double a, b; };
+  std::vector<F> recs;
+  recs.reserve(basis.size());
   for (size_t bi = 0; bi < basis.size(); ++bi) {
     const Basis& b = basis[bi];
-    const double ca = c1[bi], cb = c2[bi];
+    F r{0, 0, 0, c1[bi], c2[bi]};
     if (b.nu == 1) {
-      add3(aidx(b.n[0], 0, 0), one, one, 1.0, ca, cb);
+      r.o1 = aoff(b.n[0], 0); r.o2 = 0; r.len = 1;
     } else if (b.nu == 2) {
-      const int l = b.l[0];
-      for (int m = -l; m <= l; ++m) add3(aidx(b.n[0], l, m), aidx(b.n[1], l, m), one, 1.0, ca, cb);
+      r.o1 = aoff(b.n[0], b.l[0]); r.o2 = aoff(b.n[1], b.l[1]); r.len = 2 * b.l[0] + 1;
     } else if (b.nu == 3) {
-      const int l1 = b.l[0], l2 = b.l[1], l3 = b.l[2];
-      for (int m1 = -l1; m1 <= l1; ++m1)
-        for (int m2 = -l2; m2 <= l2; ++m2)
-          for (int m3 = -l3; m3 <= l3; ++m3) {
-            const double g = G(l1, m1, l2, m2, l3, m3);
-            if (g != 0.0) add3(aidx(b.n[0], l1, m1), aidx(b.n[1], l2, m2), aidx(b.n[2], l3, m3), g, ca, cb);
-          }
+      r.o1 = coupling(b.n[0], b.l[0], b.n[1], b.l[1], b.l[2]);
+      r.o2 = aoff(b.n[2], b.l[2]);
+      r.len = 2 * b.l[2] + 1;
     } else {
-      const int l1 = b.l[0], l2 = b.l[1], l3 = b.l[2], l4 = b.l[3], L = b.L;
-      const auto& a12 = GL(l1, l2, L);
-      const auto& a34 = GL(l3, l4, L);
-      for (const auto& x : a12)
-        for (const auto& y : a34) {
-          if (std::get<2>(x) != std::get<2>(y)) continue;
-          add4(aidx(b.n[0], l1, std::get<0>(x)), aidx(b.n[1], l2, std::get<1>(x)),
-               aidx(b.n[2], l3, std::get<0>(y)), aidx(b.n[3], l4, std::get<1>(y)),
-               std::get<3>(x) * std::get<3>(y), ca, cb);
-        }
-      if (t4.size() > kMaxTerms4) {
-        *err = "nu_max = 4 expands to more than " + std::to_string(kMaxTerms4) +
-               " product terms for this (n_max, l_max); not supported by the term-list kernel";
-        return false;
+      r.o1 = coupling(b.n[0], b.l[0], b.n[1], b.l[1], b.L);
+      r.o2 = coupling(b.n[2], b.l[2], b.n[3], b.l[3], b.L);
+      r.len = 2 * b.L + 1;
+    }
+    recs.push_back(r);
+  }
+  const int npool = next;
+  if (npool > 65535) { *err = "ACE pool of " + std::to_string(npool) + " values exceeds 65535"; return false; }
+  out->nA = nA;
+  out->nC = npool - 1 - nA;
+  out->npool = npool;
+
+  // Gaunt entries per (l1, l2, L, M), shared by all couplings of those degrees
+  std::map<std::tuple<int, int, int, int>, std::pair<int, int>> glist;
+  out->gkey.clear(); out->gval.clear(); out->comp.clear();
+  auto gaunt_list = [&](int l1, int l2, int L, int M) {
+    const auto key = std::make_tuple(l1, l2, L, M);
+    auto it = glist.find(key);
+    if (it != glist.end()) return it->second;
+    const int beg = (int)out->gval.size();
+    for (int m1 = -l1; m1 <= l1; ++m1)
+      for (int m2 = -l2; m2 <= l2; ++m2) {
+        const double g = real_gaunt(l1, m1, l2, m2, L, M);
+        if (g == 0.0) continue;
+        out->gkey.push_back((uint32_t)(m1 + l1) | ((uint32_t)(m2 + l2) << 8));
+        out->gval.push_back(g);
       }
-    }
-  }
-  out->key3.clear(); out->k3a.clear(); out->k3b.clear();
-  out->key4.clear(); out->k4a.clear(); out->k4b.clear();
-  for (const auto& kv : t3) {
-    if (kv.second.a == 0.0 && kv.second.b == 0.0) continue;
-    out->key3.push_back(kv.first);
-    out->k3a.push_back(kv.second.a);
-    out->k3b.push_back(kv.second.b);
-  }
-  std::vector<std::pair<uint32_t, Coef>> s4(t4.begin(), t4.end());
-  std::sort(s4.begin(), s4.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
-  for (const auto& kv : s4) {
-    if (kv.second.a == 0.0 && kv.second.b == 0.0) continue;
-    out->key4.push_back(kv.first);
-    out->k4a.push_back(kv.second.a);
-    out->k4b.push_back(kv.second.b);
-  }
-  // Derivative entries: d phi_c / dA[tgt] = sum_e K_c[e] A[a] A[b] A[c] over the
-  // entries e with target tgt, one per (term, position of tgt) and merged when the
-  // remaining index triple coincides.  Key = tgt << 24 | a | b << 8 | c << 16 with
-  // a <= b <= c (index nA = the constant 1), so the list is sorted by target.
-  std::map<uint32_t, Coef> td;
-  auto add_d = [&](int tgt, int a, int b, int c, const Coef& k) {
-    if (tgt == one) return;
-    int v[3] = {a, b, c};
-    std::sort(v, v + 3);
-    const uint32_t key = ((uint32_t)tgt << 24) | (uint32_t)v[0] | ((uint32_t)v[1] << 8) | ((uint32_t)v[2] << 16);
-    Coef& e = td[key];
-    e.a += k.a;
-    e.b += k.b;
+    const std::pair<int, int> v{beg, (int)out->gval.size() - beg};
+    glist.emplace(key, v);
+    return v;
   };
-  for (size_t q = 0; q < out->key3.size(); ++q) {
-    const uint32_t k = out->key3[q];
-    const int i0 = k & 255u, i1 = (k >> 8) & 255u, i2 = (k >> 16) & 255u;
-    const Coef c{out->k3a[q], out->k3b[q]};
-    add_d(i0, i1, i2, one, c);
-    add_d(i1, i0, i2, one, c);
-    add_d(i2, i0, i1, one, c);
-  }
-  for (size_t q = 0; q < out->key4.size(); ++q) {
-    const uint32_t k = out->key4[q];
-    const int i0 = k & 255u, i1 = (k >> 8) & 255u, i2 = (k >> 16) & 255u, i3 = k >> 24;
-    const Coef c{out->k4a[q], out->k4b[q]};
-    add_d(i0, i1, i2, i3, c);
-    add_d(i1, i0, i2, i3, c);
-    add_d(i2, i0, i1, i3, c);
-    add_d(i3, i0, i1, i2, c);
-  }
-  // The entries, sorted by target (the map order), are cut into chunks of
-  // kAceChunk that the kernel streams through shared memory.  Inside a chunk each
-  // target forms one contiguous piece; pieces go to the kAceAdjWarps warps,
-  // largest first to the least-loaded warp, so no two warps of a chunk write the
-  // same omega component (a target split across chunks is summed chunk by chunk).
-  out->keyd.clear(); out->kda.clear(); out->kdb.clear(); out->sched.clear();
-  for (const auto& kv : td) {
-    if (kv.second.a == 0.0 && kv.second.b == 0.0) continue;
-    out->keyd.push_back(kv.first);
-    out->kda.push_back(kv.second.a);
-    out->kdb.push_back(kv.second.b);
-  }
-  const int ne = (int)out->keyd.size();
-  const int nch = (ne + kAceChunk - 1) / kAceChunk;
-  std::vector<int> choff(nch + 1), woff, triples;
-  for (int c = 0; c <= nch; ++c) choff[c] = std::min(ne, c * kAceChunk);
-  woff.push_back(0);
-  for (int c = 0; c < nch; ++c) {
-    std::vector<std::array<int, 3>> pieces;  // (target, rel start, rel end)
-    for (int q = choff[c]; q < choff[c + 1];) {
-      const int t = (int)(out->keyd[q] >> 24);
-      int e = q;
-      while (e < choff[c + 1] && (int)(out->keyd[e] >> 24) == t) ++e;
-      pieces.push_back({t, q - choff[c], e - choff[c]});
-      q = e;
+  // one entry per C component, in pool order
+  std::vector<std::array<int, 4>> comps;   // (a1, a2, gofs, gcnt)
+  for (const Coupling& u : coup)
+    for (int M = -u.L; M <= u.L; ++M) {
+      const auto gl = gaunt_list(u.l1, u.l2, u.L, M);
+      comps.push_back({aoff(u.n1, u.l1), aoff(u.n2, u.l2), gl.first, gl.second});
+      out->comp.push_back((uint32_t)aoff(u.n1, u.l1) | ((uint32_t)aoff(u.n2, u.l2) << 16));
+      out->comp.push_back(((uint32_t)gl.first << 8) | (uint32_t)gl.second);
     }
-    std::stable_sort(pieces.begin(), pieces.end(),
-                     [](const auto& x, const auto& y) { return x[2] - x[1] > y[2] - y[1]; });
-    std::vector<std::vector<std::array<int, 3>>> bins(kAceAdjWarps);
-    std::vector<int> load(kAceAdjWarps, 0);
-    for (const auto& pc : pieces) {
-      const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-      bins[b].push_back(pc);
-      load[b] += pc[2] - pc[1];
-    }
-    for (int b = 0; b < kAceAdjWarps; ++b) {
-      for (const auto& pc : bins[b]) triples.insert(triples.end(), pc.begin(), pc.end());
-      woff.push_back((int)(triples.size() / 3));
+  if (out->gval.size() >= (size_t(1) << 24)) { *err = "too many Gaunt entries"; return false; }
+
+  // forward records, grouped by length so that the lanes of a warp run the same loop
+  std::vector<F> fw(recs);
+  std::stable_sort(fw.begin(), fw.end(), [](const F& x, const F& y) {
+    return std::make_tuple(x.len, x.o1, x.o2) < std::make_tuple(y.len, y.o1, y.o2);
+  });
+  out->fkey.clear(); out->flen.clear(); out->f1.clear(); out->f2.clear();
+  for (const F& r : fw) {
+    out->fkey.push_back((uint32_t)r.o1 | ((uint32_t)r.o2 << 16));
+    out->flen.push_back((uint32_t)r.len);
+    out->f1.push_back(r.a);
+    out->f2.push_back(r.b);
+  }
+
+  // reverse rows per segment (segment = A_p or C_u; the constant has none)
+  std::vector<int> seg_of(npool, -1), seg_start(npool, 0);
+  for (int n = 1; n <= n_max; ++n)
+    for (int l = 0; l <= l_max; ++l)
+      for (int m = 0; m < 2 * l + 1; ++m) { seg_of[aoff(n, l) + m] = aoff(n, l); seg_start[aoff(n, l) + m] = aoff(n, l); }
+  for (const Coupling& u : coup)
+    for (int m = 0; m < 2 * u.L + 1; ++m) { seg_of[u.off + m] = u.off; seg_start[u.off + m] = u.off; }
+  std::map<int, std::vector<std::array<double, 3>>> rows;   // segment -> (partner, c1, c2)
+  for (const F& r : recs) {
+    if (r.o1 == r.o2) {
+      rows[r.o1].push_back({(double)r.o2, 2.0 * r.a, 2.0 * r.b});
+    } else {
+      if (r.o1 != 0) rows[r.o1].push_back({(double)r.o2, r.a, r.b});
+      if (r.o2 != 0) rows[r.o2].push_back({(double)r.o1, r.a, r.b});
     }
   }
-  out->sched.push_back(nch);
-  out->sched.insert(out->sched.end(), choff.begin(), choff.end());
-  out->sched.insert(out->sched.end(), woff.begin(), woff.end());
-  out->sched.insert(out->sched.end(), triples.begin(), triples.end());
+  std::map<int, std::pair<int, int>> row_range;
+  out->rkey.clear(); out->r1.clear(); out->r2.clear();
+  for (const auto& kv : rows) {
+    const int beg = (int)out->rkey.size();
+    for (const auto& e : kv.second) {
+      out->rkey.push_back((uint32_t)e[0]);
+      out->r1.push_back(e[1]);
+      out->r2.push_back(e[2]);
+    }
+    row_range[kv.first] = {beg, (int)out->rkey.size()};
+  }
+  out->qrow.assign((size_t)4 * npool, 0);
+  for (int q = 1; q < npool; ++q) {
+    const auto it = row_range.find(seg_of[q]);
+    if (it != row_range.end()) {
+      out->qrow[4 * q] = it->second.first;
+      out->qrow[4 * q + 1] = it->second.second;
+    }
+    out->qrow[4 * q + 2] = q - seg_start[q];
+  }
+
+  // C -> A entries, grouped by target A component (pool index - 1), cut into
+  // pieces; the partial sums of the pieces are kept in the C part of the pool,
+  // so there may be at most nC pieces
+  std::vector<std::vector<std::pair<uint32_t, double>>> tgt(nA);
+  for (int c = 0; c < out->nC; ++c) {
+    const int qc = 1 + nA + c;
+    const auto& cp = comps[c];
+    for (int e = cp[2]; e < cp[2] + cp[3]; ++e) {
+      const int i = out->gkey[e] & 255u, j = out->gkey[e] >> 8;
+      const double g = out->gval[e];
+      tgt[cp[0] + i - 1].push_back({(uint32_t)qc | ((uint32_t)(cp[1] + j) << 16), g});
+      tgt[cp[1] + j - 1].push_back({(uint32_t)qc | ((uint32_t)(cp[0] + i) << 16), g});
+    }
+  }
+  out->bkey.clear(); out->bval.clear(); out->poff.clear(); out->tpiece.clear();
+  for (const auto& v : tgt)
+    for (const auto& e : v) { out->bkey.push_back(e.first); out->bval.push_back(e.second); }
+  for (int piece = 32;; piece *= 2) {
+    out->poff.assign(1, 0);
+    out->tpiece.assign(1, 0);
+    int pos = 0;
+    for (int t = 0; t < nA; ++t) {
+      const int cnt = (int)tgt[t].size();
+      for (int s = 0; s < cnt; s += piece) out->poff.push_back(pos + std::min(cnt, s + piece));
+      pos += cnt;
+      out->tpiece.push_back((int)out->poff.size() - 1);
+    }
+    if ((int)out->poff.size() - 1 <= out->nC) break;
+  }
   return true;
 }
 

@@ -76,7 +76,7 @@ void free_all(apip_ctx* c) {
   void* ptrs[] = {c->cell_count, c->cell_atoms, c->nnb, c->nbl, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->counts, c->flags, c->status, c->partials, c->thermo_part,
-                  c->e_scratch, c->rec3, c->rec4, c->recd, c->sched, c->mlp_w, c->mlp_ws};
+                  c->e_scratch, c->ace_tab, c->mlp_w, c->mlp_ws};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -89,7 +89,8 @@ apip_status check_params(const apip_params* p, std::string* why) {
   if (p->ace_l_max < 0 || p->ace_l_max > kLmaxCap) return bad("ace_l_max must be in [0, 4]");
   if (p->ace_nu_max < 1 || p->ace_nu_max > 4) return bad("ace_nu_max must be in [1, 4]");
   if (p->ace_n_max * (p->ace_l_max + 1) * (p->ace_l_max + 1) > 254) return bad("n_max (l_max+1)^2 must be <= 254");
-  if (p->ace_group != 0 && p->ace_group != 1 && p->ace_group != 8) return bad("ace_group must be 0, 1 or 8");
+  if (p->ace_group != 0 && p->ace_group != 1 && p->ace_group != 2 && p->ace_group != 4 && p->ace_group != 8)
+    return bad("ace_group must be 0, 1, 2, 4 or 8");
   if (!p->ace_c1 || !p->ace_c2) return bad("ace_c1 / ace_c2 must not be NULL");
   if (!(p->ace_rc > 0 && p->ace_rc_width > 0 && p->ace_rc_width <= p->ace_rc)) return bad("bad ACE cutoff");
   if (!(p->ace_eps > 0)) return bad("ace_eps must be > 0");
@@ -210,12 +211,20 @@ AceDev<T> ace_dev(apip_ctx* c) {
   t.eps = T(p.ace_eps);
   t.sqrt_eps = T(std::sqrt(p.ace_eps));
   t.a_scale = T(p.ace_a_scale);
-  t.rec3 = as<Rec<T>>(c->rec3); t.n3 = c->n3;
-  t.rec4 = as<Rec<T>>(c->rec4); t.n4 = c->n4;
-  t.recd = as<Rec<T>>(c->recd); t.nd = c->nd;
-  t.sched = c->sched;
-  t.group = p.ace_group != 0 ? p.ace_group
-                             : ((p.lam_mode == APIP_LAM_PAPER || p.lam_mode == APIP_LAM_LEARNED) ? 1 : 8);
+  t.nC = c->ace_nC;
+  t.npool = c->ace_npool;
+  unsigned char* b = static_cast<unsigned char*>(c->ace_tab);
+  t.comp = reinterpret_cast<const uint2*>(b + c->ace_off[0]);
+  t.gent = reinterpret_cast<const Ent<T>*>(b + c->ace_off[1]);
+  t.frec = reinterpret_cast<const Rec<T>*>(b + c->ace_off[2]);
+  t.nf = c->ace_nf;
+  t.qrow = reinterpret_cast<const int4*>(b + c->ace_off[3]);
+  t.arec = reinterpret_cast<const Rec<T>*>(b + c->ace_off[4]);
+  t.bent = reinterpret_cast<const Ent<T>*>(b + c->ace_off[5]);
+  t.poff = reinterpret_cast<const int*>(b + c->ace_off[6]);
+  t.npc = c->ace_npc;
+  t.tpiece = reinterpret_cast<const int*>(b + c->ace_off[7]);
+  t.group = c->ace_group;
   return t;
 }
 
@@ -354,9 +363,9 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   ctx->p.ace_c2 = nullptr;
   ctx->nmax = n_atoms_max;
   ctx->r_list = std::max(std::max(p->eam_rc, p->ace_rc), p->sw_r_w) + p->skin;
-  HostTerms terms;
-  if (!build_terms(p->ace_n_max, p->ace_l_max, p->ace_nu_max, ctx->ace_c1.data(), ctx->ace_c2.data(), nb, &terms,
-                   &why)) {
+  HostAce tab;
+  if (!build_coupled(p->ace_n_max, p->ace_l_max, p->ace_nu_max, ctx->ace_c1.data(), ctx->ace_c2.data(), nb, &tab,
+                     &why)) {
     delete ctx;
     return APIP_ERR_ARG;
   }
@@ -374,7 +383,35 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   cudaGetDevice(&ctx->dev);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->dev);
-  ctx->ace_blocks = std::max(1, sms) * 8;
+  // atoms per ACE block: the largest group whose pools leave room for two
+  // resident blocks per SM, else the largest that fits at all
+  {
+    const bool f32 = p->precision == APIP_FP32;
+    auto occ_of = [&](int g) {
+      size_t bytes = 0;
+      return f32 ? ace_occupancy<float>(p->ace_l_max, g, tab.npool, &bytes)
+                 : ace_occupancy<double>(p->ace_l_max, g, tab.npool, &bytes);
+    };
+    int group = p->ace_group, occ = 0;
+    if (group != 0) {
+      occ = occ_of(group);
+    } else {
+      for (int g : {8, 4, 2, 1}) {
+        const int o = occ_of(g);
+        if (o >= 2 || (o >= 1 && g == 1)) { group = g; occ = o; break; }
+      }
+      if (occ == 0)
+        for (int g : {8, 4, 2, 1})
+          if ((occ = occ_of(g)) >= 1) { group = g; break; }
+    }
+    cudaGetLastError();
+    if (occ < 1) {
+      delete ctx;
+      return APIP_ERR_ARG;
+    }
+    ctx->ace_group = group;
+    ctx->ace_blocks = std::max(1, sms) * occ;
+  }
   const size_t N = (size_t)n_atoms_max;
   const size_t es = esize(ctx);
   APIP_ALLOC(ctx->nnb, sizeof(int) * N);
@@ -398,32 +435,65 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->thermo_part, sizeof(double) * 4 * p1);
   APIP_ALLOC(ctx->e_scratch, sizeof(double) * 2);
   APIP_ALLOC(ctx->mlp_w, es * APIP_MLP_NPARAM);
-  ctx->n3 = (int)terms.key3.size();
-  ctx->n4 = (int)terms.key4.size();
-  ctx->nd = (int)terms.keyd.size();
-  const size_t rs = p->precision == APIP_FP32 ? sizeof(Rec<float>) : sizeof(Rec<double>);
-  APIP_ALLOC(ctx->rec3, rs * std::max(1, ctx->n3));
-  APIP_ALLOC(ctx->rec4, rs * std::max(1, ctx->n4));
-  APIP_ALLOC(ctx->recd, rs * std::max(1, ctx->nd));
-  APIP_ALLOC(ctx->sched, sizeof(int) * terms.sched.size());
-#undef APIP_ALLOC
-  auto upload = [&](void* dst, const std::vector<uint32_t>& key, const std::vector<double>& a,
-                    const std::vector<double>& b) -> cudaError_t {
-    if (key.empty()) return cudaSuccess;
-    if (p->precision == APIP_FP64) {
-      std::vector<Rec<double>> r(key.size());
-      for (size_t q = 0; q < key.size(); ++q) r[q] = Rec<double>{key[q], 0u, a[q], b[q], 0ull};
-      return cudaMemcpy(dst, r.data(), sizeof(Rec<double>) * r.size(), cudaMemcpyHostToDevice);
-    }
-    std::vector<Rec<float>> r(key.size());
-    for (size_t q = 0; q < key.size(); ++q) r[q] = Rec<float>{key[q], (float)a[q], (float)b[q], 0u};
-    return cudaMemcpy(dst, r.data(), sizeof(Rec<float>) * r.size(), cudaMemcpyHostToDevice);
+  // ACE tables: one buffer, sub-arrays 256-byte aligned
+  const bool f32 = p->precision == APIP_FP32;
+  std::vector<unsigned char> host;
+  auto put = [&](int slot, const void* src, size_t bytes) {
+    const size_t off = (host.size() + 255) / 256 * 256;
+    host.resize(off + std::max<size_t>(bytes, 16));
+    if (bytes) std::memcpy(host.data() + off, src, bytes);
+    ctx->ace_off[slot] = off;
   };
-  cudaError_t e = upload(ctx->rec3, terms.key3, terms.k3a, terms.k3b);
-  if (e == cudaSuccess) e = upload(ctx->rec4, terms.key4, terms.k4a, terms.k4b);
-  if (e == cudaSuccess) e = upload(ctx->recd, terms.keyd, terms.kda, terms.kdb);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(ctx->sched, terms.sched.data(), sizeof(int) * terms.sched.size(), cudaMemcpyHostToDevice);
+  auto put_ent = [&](int slot, const std::vector<uint32_t>& key, const std::vector<double>& v) {
+    if (f32) {
+      std::vector<Ent<float>> r(key.size());
+      for (size_t q = 0; q < key.size(); ++q) r[q] = Ent<float>{(float)v[q], key[q]};
+      put(slot, r.data(), sizeof(Ent<float>) * r.size());
+    } else {
+      std::vector<Ent<double>> r(key.size());
+      for (size_t q = 0; q < key.size(); ++q) r[q] = Ent<double>{v[q], key[q]};
+      put(slot, r.data(), sizeof(Ent<double>) * r.size());
+    }
+  };
+  auto put_rec = [&](int slot, const std::vector<uint32_t>& key, const std::vector<uint32_t>* len,
+                     const std::vector<double>& k1, const std::vector<double>& k2) {
+    if (f32) {
+      std::vector<Rec<float>> r(key.size());
+      for (size_t q = 0; q < key.size(); ++q) r[q] = Rec<float>{key[q], len ? (*len)[q] : 0u, (float)k1[q], (float)k2[q]};
+      put(slot, r.data(), sizeof(Rec<float>) * r.size());
+    } else {
+      std::vector<Rec<double>> r(key.size());
+      for (size_t q = 0; q < key.size(); ++q) r[q] = Rec<double>{key[q], len ? (*len)[q] : 0u, k1[q], k2[q]};
+      put(slot, r.data(), sizeof(Rec<double>) * r.size());
+    }
+  };
+  put(0, tab.comp.data(), sizeof(uint32_t) * tab.comp.size());
+  put_ent(1, tab.gkey, tab.gval);
+  put_rec(2, tab.fkey, &tab.flen, tab.f1, tab.f2);
+  put(3, tab.qrow.data(), sizeof(int) * tab.qrow.size());
+  put_rec(4, tab.rkey, nullptr, tab.r1, tab.r2);
+  put_ent(5, tab.bkey, tab.bval);
+  put(6, tab.poff.data(), sizeof(int) * tab.poff.size());
+  put(7, tab.tpiece.data(), sizeof(int) * tab.tpiece.size());
+  ctx->ace_nC = tab.nC;
+  ctx->ace_npool = tab.npool;
+  ctx->ace_nf = (int)tab.fkey.size();
+  ctx->ace_npc = (int)tab.poff.size() - 1;
+  {
+    int64_t* info = ctx->ace_info;
+    info[0] = tab.npool;
+    info[1] = tab.nC;
+    for (int c = 0; c < tab.nC; ++c) info[2] += tab.comp[2 * c + 1] & 255u;
+    info[3] = (int64_t)tab.fkey.size();
+    for (uint32_t l : tab.flen) info[4] += l;
+    for (int q = 1; q < tab.npool; ++q) info[5] += tab.qrow[4 * q + 1] - tab.qrow[4 * q];
+    info[6] = (int64_t)tab.bkey.size();
+    info[7] = ctx->ace_group;
+    info[8] = ctx->ace_blocks;
+  }
+  APIP_ALLOC(ctx->ace_tab, host.size());
+#undef APIP_ALLOC
+  cudaError_t e = cudaMemcpy(ctx->ace_tab, host.data(), host.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(ctx->id2idx, 0xff, sizeof(int) * N);
   if (e == cudaSuccess) e = cudaMemset(ctx->csp, 0xff, sizeof(int) * N * kCspCap);
   if (e == cudaSuccess) e = cudaMemset(ctx->cvec, 0, sizeof(double) * N);
@@ -633,6 +703,12 @@ apip_status apip_profile_read(apip_ctx* ctx, double* ms, int64_t* launches) {
     ctx->prof_ms[k] = 0.0;
     ctx->prof_n[k] = 0;
   }
+  return APIP_OK;
+}
+
+apip_status apip_ace_info(apip_ctx* ctx, int64_t* out) {
+  if (!ctx || !out) return APIP_ERR_ARG;
+  for (int k = 0; k < APIP_ACE_INFO_COUNT; ++k) out[k] = ctx->ace_info[k];
   return APIP_OK;
 }
 

@@ -16,9 +16,8 @@ constexpr int kNmaxCap = 8;    // largest n_max
 constexpr int kLmaxCap = 4;    // largest l_max
 constexpr int kCspCap = 8;     // largest csp_nnb
 constexpr int kBlock = 256;    // threads per block of the all-atom passes
-constexpr int kAceAdjWarps = 8;            // warps per ACE block
-constexpr int kAceChunk = 1024;            // table records per shared-memory stage
-constexpr int kAceThreads = 32 * kAceAdjWarps;
+constexpr int kAceWarps = 8;               // warps per ACE block
+constexpr int kAceThreads = 32 * kAceWarps;
 
 // Device status words (apip_ctx::status)
 enum {
@@ -45,41 +44,47 @@ struct Geo {
 struct EamP { double A, beta, re, D, alpha, r0, rc, rc_lo, inv_w; };   // inv_w = 1/(rc - rc_lo)
 struct SwP { double r_w, r_w_lo, d_lo, d_hi, d0, inv_w, inv_d; };  // 1/(r_w - r_w_lo), 1/(d_hi - d_lo)
 
-// One record of an ACE table: packed 8-bit A indices and the coefficients of the
-// two embedding channels; 16-byte aligned so that chunks of records can be
-// copied into shared memory by bulk asynchronous copies.
-template <typename T> struct Rec;
-template <> struct alignas(16) Rec<float> { uint32_t key; float k1, k2; uint32_t pad; };
-template <> struct alignas(16) Rec<double> { uint32_t key, pad; double k1, k2; uint64_t pad2; };
+// ACE table entries.  Rec: a forward record (key = o1 | o2 << 16, len = the
+// segment length, k1/k2 = the coefficients of the two embedding channels) or a
+// reverse-row entry (key = the partner segment's pool offset).  Ent: a Gaunt
+// entry (key = (m1 + l1) | (m2 + l2) << 8) or a C -> A entry
+// (key = C pool index | other A pool index << 16), v = the coefficient.
+template <typename T> struct alignas(sizeof(T) == 4 ? 16 : 8) Rec { uint32_t key, len; T k1, k2; };
+template <typename T> struct alignas(sizeof(T) == 4 ? 8 : 16) Ent { T v; uint32_t key; };
 
-// ACE tables on the device: terms of the folded product basis,
-//   phi_c = sum_t K_c[t] prod_{q} A[idx_q(t)],  c = 1, 2,
-// with A[nA] == 1 padding the lower body orders.  Keys hold 8-bit indices.
+// Coupled ACE tables on the device (built by build_coupled).  Per atom the pool
+// X = [1 | A (nA) | C (nC)] holds the atomic density and its Gaunt couplings;
+// every basis function is the dot product of two pool segments.
 template <typename T>
 struct AceDev {
-  int n_max, l_max, nA;         // nA = n_max (l_max+1)^2
+  int n_max, l_max, nA, nC, npool;   // nA = n_max (l_max+1)^2, npool = 1 + nA + nC
   T rc, rc_lo, eps, sqrt_eps, a_scale;
-  const Rec<T>* rec3; int n3;   // 3-index terms
-  const Rec<T>* rec4; int n4;   // 4-index terms
-  const Rec<T>* recd; int nd;   // derivative entries, sorted by target
-  const int* sched;             // adjoint schedule (HostTerms::sched)
-  int group;                    // compacted atoms per thread block (1 or 8)
+  const uint2* comp;            // [nC]: (a1 | a2 << 16, gofs << 8 | gcnt) per C component
+  const Ent<T>* gent;           // Gaunt entries
+  const Rec<T>* frec; int nf;   // forward records, grouped by length
+  const int4* qrow;             // [npool]: reverse row (begin, end) of the segment of q, m = q - segment start
+  const Rec<T>* arec;           // reverse-row entries
+  const Ent<T>* bent;           // C -> A entries, grouped by target
+  const int* poff; int npc;     // [npc + 1] piece boundaries in bent
+  const int* tpiece;            // [nA + 1] first piece of each target A component
+  int group;                    // compacted atoms per thread block (1, 2, 4 or 8)
 };
 
-struct HostTerms {
-  std::vector<uint32_t> key3, key4, keyd;
-  std::vector<double> k3a, k3b, k4a, k4b, kda, kdb;
-  // adjoint schedule: sched[0] = number of chunks nch; then nch + 1 entry offsets
-  // of the chunks; then nch * kAceAdjWarps + 1 offsets (in pieces) of the pieces of
-  // chunk c, warp w at index c * kAceAdjWarps + w; then the pieces as (target,
-  // start, end) relative to their chunk
-  std::vector<int> sched;
+struct HostAce {
+  int nA = 0, nC = 0, npool = 0;
+  std::vector<uint32_t> comp;                 // [2 nC]
+  std::vector<uint32_t> gkey; std::vector<double> gval;
+  std::vector<uint32_t> fkey, flen; std::vector<double> f1, f2;
+  std::vector<int> qrow;                      // [4 npool]
+  std::vector<uint32_t> rkey; std::vector<double> r1, r2;
+  std::vector<uint32_t> bkey; std::vector<double> bval;
+  std::vector<int> poff, tpiece;
 };
 
 // ace_tables.cpp
 int64_t basis_size(int n_max, int l_max, int nu_max);
-bool build_terms(int n_max, int l_max, int nu_max, const double* c1, const double* c2,
-                 int64_t n_basis, HostTerms* out, std::string* err);
+bool build_coupled(int n_max, int l_max, int nu_max, const double* c1, const double* c2, int64_t n_basis,
+                   HostAce* out, std::string* err);
 // real Y_lm normalisation N_lm (times sqrt 2 for m != 0), index l^2 + l + m
 void ylm_norms(int l_max, double* out);
 // real Gaunt coefficient int Y_l1m1 Y_l2m2 Y_l3m3 dOmega (the library's own construction)
@@ -134,11 +139,13 @@ struct apip_ctx {
   double prof_ms[APIP_PHASE_COUNT] = {};
   int64_t prof_n[APIP_PHASE_COUNT] = {};
 
-  // ACE tables (element size = precision)
-  void* rec3 = nullptr; int n3 = 0;   // Rec<T> arrays
-  void* rec4 = nullptr; int n4 = 0;
-  void* recd = nullptr; int nd = 0;
-  int* sched = nullptr;
+  // ACE tables (element size = precision): one device buffer, sub-arrays at
+  // the byte offsets ace_off (order of AceDev's pointers)
+  void* ace_tab = nullptr;
+  size_t ace_off[8] = {};
+  int ace_nf = 0, ace_npc = 0, ace_nC = 0, ace_npool = 0;
+  int ace_group = 1;
+  int64_t ace_info[APIP_ACE_INFO_COUNT] = {};
 
   // learned indicator
   void* mlp_w = nullptr;       // APIP_MLP_NPARAM weights (element size = precision)

@@ -80,5 +80,8 @@ void launch_mlp_adam(float* p, const float* g, float* m, float* v, int t, float 
 // ACE (kernels_ace_f32.cu, kernels_ace_f64.cu)
 template <typename T> void ace_set_norms(const double* norms, int count);
 template <typename T> void launch_ace(const Args<T>& a, const AceDev<T>& ace, int blocks, cudaStream_t s);
+// resident blocks per SM of the ACE kernel for ace.group atoms per block and a
+// pool of npool values (0 if its shared memory does not fit); sets smem_bytes
+template <typename T> int ace_occupancy(int l_max, int group, int npool, size_t* smem_bytes);
 
 }  // namespace apip

@@ -22,4 +22,8 @@ template <> void launch_ace<float>(const Args<float>& a, const AceDev<float>& t,
   launch_ace_impl<float>(a, t, blocks, s);
 }
 
+template <> int ace_occupancy<float>(int l_max, int group, int npool, size_t* smem_bytes) {
+  return ace_occupancy_impl<float>(l_max, group, npool, smem_bytes);
+}
+
 }  // namespace apip

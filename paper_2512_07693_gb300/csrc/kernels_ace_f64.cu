@@ -19,4 +19,8 @@ template <> void launch_ace<double>(const Args<double>& a, const AceDev<double>&
   launch_ace_impl<double>(a, t, blocks, s);
 }
 
+template <> int ace_occupancy<double>(int l_max, int group, int npool, size_t* smem_bytes) {
+  return ace_occupancy_impl<double>(l_max, group, npool, smem_bytes);
+}
+
 }  // namespace apip

@@ -1,0 +1,73 @@
+"""Parity at full size: the 248 757-atom void crystal (float32 path, the launch
+configuration that bench.py times) evaluated once on the GPU, and sampled atoms
+checked one by one against the oracle.
+
+The oracle cannot run the whole crystal, but every per-atom output is local.
+E_j depends on the atoms within r_w = 5 A of j (ACE, EAM, the weights of d_j)
+and on the CSP partners of those atoms (detected within 4.5 A), so it depends
+on positions within 9.5 A of j; F_i = -dE/dx_i involves the E_j with j within
+9.5 A of i.  A cluster of all atoms within 20 A of the sampled atom, placed in
+an empty box, therefore reproduces E_i, lam_i and F_i exactly (up to rounding).
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import run_oracle, to_dev, torch_cuda
+from paper_2512_07693_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+R_CLUSTER = 20.0
+
+
+def _cluster(s, i):
+    d = s["pos"] - s["pos"][i]
+    d -= s["box"] * np.rint(d / s["box"])
+    keep = np.flatnonzero(np.sum(d * d, axis=1) < R_CLUSTER ** 2)
+    box = np.full(3, 2 * R_CLUSTER + 40.0)
+    pos = d[keep] + 0.5 * box
+    c = W._finish(pos, np.zeros_like(pos), box)
+    c["ids"] = s["ids"][keep].copy()
+    c["prm"] = s["prm"]
+    return c, int(np.flatnonzero(keep == i)[0])
+
+
+def test_void250k_full_size_sampled_atoms_fp32():
+    torch = torch_cuda()
+    from paper_2512_07693_gb300 import apip
+    s = W.config("void250k", apip.apip_ace_basis_size)
+    n = len(s["pos"])
+    assert n == 248757
+    m = apip.Apip(s["prm"], n, precision="fp32", lam_mode="paper", max_nb=80, cell_cap=48)
+    t = to_dev(torch, s)
+    box = [float(x) for x in s["box"]]
+    m.init_csp_pairs(t["pos"], box, t["ids"])
+    F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    e = torch.empty(n, dtype=torch.float64, device="cuda")
+    m.energy_forces(t["pos"], box, t["types"], t["ids"], F, e)
+    m.sync()
+    F = F.cpu().numpy()
+    e = e.cpu().numpy()
+    lam = m.field("lam", n).cpu().numpy()
+    dlam = m.field("dlam", n).cpu().numpy()
+    m.close()
+    assert np.abs(F.sum(axis=0)).max() < 1e-2     # 249 k atoms, float32 pair terms
+    rng = np.random.default_rng(11)
+    core = np.flatnonzero(lam == 1.0)
+    trans = np.flatnonzero((lam > 0) & (lam < 1) & (dlam != 0))
+    # fast atoms within r_w of the transition region carry grad-lambda forces
+    near = np.flatnonzero(lam == 0.0)
+    dc = s["pos"][near][:, None, :] - s["pos"][trans[:200]][None, :, :]
+    dc -= s["box"] * np.rint(dc / s["box"])
+    near = near[np.min(np.sum(dc * dc, axis=2), axis=1) < 25.0]
+    bulk = np.flatnonzero(lam == 0.0)
+    assert len(core) and len(trans) and len(near)
+    sample = np.concatenate([rng.choice(core, 2, replace=False), rng.choice(trans, 3, replace=False),
+                             rng.choice(near, 2, replace=False), rng.choice(bulk, 1)])
+    for i in sample:
+        c, k = _cluster(s, i)
+        o = run_oracle(c)
+        assert abs(lam[i] - o["lam"][k]) < 1e-5, (i, lam[i], o["lam"][k])
+        assert abs(e[i] - o["e_atom"][k]) <= 1e-5, (i, e[i], o["e_atom"][k])
+        err = np.abs(F[i] - o["F"][k]).max()
+        assert err <= 2e-4, (i, lam[i], err)

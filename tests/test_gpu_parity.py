@@ -67,9 +67,9 @@ def _check(s, prec="fp64", **kw):
     return g, o
 
 
-@pytest.mark.parametrize("prec,group", [("fp64", 0), ("fp32", 0), ("fp64", 8), ("fp32", 8)])
+@pytest.mark.parametrize("prec,group", [("fp64", 0), ("fp64", 1), ("fp64", 4), ("fp32", 0), ("fp32", 2), ("fp32", 8)])
 def test_mixed_system_parity(prec, group):
-    """group = compacted atoms per ACE thread block (0: automatic, 1 here)."""
+    """group = compacted atoms per ACE thread block (0: automatic)."""
     s = small()
     g, o = _check(s, prec, ace_group=group)
     # every regime is exercised
@@ -82,6 +82,29 @@ def test_nu4_ragged(prec):
     s = small(cells=(7, 6, 6), adds_eam=True, acecfg=(4, 3, 4), seed=5)
     assert len(s["pos"]) % 32 != 0
     _check(s, prec)
+
+
+_ORACLE_844 = {}
+
+
+def _crack_basis_system():
+    """The crack workload's basis (n_max 8, l_max 4, nu <= 4: 90970 functions,
+    a pool of 13188 values per atom) on a small vacancy crystal; the oracle result
+    is shared by the float64 and float32 cases."""
+    s = small(cells=(6, 6, 6), acecfg=(8, 4, 4), seed=9, d_lo=0.3, d_hi=0.9)
+    if "o" not in _ORACLE_844:
+        o = run_oracle(s)
+        o["switch_dlo"] = s["prm"]["switch"]["d_lo"]
+        _ORACLE_844["o"] = o
+    return s, _ORACLE_844["o"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_crack_basis_nu4_lmax4(prec):
+    s, o = _crack_basis_system()
+    assert len(o["P"]) > 10
+    g = run_gpu(s, precision=prec)
+    compare(g, o, prec)
 
 
 def test_pure_ace_precise_model_nu4_fp64():
@@ -227,6 +250,11 @@ def test_error_paths():
     with pytest.raises(apip.ApipError) as e:
         small_nb.sync()
     assert e.value.status == apip.APIP_ERR_NB_OVERFLOW and "max_nb = 20" in str(e.value)
+    # a group of atoms per ACE block whose pools exceed shared memory: rejected at
+    # creation (8 atoms x 2 pools x 1807 values x 8 bytes = 231 KB)
+    with pytest.raises(apip.ApipError) as e:
+        apip.Apip(s["prm"], n, precision="fp64", ace_group=8)
+    assert e.value.status == apip.APIP_ERR_ARG
     # empty system
     E = torch.ones(1, dtype=torch.float64, device="cuda")
     m.energy_forces(t["pos"][:0], box, t["types"][:0], t["ids"][:0], F[:0], e_total_out=E)
