@@ -45,9 +45,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ace-steps", type=int, default=5, help="steps of the all-ACE comparison run")
     ap.add_argument("--e2e-steps", type=int, default=50)
-    ap.add_argument("--ace-group", type=int, default=0, choices=[0, 1, 2, 4, 8],
+    ap.add_argument("--ace-group", type=int, default=0, choices=[0, 1, 2, 4, 8, 32],
                     help="compacted atoms per ACE thread block (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=None,
+                    help="scale the void workload to cells^3 (small cases for profiling; not the metric)")
     return ap.parse_args()
 
 
@@ -195,16 +197,13 @@ def timed_steps(torch, m, t, box, steps, flush, thermo=None):
 def ace_flops_per_atom(s, nnb_rc, info):
     """Algorithmic float32 operations of the ACE kernel per compacted atom, a
     multiply-add counted as 2: per neighbour within r_c, A accumulation 2 n NLM and
-    the force contraction (u, v) 4 n NLM + 8 NLM; per atom, the Gaunt couplings 3
-    per product, the basis dot products 2 per segment element + 4 per record (two
-    channels), the reverse rows 4 per row element, the C -> A entries 3 each.
-    Basis evaluation (R, Y) is not counted.  ``info`` = apip_ace_info."""
+    the force contraction (u, v) 4 n NLM + 8 NLM; plus the basis work forward and
+    adjoint as the library counts it from its tables (apip_ace_info
+    "table_flops").  Basis-function evaluation (R, Y) is not counted."""
     a = s["prm"]["ace"]
     nlm = (a["l_max"] + 1) ** 2
     per_nb = 2 * a["n_max"] * nlm + 4 * a["n_max"] * nlm + 8 * nlm
-    per_atom = (3 * info["gaunt_products"] + 2 * info["record_len_sum"] + 4 * info["records"]
-                + 4 * info["row_len_sum"] + 3 * info["c_to_a_entries"])
-    return nnb_rc * per_nb + per_atom, per_nb
+    return nnb_rc * per_nb + info["table_flops"], per_nb
 
 
 def run_ours(args):
@@ -221,7 +220,7 @@ def run_ours(args):
     build.build()
     from paper_2512_07693_gb300 import apip, workloads as W
 
-    s = W.config(WORKLOAD, apip.apip_ace_basis_size)
+    s = W.config(WORKLOAD, apip.apip_ace_basis_size, scale=args.cells)
     n = len(s["pos"])
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -337,7 +336,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "atoms": n, "ace": "n_max 6, l_max 3, nu<=3", "x_ace": x_ace,
+        "config": {"workload": WORKLOAD if args.cells is None else f"void recipe at {args.cells}^3 cells",
+                   "atoms": n, "ace": "n_max 6, l_max 3, nu<=3", "x_ace": x_ace,
                    "precision": "fp32 pair arithmetic, fp64 positions/velocities/forces/reductions",
                    "l2": "flushed (512 MB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "all_ace_atom_steps_per_s": all_ace * world,

@@ -68,6 +68,15 @@ enum { APIP_FP64 = 0, APIP_FP32 = 1 };
  *                  main text after Eq. 5); weights from apip_set_mlp. */
 enum { APIP_LAM_PAPER = 0, APIP_LAM_CONST0 = 1, APIP_LAM_CONST1 = 2, APIP_LAM_LEARNED = 3 };
 
+/* How the two models are combined.
+ * APIP_MIX_ENERGY: the conservative AP potential, E = sum_i [lam_i E_i^prec +
+ *   (1 - lam_i) E_i^EAM] (Eq. 4) and F = -grad E (Eq. 5).
+ * APIP_MIX_FORCE: force mixing (Eq. 3), the non-conservative comparison:
+ *   F_i = (1 - lam_i) F_i^EAM + lam_i F_i^prec with F^m = -grad sum_k E_k^m; the
+ *   precise model is evaluated on the atoms with lam > 0 and on every atom within
+ *   the ACE cutoff of one; grad_lambda is ignored.  The energy output is Eq. 4. */
+enum { APIP_MIX_ENERGY = 0, APIP_MIX_FORCE = 1 };
+
 /* Learned indicator network: radial descriptors
  *   G_im = sum_{j, r_ij < ace_rc} exp(-eta (r_ij - mu_m)^2) fc(r_ij),  m = 0..31,
  *   mu_m = 1.5 + m (5.0 - 1.5)/31 A, eta = 1/(2 * 0.15^2) A^-2, fc the ACE cutoff function,
@@ -97,11 +106,14 @@ typedef struct apip_params {
      order <= nu_max, E = c1.B + (( c2.B )^2 + eps^2)^(1/4) - sqrt(eps).
      n_max in [1, 8], l_max in [0, 4], nu_max in [1, 4], n_max (l_max+1)^2 <= 254. */
   int32_t ace_n_max, ace_l_max, ace_nu_max;
-  int32_t ace_group;         /* compacted atoms per ACE thread block: 1, 2, 4 or 8, or 0 =
-                                automatic (the largest whose two per-atom pools of
-                                1 + n_max (l_max+1)^2 + couplings values leave room for two
-                                resident blocks per SM).  A group whose pools do not fit in
-                                shared memory is rejected by apip_create (APIP_ERR_ARG). */
+  int32_t ace_group;         /* compacted atoms per ACE thread block, or 0 = automatic.
+                                Body order <= 3 (streamed): 4 or 32 (automatic: 4 for the
+                                paper and learned switches, 32 for constant lam).  Body
+                                order 4 (pool): 1, 2, 4 or 8 (automatic: the largest whose
+                                two per-atom pools leave room for two resident blocks per
+                                SM).  A group the evaluation does not provide, or whose
+                                shared memory does not fit, is rejected by apip_create
+                                (APIP_ERR_ARG). */
   double ace_rc, ace_rc_width, ace_eps, ace_a_scale;
   const double* ace_c1;      /* host, ace_n_basis entries (copied) */
   const double* ace_c2;      /* host, ace_n_basis entries (copied) */
@@ -116,6 +128,7 @@ typedef struct apip_params {
   double skin;
   int32_t max_nb;            /* neighbour capacity per atom (<= 256) */
   int32_t cell_cap;          /* atom capacity per cell (<= 256) */
+  int32_t mixing;            /* APIP_MIX_ENERGY or APIP_MIX_FORCE */
 } apip_params;
 
 /* Number of product-basis functions of the canonical ACE basis (the length of
@@ -162,6 +175,13 @@ apip_status apip_energy_forces(apip_ctx* ctx, const double* pos, const double bo
                                const int32_t* type, const int32_t* id, int64_t n,
                                double* force_out, double* e_atom_out, double* e_total_out,
                                void* stream);
+
+/* Constant lam on a subset of atoms (Appendix B): lam_fixed (device, float64,
+ * n entries, caller-owned and kept alive while set) holds NaN for atoms whose lam
+ * follows the switch and the constant value (in [0, 1]) for the others; those
+ * have dlam = 0 and so no grad-lambda force of their own.  Applies to every later
+ * call; NULL clears it.  Errors: APIP_ERR_ARG (n outside [0, n_atoms_max]). */
+apip_status apip_set_lam_fixed(apip_ctx* ctx, const double* lam_fixed, int64_t n);
 
 /* n_steps velocity-Verlet NVE steps (float64 state).  On entry force holds F(pos)
  * (from apip_energy_forces); on exit pos, vel, force are advanced and wrapped into
@@ -210,18 +230,26 @@ apip_status apip_profile(apip_ctx* ctx, int32_t enable);
 apip_status apip_profile_read(apip_ctx* ctx, double* ms, int64_t* launches);
 
 /* Sizes of the ACE evaluation that apip_create built, for work accounting
- * (host call, no device work).  out (host, APIP_ACE_INFO_COUNT entries):
- *   [0] pool values per atom: 1 + n_max (l_max+1)^2 + coupling components
- *   [1] coupling components C_{(p1 p2) L M}
- *   [2] Gaunt products summed over the components (one multiply-add pair each)
- *   [3] basis records (one dot product of two pool segments each)
+ * (host call, no device work).  Body order <= 3 uses the streamed evaluation
+ * (couplings C_{(p1 p2) L M} = sum G A_{p1} A_{p2} formed in registers and
+ * contracted with their nu = 3 partners), body order 4 the coupling pool (all C
+ * of an atom stored, every basis function a dot product of two pool segments).
+ * out (host, APIP_ACE_INFO_COUNT entries):
+ *   [0] values per atom in shared memory: 1 + n_max (l_max+1)^2 (+ pool couplings)
+ *   [1] couplings (streamed) or coupling components (pool)
+ *   [2] Gaunt products per atom (one multiply and one multiply-add each)
+ *   [3] basis records (nu = 1, 2 records and nu = 3 partners, or pool records)
  *   [4] sum over the records of their segment length
- *   [5] sum over the pool values of the length of their reverse row
- *   [6] C -> A back-propagation entries
+ *   [5] pool: sum over the pool values of the length of their reverse row
+ *   [6] pool: C -> A back-propagation entries
  *   [7] compacted atoms per ACE thread block
  *   [8] ACE thread blocks per launch
+ *   [9] evaluation: 0 = pool, 1 = streamed
+ *   [10] floating-point operations per compacted atom of the table work (forward
+ *        and adjoint; a multiply-add counts 2); the per-neighbour work is not
+ *        included
  * Errors: APIP_ERR_ARG (NULL argument). */
-#define APIP_ACE_INFO_COUNT 9
+#define APIP_ACE_INFO_COUNT 11
 apip_status apip_ace_info(apip_ctx* ctx, int64_t* out);
 
 /* Learned indicator (workload row: MLP on radial descriptors trained on per-atom

@@ -14,7 +14,12 @@ lam is the ACE weight (the paper's lambda is 1 - lam).  ``lam_mode``:
   "const1" lam = 1 everywhere (pure ACE)
 and ``lam_const`` (float array, NaN = follow Eq. 2) fixes lam on a subset
 (Appendix B).  ``grad_lambda=False`` drops F^(grad lambda) (the non-conservative
-ablation of Fig. 3b / Fig. S2).
+ablation of Fig. 3b / Fig. S2).  ``mixing="force"`` replaces Eq. 5 by force
+mixing (Eq. 3, the other ablation of Fig. 5): each atom's force is the
+lam-weighted combination of the full fast and full precise forces,
+    F_i = (1 - lam_i) F_i^EAM + lam_i F_i^prec,   F^m = -grad sum_k E_k^m,
+which is not the gradient of any energy and violates Newton's third law.  The
+reported energy is still Eq. 4.
 """
 import math
 
@@ -33,7 +38,7 @@ def cutoff(prm):
 
 
 def energy_forces(pos, box, ids, partners, prm, model=None, lam_mode="paper",
-                  lam_const=None, grad_lambda=True, forces=True):
+                  lam_const=None, grad_lambda=True, forces=True, mixing="energy"):
     """Return a dict with E (fsum), per-atom terms and F (n, 3)."""
     pos = np.asarray(pos, dtype=np.float64)
     n = len(pos)
@@ -70,6 +75,15 @@ def energy_forces(pos, box, ids, partners, prm, model=None, lam_mode="paper",
                zeta=zeta, g=g, wbar=wbar, d=d, lam=lam, dlam=dlam, P=P)
     if not forces:
         return out
+    if mixing == "force":
+        f_fast = eam_forces(n, i, j, rvec, r, zeta, np.ones(n), prm["eam"])
+        everyone = np.arange(n)
+        _, f_ace = ace_mod.ace_energy_forces(model, n, i, j, rvec, r, everyone, weights=np.ones(n))
+        f_prec = beta * f_fast + f_ace
+        out["F"] = (1.0 - lam)[:, None] * f_fast + lam[:, None] * f_prec
+        return out
+    if mixing != "energy":
+        raise ValueError(mixing)
     F += eam_forces(n, i, j, rvec, r, zeta, 1.0 - lam + beta * lam, prm["eam"])
     F += ace_f
     if grad_lambda and lam_mode in ("paper", "learned"):

@@ -20,6 +20,8 @@ STATUS_NAMES = {0: "APIP_OK", 1: "APIP_ERR_ARG", 2: "APIP_ERR_CUDA", 3: "APIP_ER
 APIP_STATIC_MAX_ATOMS = 4096 * 4096
 APIP_FP64, APIP_FP32 = 0, 1
 APIP_LAM_PAPER, APIP_LAM_CONST0, APIP_LAM_CONST1, APIP_LAM_LEARNED = 0, 1, 2, 3
+APIP_MIX_ENERGY, APIP_MIX_FORCE = 0, 1
+MIXING = {"energy": APIP_MIX_ENERGY, "force": APIP_MIX_FORCE}
 LAM_MODES = {"paper": APIP_LAM_PAPER, "const0": APIP_LAM_CONST0, "const1": APIP_LAM_CONST1,
              "learned": APIP_LAM_LEARNED}
 APIP_MLP_NPARAM = 10497
@@ -44,7 +46,7 @@ class ApipParams(ctypes.Structure):
         ("sw_r_w", _c_double), ("sw_r_w_width", _c_double), ("sw_d_lo", _c_double), ("sw_d_hi", _c_double),
         ("sw_d0", _c_double),
         ("csp_rcut", _c_double), ("csp_nnb", _c_int32), ("nb_pad", _c_int32),
-        ("skin", _c_double), ("max_nb", _c_int32), ("cell_cap", _c_int32),
+        ("skin", _c_double), ("max_nb", _c_int32), ("cell_cap", _c_int32), ("mixing", _c_int32),
     ]
 
 
@@ -71,6 +73,7 @@ def _load():
         "apip_ace_info": (ctypes.c_int, [_vp, P(_c_int64)]),
         "apip_reduce_energy_static": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
         "apip_set_mlp": (ctypes.c_int, [_vp, _vp, _vp]),
+        "apip_set_lam_fixed": (ctypes.c_int, [_vp, _vp, _c_int64]),
         "apip_descriptors": (ctypes.c_int, [_vp, _vp, P(_c_double), _vp, _c_int64, _vp, _vp]),
         "apip_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, _c_int64, _vp, _vp, _vp, _vp]),
         "apip_mlp_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _c_int32, ctypes.c_float, _vp]),
@@ -178,8 +181,8 @@ def apip_profile_read(ctx):
     return {name: (ms[k], nl[k]) for k, name in enumerate(PHASES)}
 
 
-ACE_INFO = ("pool", "couplings", "gaunt_products", "records", "record_len_sum", "row_len_sum",
-            "c_to_a_entries", "group", "blocks")
+ACE_INFO = ("values_per_atom", "couplings", "gaunt_products", "records", "record_len_sum", "row_len_sum",
+            "c_to_a_entries", "group", "blocks", "kind", "table_flops")
 
 
 def apip_ace_info(ctx):
@@ -202,6 +205,12 @@ def apip_reduce_energy_static(e_atom, n, e_total, stream=None):
 
 def apip_set_mlp(ctx, params, stream=None):
     _check(ctx, lib.apip_set_mlp(ctx, _ptr(params), _stream(stream)))
+
+
+def apip_set_lam_fixed(ctx, lam_fixed, n):
+    """Constant lam on a subset (float64 device tensor, NaN = follow the switch),
+    or None to clear."""
+    _check(ctx, lib.apip_set_lam_fixed(ctx, _ptr(lam_fixed), int(n)))
 
 
 def apip_descriptors(ctx, pos, box, id, n, desc_bf16, stream=None):
@@ -239,7 +248,7 @@ def mlp_unflat(flat):
 
 # ---------------------------------------------------------------- helpers
 def make_params(prm, precision="fp64", lam_mode="paper", grad_lambda=True, skin=0.5, max_nb=96, cell_cap=64,
-                ace_group=0):
+                ace_group=0, mixing="energy"):
     """apip_params from a parameter dict (keys eam, ace, switch, csp,
     precise_adds_eam).  The returned structure keeps the coefficient arrays
     alive through its ``_keep`` attribute."""
@@ -267,6 +276,7 @@ def make_params(prm, precision="fp64", lam_mode="paper", grad_lambda=True, skin=
     p.sw_d_lo, p.sw_d_hi, p.sw_d0 = s["d_lo"], s["d_hi"], s["d0"]
     p.csp_rcut, p.csp_nnb = c["rcut"], c["nnb"]
     p.skin, p.max_nb, p.cell_cap = skin, max_nb, cell_cap
+    p.mixing = MIXING[mixing]
     p._keep = (c1, c2)
     return p
 
@@ -313,6 +323,10 @@ class Apip:
 
     def set_mlp(self, params, stream=None):
         apip_set_mlp(self.ctx, params, stream)
+
+    def set_lam_fixed(self, lam_fixed):
+        self._lam_fixed = lam_fixed   # the library reads it on later calls
+        apip_set_lam_fixed(self.ctx, lam_fixed, 0 if lam_fixed is None else lam_fixed.shape[0])
 
     def descriptors(self, pos, box, ids, desc_bf16, stream=None):
         apip_descriptors(self.ctx, pos, box, ids, pos.shape[0], desc_bf16, stream)

@@ -22,6 +22,7 @@
 #include <tuple>
 
 #include "apip_internal.h"
+#include "gaunt_layout.h"
 
 namespace apip {
 namespace {
@@ -303,17 +304,110 @@ bool build_coupled(int n_max, int l_max, int nu_max, const double* c1, const dou
   out->bkey.clear(); out->bval.clear(); out->poff.clear(); out->tpiece.clear();
   for (const auto& v : tgt)
     for (const auto& e : v) { out->bkey.push_back(e.first); out->bval.push_back(e.second); }
-  for (int piece = 32;; piece *= 2) {
-    out->poff.assign(1, 0);
-    out->tpiece.assign(1, 0);
-    int pos = 0;
+  // piece length: a target's entries are cut into ceil(cnt / len) nearly equal
+  // pieces; the length minimises the step's critical path, (rounds of
+  // kAceThreads pieces) x (len + a per-piece overhead of 8 entries) plus the
+  // pieces a target sums afterwards, with at most nC pieces
+  auto cut = [&](int len, bool emit) {
+    int np = 0, pos = 0;
+    if (emit) { out->poff.assign(1, 0); out->tpiece.assign(1, 0); }
     for (int t = 0; t < nA; ++t) {
       const int cnt = (int)tgt[t].size();
-      for (int s = 0; s < cnt; s += piece) out->poff.push_back(pos + std::min(cnt, s + piece));
+      const int k = (cnt + len - 1) / len;
+      for (int q = 1; q <= k; ++q)
+        if (emit) out->poff.push_back(pos + (int)((int64_t)cnt * q / k));
+      np += k;
       pos += cnt;
-      out->tpiece.push_back((int)out->poff.size() - 1);
+      if (emit) out->tpiece.push_back((int)out->poff.size() - 1);
     }
-    if ((int)out->poff.size() - 1 <= out->nC) break;
+    return np;
+  };
+  int best_len = 0;
+  int64_t best_cost = -1;
+  for (int len = 1; len <= std::max<int>(1, (int)out->bkey.size()); len = len < 64 ? len + 1 : len + len / 8) {
+    const int np = cut(len, false);
+    if (np > std::max(out->nC, 0)) continue;
+    const int64_t cost = (int64_t)((np + kAceThreads - 1) / kAceThreads) * (len + 8) + (np + nA - 1) / nA;
+    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best_len = len; }
+  }
+  cut(std::max(best_len, 1), true);
+  return true;
+}
+
+void gaunt_fill(double* out) {
+  for (int l1 = 0; l1 <= kGauntLmax; ++l1)
+    for (int l2 = l1; l2 <= kGauntLmax; ++l2)
+      for (int L = 0; L <= kGauntLmax; ++L) {
+        if (!gaunt_type_valid(l1, l2, L)) continue;
+        int e = gaunt_offset(l1, l2, L);
+        for (int m1 = -l1; m1 <= l1; ++m1)
+          for (int m2 = -l2; m2 <= l2; ++m2)
+            for (int v = 0; v < 2; ++v) {
+              const int M = gaunt_cand(m1, m2, v, L);
+              if (M != kNoM) out[e++] = real_gaunt(l1, m1, l2, m2, L, M);
+            }
+      }
+}
+
+// Streamed tables (body order <= 3): couplings C_{(p1 p2) L} with l1 <= l2 (the
+// factors swapped where needed; C is symmetric in them), sorted by type so that
+// neighbouring thread slices run the same unrolled code, each with its list of
+// nu = 3 partners (p3, c1, c2); nu = 1, 2 functions as dot products of A segments.
+bool build_streamed(int n_max, int l_max, int nu_max, const double* c1, const double* c2, int64_t n_basis,
+                    HostStream* out, std::string* err) {
+  if (nu_max > 3) { *err = "the streamed ACE evaluation covers body order <= 3"; return false; }
+  const int nlm = (l_max + 1) * (l_max + 1);
+  const auto basis = enumerate(n_max, l_max, nu_max);
+  if ((int64_t)basis.size() != n_basis) {
+    *err = "ace_n_basis does not match the canonical basis size " + std::to_string(basis.size());
+    return false;
+  }
+  auto abase = [&](int n, int l) { return (n - 1) * nlm + l * l; };   // A index of m = -l
+  struct Cp { int a1, a2, l1, l2, L; std::vector<std::array<double, 3>> part; };
+  std::map<std::tuple<int, int, int>, int> index;
+  std::vector<Cp> cps;
+  *out = HostStream{};
+  for (size_t bi = 0; bi < basis.size(); ++bi) {
+    const Basis& b = basis[bi];
+    if (b.nu == 1) {
+      out->pkey.push_back((uint32_t)abase(b.n[0], 0) | (0xffffu << 16));
+      out->plen.push_back(1);
+      out->p1.push_back(c1[bi]);
+      out->p2.push_back(c2[bi]);
+    } else if (b.nu == 2) {
+      out->pkey.push_back((uint32_t)abase(b.n[0], b.l[0]) | ((uint32_t)abase(b.n[1], b.l[1]) << 16));
+      out->plen.push_back((uint32_t)(2 * b.l[0] + 1));
+      out->p1.push_back(c1[bi]);
+      out->p2.push_back(c2[bi]);
+    } else {
+      int a1 = abase(b.n[0], b.l[0]), a2 = abase(b.n[1], b.l[1]), l1 = b.l[0], l2 = b.l[1];
+      if (l1 > l2) { std::swap(a1, a2); std::swap(l1, l2); }
+      const auto key = std::make_tuple(a1, a2, b.l[2]);
+      auto it = index.find(key);
+      if (it == index.end()) {
+        it = index.emplace(key, (int)cps.size()).first;
+        cps.push_back({a1, a2, l1, l2, b.l[2], {}});
+      }
+      cps[it->second].part.push_back({(double)abase(b.n[2], b.l[2]), c1[bi], c2[bi]});
+    }
+  }
+  std::stable_sort(cps.begin(), cps.end(), [](const Cp& x, const Cp& y) {
+    return std::make_tuple(gaunt_type(x.l1, x.l2, x.L), -(int)x.part.size(), x.a1, x.a2) <
+           std::make_tuple(gaunt_type(y.l1, y.l2, y.L), -(int)y.part.size(), y.a1, y.a2);
+  });
+  for (const Cp& c : cps) {
+    if (!gaunt_type_valid(c.l1, c.l2, c.L)) { *err = "internal: invalid coupling type"; return false; }
+    const uint32_t beg = (uint32_t)out->tkey.size();
+    for (const auto& p : c.part) {
+      out->tkey.push_back((uint32_t)p[0]);
+      out->t1.push_back(p[1]);
+      out->t2.push_back(p[2]);
+    }
+    out->cpl.push_back((uint32_t)c.a1 | ((uint32_t)c.a2 << 8) | ((uint32_t)gaunt_type(c.l1, c.l2, c.L) << 16));
+    out->cpl.push_back(beg);
+    out->cpl.push_back((uint32_t)out->tkey.size());
+    out->cpl.push_back(0u);
+    out->gaunt_products += gaunt_count(c.l1, c.l2, c.L);
   }
   return true;
 }

@@ -13,6 +13,7 @@
 #include <new>
 #include <string>
 
+#include "gaunt_layout.h"
 #include "kernels.h"
 
 using namespace apip;
@@ -73,7 +74,7 @@ void free_all(apip_ctx* c) {
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   c->prof_pending.clear();
   c->prof_pool.clear();
-  void* ptrs[] = {c->cell_count, c->cell_atoms, c->nnb, c->nbl, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
+  void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nbl, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->counts, c->flags, c->status, c->partials, c->thermo_part,
                   c->e_scratch, c->ace_tab, c->mlp_w, c->mlp_ws};
@@ -89,9 +90,11 @@ apip_status check_params(const apip_params* p, std::string* why) {
   if (p->ace_l_max < 0 || p->ace_l_max > kLmaxCap) return bad("ace_l_max must be in [0, 4]");
   if (p->ace_nu_max < 1 || p->ace_nu_max > 4) return bad("ace_nu_max must be in [1, 4]");
   if (p->ace_n_max * (p->ace_l_max + 1) * (p->ace_l_max + 1) > 254) return bad("n_max (l_max+1)^2 must be <= 254");
-  if (p->ace_group != 0 && p->ace_group != 1 && p->ace_group != 2 && p->ace_group != 4 && p->ace_group != 8)
-    return bad("ace_group must be 0, 1, 2, 4 or 8");
+  if (p->ace_group != 0 && p->ace_group != 1 && p->ace_group != 2 && p->ace_group != 4 && p->ace_group != 8 &&
+      p->ace_group != 32)
+    return bad("ace_group must be 0, 1, 2, 4, 8 or 32");
   if (!p->ace_c1 || !p->ace_c2) return bad("ace_c1 / ace_c2 must not be NULL");
+  if (p->mixing != APIP_MIX_ENERGY && p->mixing != APIP_MIX_FORCE) return bad("unknown mixing");
   if (!(p->ace_rc > 0 && p->ace_rc_width > 0 && p->ace_rc_width <= p->ace_rc)) return bad("bad ACE cutoff");
   if (!(p->ace_eps > 0)) return bad("ace_eps must be > 0");
   if (!(p->eam_rc > 0 && p->eam_rc_width > 0 && p->eam_rc_width <= p->eam_rc)) return bad("bad EAM cutoff");
@@ -129,10 +132,14 @@ apip_status set_geometry(apip_ctx* ctx, const double* box, cudaStream_t s) {
   if (ncell > ctx->ncell_alloc) {
     if (ctx->cell_count) cudaFree(ctx->cell_count);
     if (ctx->cell_atoms) cudaFree(ctx->cell_atoms);
+    if (ctx->cell_q) cudaFree(ctx->cell_q);
     ctx->cell_count = nullptr;
     ctx->cell_atoms = nullptr;
+    ctx->cell_q = nullptr;
     APIP_CK(cudaMalloc(&ctx->cell_count, sizeof(int) * ncell));
     APIP_CK(cudaMalloc(&ctx->cell_atoms, sizeof(int) * (size_t)ncell * ctx->p.cell_cap));
+    if (ctx->p.precision == APIP_FP32)
+      APIP_CK(cudaMalloc(&ctx->cell_q, sizeof(uint4) * (size_t)ncell * ctx->p.cell_cap));
     ctx->ncell_alloc = ncell;
   }
   ctx->ncell = ncell;
@@ -157,8 +164,10 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.csp_nnb = p.csp_nnb;
   a.lam_mode = p.lam_mode;
   a.precise_adds_eam = p.precise_adds_eam;
-  a.grad_lambda = p.grad_lambda;
+  a.force_mix = p.mixing == APIP_MIX_FORCE;
+  a.grad_lambda = a.force_mix ? 0 : p.grad_lambda;
   a.eam_force = 1;
+  a.lam_fixed = c->lam_fixed;
   a.geo = c->geo;
   a.eam = {p.eam_A, p.eam_beta, p.eam_re, p.eam_D, p.eam_alpha, p.eam_r0, p.eam_rc, p.eam_rc - p.eam_rc_width,
            1.0 / p.eam_rc_width};
@@ -171,6 +180,7 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.id = id;
   a.nnb = c->nnb; a.nbl = c->nbl; a.pos_ref = c->pos_ref; a.posq = c->posq; a.posq_ref = c->posq_ref;
   a.id2idx = c->id2idx; a.csp = c->csp; a.cell_count = c->cell_count; a.cell_atoms = c->cell_atoms;
+  a.cell_q = c->cell_q;
   a.zeta = as<T>(c->zeta); a.xi_p = as<T>(c->xi_p); a.e_eam = as<T>(c->e_eam); a.g = as<T>(c->g);
   a.wbar = as<T>(c->wbar); a.dd = as<T>(c->dd); a.lam = as<T>(c->lam); a.dlam = as<T>(c->dlam);
   a.e_ace = as<T>(c->e_ace);
@@ -211,9 +221,19 @@ AceDev<T> ace_dev(apip_ctx* c) {
   t.eps = T(p.ace_eps);
   t.sqrt_eps = T(std::sqrt(p.ace_eps));
   t.a_scale = T(p.ace_a_scale);
+  t.kind = c->ace_kind;
   t.nC = c->ace_nC;
   t.npool = c->ace_npool;
   unsigned char* b = static_cast<unsigned char*>(c->ace_tab);
+  if (t.kind == kAceStreamed) {
+    t.prec = reinterpret_cast<const Rec<T>*>(b + c->ace_off[0]);
+    t.npr = c->ace_npr;
+    t.cpl = reinterpret_cast<const uint4*>(b + c->ace_off[1]);
+    t.ncpl = c->ace_ncpl;
+    t.part = reinterpret_cast<const Rec<T>*>(b + c->ace_off[2]);
+    t.group = c->ace_group;
+    return t;
+  }
   t.comp = reinterpret_cast<const uint2*>(b + c->ace_off[0]);
   t.gent = reinterpret_cast<const Ent<T>*>(b + c->ace_off[1]);
   t.frec = reinterpret_cast<const Rec<T>*>(b + c->ace_off[2]);
@@ -231,6 +251,8 @@ AceDev<T> ace_dev(apip_ctx* c) {
 apip_status check_call(apip_ctx* ctx, const double* pos, const int32_t* id, int64_t n) {
   if (!ctx) return APIP_ERR_ARG;
   if (n < 0 || n > ctx->nmax) return fail(ctx, APIP_ERR_ARG, "n must be in [0, n_atoms_max]");
+  if (ctx->lam_fixed && n > ctx->lam_fixed_n)
+    return fail(ctx, APIP_ERR_ARG, "lam_fixed holds fewer than n entries");
   if (n > 0 && (!pos || !id)) return fail(ctx, APIP_ERR_ARG, "pos and id must not be NULL");
   return APIP_OK;
 }
@@ -262,8 +284,10 @@ template <typename T>
 void force_pipeline(apip_ctx* c, Args<T>& a, cudaStream_t s) {
   { Phase ph(c, APIP_PHASE_NEIGHBOR, 4, s); launch_neighbors<T>(a, c->ncell, s); }
   { Phase ph(c, APIP_PHASE_PASS1, 1, s); pass1<T>(a, s); }
-  { Phase ph(c, APIP_PHASE_PASS2, 1, s); launch_pass2<T>(a, s); }
-  { Phase ph(c, APIP_PHASE_ACE, 1, s); launch_ace<T>(a, ace_dev<T>(c), c->ace_blocks, s); }
+  { Phase ph(c, APIP_PHASE_PASS2, 1, s); launch_pass2<T>(a, s); if (a.force_mix) launch_fm_buffer<T>(a, s); }
+  { Phase ph(c, APIP_PHASE_ACE, 1, s); const AceDev<T> t = ace_dev<T>(c);
+    if (t.kind == kAceStreamed) launch_ace_stream<T>(a, t, c->ace_blocks, s);
+    else launch_ace_pool<T>(a, t, c->ace_blocks, s); }
   if (a.lam_mode == APIP_LAM_PAPER && a.grad_lambda) {
     Phase ph(c, APIP_PHASE_CSP, 1, s);
     launch_csp_force<T>(a, s);
@@ -363,12 +387,19 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   ctx->p.ace_c2 = nullptr;
   ctx->nmax = n_atoms_max;
   ctx->r_list = std::max(std::max(p->eam_rc, p->ace_rc), p->sw_r_w) + p->skin;
+  // body order <= 3: streamed couplings; body order 4: the coupling pool
+  const bool streamed = p->ace_nu_max <= 3;
   HostAce tab;
-  if (!build_coupled(p->ace_n_max, p->ace_l_max, p->ace_nu_max, ctx->ace_c1.data(), ctx->ace_c2.data(), nb, &tab,
-                     &why)) {
+  HostStream st;
+  if (streamed ? !build_streamed(p->ace_n_max, p->ace_l_max, p->ace_nu_max, ctx->ace_c1.data(), ctx->ace_c2.data(),
+                                 nb, &st, &why)
+               : !build_coupled(p->ace_n_max, p->ace_l_max, p->ace_nu_max, ctx->ace_c1.data(), ctx->ace_c2.data(),
+                                nb, &tab, &why)) {
     delete ctx;
     return APIP_ERR_ARG;
   }
+  ctx->ace_kind = streamed ? kAceStreamed : kAcePool;
+  const int nA = p->ace_n_max * (p->ace_l_max + 1) * (p->ace_l_max + 1);
   auto fail_create = [&](cudaError_t e) {
     free_all(ctx);
     delete ctx;
@@ -383,18 +414,32 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   cudaGetDevice(&ctx->dev);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->dev);
-  // atoms per ACE block: the largest group whose pools leave room for two
-  // resident blocks per SM, else the largest that fits at all
+  // atoms per ACE block.  Pool kernel: the largest group whose pools leave room
+  // for two resident blocks per SM, else the largest that fits.  Streamed
+  // kernel: 4 atoms per block for the adaptive switches (few compacted atoms,
+  // spread over many blocks), 32 for constant lam (every atom compacted).
   {
     const bool f32 = p->precision == APIP_FP32;
     auto occ_of = [&](int g) {
-      size_t bytes = 0;
-      return f32 ? ace_occupancy<float>(p->ace_l_max, g, tab.npool, &bytes)
-                 : ace_occupancy<double>(p->ace_l_max, g, tab.npool, &bytes);
+      if (f32) {
+        AceDev<float> t{};
+        t.kind = ctx->ace_kind; t.l_max = p->ace_l_max; t.nA = nA; t.npool = tab.npool; t.group = g;
+        return streamed ? ace_stream_occupancy<float>(t) : ace_pool_occupancy<float>(t);
+      }
+      AceDev<double> t{};
+      t.kind = ctx->ace_kind; t.l_max = p->ace_l_max; t.nA = nA; t.npool = tab.npool; t.group = g;
+      return streamed ? ace_stream_occupancy<double>(t) : ace_pool_occupancy<double>(t);
     };
     int group = p->ace_group, occ = 0;
     if (group != 0) {
-      occ = occ_of(group);
+      occ = occ_of(group);   // 0 for a group the kernel does not provide
+    } else if (streamed) {
+      const bool adaptive = p->lam_mode == APIP_LAM_PAPER || p->lam_mode == APIP_LAM_LEARNED;
+      const int order_a[2] = {4, 32}, order_c[2] = {32, 4};
+      for (int q = 0; q < 2 && occ == 0; ++q) {
+        group = adaptive ? order_a[q] : order_c[q];
+        occ = occ_of(group);
+      }
     } else {
       for (int g : {8, 4, 2, 1}) {
         const int o = occ_of(g);
@@ -467,19 +512,44 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
       put(slot, r.data(), sizeof(Rec<double>) * r.size());
     }
   };
-  put(0, tab.comp.data(), sizeof(uint32_t) * tab.comp.size());
-  put_ent(1, tab.gkey, tab.gval);
-  put_rec(2, tab.fkey, &tab.flen, tab.f1, tab.f2);
-  put(3, tab.qrow.data(), sizeof(int) * tab.qrow.size());
-  put_rec(4, tab.rkey, nullptr, tab.r1, tab.r2);
-  put_ent(5, tab.bkey, tab.bval);
-  put(6, tab.poff.data(), sizeof(int) * tab.poff.size());
-  put(7, tab.tpiece.data(), sizeof(int) * tab.tpiece.size());
-  ctx->ace_nC = tab.nC;
-  ctx->ace_npool = tab.npool;
-  ctx->ace_nf = (int)tab.fkey.size();
-  ctx->ace_npc = (int)tab.poff.size() - 1;
-  {
+  if (streamed) {
+    put_rec(0, st.pkey, &st.plen, st.p1, st.p2);
+    put(1, st.cpl.data(), sizeof(uint32_t) * st.cpl.size());
+    put_rec(2, st.tkey, nullptr, st.t1, st.t2);
+    ctx->ace_npr = (int)st.pkey.size();
+    ctx->ace_ncpl = (int)(st.cpl.size() / 4);
+    ctx->ace_npool = 1 + nA;
+    int64_t* info = ctx->ace_info;
+    info[0] = 1 + nA;
+    info[1] = ctx->ace_ncpl;
+    info[2] = st.gaunt_products;
+    info[3] = (int64_t)(st.pkey.size() + st.tkey.size());
+    int64_t part_len = 0, pair_len = 0;
+    for (size_t u = 0; u < st.cpl.size() / 4; ++u) {
+      const int L = (int)((st.cpl[4 * u] >> 16) % 5);
+      part_len += (int64_t)(st.cpl[4 * u + 2] - st.cpl[4 * u + 1]) * (2 * L + 1);
+    }
+    for (uint32_t l : st.plen) pair_len += l;
+    info[4] = part_len + pair_len;
+    // forward: 3 per Gaunt product (C), 2 per partner element + 4 per partner (two
+    // channels), 2 per pair element + 4 per pair record; adjoint: 3 per product (C
+    // again) + 5 per product (back onto A), 4 per partner element + 2 per partner,
+    // 4 per pair element + 2 per pair record
+    info[10] = 11 * st.gaunt_products + 6 * part_len + 6 * (int64_t)st.tkey.size() + 6 * pair_len +
+               6 * (int64_t)st.pkey.size();
+  } else {
+    put(0, tab.comp.data(), sizeof(uint32_t) * tab.comp.size());
+    put_ent(1, tab.gkey, tab.gval);
+    put_rec(2, tab.fkey, &tab.flen, tab.f1, tab.f2);
+    put(3, tab.qrow.data(), sizeof(int) * tab.qrow.size());
+    put_rec(4, tab.rkey, nullptr, tab.r1, tab.r2);
+    put_ent(5, tab.bkey, tab.bval);
+    put(6, tab.poff.data(), sizeof(int) * tab.poff.size());
+    put(7, tab.tpiece.data(), sizeof(int) * tab.tpiece.size());
+    ctx->ace_nC = tab.nC;
+    ctx->ace_npool = tab.npool;
+    ctx->ace_nf = (int)tab.fkey.size();
+    ctx->ace_npc = (int)tab.poff.size() - 1;
     int64_t* info = ctx->ace_info;
     info[0] = tab.npool;
     info[1] = tab.nC;
@@ -488,9 +558,13 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
     for (uint32_t l : tab.flen) info[4] += l;
     for (int q = 1; q < tab.npool; ++q) info[5] += tab.qrow[4 * q + 1] - tab.qrow[4 * q];
     info[6] = (int64_t)tab.bkey.size();
-    info[7] = ctx->ace_group;
-    info[8] = ctx->ace_blocks;
+    // couplings 3 per Gaunt product, basis records 2 per element + 4 each, reverse
+    // rows 4 per element, C -> A entries 3 each
+    info[10] = 3 * info[2] + 2 * info[4] + 4 * info[3] + 4 * info[5] + 3 * info[6];
   }
+  ctx->ace_info[7] = ctx->ace_group;
+  ctx->ace_info[8] = ctx->ace_blocks;
+  ctx->ace_info[9] = ctx->ace_kind;
   APIP_ALLOC(ctx->ace_tab, host.size());
 #undef APIP_ALLOC
   cudaError_t e = cudaMemcpy(ctx->ace_tab, host.data(), host.size(), cudaMemcpyHostToDevice);
@@ -506,8 +580,16 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   if (e != cudaSuccess) return fail_create(e);
   double norms[(kLmaxCap + 1) * (kLmaxCap + 1)];
   ylm_norms(kLmaxCap, norms);
-  if (p->precision == APIP_FP64) ace_set_norms<double>(norms, (kLmaxCap + 1) * (kLmaxCap + 1));
-  else ace_set_norms<float>(norms, (kLmaxCap + 1) * (kLmaxCap + 1));
+  const int nn = (kLmaxCap + 1) * (kLmaxCap + 1);
+  if (streamed) {
+    std::vector<double> gv(kGauntTotal);
+    gaunt_fill(gv.data());
+    if (p->precision == APIP_FP64) ace_stream_set_consts<double>(norms, nn, gv.data());
+    else ace_stream_set_consts<float>(norms, nn, gv.data());
+  } else {
+    if (p->precision == APIP_FP64) ace_pool_set_norms<double>(norms, nn);
+    else ace_pool_set_norms<float>(norms, nn);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail_create(e);
   *out = ctx;
@@ -703,6 +785,14 @@ apip_status apip_profile_read(apip_ctx* ctx, double* ms, int64_t* launches) {
     ctx->prof_ms[k] = 0.0;
     ctx->prof_n[k] = 0;
   }
+  return APIP_OK;
+}
+
+apip_status apip_set_lam_fixed(apip_ctx* ctx, const double* lam_fixed, int64_t n) {
+  if (!ctx) return APIP_ERR_ARG;
+  if (lam_fixed && (n < 0 || n > ctx->nmax)) return fail(ctx, APIP_ERR_ARG, "n must be in [0, n_atoms_max]");
+  ctx->lam_fixed = lam_fixed;
+  ctx->lam_fixed_n = lam_fixed ? n : 0;
   return APIP_OK;
 }
 

@@ -52,11 +52,18 @@ struct SwP { double r_w, r_w_lo, d_lo, d_hi, d0, inv_w, inv_d; };  // 1/(r_w - r
 template <typename T> struct alignas(sizeof(T) == 4 ? 16 : 8) Rec { uint32_t key, len; T k1, k2; };
 template <typename T> struct alignas(sizeof(T) == 4 ? 8 : 16) Ent { T v; uint32_t key; };
 
-// Coupled ACE tables on the device (built by build_coupled).  Per atom the pool
-// X = [1 | A (nA) | C (nC)] holds the atomic density and its Gaunt couplings;
-// every basis function is the dot product of two pool segments.
+// ACE tables on the device.  Two evaluations:
+//  pool (body order 4, built by build_coupled): per atom the pool
+//    X = [1 | A (nA) | C (nC)] holds the atomic density and its Gaunt couplings,
+//    every basis function is the dot product of two pool segments;
+//  streamed (body order <= 3, built by build_streamed): the couplings are formed
+//    one at a time in registers and contracted with their nu = 3 partners; nu = 1, 2
+//    functions are dot products of A segments.
+constexpr int kAcePool = 0, kAceStreamed = 1;
+
 template <typename T>
 struct AceDev {
+  int kind;                     // kAcePool or kAceStreamed
   int n_max, l_max, nA, nC, npool;   // nA = n_max (l_max+1)^2, npool = 1 + nA + nC
   T rc, rc_lo, eps, sqrt_eps, a_scale;
   const uint2* comp;            // [nC]: (a1 | a2 << 16, gofs << 8 | gcnt) per C component
@@ -67,7 +74,18 @@ struct AceDev {
   const Ent<T>* bent;           // C -> A entries, grouped by target
   const int* poff; int npc;     // [npc + 1] piece boundaries in bent
   const int* tpiece;            // [nA + 1] first piece of each target A component
-  int group;                    // compacted atoms per thread block (1, 2, 4 or 8)
+  // streamed tables
+  const Rec<T>* prec; int npr;  // nu 1, 2: key a1 | a2 << 16 (A indices; a2 = 0xffff: the constant 1), len
+  const uint4* cpl; int ncpl;   // couplings: (a1 | a2 << 8 | type << 16, partner begin, partner end, 0)
+  const Rec<T>* part;           // nu = 3 partners: key = A index of A_{p3, m = -l3}
+  int group;                    // compacted atoms per thread block
+};
+
+struct HostStream {
+  std::vector<uint32_t> pkey, plen; std::vector<double> p1, p2;   // nu 1, 2 records
+  std::vector<uint32_t> cpl;                                       // [4 per coupling]
+  std::vector<uint32_t> tkey; std::vector<double> t1, t2;          // partners
+  int64_t gaunt_products = 0;                                      // candidates over all couplings
 };
 
 struct HostAce {
@@ -85,6 +103,10 @@ struct HostAce {
 int64_t basis_size(int n_max, int l_max, int nu_max);
 bool build_coupled(int n_max, int l_max, int nu_max, const double* c1, const double* c2, int64_t n_basis,
                    HostAce* out, std::string* err);
+bool build_streamed(int n_max, int l_max, int nu_max, const double* c1, const double* c2, int64_t n_basis,
+                    HostStream* out, std::string* err);
+// real Gaunt values in the canonical layout of gaunt_layout.h (kGauntTotal entries)
+void gaunt_fill(double* out);
 // real Y_lm normalisation N_lm (times sqrt 2 for m != 0), index l^2 + l + m
 void ylm_norms(int l_max, double* out);
 // real Gaunt coefficient int Y_l1m1 Y_l2m2 Y_l3m3 dOmega (the library's own construction)
@@ -102,11 +124,14 @@ struct apip_ctx {
   bool geo_set = false;
   int ncell = 0, ncell_alloc = 0;
   bool csp_ready = false;
+  const double* lam_fixed = nullptr;  // caller's per-atom constant lam (NaN = switch)
+  int64_t lam_fixed_n = 0;
   std::string err;
   std::vector<double> ace_c1, ace_c2;
 
   // neighbour structures
   int* cell_count = nullptr;
+  uint4* cell_q = nullptr;     // FP32 path: posq of the cell members in cell order
   int* cell_atoms = nullptr;
   int* nnb = nullptr;
   int* nbl = nullptr;          // column-major [max_nb][nmax]
@@ -145,6 +170,7 @@ struct apip_ctx {
   size_t ace_off[8] = {};
   int ace_nf = 0, ace_npc = 0, ace_nC = 0, ace_npool = 0;
   int ace_group = 1;
+  int ace_kind = 0, ace_npr = 0, ace_ncpl = 0;
   int64_t ace_info[APIP_ACE_INFO_COUNT] = {};
 
   // learned indicator

@@ -63,6 +63,28 @@ template <> struct Acc<double> {
   __device__ __forceinline__ double value() const { return s; }
 };
 
+// r = |d| and 1/r from r^2: in float32 through the reciprocal square root
+// (rsqrtf, within 2 ulp), in float64 by the correctly rounded square root and a
+// division.
+template <typename T> __device__ __forceinline__ void len_inv(T r2, T* r, T* ir);
+template <> __device__ __forceinline__ void len_inv<float>(float r2, float* r, float* ir) {
+  *ir = rsqrtf(r2);
+  *r = r2 * *ir;
+}
+template <> __device__ __forceinline__ void len_inv<double>(double r2, double* r, double* ir) {
+  *r = sqrt(r2);
+  *ir = 1.0 / *r;
+}
+
+// Plain running sum, for the float32 sums whose rounding (~1e-7 relative over
+// some tens of terms) is far below their tolerance: per-atom forces and the
+// switch weights.  Energies keep the compensated Acc.
+template <typename T> struct Sum {
+  T s = T(0);
+  __device__ __forceinline__ void add(T v) { s += v; }
+  __device__ __forceinline__ T value() const { return s; }
+};
+
 // Positions.  FP64 path: the caller's float64 array, minimum image with rint.
 // FP32 path: each coordinate as a 32-bit fixed-point fraction of the box,
 // q = floor(x_wrapped / L * 2^32).  The unsigned difference q_j - q_i read as a

@@ -14,6 +14,8 @@ struct Args {
   int n, nmax, max_nb, cell_cap, csp_nnb;
   int lam_mode, precise_adds_eam, grad_lambda;
   int eam_force;          // pass 2 computes the (unweighted) EAM force
+  int force_mix;          // force mixing (Eq. 3) instead of the AP force (Eq. 5)
+  const double* lam_fixed;  // per-atom constant lam (NaN = switch) or null
   PosView<T> pv;
   Geo geo;
   EamP eam;
@@ -24,6 +26,7 @@ struct Args {
   const int* id;          // caller ids [n]
   int* nnb; int* nbl; double* pos_ref; uint4* posq; uint4* posq_ref; int* id2idx; int* csp;
   int* cell_count; int* cell_atoms;
+  uint4* cell_q;          // FP32 path: fixed-point positions of the cell members, cell order
   T* zeta; T* xi_p; T* e_eam; T* g; T* wbar; T* dd; T* lam; T* dlam; T* e_ace;
   double* cvec; int* ace_list; int* counts; int* flags; int* status;
   double* partials; int n_part_p1;
@@ -53,6 +56,9 @@ template <typename T> void launch_neighbors(const Args<T>& a, int ncell, cudaStr
 void launch_csp_init(const Args<double>& a, cudaStream_t s);
 template <typename T> void launch_pass1(const Args<T>& a, cudaStream_t s);
 template <typename T> void launch_pass2(const Args<T>& a, cudaStream_t s);
+// force mixing: append to the compacted list every atom with lam = 0 that has a
+// neighbour within the ACE cutoff with lam > 0 (the precise model's buffer)
+template <typename T> void launch_fm_buffer(const Args<T>& a, cudaStream_t s);
 template <typename T> void launch_csp_force(const Args<T>& a, cudaStream_t s);
 void launch_final(double* partials, int n_part, double* e_total, double* e_pot_slot,
                   const double* thermo_part, int n_tblocks, double* thermo_slot, int* flags,
@@ -77,11 +83,14 @@ void launch_mlp_loss_grad(const uint16_t* desc, const float* y, int batch, const
 size_t mlp_workspace_floats(int batch);
 void launch_mlp_adam(float* p, const float* g, float* m, float* v, int t, float lr, cudaStream_t s);
 
-// ACE (kernels_ace_f32.cu, kernels_ace_f64.cu)
-template <typename T> void ace_set_norms(const double* norms, int count);
-template <typename T> void launch_ace(const Args<T>& a, const AceDev<T>& ace, int blocks, cudaStream_t s);
-// resident blocks per SM of the ACE kernel for ace.group atoms per block and a
-// pool of npool values (0 if its shared memory does not fit); sets smem_bytes
-template <typename T> int ace_occupancy(int l_max, int group, int npool, size_t* smem_bytes);
+// ACE: body order 4 (kernels_ace_f32.cu, kernels_ace_f64.cu) and body order
+// <= 3 (kernels_ace3_f32.cu, kernels_ace3_f64.cu).  The occupancy queries return
+// resident blocks per SM for ace.group atoms per block (0 if it does not fit).
+template <typename T> void ace_pool_set_norms(const double* norms, int count);
+template <typename T> void launch_ace_pool(const Args<T>& a, const AceDev<T>& ace, int blocks, cudaStream_t s);
+template <typename T> int ace_pool_occupancy(const AceDev<T>& ace);
+template <typename T> void ace_stream_set_consts(const double* norms, int count, const double* gaunt);
+template <typename T> void launch_ace_stream(const Args<T>& a, const AceDev<T>& ace, int blocks, cudaStream_t s);
+template <typename T> int ace_stream_occupancy(const AceDev<T>& ace);
 
 }  // namespace apip

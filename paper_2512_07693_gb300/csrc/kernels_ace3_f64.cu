@@ -1,0 +1,37 @@
+// double instantiation of the body-order <= 3 ACE kernel (ace_stream.cuh).
+#include "apip_internal.h"
+#include "gaunt_layout.h"
+
+namespace apip {
+namespace {
+__constant__ double c_norm[(kLmaxCap + 1) * (kLmaxCap + 1)];
+__constant__ double c_gaunt[kGauntTotal];
+struct Consts {
+  static __device__ __forceinline__ double ynorm(int k) { return c_norm[k]; }
+  static __device__ __forceinline__ double gaunt(int e) { return c_gaunt[e]; }
+};
+}  // namespace
+}  // namespace apip
+
+#include "ace_stream.cuh"
+
+namespace apip {
+
+template <> void ace_stream_set_consts<double>(const double* norms, int count, const double* gaunt) {
+  double f[(kLmaxCap + 1) * (kLmaxCap + 1)];
+  for (int k = 0; k < count; ++k) f[k] = (double)norms[k];
+  cudaMemcpyToSymbol(c_norm, f, sizeof(double) * count);
+  static double gv[kGauntTotal];
+  for (int e = 0; e < kGauntTotal; ++e) gv[e] = (double)gaunt[e];
+  cudaMemcpyToSymbol(c_gaunt, gv, sizeof(double) * kGauntTotal);
+}
+
+template <> void launch_ace_stream<double>(const Args<double>& a, const AceDev<double>& t, int blocks, cudaStream_t s) {
+  stream_dispatch<double, Consts>(&a, t, blocks, s, false);
+}
+
+template <> int ace_stream_occupancy<double>(const AceDev<double>& t) {
+  return stream_dispatch<double, Consts>(nullptr, t, 0, nullptr, true);
+}
+
+}  // namespace apip

@@ -1,29 +1,31 @@
-// float32 instantiation of the ACE kernels (pair arithmetic in float32 with
-// compensated channel sums; forces accumulated in float64).
+// float instantiation of the body-order-4 ACE kernel (ace_pool.cuh).
 #include "apip_internal.h"
 
 namespace apip {
-__constant__ float c_norm_f[(kLmaxCap + 1) * (kLmaxCap + 1)];
+namespace {
+__constant__ float c_norm[(kLmaxCap + 1) * (kLmaxCap + 1)];
+struct Consts {
+  static __device__ __forceinline__ float ynorm(int k) { return c_norm[k]; }
+};
+}  // namespace
 }  // namespace apip
 
-#include "ace_device.cuh"
+#include "ace_pool.cuh"
 
 namespace apip {
 
-template <> __device__ __forceinline__ float ynorm<float>(int k) { return c_norm_f[k]; }
-
-template <> void ace_set_norms<float>(const double* norms, int count) {
+template <> void ace_pool_set_norms<float>(const double* norms, int count) {
   float f[(kLmaxCap + 1) * (kLmaxCap + 1)];
   for (int k = 0; k < count; ++k) f[k] = (float)norms[k];
-  cudaMemcpyToSymbol(c_norm_f, f, sizeof(float) * count);
+  cudaMemcpyToSymbol(c_norm, f, sizeof(float) * count);
 }
 
-template <> void launch_ace<float>(const Args<float>& a, const AceDev<float>& t, int blocks, cudaStream_t s) {
-  launch_ace_impl<float>(a, t, blocks, s);
+template <> void launch_ace_pool<float>(const Args<float>& a, const AceDev<float>& t, int blocks, cudaStream_t s) {
+  pool_dispatch<float, Consts>(&a, t, blocks, s, false);
 }
 
-template <> int ace_occupancy<float>(int l_max, int group, int npool, size_t* smem_bytes) {
-  return ace_occupancy_impl<float>(l_max, group, npool, smem_bytes);
+template <> int ace_pool_occupancy<float>(const AceDev<float>& t) {
+  return pool_dispatch<float, Consts>(nullptr, t, 0, nullptr, true);
 }
 
 }  // namespace apip

@@ -1,26 +1,31 @@
-// float64 instantiation of the ACE kernels (the parity path).
+// double instantiation of the body-order-4 ACE kernel (ace_pool.cuh).
 #include "apip_internal.h"
 
 namespace apip {
-__constant__ double c_norm_d[(kLmaxCap + 1) * (kLmaxCap + 1)];
+namespace {
+__constant__ double c_norm[(kLmaxCap + 1) * (kLmaxCap + 1)];
+struct Consts {
+  static __device__ __forceinline__ double ynorm(int k) { return c_norm[k]; }
+};
+}  // namespace
 }  // namespace apip
 
-#include "ace_device.cuh"
+#include "ace_pool.cuh"
 
 namespace apip {
 
-template <> __device__ __forceinline__ double ynorm<double>(int k) { return c_norm_d[k]; }
-
-template <> void ace_set_norms<double>(const double* norms, int count) {
-  cudaMemcpyToSymbol(c_norm_d, norms, sizeof(double) * count);
+template <> void ace_pool_set_norms<double>(const double* norms, int count) {
+  double f[(kLmaxCap + 1) * (kLmaxCap + 1)];
+  for (int k = 0; k < count; ++k) f[k] = (double)norms[k];
+  cudaMemcpyToSymbol(c_norm, f, sizeof(double) * count);
 }
 
-template <> void launch_ace<double>(const Args<double>& a, const AceDev<double>& t, int blocks, cudaStream_t s) {
-  launch_ace_impl<double>(a, t, blocks, s);
+template <> void launch_ace_pool<double>(const Args<double>& a, const AceDev<double>& t, int blocks, cudaStream_t s) {
+  pool_dispatch<double, Consts>(&a, t, blocks, s, false);
 }
 
-template <> int ace_occupancy<double>(int l_max, int group, int npool, size_t* smem_bytes) {
-  return ace_occupancy_impl<double>(l_max, group, npool, smem_bytes);
+template <> int ace_pool_occupancy<double>(const AceDev<double>& t) {
+  return pool_dispatch<double, Consts>(nullptr, t, 0, nullptr, true);
 }
 
 }  // namespace apip

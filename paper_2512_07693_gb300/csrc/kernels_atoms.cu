@@ -18,6 +18,20 @@ __device__ __forceinline__ double wrap1(double x, double L, double invL) {
   return w;
 }
 
+// wrap1 for a position that is normally already in [0, L) (the drift of one
+// step): the range test is made on the bit patterns (non-negative doubles order
+// as integers), which keeps it off the float64 pipe.
+__device__ __forceinline__ double wrap_near(double x, double L, double invL) {
+  const long long b = __double_as_longlong(x), bl = __double_as_longlong(L);
+  if (b >= 0 && b < bl) return x;
+  return wrap1(x, L, invL);
+}
+
+// isfinite from the exponent bits.
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+
 __device__ __forceinline__ int cell_of(double xw, double L, int nc) {
   int c = (int)(xw * ((double)nc / L));
   return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
@@ -33,7 +47,7 @@ __device__ __forceinline__ int cell_of(double xw, double L, int nc) {
 template <typename T>
 __device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, double y, double z,
                                           bool wrapped = false) {
-  if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicOr(&a.status[ST_BAD_INPUT], 1);
+  if (!finite_bits(x) || !finite_bits(y) || !finite_bits(z)) atomicOr(&a.status[ST_BAD_INPUT], 1);
   const int idv = a.id[i];
   if (idv < 0 || idv >= a.nmax) atomicOr(&a.status[ST_BAD_INPUT], 1);
   else a.id2idx[idv] = i;
@@ -92,8 +106,11 @@ __global__ void k_bin(Args<T> a) {
 }
 
 // Order each cell by atom index so that neighbour order (and thus every sum
-// over neighbours) does not depend on the order of the binning atomics.
-__global__ void k_cell_sort(const int* flags, const int* cell_count, int* cell_atoms, int ncell, int cap) {
+// over neighbours) does not depend on the order of the binning atomics; in the
+// FP32 path also copy the members' fixed-point positions into cell order, so
+// that the list build streams them without an index indirection.
+__global__ void k_cell_sort(const int* flags, const int* cell_count, int* cell_atoms, int ncell, int cap,
+                            const uint4* posq, uint4* cell_q) {
   if (!flags[0]) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
@@ -105,6 +122,8 @@ __global__ void k_cell_sort(const int* flags, const int* cell_count, int* cell_a
     while (m >= 0 && v[m] > x) { v[m + 1] = v[m]; --m; }
     v[m + 1] = x;
   }
+  if (cell_q)
+    for (int k = 0; k < cnt; ++k) cell_q[(size_t)c * cap + k] = posq[v[k]];
 }
 
 template <typename T>
@@ -127,13 +146,32 @@ __global__ void k_nbfill(Args<T> a) {
         const int cell = (cz * a.geo.nc[1] + cy) * a.geo.nc[0] + cx;
         const int m = min(a.cell_count[cell], a.cell_cap);
         const int* v = a.cell_atoms + (size_t)cell * a.cell_cap;
-        for (int k = 0; k < m; ++k) {
-          const int j = v[k];
-          if (j == i) continue;
-          const auto d = a.pv.vec(si, j);
-          if ((double)dot3(d, d) < a.r_list2) {
-            if (cnt < a.max_nb) a.nbl[(size_t)cnt * a.nmax + i] = j;
-            ++cnt;
+        if constexpr (sizeof(T) == 4) {
+          // float comparison against r_list^2 rounded up: the list holds every pair
+          // whose float distance is below r_list (and perhaps a few at r_list)
+          const uint4* cq = a.cell_q + (size_t)cell * a.cell_cap;
+          const float rl2 = __double2float_ru(a.r_list2);
+          for (int k = 0; k < m; ++k) {
+            const uint4 o = cq[k];
+            const float dx = (float)(int)(o.x - si.q.x) * a.pv.unit[0];
+            const float dy = (float)(int)(o.y - si.q.y) * a.pv.unit[1];
+            const float dz = (float)(int)(o.z - si.q.z) * a.pv.unit[2];
+            if (dx * dx + dy * dy + dz * dz < rl2) {
+              const int j = v[k];
+              if (j == i) continue;
+              if (cnt < a.max_nb) a.nbl[(size_t)cnt * a.nmax + i] = j;
+              ++cnt;
+            }
+          }
+        } else {
+          for (int k = 0; k < m; ++k) {
+            const int j = v[k];
+            if (j == i) continue;
+            const auto d = a.pv.vec(si, j);
+            if ((double)dot3(d, d) < a.r_list2) {
+              if (cnt < a.max_nb) a.nbl[(size_t)cnt * a.nmax + i] = j;
+              ++cnt;
+            }
           }
         }
       }
@@ -220,7 +258,7 @@ __global__ void k_csp_init(Args<double> a) {
 // ------------------------------------------------------------------ pass 1
 // zeta_i and E_i^EAM (Eq. B1, S8), xi'(zeta_i), and g_i = CSP^list_i (Eq. B3).
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_pass1(Args<T> a) {
+__global__ void __launch_bounds__(kBlock, 8) k_pass1(Args<T> a) {
   __shared__ double sh[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double e_out = 0.0;
@@ -232,12 +270,14 @@ __global__ void __launch_bounds__(kBlock) k_pass1(Args<T> a) {
             alpha = T(a.eam.alpha), r0 = T(a.eam.r0);
     Acc<T> zeta, pair;
     const int cnt = a.nnb[i];
-    for (int s = 0; s < cnt; ++s) {
-      const int j = a.nbl[(size_t)s * a.nmax + i];
+    const int* nb = a.nbl + i;
+    for (int s = 0; s < cnt; ++s, nb += a.nmax) {
+      const int j = *nb;
       const auto d = a.pv.vec(si, j);
       const T r2 = dot3(d, d);
       if (r2 < rc2) {
-        const T r = sqrt(r2);
+        T r, ir;
+        len_inv(r2, &r, &ir);
         T dfc;
         const T fc = ftrans(r, rlo, rc, inv_w, &dfc);
         const T x = exp(-alpha * (r - r0));
@@ -296,18 +336,20 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
     const T A = T(a.eam.A), beta = T(a.eam.beta), re = T(a.eam.re), D = T(a.eam.D),
             alpha = T(a.eam.alpha), r0 = T(a.eam.r0);
     const T xi_i = a.xi_p[i];
-    Acc<T> wbar, S, fx, fy, fz;
+    Sum<T> wbar, S, fx, fy, fz;
     wbar.add(T(1));
     if (paper) S.add(a.g[i]);
     const int cnt = a.nnb[i];
-    for (int s = 0; s < cnt; ++s) {
-      const int j = a.nbl[(size_t)s * a.nmax + i];
+    const int* nb = a.nbl + i;
+    for (int s = 0; s < cnt; ++s, nb += a.nmax) {
+      const int j = *nb;
       const auto d = a.pv.vec(si, j);
       const T r2 = dot3(d, d);
       const bool in_w = paper && r2 < rw2;
       const bool in_e = a.eam_force && r2 < rc2;
       if (!(in_w || in_e)) continue;
-      const T r = sqrt(r2);
+      T r, ir;
+      len_inv(r2, &r, &ir);
       if (in_w) {
         T dw;
         const T w = ftrans(r, rwlo, rw, rw_inv, &dw);
@@ -321,7 +363,7 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
         const T drho = er * (dfc - beta * fc);
         const T x = exp(-alpha * (r - r0));
         const T dphi = D * (T(2) * alpha * (x - x * x) * fc + (x * x - T(2) * x) * dfc);
-        const T sc = ((xi_i + a.xi_p[j]) * drho + dphi) / r;
+        const T sc = ((xi_i + a.xi_p[j]) * drho + dphi) * ir;
         fx.add(sc * d.x);
         fy.add(sc * d.y);
         fz.add(sc * d.z);
@@ -335,14 +377,24 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
     } else {
       lam = a.lam_mode == APIP_LAM_CONST1 ? T(1) : T(0);
     }
+    if (a.lam_fixed) {
+      const double f = a.lam_fixed[i];
+      if (f == f) {   // not NaN: constant lam on this atom (Appendix B)
+        lam = T(f);
+        dl = T(0);
+      }
+    }
     a.lam[i] = lam;
     a.dlam[i] = dl;
     a.wbar[i] = wb;
     a.dd[i] = dv;
     if (a.force) {
-      a.force[3 * i] = (double)fx.value();
-      a.force[3 * i + 1] = (double)fy.value();
-      a.force[3 * i + 2] = (double)fz.value();
+      // force mixing (Eq. 3): this atom's EAM force enters with (1 - lam_i) from the
+      // fast model plus, when the precise model contains the EAM, lam_i from it
+      const T wf = a.force_mix ? T(1) - lam + (a.precise_adds_eam ? lam : T(0)) : T(1);
+      a.force[3 * i] = (double)(wf * fx.value());
+      a.force[3 * i + 1] = (double)(wf * fy.value());
+      a.force[3 * i + 2] = (double)(wf * fz.value());
     }
   }
   const bool pred = active && lam > T(0);
@@ -459,7 +511,7 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* 
     if (mode != 2) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        x[q] = wrap1(pos[3 * i + q] + dt * v[q], a.geo.L[q], a.geo.invL[q]);
+        x[q] = wrap_near(pos[3 * i + q] + dt * v[q], a.geo.L[q], a.geo.invL[q]);
         pos[3 * i + q] = x[q];
       }
       prep_atom(a, i, x[0], x[1], x[2], true);
@@ -515,7 +567,8 @@ template <typename T> void launch_prep(const Args<T>& a, cudaStream_t s) {
 template <typename T> void launch_neighbors(const Args<T>& a, int ncell, cudaStream_t s) {
   k_cell_clear<<<nblocks(ncell), kBlock, 0, s>>>(a.flags, a.cell_count, ncell);
   k_bin<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
-  k_cell_sort<<<nblocks(ncell), kBlock, 0, s>>>(a.flags, a.cell_count, a.cell_atoms, ncell, a.cell_cap);
+  k_cell_sort<<<nblocks(ncell), kBlock, 0, s>>>(a.flags, a.cell_count, a.cell_atoms, ncell, a.cell_cap,
+                                                 sizeof(T) == 4 ? a.posq : nullptr, sizeof(T) == 4 ? a.cell_q : nullptr);
   k_nbfill<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
 }
 
@@ -525,6 +578,38 @@ void launch_csp_init(const Args<double>& a, cudaStream_t s) {
 
 template <typename T> void launch_pass1(const Args<T>& a, cudaStream_t s) {
   k_pass1<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+}
+
+// Force mixing: the precise model's forces on the atoms with lam > 0 need E^prec
+// of every atom within the ACE cutoff of them; those with lam = 0 are appended
+// to the compacted list after pass 2.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_fm_buffer(Args<T> a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool pred = false;
+  if (i < a.n && a.lam[i] == T(0)) {
+    const auto si = a.pv.self(i);
+    const T rc2 = a.ace_rc * a.ace_rc;
+    const int cnt = a.nnb[i];
+    const int* nb = a.nbl + i;
+    for (int s = 0; s < cnt && !pred; ++s, nb += a.nmax) {
+      const int j = *nb;
+      if (a.lam[j] > T(0)) {
+        const auto d = a.pv.vec(si, j);
+        pred = dot3(d, d) < rc2;
+      }
+    }
+  }
+  const unsigned mask = __ballot_sync(0xffffffffu, pred);
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0 && mask) base = atomicAdd(&a.counts[0], __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (pred) a.ace_list[base + __popc(mask & ((1u << lane) - 1u))] = i;
+}
+
+template <typename T> void launch_fm_buffer(const Args<T>& a, cudaStream_t s) {
+  k_fm_buffer<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
 }
 
 template <typename T> void launch_pass2(const Args<T>& a, cudaStream_t s) {
@@ -561,6 +646,7 @@ template <typename T> void launch_get_field(const Args<T>& a, int field, void* d
   template void launch_neighbors<T>(const Args<T>&, int, cudaStream_t);                           \
   template void launch_pass1<T>(const Args<T>&, cudaStream_t);                                    \
   template void launch_pass2<T>(const Args<T>&, cudaStream_t);                                    \
+  template void launch_fm_buffer<T>(const Args<T>&, cudaStream_t);                                \
   template void launch_csp_force<T>(const Args<T>&, cudaStream_t);                                \
   template void launch_verlet<T>(const Args<T>&, int, double*, double*, const double*,            \
                                  const double*, double, double*, cudaStream_t);                   \

@@ -20,14 +20,17 @@ def to_dev(torch, s):
                 inv_mass=torch.tensor(1.0 / (s["mass"] * 1.0364269e-4), dtype=torch.float64, device=dev))
 
 
-def run_gpu(s, precision="fp64", lam_mode="paper", grad_lambda=True, max_nb=96, fields=True, prm=None, ace_group=0):
+def run_gpu(s, precision="fp64", lam_mode="paper", grad_lambda=True, max_nb=96, fields=True, prm=None, ace_group=0,
+            mixing="energy", lam_fixed=None):
     torch = torch_cuda()
     from paper_2512_07693_gb300 import apip
     prm = prm or s["prm"]
     n = len(s["pos"])
     m = apip.Apip(prm, n, precision=precision, lam_mode=lam_mode, grad_lambda=grad_lambda, max_nb=max_nb,
-                  ace_group=ace_group)
+                  ace_group=ace_group, mixing=mixing)
     t = to_dev(torch, s)
+    if lam_fixed is not None:
+        m.set_lam_fixed(torch.tensor(lam_fixed, dtype=torch.float64, device="cuda"))
     box = [float(x) for x in s["box"]]
     if lam_mode == "paper":
         m.init_csp_pairs(t["pos"], box, t["ids"])
@@ -49,12 +52,12 @@ def run_gpu(s, precision="fp64", lam_mode="paper", grad_lambda=True, max_nb=96, 
     return out
 
 
-def run_oracle(s, lam_mode="paper", grad_lambda=True, prm=None, model=None):
+def run_oracle(s, lam_mode="paper", grad_lambda=True, prm=None, model=None, mixing="energy", lam_const=None):
     from oracle import ace, apip, csp
     prm = prm or s["prm"]
     part = csp.init_pairs(s["pos"], s["box"], s["ids"], prm["csp"]["rcut"], prm["csp"]["nnb"])
     model = model or ace.AceModel(prm["ace"])
     res = apip.energy_forces(s["pos"], s["box"], s["ids"], part, prm, model=model, lam_mode=lam_mode,
-                             grad_lambda=grad_lambda)
+                             grad_lambda=grad_lambda, mixing=mixing, lam_const=lam_const)
     res["partners"] = part
     return res

@@ -67,21 +67,24 @@ def _check(s, prec="fp64", **kw):
     return g, o
 
 
-@pytest.mark.parametrize("prec,group", [("fp64", 0), ("fp64", 1), ("fp64", 4), ("fp32", 0), ("fp32", 2), ("fp32", 8)])
+@pytest.mark.parametrize("prec,group", [("fp64", 0), ("fp64", 32), ("fp32", 0), ("fp32", 4), ("fp32", 32)])
 def test_mixed_system_parity(prec, group):
-    """group = compacted atoms per ACE thread block (0: automatic)."""
+    """Body order 3 (the streamed kernel); group = compacted atoms per ACE thread
+    block (0: automatic)."""
     s = small()
     g, o = _check(s, prec, ace_group=group)
     # every regime is exercised
     assert np.any(o["lam"] == 1.0) and np.any(o["lam"] == 0.0) and np.count_nonzero(o["dlam"]) > 10
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_nu4_ragged(prec):
-    """4-body terms, N not a multiple of 32 (precise = EAM + ACE as in the workloads)."""
+@pytest.mark.parametrize("prec,group", [("fp64", 0), ("fp32", 0), ("fp64", 1), ("fp32", 2), ("fp64", 4),
+                                        ("fp32", 8)])
+def test_nu4_ragged(prec, group):
+    """4-body terms (the pool kernel) with every group size, N not a multiple of 32
+    (precise = EAM + ACE as in the workloads)."""
     s = small(cells=(7, 6, 6), adds_eam=True, acecfg=(4, 3, 4), seed=5)
     assert len(s["pos"]) % 32 != 0
-    _check(s, prec)
+    _check(s, prec, ace_group=group)
 
 
 _ORACLE_844 = {}
@@ -154,6 +157,24 @@ def test_neighbour_list_and_csp_pairs_exact():
         got = set(g["nblist"][a][: g["nnb"][a]].tolist())
         assert got == sets[a], a
     assert np.array_equal(g["csp"], o["partners"])
+
+
+def test_neighbour_list_fp32_brackets_the_cutoff():
+    """The float32 list (fixed-point pair vectors, float distances) holds every
+    pair within r_list - 1e-4 A and none beyond r_list + 1e-4 A."""
+    s = small(cells=(6, 7, 6), sigma=0.1)
+    g = run_gpu(s, "fp32")
+    n = len(s["pos"])
+    rl = 5.5
+    inner = [set() for _ in range(n)]
+    outer = [set() for _ in range(n)]
+    for cut, sets in ((rl - 1e-4, inner), (rl + 1e-4, outer)):
+        i, j, _, _ = pairs(s["pos"], s["box"], cut)
+        for a, b in zip(i.tolist(), j.tolist()):
+            sets[a].add(b)
+    for a in range(n):
+        got = set(g["nblist"][a][: g["nnb"][a]].tolist())
+        assert inner[a] <= got <= outer[a], a
 
 
 def test_vacancy2k_config_fp64():
@@ -250,10 +271,15 @@ def test_error_paths():
     with pytest.raises(apip.ApipError) as e:
         small_nb.sync()
     assert e.value.status == apip.APIP_ERR_NB_OVERFLOW and "max_nb = 20" in str(e.value)
-    # a group of atoms per ACE block whose pools exceed shared memory: rejected at
-    # creation (8 atoms x 2 pools x 1807 values x 8 bytes = 231 KB)
+    # group sizes that are rejected at creation: one the streamed (body order 3)
+    # kernel does not provide, and pools that exceed shared memory (the crack
+    # basis in float64: 2 atoms x 2 pools x 13188 values x 8 bytes = 422 KB)
     with pytest.raises(apip.ApipError) as e:
         apip.Apip(s["prm"], n, precision="fp64", ace_group=8)
+    assert e.value.status == apip.APIP_ERR_ARG
+    crack = dict(s["prm"], ace=W.ace_params(8, 4, 4, 2, nbasis(8, 4, 4)))
+    with pytest.raises(apip.ApipError) as e:
+        apip.Apip(crack, n, precision="fp64", ace_group=2)
     assert e.value.status == apip.APIP_ERR_ARG
     # empty system
     E = torch.ones(1, dtype=torch.float64, device="cuda")

@@ -160,3 +160,27 @@ def test_nve_energy_is_conserved():
     assert H[0.001] < 1e-4
     # Verlet energy error is second order in dt
     assert H[0.002] / H[0.001] == pytest.approx(4.0, rel=0.35)
+
+
+def test_force_mixing_combines_the_two_complete_forces(sysA):
+    """Eq. 3 (force mixing): F_i = (1 - lam_i) F_i^fast + lam_i F_i^prec with the
+    complete forces of the two models, here taken from two independent constant
+    switches (lam = 0: the fast model everywhere; lam = 1: the precise model
+    everywhere, Appendix B), and lam from the paper's switch."""
+    s, prm, part, model, res = sysA
+    fm = apip.energy_forces(s["pos"], s["box"], s["ids"], part, prm, model=model, mixing="force")
+    f0 = apip.energy_forces(s["pos"], s["box"], s["ids"], part, prm, model=model, lam_mode="const0")["F"]
+    f1 = apip.energy_forces(s["pos"], s["box"], s["ids"], part, prm, model=model, lam_mode="const1")["F"]
+    lam = res["lam"][:, None]
+    np.testing.assert_allclose(fm["F"], (1 - lam) * f0 + lam * f1, atol=1e-11)
+    assert fm["E"] == res["E"]
+
+
+def test_force_mixing_breaks_newton_and_differs_from_the_gradient(sysA):
+    """Force mixing is not the gradient of Eq. 4 and does not conserve momentum
+    (the qualitative statements after Eq. 3)."""
+    s, prm, part, model, res = sysA
+    fm = apip.energy_forces(s["pos"], s["box"], s["ids"], part, prm, model=model, mixing="force")
+    assert np.abs(fm["F"].sum(axis=0)).max() > 1e-3
+    assert np.abs(res["F"].sum(axis=0)).max() < 1e-10
+    assert np.abs(fm["F"] - res["F"]).max() > 1e-2
