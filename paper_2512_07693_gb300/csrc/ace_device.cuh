@@ -80,9 +80,9 @@ __device__ __forceinline__ void for_each_ylm(T x, T y, T z, F&& f) {
 template <typename T>
 __device__ __forceinline__ void radial(T r, const AceDev<T>& t, T* R, T* dR) {
   T dfc;
-  const T fc = ftrans(r, t.rc_lo, t.rc, T(1) / (t.rc - t.rc_lo), &dfc);
-  const T x = T(1) - T(2) * r / t.rc;
-  const T dxdr = T(-2) / t.rc;
+  const T fc = ftrans(r, t.rc_lo, t.rc, t.inv_width, &dfc);
+  const T x = T(1) - t.two_over_rc * r;
+  const T dxdr = -t.two_over_rc;
   T tm2 = T(1), tm1 = x, dm2 = T(0), dm1 = T(1);
 #pragma unroll
   for (int n = 0; n < kNmaxCap; ++n) {
@@ -261,7 +261,7 @@ __device__ __forceinline__ void atom_scalars(const Args<T>& a, const AceDev<T>& 
     trans = (a.grad_lambda && (a.lam_mode == APIP_LAM_PAPER || a.lam_mode == APIP_LAM_LEARNED) && dl != T(0))
                 ? 1 : 0;
     et = trans ? delta * dl / a.wbar[i] : T(0);
-    D = a.dd[i] + T(a.sw.d0);
+    D = a.dd[i] + a.k.sw_d0;
     xi = a.xi_p[i];
   }
   g.lam[k] = lam; g.delta[k] = delta; g.et[k] = et; g.D[k] = D; g.xi[k] = xi; g.trans[k] = trans;
@@ -275,8 +275,8 @@ __device__ __forceinline__ double pair_forces(const Args<T>& a, const AceDev<T>&
   constexpr int NLM = (LMAX + 1) * (LMAX + 1);
   const int tid = threadIdx.x;
   const T rc2 = t.rc * t.rc;
-  const T rcE2 = T(a.eam.rc * a.eam.rc), rcE = T(a.eam.rc), rcE_lo = T(a.eam.rc_lo), rcE_inv = T(a.eam.inv_w);
-  const T rw2 = T(a.sw.r_w * a.sw.r_w), rw = T(a.sw.r_w), rw_lo = T(a.sw.r_w_lo), rw_inv = T(a.sw.inv_w);
+  const T rcE2 = a.k.eam_rc2, rcE = a.k.eam_rc, rcE_lo = a.k.eam_rc_lo, rcE_inv = a.k.eam_inv_w;
+  const T rw2 = a.k.sw_r_w2, rw = a.k.sw_r_w, rw_lo = a.k.sw_r_w_lo, rw_inv = a.k.sw_inv_w;
   // (force mixing weights the EAM force per atom in pass 2: no correction here)
   const bool eam_corr = !a.precise_adds_eam && a.eam_force && !a.force_mix;
   const int n_max = t.n_max;
@@ -326,10 +326,10 @@ __device__ __forceinline__ double pair_forces(const Args<T>& a, const AceDev<T>&
     if (in_e) {
       T dfc;
       const T fc = ftrans(r, rcE_lo, rcE, rcE_inv, &dfc);
-      const T er = T(a.eam.A) * exp(-T(a.eam.beta) * (r - T(a.eam.re)));
-      const T drho = er * (dfc - T(a.eam.beta) * fc);
-      const T x = exp(-T(a.eam.alpha) * (r - T(a.eam.r0)));
-      const T dphi = T(a.eam.D) * (T(2) * T(a.eam.alpha) * (x - x * x) * fc + (x * x - T(2) * x) * dfc);
+      const T er = a.k.eam_A * exp(-a.k.eam_beta * (r - a.k.eam_re));
+      const T drho = er * (dfc - a.k.eam_beta * fc);
+      const T x = exp(-a.k.eam_alpha * (r - a.k.eam_r0));
+      const T dphi = a.k.eam_D * (T(2) * a.k.eam_alpha * (x - x * x) * fc + (x * x - T(2) * x) * dfc);
       sr -= g.lam[k] * (g.xi[k] * drho + T(0.5) * dphi);
     }
     if (in_w) {

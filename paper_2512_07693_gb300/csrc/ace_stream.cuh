@@ -63,6 +63,13 @@ __device__ __forceinline__ void coupling(const T* Ak, T* Gk, int a1, int a2, int
                                          T dfs, Acc<T>& f1, Acc<T>& f2) {
   constexpr int N1 = 2 * L1 + 1, N2 = 2 * L2 + 1, NM = 2 * LL + 1;
   constexpr int G0 = gaunt_offset(L1, L2, LL);
+  constexpr int PF = 1;   // forward: partner records loaded ahead of the coupling arithmetic
+  Rec<T> pr[PF];
+  if constexpr (!ADJ) {
+#pragma unroll
+    for (int q = 0; q < PF; ++q)
+      if (pb + q < pe) pr[q] = ld(part + pb + q);
+  }
   T x1[N1], x2[N2], C[NM];
 #pragma unroll
   for (int i = 0; i < N1; ++i) x1[i] = Ak[(a1 + i) * NAT];
@@ -89,7 +96,19 @@ __device__ __forceinline__ void coupling(const T* Ak, T* Gk, int a1, int a2, int
     // the few partners of one coupling are summed plainly, the coupling's total
     // enters the compensated per-slice sums
     T s1 = T(0), s2 = T(0);
-    for (int p = pb; p < pe; ++p) {
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      if (pb + q < pe) {
+        const Rec<T> r = pr[q];
+        const T* y = Ak + r.key * NAT;
+        T d = T(0);
+#pragma unroll
+        for (int M = 0; M < NM; ++M) d += C[M] * y[M * NAT];
+        s1 += r.k1 * d;
+        s2 += r.k2 * d;
+      }
+    }
+    for (int p = pb + PF; p < pe; ++p) {
       const Rec<T> r = ld(part + p);
       const T* y = Ak + r.key * NAT;
       T d = T(0);

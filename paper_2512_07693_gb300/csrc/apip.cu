@@ -74,7 +74,7 @@ void free_all(apip_ctx* c) {
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   c->prof_pending.clear();
   c->prof_pool.clear();
-  void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nbl, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
+  void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->counts, c->flags, c->status, c->partials, c->thermo_part,
                   c->e_scratch, c->ace_tab, c->mlp_w, c->mlp_ws};
@@ -173,12 +173,16 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
            1.0 / p.eam_rc_width};
   a.sw = {p.sw_r_w, p.sw_r_w - p.sw_r_w_width, p.sw_d_lo, p.sw_d_hi, p.sw_d0, 1.0 / p.sw_r_w_width,
           1.0 / (p.sw_d_hi - p.sw_d_lo)};
+  a.k = {T(p.eam_A), T(p.eam_beta), T(p.eam_re), T(p.eam_D), T(p.eam_alpha), T(p.eam_r0), T(p.eam_rc),
+         T(p.eam_rc * p.eam_rc), T(p.eam_rc - p.eam_rc_width), T(1.0 / p.eam_rc_width),
+         T(p.sw_r_w), T(p.sw_r_w * p.sw_r_w), T(p.sw_r_w - p.sw_r_w_width), T(1.0 / p.sw_r_w_width),
+         T(p.sw_d_lo), T(p.sw_d_hi), T(1.0 / (p.sw_d_hi - p.sw_d_lo)), T(p.sw_d0)};
   a.r_list2 = c->r_list * c->r_list;
   a.skin_half2 = 0.25 * p.skin * p.skin;
   a.csp_rcut2 = p.csp_rcut * p.csp_rcut;
   a.pos = pos;
   a.id = id;
-  a.nnb = c->nnb; a.nbl = c->nbl; a.pos_ref = c->pos_ref; a.posq = c->posq; a.posq_ref = c->posq_ref;
+  a.nnb = c->nnb; a.nbl = c->nbl; a.nbl_tmp = c->nbl_tmp; a.pos_ref = c->pos_ref; a.posq = c->posq; a.posq_ref = c->posq_ref;
   a.id2idx = c->id2idx; a.csp = c->csp; a.cell_count = c->cell_count; a.cell_atoms = c->cell_atoms;
   a.cell_q = c->cell_q;
   a.zeta = as<T>(c->zeta); a.xi_p = as<T>(c->xi_p); a.e_eam = as<T>(c->e_eam); a.g = as<T>(c->g);
@@ -221,6 +225,8 @@ AceDev<T> ace_dev(apip_ctx* c) {
   t.eps = T(p.ace_eps);
   t.sqrt_eps = T(std::sqrt(p.ace_eps));
   t.a_scale = T(p.ace_a_scale);
+  t.two_over_rc = T(2.0 / p.ace_rc);
+  t.inv_width = T(1.0 / p.ace_rc_width);
   t.kind = c->ace_kind;
   t.nC = c->ace_nC;
   t.npool = c->ace_npool;
@@ -282,7 +288,7 @@ void pass1(const Args<T>& a, cudaStream_t s) {
 // The force pipeline after prep (or after the drift of a Verlet step).
 template <typename T>
 void force_pipeline(apip_ctx* c, Args<T>& a, cudaStream_t s) {
-  { Phase ph(c, APIP_PHASE_NEIGHBOR, 4, s); launch_neighbors<T>(a, c->ncell, s); }
+  { Phase ph(c, APIP_PHASE_NEIGHBOR, 5, s); launch_neighbors<T>(a, c->ncell, s); }
   { Phase ph(c, APIP_PHASE_PASS1, 1, s); pass1<T>(a, s); }
   { Phase ph(c, APIP_PHASE_PASS2, 1, s); launch_pass2<T>(a, s); if (a.force_mix) launch_fm_buffer<T>(a, s); }
   { Phase ph(c, APIP_PHASE_ACE, 1, s); const AceDev<T> t = ace_dev<T>(c);
@@ -461,6 +467,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   const size_t es = esize(ctx);
   APIP_ALLOC(ctx->nnb, sizeof(int) * N);
   APIP_ALLOC(ctx->nbl, sizeof(int) * N * p->max_nb);
+  APIP_ALLOC(ctx->nbl_tmp, sizeof(int) * N * p->max_nb);
   APIP_ALLOC(ctx->pos_ref, sizeof(double) * 3 * N);
   if (p->precision == APIP_FP32) {
     APIP_ALLOC(ctx->posq, sizeof(uint4) * N);

@@ -66,6 +66,7 @@ struct AceDev {
   int kind;                     // kAcePool or kAceStreamed
   int n_max, l_max, nA, nC, npool;   // nA = n_max (l_max+1)^2, npool = 1 + nA + nC
   T rc, rc_lo, eps, sqrt_eps, a_scale;
+  T two_over_rc, inv_width;     // 2 / rc and 1 / (rc - rc_lo) of the radial basis
   const uint2* comp;            // [nC]: (a1 | a2 << 16, gofs << 8 | gcnt) per C component
   const Ent<T>* gent;           // Gaunt entries
   const Rec<T>* frec; int nf;   // forward records, grouped by length
@@ -135,6 +136,7 @@ struct apip_ctx {
   int* cell_atoms = nullptr;
   int* nnb = nullptr;
   int* nbl = nullptr;          // column-major [max_nb][nmax]
+  int* nbl_tmp = nullptr;      // list build scratch, same layout
   double* pos_ref = nullptr;   // [nmax][3]
   uint4* posq = nullptr;       // FP32 path: fixed-point wrapped position (x, y, z, 0)
   uint4* posq_ref = nullptr;   // FP32 path: posq at the last neighbour-list build

@@ -8,6 +8,15 @@
 
 namespace apip {
 
+// The model parameters the per-atom passes use, converted (and squared) once on
+// the host in the path precision: float64 arithmetic is slow on this GPU, so no
+// kernel converts parameters per thread.
+template <typename T>
+struct PassK {
+  T eam_A, eam_beta, eam_re, eam_D, eam_alpha, eam_r0, eam_rc, eam_rc2, eam_rc_lo, eam_inv_w;
+  T sw_r_w, sw_r_w2, sw_r_w_lo, sw_inv_w, sw_d_lo, sw_d_hi, sw_inv_d, sw_d0;
+};
+
 // Everything a kernel of the force pipeline may need, passed by value.
 template <typename T>
 struct Args {
@@ -20,11 +29,12 @@ struct Args {
   Geo geo;
   EamP eam;
   SwP sw;
+  PassK<T> k;
   double r_list2, skin_half2, csp_rcut2;
 
   const double* pos;      // caller positions [n][3]
   const int* id;          // caller ids [n]
-  int* nnb; int* nbl; double* pos_ref; uint4* posq; uint4* posq_ref; int* id2idx; int* csp;
+  int* nnb; int* nbl; int* nbl_tmp; double* pos_ref; uint4* posq; uint4* posq_ref; int* id2idx; int* csp;
   int* cell_count; int* cell_atoms;
   uint4* cell_q;          // FP32 path: fixed-point positions of the cell members, cell order
   T* zeta; T* xi_p; T* e_eam; T* g; T* wbar; T* dd; T* lam; T* dlam; T* e_ace;
@@ -39,12 +49,12 @@ struct Args {
 // EAM density and pair terms of one neighbour at distance r < rc (Eq. B1, S7-S8):
 // rho(r) = A exp(-beta (r - r_e)) fc(r), Phi(r) = D [x^2 - 2x] fc(r), x = exp(-alpha (r - r_0)).
 template <typename T>
-__device__ __forceinline__ void eam_terms(const EamP& e, T r, T* rho, T* phi) {
+__device__ __forceinline__ void eam_terms(const PassK<T>& k, T r, T* rho, T* phi) {
   T dfc;
-  const T fc = ftrans(r, T(e.rc_lo), T(e.rc), T(e.inv_w), &dfc);
-  const T x = exp(-T(e.alpha) * (r - T(e.r0)));
-  *rho = T(e.A) * exp(-T(e.beta) * (r - T(e.re))) * fc;
-  *phi = T(e.D) * (x * x - T(2) * x) * fc;
+  const T fc = ftrans(r, k.eam_rc_lo, k.eam_rc, k.eam_inv_w, &dfc);
+  const T x = exp(-k.eam_alpha * (r - k.eam_r0));
+  *rho = k.eam_A * exp(-k.eam_beta * (r - k.eam_re)) * fc;
+  *phi = k.eam_D * (x * x - T(2) * x) * fc;
 }
 
 template <typename T> Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n,

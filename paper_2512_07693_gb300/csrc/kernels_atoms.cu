@@ -126,6 +126,9 @@ __global__ void k_cell_sort(const int* flags, const int* cell_count, int* cell_a
     for (int k = 0; k < cnt; ++k) cell_q[(size_t)c * cap + k] = posq[v[k]];
 }
 
+// One thread per atom: the candidates go to the scratch list in cell order,
+// those beyond the EAM cutoff marked by bit 31; k_nborder then writes the
+// final list.
 template <typename T>
 __global__ void k_nbfill(Args<T> a) {
   if (!a.flags[0]) return;
@@ -136,47 +139,52 @@ __global__ void k_nbfill(Args<T> a) {
   for (int k = 0; k < 3; ++k)
     c[k] = cell_of(wrap1(a.pos[3 * i + k], a.geo.L[k], a.geo.invL[k]), a.geo.L[k], a.geo.nc[k]);
   const auto si = a.pv.self(i);
-  int cnt = 0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int cz = (c[2] + dz + a.geo.nc[2]) % a.geo.nc[2];
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int cy = (c[1] + dy + a.geo.nc[1]) % a.geo.nc[1];
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int cx = (c[0] + dx + a.geo.nc[0]) % a.geo.nc[0];
-        const int cell = (cz * a.geo.nc[1] + cy) * a.geo.nc[0] + cx;
-        const int m = min(a.cell_count[cell], a.cell_cap);
-        const int* v = a.cell_atoms + (size_t)cell * a.cell_cap;
-        if constexpr (sizeof(T) == 4) {
-          // float comparison against r_list^2 rounded up: the list holds every pair
-          // whose float distance is below r_list (and perhaps a few at r_list)
-          const uint4* cq = a.cell_q + (size_t)cell * a.cell_cap;
-          const float rl2 = __double2float_ru(a.r_list2);
-          for (int k = 0; k < m; ++k) {
-            const uint4 o = cq[k];
-            const float dx = (float)(int)(o.x - si.q.x) * a.pv.unit[0];
-            const float dy = (float)(int)(o.y - si.q.y) * a.pv.unit[1];
-            const float dz = (float)(int)(o.z - si.q.z) * a.pv.unit[2];
-            if (dx * dx + dy * dy + dz * dz < rl2) {
+  // calls f(j, r^2) for every atom j != i within r_list, in cell order
+  auto scan = [&](auto&& f) {
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int cz = (c[2] + dz + a.geo.nc[2]) % a.geo.nc[2];
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int cy = (c[1] + dy + a.geo.nc[1]) % a.geo.nc[1];
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int cx = (c[0] + dx + a.geo.nc[0]) % a.geo.nc[0];
+          const int cell = (cz * a.geo.nc[1] + cy) * a.geo.nc[0] + cx;
+          const int m = min(a.cell_count[cell], a.cell_cap);
+          const int* v = a.cell_atoms + (size_t)cell * a.cell_cap;
+          if constexpr (sizeof(T) == 4) {
+            // float comparison against r_list^2 rounded up: the list holds every pair
+            // whose float distance is below r_list (and perhaps a few at r_list)
+            const uint4* cq = a.cell_q + (size_t)cell * a.cell_cap;
+            const float rl2 = __double2float_ru(a.r_list2);
+            for (int k = 0; k < m; ++k) {
+              const uint4 o = cq[k];
+              const float ex = (float)(int)(o.x - si.q.x) * a.pv.unit[0];
+              const float ey = (float)(int)(o.y - si.q.y) * a.pv.unit[1];
+              const float ez = (float)(int)(o.z - si.q.z) * a.pv.unit[2];
+              const float r2 = ex * ex + ey * ey + ez * ez;
+              if (r2 < rl2) {
+                const int j = v[k];
+                if (j != i) f(j, r2);
+              }
+            }
+          } else {
+            for (int k = 0; k < m; ++k) {
               const int j = v[k];
               if (j == i) continue;
-              if (cnt < a.max_nb) a.nbl[(size_t)cnt * a.nmax + i] = j;
-              ++cnt;
-            }
-          }
-        } else {
-          for (int k = 0; k < m; ++k) {
-            const int j = v[k];
-            if (j == i) continue;
-            const auto d = a.pv.vec(si, j);
-            if ((double)dot3(d, d) < a.r_list2) {
-              if (cnt < a.max_nb) a.nbl[(size_t)cnt * a.nmax + i] = j;
-              ++cnt;
+              const auto d = a.pv.vec(si, j);
+              const T r2 = dot3(d, d);
+              if ((double)r2 < a.r_list2) f(j, r2);
             }
           }
         }
       }
     }
-  }
+  };
+  const T rin2 = a.k.eam_rc2;
+  int cnt = 0;
+  scan([&](int j, T r2) {
+    if (cnt < a.max_nb) a.nbl_tmp[(size_t)cnt * a.nmax + i] = r2 < rin2 ? j : (int)((unsigned)j | 0x80000000u);
+    ++cnt;
+  });
   if (cnt > a.max_nb) {
     atomicOr(&a.status[ST_NB_OVERFLOW], 1);
     atomicMax(&a.status[ST_MAX_NNB], cnt);
@@ -188,6 +196,25 @@ __global__ void k_nbfill(Args<T> a) {
     a.pos_ref[3 * i] = a.pos[3 * i];
     a.pos_ref[3 * i + 1] = a.pos[3 * i + 1];
     a.pos_ref[3 * i + 2] = a.pos[3 * i + 2];
+  }
+}
+
+// The final list: the entries within the EAM cutoff (at build time) first, then
+// the rest, each part in cell order, so that the lanes of a warp take the same
+// branches at the same list position in the passes.
+__global__ void k_nborder(const int* flags, const int* nnb, const int* tmp, int* nbl, int n, int nmax) {
+  if (!flags[0]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int cnt = nnb[i];
+  int p = 0;
+  for (int s = 0; s < cnt; ++s) {
+    const int e = tmp[(size_t)s * nmax + i];
+    if (e >= 0) nbl[(size_t)(p++) * nmax + i] = e;
+  }
+  for (int s = 0; s < cnt; ++s) {
+    const int e = tmp[(size_t)s * nmax + i];
+    if (e < 0) nbl[(size_t)(p++) * nmax + i] = e & 0x7fffffff;
   }
 }
 
@@ -264,10 +291,9 @@ __global__ void __launch_bounds__(kBlock, 8) k_pass1(Args<T> a) {
   double e_out = 0.0;
   if (i < a.n) {
     const auto si = a.pv.self(i);
-    const T rc2 = T(a.eam.rc * a.eam.rc), rc = T(a.eam.rc), rlo = T(a.eam.rc_lo);
-    const T inv_w = T(a.eam.inv_w);
-    const T A = T(a.eam.A), beta = T(a.eam.beta), re = T(a.eam.re), D = T(a.eam.D),
-            alpha = T(a.eam.alpha), r0 = T(a.eam.r0);
+    const T rc2 = a.k.eam_rc2, rc = a.k.eam_rc, rlo = a.k.eam_rc_lo, inv_w = a.k.eam_inv_w;
+    const T A = a.k.eam_A, beta = a.k.eam_beta, re = a.k.eam_re, D = a.k.eam_D, alpha = a.k.eam_alpha,
+            r0 = a.k.eam_r0;
     Acc<T> zeta, pair;
     const int cnt = a.nnb[i];
     const int* nb = a.nbl + i;
@@ -329,12 +355,10 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
   if (active) {
     const auto si = a.pv.self(i);
     const bool paper = a.lam_mode == APIP_LAM_PAPER || a.lam_mode == APIP_LAM_LEARNED;
-    const T rw2 = T(a.sw.r_w * a.sw.r_w), rw = T(a.sw.r_w), rwlo = T(a.sw.r_w_lo);
-    const T rw_inv = T(a.sw.inv_w);
-    const T rc2 = T(a.eam.rc * a.eam.rc), rc = T(a.eam.rc), rlo = T(a.eam.rc_lo);
-    const T inv_w = T(a.eam.inv_w);
-    const T A = T(a.eam.A), beta = T(a.eam.beta), re = T(a.eam.re), D = T(a.eam.D),
-            alpha = T(a.eam.alpha), r0 = T(a.eam.r0);
+    const T rw2 = a.k.sw_r_w2, rw = a.k.sw_r_w, rwlo = a.k.sw_r_w_lo, rw_inv = a.k.sw_inv_w;
+    const T rc2 = a.k.eam_rc2, rc = a.k.eam_rc, rlo = a.k.eam_rc_lo, inv_w = a.k.eam_inv_w;
+    const T A = a.k.eam_A, beta = a.k.eam_beta, re = a.k.eam_re, D = a.k.eam_D, alpha = a.k.eam_alpha,
+            r0 = a.k.eam_r0;
     const T xi_i = a.xi_p[i];
     Sum<T> wbar, S, fx, fy, fz;
     wbar.add(T(1));
@@ -372,8 +396,8 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
     T dv = T(0), dl = T(0), wb = T(1);
     if (paper) {
       wb = wbar.value();
-      dv = S.value() / wb - T(a.sw.d0);
-      lam = ftrans_c(dv, T(a.sw.d_lo), T(a.sw.d_hi), T(a.sw.inv_d), &dl);
+      dv = S.value() / wb - a.k.sw_d0;
+      lam = ftrans_c(dv, a.k.sw_d_lo, a.k.sw_d_hi, a.k.sw_inv_d, &dl);
     } else {
       lam = a.lam_mode == APIP_LAM_CONST1 ? T(1) : T(0);
     }
@@ -570,6 +594,7 @@ template <typename T> void launch_neighbors(const Args<T>& a, int ncell, cudaStr
   k_cell_sort<<<nblocks(ncell), kBlock, 0, s>>>(a.flags, a.cell_count, a.cell_atoms, ncell, a.cell_cap,
                                                  sizeof(T) == 4 ? a.posq : nullptr, sizeof(T) == 4 ? a.cell_q : nullptr);
   k_nbfill<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+  k_nborder<<<nblocks(a.n), kBlock, 0, s>>>(a.flags, a.nnb, a.nbl_tmp, a.nbl, a.n, a.nmax);
 }
 
 void launch_csp_init(const Args<double>& a, cudaStream_t s) {

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(128) k_pass1_learned(Args<T> a) {
   double e_out = 0.0;
   if (i < a.n) {
     const auto si = a.pv.self(i);
-    const T rcE2 = T(a.eam.rc * a.eam.rc);
+    const T rcE2 = a.k.eam_rc2;
     const T rc2 = a.ace_rc * a.ace_rc, inv_w = T(1) / (a.ace_rc - a.ace_rc_lo);
     Acc<T> zeta, pair;
     T G[kIn];
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(128) k_pass1_learned(Args<T> a) {
       const T r = sqrt(r2);
       if (r2 < rcE2) {
         T rho, phi;
-        eam_terms(a.eam, r, &rho, &phi);
+        eam_terms(a.k, r, &rho, &phi);
         zeta.add(rho);
         pair.add(phi);
       }
