@@ -176,6 +176,21 @@ apip_status apip_energy_forces(apip_ctx* ctx, const double* pos, const double bo
                                double* force_out, double* e_atom_out, double* e_total_out,
                                void* stream);
 
+/* A spherical repulsive indenter (an external potential of the indentation
+ * workload, not part of the AP Hamiltonian): for r = |x_i - c| < radius,
+ * E_i = k/3 (radius - r)^3 and F_i = k (radius - r)^2 (x_i - c)/r, added to E,
+ * e_atom and F.  The centre (host, Angstrom) moves at velocity (host, A/ps) during
+ * apip_verlet_step (by velocity * dt per step, with the drift); the work
+ * W = int (sum_i F_i) . velocity dt done on the atoms accumulates on the device
+ * (midpoint rule), so that H - W is conserved.  radius <= 0 removes it; every
+ * call resets W to 0.  Errors: APIP_ERR_ARG. */
+apip_status apip_set_indenter(apip_ctx* ctx, const double center[3], const double velocity[3], double radius,
+                              double k);
+
+/* The indenter's current centre and accumulated work W (host outputs;
+ * synchronises the device).  Errors: APIP_ERR_ARG (NULL argument), APIP_ERR_CUDA. */
+apip_status apip_indenter_state(apip_ctx* ctx, double center[3], double* work);
+
 /* Constant lam on a subset of atoms (Appendix B): lam_fixed (device, float64,
  * n entries, caller-owned and kept alive while set) holds NaN for atoms whose lam
  * follows the switch and the constant value (in [0, 1]) for the others; those

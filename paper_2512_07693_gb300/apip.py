@@ -74,6 +74,8 @@ def _load():
         "apip_reduce_energy_static": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
         "apip_set_mlp": (ctypes.c_int, [_vp, _vp, _vp]),
         "apip_set_lam_fixed": (ctypes.c_int, [_vp, _vp, _c_int64]),
+        "apip_set_indenter": (ctypes.c_int, [_vp, P(_c_double), P(_c_double), _c_double, _c_double]),
+        "apip_indenter_state": (ctypes.c_int, [_vp, P(_c_double), P(_c_double)]),
         "apip_descriptors": (ctypes.c_int, [_vp, _vp, P(_c_double), _vp, _c_int64, _vp, _vp]),
         "apip_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, _c_int64, _vp, _vp, _vp, _vp]),
         "apip_mlp_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _c_int32, ctypes.c_float, _vp]),
@@ -213,6 +215,21 @@ def apip_set_lam_fixed(ctx, lam_fixed, n):
     _check(ctx, lib.apip_set_lam_fixed(ctx, _ptr(lam_fixed), int(n)))
 
 
+def apip_set_indenter(ctx, center, velocity, radius, k):
+    """Spherical indenter (host centre and velocity); radius <= 0 removes it."""
+    c = (_c_double * 3)(*[float(v) for v in center])
+    v = (_c_double * 3)(*[float(x) for x in velocity])
+    _check(ctx, lib.apip_set_indenter(ctx, c, v, float(radius), float(k)))
+
+
+def apip_indenter_state(ctx):
+    """(centre as a list, accumulated work W)."""
+    c = (_c_double * 3)()
+    w = _c_double()
+    _check(ctx, lib.apip_indenter_state(ctx, c, ctypes.byref(w)))
+    return [c[0], c[1], c[2]], w.value
+
+
 def apip_descriptors(ctx, pos, box, id, n, desc_bf16, stream=None):
     _check(ctx, lib.apip_descriptors(ctx, _ptr(pos), _box(box), _ptr(id), int(n), _ptr(desc_bf16), _stream(stream)))
 
@@ -323,6 +340,12 @@ class Apip:
 
     def set_mlp(self, params, stream=None):
         apip_set_mlp(self.ctx, params, stream)
+
+    def set_indenter(self, center, velocity, radius, k):
+        apip_set_indenter(self.ctx, center, velocity, radius, k)
+
+    def indenter_state(self):
+        return apip_indenter_state(self.ctx)
 
     def set_lam_fixed(self, lam_fixed):
         self._lam_fixed = lam_fixed   # the library reads it on later calls

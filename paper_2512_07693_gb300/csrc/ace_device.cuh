@@ -338,20 +338,30 @@ __device__ __forceinline__ double pair_forces(const Args<T>& a, const AceDev<T>&
       sr += g.et[k] * (a.g[j] - g.D[k]) * dw;
       atomicAdd(&a.cvec[j], (double)(g.et[k] * w));
     }
-    const double f0 = (double)(sr * ex + gx), f1 = (double)(sr * ey + gy), f2 = (double)(sr * ez + gz);
-    // AP (Eq. 5): omega already carries lam_i, and the pair term is antisymmetric.
-    // Force mixing (Eq. 3): each receiving atom takes its own lam of the precise
-    // model's force (omega without lam).
-    const double wj = a.force_mix ? (double)a.lam[j] : 1.0, wi = a.force_mix ? (double)g.lam[k] : 1.0;
-    if (wj != 0.0) {
-      atomicAdd(&a.force[3 * j], -wj * f0);
-      atomicAdd(&a.force[3 * j + 1], -wj * f1);
-      atomicAdd(&a.force[3 * j + 2], -wj * f2);
-    }
-    if (wi != 0.0) {
-      atomicAdd(&a.force[3 * i], wi * f0);
-      atomicAdd(&a.force[3 * i + 1], wi * f1);
-      atomicAdd(&a.force[3 * i + 2], wi * f2);
+    const T fx = sr * ex + gx, fy = sr * ey + gy, fz = sr * ez + gz;
+    if (!a.force_mix) {
+      // AP (Eq. 5): omega already carries lam_i, and the pair term is antisymmetric
+      const double f0 = (double)fx, f1 = (double)fy, f2 = (double)fz;
+      atomicAdd(&a.force[3 * j], -f0);
+      atomicAdd(&a.force[3 * j + 1], -f1);
+      atomicAdd(&a.force[3 * j + 2], -f2);
+      atomicAdd(&a.force[3 * i], f0);
+      atomicAdd(&a.force[3 * i + 1], f1);
+      atomicAdd(&a.force[3 * i + 2], f2);
+    } else {
+      // force mixing (Eq. 3): each receiving atom takes its own lam of the precise
+      // model's force (omega without lam)
+      const T wj = a.lam[j], wi = g.lam[k];
+      if (wj != T(0)) {
+        atomicAdd(&a.force[3 * j], -(double)(wj * fx));
+        atomicAdd(&a.force[3 * j + 1], -(double)(wj * fy));
+        atomicAdd(&a.force[3 * j + 2], -(double)(wj * fz));
+      }
+      if (wi != T(0)) {
+        atomicAdd(&a.force[3 * i], (double)(wi * fx));
+        atomicAdd(&a.force[3 * i + 1], (double)(wi * fy));
+        atomicAdd(&a.force[3 * i + 2], (double)(wi * fz));
+      }
     }
   }
   double e_part = 0.0;

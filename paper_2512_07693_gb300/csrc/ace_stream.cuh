@@ -201,6 +201,18 @@ __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev
   const int count = a.counts[0];
   const int ngroups = (count + NAT - 1) / NAT;
   double e_part = 0.0;
+  if (blockIdx.x < ngroups) {
+    // bring the basis tables into this SM's L1 while step 1 runs (they are read by
+    // every group; 128-byte lines, one prefetch per thread and line)
+    auto prefetch = [&](const void* p, size_t bytes) {
+      const char* c = static_cast<const char*>(p);
+      for (size_t o = (size_t)tid * 128; o < bytes; o += (size_t)kAceThreads * 128)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(c + o));
+    };
+    prefetch(t.cpl, sizeof(uint4) * (size_t)t.ncpl);
+    prefetch(t.part, sizeof(Rec<T>) * (size_t)t.npart);
+    prefetch(t.prec, sizeof(Rec<T>) * (size_t)t.npr);
+  }
 
   for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     group_setup<T, NAT>(a, grp, count, g);

@@ -77,7 +77,7 @@ void free_all(apip_ctx* c) {
   void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->counts, c->flags, c->status, c->partials, c->thermo_part,
-                  c->e_scratch, c->ace_tab, c->mlp_w, c->mlp_ws};
+                  c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_ws};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -153,6 +153,20 @@ apip_status set_geometry(apip_ctx* ctx, const double* box, cudaStream_t s) {
 
 namespace apip {
 
+// The indenter centre for the kernels: as given (FP64 path) and as wrapped
+// fixed-point coordinates (FP32 path).
+template <typename T>
+void set_ind_center(Args<T>& a, const Geo& g, const double c[3]) {
+  unsigned q[3];
+  for (int k = 0; k < 3; ++k) {
+    a.ind_c[k] = c[k];
+    double w = c[k] - g.L[k] * std::floor(c[k] * g.invL[k]);
+    if (w >= g.L[k]) w -= g.L[k];
+    q[k] = (unsigned)((unsigned long long)(w * g.inv_unit[k]) & 0xffffffffull);
+  }
+  a.ind_q = make_uint4(q[0], q[1], q[2], 0u);
+}
+
 template <typename T>
 Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* force, double* e_atom) {
   Args<T> a{};
@@ -168,6 +182,13 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.grad_lambda = a.force_mix ? 0 : p.grad_lambda;
   a.eam_force = 1;
   a.lam_fixed = c->lam_fixed;
+  a.ind_on = c->ind_on ? 1 : 0;
+  a.ind_acc = c->ind_acc;
+  a.ind_R = T(c->ind_R);
+  a.ind_R2 = T(c->ind_R * c->ind_R);
+  a.ind_K = T(c->ind_K);
+  for (int k = 0; k < 3; ++k) a.ind_v[k] = c->ind_v[k];
+  set_ind_center(a, c->geo, c->ind_c);
   a.geo = c->geo;
   a.eam = {p.eam_A, p.eam_beta, p.eam_re, p.eam_D, p.eam_alpha, p.eam_r0, p.eam_rc, p.eam_rc - p.eam_rc_width,
            1.0 / p.eam_rc_width};
@@ -237,6 +258,7 @@ AceDev<T> ace_dev(apip_ctx* c) {
     t.cpl = reinterpret_cast<const uint4*>(b + c->ace_off[1]);
     t.ncpl = c->ace_ncpl;
     t.part = reinterpret_cast<const Rec<T>*>(b + c->ace_off[2]);
+    t.npart = c->ace_npart;
     t.group = c->ace_group;
     return t;
   }
@@ -313,6 +335,7 @@ apip_status energy_forces_t(apip_ctx* c, const double* pos, const int32_t* id, i
   Phase ph(c, APIP_PHASE_REDUCE, 1, s);
   launch_final(c->partials, a.n_part_p1 + c->ace_blocks, e_total, nullptr, nullptr, 0, nullptr,
                c->flags, c->counts, nullptr, s);
+  if (a.ind_on) launch_ind_work(c->ind_acc, 0.0, s);
   return launch_status(c);
 }
 
@@ -352,7 +375,12 @@ apip_status verlet_t(apip_ctx* c, double* pos, double* vel, double* force, const
   const int n_part = a.n_part_p1 + c->ace_blocks;
   for (int k = 0; k < steps; ++k) {
     { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, k == 0 ? 0 : 1, pos, vel, force, inv_mass, dt, c->thermo_part, s); }
+    if (a.ind_on) {   // the indenter centre moves with the drift
+      for (int q = 0; q < 3; ++q) c->ind_c[q] += dt * c->ind_v[q];
+      set_ind_center(a, c->geo, c->ind_c);
+    }
     force_pipeline<T>(c, a, s);
+    if (a.ind_on) launch_ind_work(c->ind_acc, dt, s);
     Phase ph(c, APIP_PHASE_REDUCE, 1, s);
     launch_final(c->partials, n_part, nullptr, thermo ? thermo + 5 * k : nullptr,
                  (thermo && k > 0) ? c->thermo_part : nullptr, ntb, thermo ? thermo + 5 * (k - 1) : nullptr,
@@ -486,6 +514,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->partials, sizeof(double) * (p1 + ctx->ace_blocks));
   APIP_ALLOC(ctx->thermo_part, sizeof(double) * 4 * p1);
   APIP_ALLOC(ctx->e_scratch, sizeof(double) * 2);
+  APIP_ALLOC(ctx->ind_acc, sizeof(double) * 3);
   APIP_ALLOC(ctx->mlp_w, es * APIP_MLP_NPARAM);
   // ACE tables: one buffer, sub-arrays 256-byte aligned
   const bool f32 = p->precision == APIP_FP32;
@@ -525,6 +554,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
     put_rec(2, st.tkey, nullptr, st.t1, st.t2);
     ctx->ace_npr = (int)st.pkey.size();
     ctx->ace_ncpl = (int)(st.cpl.size() / 4);
+    ctx->ace_npart = (int)st.tkey.size();
     ctx->ace_npool = 1 + nA;
     int64_t* info = ctx->ace_info;
     info[0] = 1 + nA;
@@ -578,6 +608,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   if (e == cudaSuccess) e = cudaMemset(ctx->id2idx, 0xff, sizeof(int) * N);
   if (e == cudaSuccess) e = cudaMemset(ctx->csp, 0xff, sizeof(int) * N * kCspCap);
   if (e == cudaSuccess) e = cudaMemset(ctx->cvec, 0, sizeof(double) * N);
+  if (e == cudaSuccess) e = cudaMemset(ctx->ind_acc, 0, sizeof(double) * 3);
   if (e == cudaSuccess) e = cudaMemset(ctx->counts, 0, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMemset(ctx->flags, 0xff, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(int) * ST_COUNT);
@@ -792,6 +823,36 @@ apip_status apip_profile_read(apip_ctx* ctx, double* ms, int64_t* launches) {
     ctx->prof_ms[k] = 0.0;
     ctx->prof_n[k] = 0;
   }
+  return APIP_OK;
+}
+
+apip_status apip_set_indenter(apip_ctx* ctx, const double center[3], const double velocity[3], double radius,
+                              double k) {
+  if (!ctx) return APIP_ERR_ARG;
+  if (radius > 0.0) {
+    if (!center || !velocity) return fail(ctx, APIP_ERR_ARG, "center and velocity must not be NULL");
+    if (!(k > 0.0)) return fail(ctx, APIP_ERR_ARG, "the indenter stiffness must be > 0");
+    for (int q = 0; q < 3; ++q) {
+      if (!std::isfinite(center[q]) || !std::isfinite(velocity[q]))
+        return fail(ctx, APIP_ERR_ARG, "non-finite indenter centre or velocity");
+      ctx->ind_c[q] = center[q];
+      ctx->ind_v[q] = velocity[q];
+    }
+  }
+  ctx->ind_on = radius > 0.0;
+  ctx->ind_R = radius > 0.0 ? radius : 0.0;
+  ctx->ind_K = k;
+  APIP_CK(cudaMemset(ctx->ind_acc, 0, sizeof(double) * 3));
+  return APIP_OK;
+}
+
+apip_status apip_indenter_state(apip_ctx* ctx, double center[3], double* work) {
+  if (!ctx || !center || !work) return APIP_ERR_ARG;
+  APIP_CK(cudaDeviceSynchronize());
+  double acc[3];
+  APIP_CK(cudaMemcpy(acc, ctx->ind_acc, sizeof(acc), cudaMemcpyDeviceToHost));
+  for (int q = 0; q < 3; ++q) center[q] = ctx->ind_c[q];
+  *work = acc[0];
   return APIP_OK;
 }
 

@@ -78,7 +78,7 @@ struct AceDev {
   // streamed tables
   const Rec<T>* prec; int npr;  // nu 1, 2: key a1 | a2 << 16 (A indices; a2 = 0xffff: the constant 1), len
   const uint4* cpl; int ncpl;   // couplings: (a1 | a2 << 8 | type << 16, partner begin, partner end, 0)
-  const Rec<T>* part;           // nu = 3 partners: key = A index of A_{p3, m = -l3}
+  const Rec<T>* part; int npart;  // nu = 3 partners: key = A index of A_{p3, m = -l3}
   int group;                    // compacted atoms per thread block
 };
 
@@ -126,6 +126,9 @@ struct apip_ctx {
   int ncell = 0, ncell_alloc = 0;
   bool csp_ready = false;
   const double* lam_fixed = nullptr;  // caller's per-atom constant lam (NaN = switch)
+  bool ind_on = false;                 // spherical indenter
+  double ind_c[3] = {}, ind_v[3] = {}, ind_R = 0.0, ind_K = 0.0;
+  double* ind_acc = nullptr;           // [3] device: W, (sum F).v old, new
   int64_t lam_fixed_n = 0;
   std::string err;
   std::vector<double> ace_c1, ace_c2;
@@ -172,7 +175,7 @@ struct apip_ctx {
   size_t ace_off[8] = {};
   int ace_nf = 0, ace_npc = 0, ace_nC = 0, ace_npool = 0;
   int ace_group = 1;
-  int ace_kind = 0, ace_npr = 0, ace_ncpl = 0;
+  int ace_kind = 0, ace_npr = 0, ace_ncpl = 0, ace_npart = 0;
   int64_t ace_info[APIP_ACE_INFO_COUNT] = {};
 
   // learned indicator

@@ -77,8 +77,7 @@ template <> __device__ __forceinline__ void len_inv<double>(double r2, double* r
 }
 
 // Plain running sum, for the float32 sums whose rounding (~1e-7 relative over
-// some tens of terms) is far below their tolerance: per-atom forces and the
-// switch weights.  Energies keep the compensated Acc.
+// some tens of terms) is far below their tolerance (the switch weights).
 template <typename T> struct Sum {
   T s = T(0);
   __device__ __forceinline__ void add(T v) { s += v; }
@@ -143,6 +142,53 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   if (w == 0) v = warp_sum(v);
   __syncthreads();
   return v;
+}
+
+// Block-wide sum of a value of the path precision, returned in float64 (valid
+// in thread 0): the warp-level part in T, the rest in float64 (float64 adds are
+// slow on this GPU; 32 float32 terms round at ~1e-7 of their sum).
+template <typename T>
+__device__ __forceinline__ double block_sum_t(T v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = (double)v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  double d = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (w == 0) d = warp_sum(d);
+  __syncthreads();
+  return d;
+}
+
+// Block-wide sums of four float64 values (valid in thread 0, out[0..3]).  The
+// first two exchange steps halve the values a lane carries (it keeps two of the
+// four partial sums, then one), so a lane does 2 + 1 + 3 = 6 float64 adds
+// instead of 4 x 5.  sh holds 4 x 32 doubles; blockDim.x <= 1024.
+__device__ __forceinline__ void block_sum4(const double v[4], double* sh, double out[4]) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool b16 = (lane & 16) != 0, b8 = (lane & 8) != 0;
+  double k0 = b16 ? v[2] : v[0], k1 = b16 ? v[3] : v[1];
+  k0 += __shfl_xor_sync(full, b16 ? v[0] : v[2], 16);
+  k1 += __shfl_xor_sync(full, b16 ? v[1] : v[3], 16);
+  double k = b8 ? k1 : k0;
+  k += __shfl_xor_sync(full, b8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(full, k, 4);
+  k += __shfl_xor_sync(full, k, 2);
+  k += __shfl_xor_sync(full, k, 1);
+  // lane 8 q' holds the warp sum of value q = 2 (lane >> 4) + ((lane >> 3) & 1)
+  if ((lane & 7) == 0) sh[((b16 ? 2 : 0) + (b8 ? 1 : 0)) * 32 + w] = k;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (w == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double d = lane < nw ? sh[q * 32 + lane] : 0.0;
+      d = warp_sum(d);
+      if (lane == 0) out[q] = d;
+    }
+  }
+  __syncthreads();
 }
 
 }  // namespace apip

@@ -25,6 +25,13 @@ struct Args {
   int eam_force;          // pass 2 computes the (unweighted) EAM force
   int force_mix;          // force mixing (Eq. 3) instead of the AP force (Eq. 5)
   const double* lam_fixed;  // per-atom constant lam (NaN = switch) or null
+  // spherical indenter (external potential), ind_on = 0 when absent
+  int ind_on;
+  double ind_c[3];        // centre (FP64 path)
+  uint4 ind_q;            // centre as fixed-point coordinates (FP32 path)
+  T ind_R, ind_R2, ind_K;
+  double ind_v[3];        // centre velocity
+  double* ind_acc;        // [3] device: work W, (sum F).v of the previous and of this evaluation
   PosView<T> pv;
   Geo geo;
   EamP eam;
@@ -57,6 +64,40 @@ __device__ __forceinline__ void eam_terms(const PassK<T>& k, T r, T* rho, T* phi
   *phi = k.eam_D * (x * x - T(2) * x) * fc;
 }
 
+// Vector from the indenter centre to atom i (minimum image) and its square.
+template <typename T>
+__device__ __forceinline__ V3<T> ind_vec(const Args<T>& a, int i, T* r2);
+template <>
+__device__ __forceinline__ V3<float> ind_vec<float>(const Args<float>& a, int i, float* r2) {
+  const uint4 q = a.posq[i];
+  const V3<float> d{(float)(int)(q.x - a.ind_q.x) * a.pv.unit[0], (float)(int)(q.y - a.ind_q.y) * a.pv.unit[1],
+                    (float)(int)(q.z - a.ind_q.z) * a.pv.unit[2]};
+  *r2 = dot3(d, d);
+  return d;
+}
+template <>
+__device__ __forceinline__ V3<double> ind_vec<double>(const Args<double>& a, int i, double* r2) {
+  double d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    d[k] = a.pos[3 * i + k] - a.ind_c[k];
+    d[k] -= a.geo.L[k] * rint(d[k] * a.geo.invL[k]);
+  }
+  *r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  return {d[0], d[1], d[2]};
+}
+
+// Indenter energy K/3 (R - r)^3 of atom i (zero outside the sphere or without one).
+template <typename T>
+__device__ __forceinline__ T ind_energy(const Args<T>& a, int i) {
+  if (!a.ind_on) return T(0);
+  T r2;
+  ind_vec(a, i, &r2);
+  if (!(r2 < a.ind_R2)) return T(0);
+  const T gap = a.ind_R - sqrt(r2);
+  return a.ind_K / T(3) * gap * gap * gap;
+}
+
 template <typename T> Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n,
                                         double* force, double* e_atom);
 
@@ -69,6 +110,8 @@ template <typename T> void launch_pass2(const Args<T>& a, cudaStream_t s);
 // force mixing: append to the compacted list every atom with lam = 0 that has a
 // neighbour within the ACE cutoff with lam > 0 (the precise model's buffer)
 template <typename T> void launch_fm_buffer(const Args<T>& a, cudaStream_t s);
+// indenter work: W += dt/2 ((sum F).v old + new) when dt > 0; then old = new, new = 0
+void launch_ind_work(double* acc, double dt, cudaStream_t s);
 template <typename T> void launch_csp_force(const Args<T>& a, cudaStream_t s);
 void launch_final(double* partials, int n_part, double* e_total, double* e_pot_slot,
                   const double* thermo_part, int n_tblocks, double* thermo_slot, int* flags,

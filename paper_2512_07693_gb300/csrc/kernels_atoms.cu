@@ -288,7 +288,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock, 8) k_pass1(Args<T> a) {
   __shared__ double sh[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double e_out = 0.0;
+  T e_out = T(0);
   if (i < a.n) {
     const auto si = a.pv.self(i);
     const T rc2 = a.k.eam_rc2, rc = a.k.eam_rc, rlo = a.k.eam_rc_lo, inv_w = a.k.eam_inv_w;
@@ -317,8 +317,9 @@ __global__ void __launch_bounds__(kBlock, 8) k_pass1(Args<T> a) {
     a.zeta[i] = z;
     a.xi_p[i] = z > T(0) ? T(-0.5) / sz : T(0);
     a.e_eam[i] = e;
-    if (a.e_atom) a.e_atom[i] = (double)e;
-    e_out = (double)e;
+    const T e_ind = ind_energy(a, i);   // the external indenter, if any
+    if (a.e_atom) a.e_atom[i] = (double)e + (double)e_ind;
+    e_out = e + e_ind;
     T g = T(0);
     if (a.lam_mode == APIP_LAM_PAPER) {
       Acc<T> gs;
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_pass1(Args<T> a) {
     }
     a.g[i] = g;
   }
-  const double tot = block_sum(e_out, sh);
+  const double tot = block_sum_t(e_out, sh);
   if (threadIdx.x == 0) a.partials[blockIdx.x] = tot;
 }
 
@@ -352,6 +353,7 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = i < a.n;
   T lam = T(0);
+  double ind_fv = 0.0;   // this atom's indenter force . centre velocity
   if (active) {
     const auto si = a.pv.self(i);
     const bool paper = a.lam_mode == APIP_LAM_PAPER || a.lam_mode == APIP_LAM_LEARNED;
@@ -360,7 +362,10 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
     const T A = a.k.eam_A, beta = a.k.eam_beta, re = a.k.eam_re, D = a.k.eam_D, alpha = a.k.eam_alpha,
             r0 = a.k.eam_r0;
     const T xi_i = a.xi_p[i];
-    Sum<T> wbar, S, fx, fy, fz;
+    // the force components keep compensated sums: their rounding decides how well
+    // the float32 path conserves the total momentum; the switch weights do not
+    Sum<T> wbar, S;
+    Acc<T> fx, fy, fz;
     wbar.add(T(1));
     if (paper) S.add(a.g[i]);
     const int cnt = a.nnb[i];
@@ -416,10 +421,29 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
       // force mixing (Eq. 3): this atom's EAM force enters with (1 - lam_i) from the
       // fast model plus, when the precise model contains the EAM, lam_i from it
       const T wf = a.force_mix ? T(1) - lam + (a.precise_adds_eam ? lam : T(0)) : T(1);
-      a.force[3 * i] = (double)(wf * fx.value());
-      a.force[3 * i + 1] = (double)(wf * fy.value());
-      a.force[3 * i + 2] = (double)(wf * fz.value());
+      T gx = wf * fx.value(), gy = wf * fy.value(), gz = wf * fz.value();
+      if (a.ind_on) {   // indenter: K (R - r)^2 (x_i - c) / r
+        T r2;
+        const V3<T> d = ind_vec(a, i, &r2);
+        if (r2 < a.ind_R2 && r2 > T(0)) {
+          const T r = sqrt(r2), gap = a.ind_R - r;
+          const T sc = a.ind_K * gap * gap / r;
+          gx += sc * d.x;
+          gy += sc * d.y;
+          gz += sc * d.z;
+          ind_fv = (double)(sc * d.x) * a.ind_v[0] + (double)(sc * d.y) * a.ind_v[1] +
+                   (double)(sc * d.z) * a.ind_v[2];
+        }
+      }
+      a.force[3 * i] = (double)gx;
+      a.force[3 * i + 1] = (double)gy;
+      a.force[3 * i + 2] = (double)gz;
     }
+  }
+  if (a.ind_on && __syncthreads_or(ind_fv != 0.0)) {
+    __shared__ double shw[32];
+    const double t = block_sum(ind_fv, shw);
+    if (threadIdx.x == 0) atomicAdd(&a.ind_acc[2], t);
   }
   const bool pred = active && lam > T(0);
   const unsigned mask = __ballot_sync(0xffffffffu, pred);
@@ -428,6 +452,14 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
   if (lane == 0 && mask) base = atomicAdd(&a.counts[0], __popc(mask));
   base = __shfl_sync(0xffffffffu, base, 0);
   if (pred) a.ace_list[base + __popc(mask & ((1u << lane) - 1u))] = i;
+}
+
+// Indenter work by the midpoint rule over one step (dt > 0), or just the shift of
+// the last (sum F).v (dt = 0, a plain force evaluation).
+__global__ void k_ind_work(double* acc, double dt) {
+  acc[0] += 0.5 * dt * (acc[1] + acc[2]);
+  acc[1] = acc[2];
+  acc[2] = 0.0;
 }
 
 // -------------------------------------------- grad-lambda force, CSP part
@@ -507,7 +539,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* pos, double* vel,
                                                    const double* force, const double* inv_mass,
                                                    double dt, double* thermo_part) {
-  __shared__ double sh[32];
+  __shared__ double sh4[4 * 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && mode != 2) a.counts[0] = 0;
   double ke = 0.0, p[3] = {0.0, 0.0, 0.0};
@@ -543,10 +575,10 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* 
   }
   if (mode != 0) {
     const double vals[4] = {ke, p[0], p[1], p[2]};
-    for (int q = 0; q < 4; ++q) {
-      const double t = block_sum(vals[q], sh);
-      if (threadIdx.x == 0) thermo_part[4 * blockIdx.x + q] = t;
-    }
+    double tot[4];
+    block_sum4(vals, sh4, tot);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < 4; ++q) thermo_part[4 * blockIdx.x + q] = tot[q];
   }
 }
 
@@ -632,6 +664,8 @@ __global__ void __launch_bounds__(kBlock) k_fm_buffer(Args<T> a) {
   base = __shfl_sync(0xffffffffu, base, 0);
   if (pred) a.ace_list[base + __popc(mask & ((1u << lane) - 1u))] = i;
 }
+
+void launch_ind_work(double* acc, double dt, cudaStream_t s) { k_ind_work<<<1, 1, 0, s>>>(acc, dt); }
 
 template <typename T> void launch_fm_buffer(const Args<T>& a, cudaStream_t s) {
   k_fm_buffer<T><<<nblocks(a.n), kBlock, 0, s>>>(a);

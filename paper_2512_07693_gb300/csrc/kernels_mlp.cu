@@ -185,8 +185,9 @@ __global__ void __launch_bounds__(128) k_pass1_learned(Args<T> a) {
     a.zeta[i] = zz;
     a.xi_p[i] = zz > T(0) ? T(-0.5) / sz : T(0);
     a.e_eam[i] = e;
-    if (a.e_atom) a.e_atom[i] = (double)e;
-    e_out = (double)e;
+    const T e_ind = ind_energy(a, i);   // the external indenter, if any
+    if (a.e_atom) a.e_atom[i] = (double)e + (double)e_ind;
+    e_out = (double)e + (double)e_ind;
     a.g[i] = mlp_forward<T>(w, G, nullptr);
   }
   const double tot = block_sum(e_out, sh);

@@ -128,11 +128,14 @@ def crack_slab(nx=200, ny=100, nz=50, opening=2.0, vacuum=15.0, sigma=0.03,
     h = np.clip(opening * (1.0 - x / (0.5 * box[0])), 0.0, None)
     keep = np.abs(y - 0.5 * box[1]) >= 0.5 * h
     pos = pos[keep]
+    z0 = pos[:, 2].copy()
     pos = displace(pos, sigma, seed)
     box = box + np.array([0.0, 0.0, vacuum])
     pos[:, 2] += 0.5 * vacuum
     vel = maxwell(len(pos), temp, seed + 1000)
-    return _finish(pos, vel, box)
+    # the atoms within 3 A (about two (001) layers) of the two free z-surfaces
+    surface = (z0 < 3.0) | (z0 > z0.max() - 3.0)
+    return _finish(pos, vel, box, surface=surface)
 
 
 def training_config(k, cells=10, base_seed=5):
@@ -164,7 +167,10 @@ def config(name, n_basis_fn, scale=None):
       void250k  : 50^3 cells minus a central void of radius 15 A (248 k atoms),
                   300 K; same ACE; FP64 and FP32; 1000 NVE steps
       crack2m   : 200 x 100 x 50 cell slab with a wedge crack (~2.0 M atoms);
-                  ACE n_max 8, l_max 4, nu <= 4; FP32
+                  ACE n_max 8, l_max 4, nu <= 4; FP32.  ``lam_fixed`` pins the
+                  atoms of the two free z-surfaces to the fast model (lam = 0, a
+                  constant-switch subset of Appendix B; NaN elsewhere), so that the
+                  precise region is the crack
     """
     switch = {}
     if name == "vacancy2k":
@@ -187,7 +193,7 @@ def config(name, n_basis_fn, scale=None):
         else:
             s = crack_slab(nx=2 * scale, ny=scale, nz=scale // 2 + 1)
         nm, lm, nu, seed = 8, 4, 4, 2
-        s.update(dt=0.001, steps=100, precision="fp32")
+        s.update(dt=0.001, steps=100, precision="fp32", lam_fixed=np.where(s["surface"], 0.0, np.nan))
     else:
         raise KeyError(name)
     prm = dict(precise_adds_eam=True, eam=dict(EAM), switch=dict(SWITCH, **switch), csp=dict(CSP),

@@ -348,3 +348,26 @@ def test_descriptor_constant_g_and_hand_example():
     assert d[3] == pytest.approx(5 - 0.25)
     assert lam[3] == 1.0 and dlam[3] == 0.0                   # d > d_hi -> ACE
     assert lam[0] == pytest.approx(1 - float(ftrans.f_trans(d[0], 0.5, 1.5)))
+
+
+def test_indenter_closed_form_and_gradient():
+    """The indenter of the indentation workload: E = K/3 (R - r)^3 inside the sphere,
+    zero outside, F = -grad E (central differences), continuous at r = R."""
+    from oracle import indenter
+    box = np.array([30.0, 30.0, 30.0])
+    c = np.array([15.0, 15.0, 15.0])
+    pos = np.array([[15.0, 15.0, 12.0], [15.0, 17.5, 15.0], [22.0, 15.0, 15.0], [15.0, 15.0, 10.0001]])
+    e, f = indenter.energy_forces(pos, box, c, 5.0, 10.0)
+    np.testing.assert_allclose(e[0], 10.0 / 3.0 * 2.0 ** 3, rtol=1e-15)
+    np.testing.assert_allclose(f[0], [0.0, 0.0, -10.0 * 2.0 ** 2], rtol=1e-15)
+    assert e[2] == 0.0 and np.all(f[2] == 0.0)
+    assert e[3] < 1e-11
+    h = 1e-6
+    for a in (0, 1, 3):
+        for q in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[a, q] += h
+            pm[a, q] -= h
+            fd = -(indenter.energy_forces(pp, box, c, 5.0, 10.0)[0].sum()
+                   - indenter.energy_forces(pm, box, c, 5.0, 10.0)[0].sum()) / (2 * h)
+            assert abs(fd - f[a, q]) < 1e-6
