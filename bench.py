@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ace-steps", type=int, default=5, help="steps of the all-ACE comparison run")
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--drift-steps", type=int, default=10000,
+                    help="NVE steps after the timed run over which the energy drift is fitted (10 ps)")
     ap.add_argument("--ace-group", type=int, default=0, choices=[0, 1, 2, 4, 8, 32],
                     help="compacted atoms per ACE thread block (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -243,7 +245,24 @@ def run_ours(args):
     th = thermo.cpu().numpy()
     H = (th[:, 0] + th[:, 1]) / n
     tps = np.arange(args.steps) * 0.001
-    drift = float(np.polyfit(tps, H, 1)[0]) if args.steps > 2 else None
+    drift_timed = float(np.polyfit(tps, H, 1)[0]) if args.steps > 2 else None
+    # energy drift: least-squares slope of H/N over a 10 ps NVE continuation (untimed;
+    # 100 steps per call), after the timed steps let the start-up transient decay
+    drift, drift_window = None, None
+    if args.drift_steps >= 100:
+        nd = args.drift_steps // 100 * 100
+        thd = torch.zeros((nd, 5), dtype=torch.float64, device="cuda")
+        for q in range(0, nd, 100):
+            m.verlet_step(t["pos"], t["vel"], t["F"], t["inv_mass"], box, t["types"], t["ids"], 0.001, 100,
+                          thd[q:q + 100])
+        torch.cuda.synchronize()
+        m.sync()
+        hd = thd.cpu().numpy()
+        Hd = (hd[:, 0] + hd[:, 1]) / n
+        drift = float(np.polyfit(np.arange(nd) * 0.001, Hd, 1)[0])
+        drift_window = {"ps": nd * 0.001, "start_ps": (args.warmup + args.steps) * 0.001,
+                        "H_std_ev_per_atom": float(Hd.std()),
+                        "momentum_change": [float(v) for v in hd[-1, 2:] - th[0, 2:]]}
     lam = m.field("lam", n).cpu().numpy()
     x_ace = float((lam > 0).mean())
     pmom = th[-1, 2:] - th[0, 2:]
@@ -343,6 +362,8 @@ def run_ours(args):
         "all_ace_atom_steps_per_s": all_ace * world,
         "speedup_vs_all_ace": value / (all_ace * world),
         "nve_drift_ev_per_atom_ps": drift,
+        "nve_drift_window": drift_window,
+        "nve_drift_timed_steps_ev_per_atom_ps": drift_timed,
         "momentum_change": [float(v) for v in pmom],
         "phase_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()},
         "phase_ms_per_step_all_ace": {k: v[0] / 2 for k, v in prof_a.items()},

@@ -74,7 +74,7 @@ void free_all(apip_ctx* c) {
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   c->prof_pending.clear();
   c->prof_pool.clear();
-  void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
+  void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nnb_e, c->posg, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->counts, c->flags, c->status, c->partials, c->thermo_part,
                   c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_ws};
@@ -200,9 +200,14 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
          T(p.sw_d_lo), T(p.sw_d_hi), T(1.0 / (p.sw_d_hi - p.sw_d_lo)), T(p.sw_d0)};
   a.r_list2 = c->r_list * c->r_list;
   a.skin_half2 = 0.25 * p.skin * p.skin;
+  // a pair now within eam_rc was within eam_rc + skin at the last build (each atom
+  // moved less than skin / 2); the margin covers the rounding of the trigger
+  a.r_e_in2 = p.eam_rc * p.eam_rc;
+  a.r_e_mid2 = (p.eam_rc + p.skin + 1e-3) * (p.eam_rc + p.skin + 1e-3);
   a.csp_rcut2 = p.csp_rcut * p.csp_rcut;
   a.pos = pos;
   a.id = id;
+  a.nnb_e = c->nnb_e; a.posg = c->posg;
   a.nnb = c->nnb; a.nbl = c->nbl; a.nbl_tmp = c->nbl_tmp; a.pos_ref = c->pos_ref; a.posq = c->posq; a.posq_ref = c->posq_ref;
   a.id2idx = c->id2idx; a.csp = c->csp; a.cell_count = c->cell_count; a.cell_atoms = c->cell_atoms;
   a.cell_q = c->cell_q;
@@ -494,12 +499,14 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   const size_t N = (size_t)n_atoms_max;
   const size_t es = esize(ctx);
   APIP_ALLOC(ctx->nnb, sizeof(int) * N);
+  APIP_ALLOC(ctx->nnb_e, sizeof(int) * N);
   APIP_ALLOC(ctx->nbl, sizeof(int) * N * p->max_nb);
   APIP_ALLOC(ctx->nbl_tmp, sizeof(int) * N * p->max_nb);
   APIP_ALLOC(ctx->pos_ref, sizeof(double) * 3 * N);
   if (p->precision == APIP_FP32) {
     APIP_ALLOC(ctx->posq, sizeof(uint4) * N);
     APIP_ALLOC(ctx->posq_ref, sizeof(uint4) * N);
+    APIP_ALLOC(ctx->posg, sizeof(uint4) * N);
   }
   APIP_ALLOC(ctx->id2idx, sizeof(int) * N);
   APIP_ALLOC(ctx->csp, sizeof(int) * N * kCspCap);
@@ -615,6 +622,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   if (e == cudaSuccess) e = cudaMemset(ctx->pos_ref, 0, sizeof(double) * 3 * N);
   if (e == cudaSuccess && ctx->posq_ref) e = cudaMemset(ctx->posq_ref, 0, sizeof(uint4) * N);
   if (e == cudaSuccess) e = cudaMemset(ctx->nnb, 0, sizeof(int) * N);
+  if (e == cudaSuccess) e = cudaMemset(ctx->nnb_e, 0, sizeof(int) * N);
   if (e != cudaSuccess) return fail_create(e);
   double norms[(kLmaxCap + 1) * (kLmaxCap + 1)];
   ylm_norms(kLmaxCap, norms);

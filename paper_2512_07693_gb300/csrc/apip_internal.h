@@ -138,6 +138,8 @@ struct apip_ctx {
   uint4* cell_q = nullptr;     // FP32 path: posq of the cell members in cell order
   int* cell_atoms = nullptr;
   int* nnb = nullptr;
+  int* nnb_e = nullptr;        // entries within eam_rc + skin at build time (they come first)
+  uint4* posg = nullptr;       // FP32 path: posq with g in .w (pass 1 -> pass 2)
   int* nbl = nullptr;          // column-major [max_nb][nmax]
   int* nbl_tmp = nullptr;      // list build scratch, same layout
   double* pos_ref = nullptr;   // [nmax][3]

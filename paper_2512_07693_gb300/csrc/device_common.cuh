@@ -96,26 +96,32 @@ template <> struct PosView<double> {
   const double* pos;
   double L[3], invL[3];
   struct Self { double x, y, z; };
+  using Rec = Self;   // what a neighbour's separation needs (fetch, then vec_of)
   __device__ __forceinline__ Self self(int i) const { return {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]}; }
-  __device__ __forceinline__ V3<double> vec(const Self& s, int j) const {
-    double dx = pos[3 * j] - s.x, dy = pos[3 * j + 1] - s.y, dz = pos[3 * j + 2] - s.z;
+  __device__ __forceinline__ Rec fetch(int j) const { return self(j); }
+  __device__ __forceinline__ V3<double> vec_of(const Self& s, const Rec& o) const {
+    double dx = o.x - s.x, dy = o.y - s.y, dz = o.z - s.z;
     dx -= L[0] * rint(dx * invL[0]);
     dy -= L[1] * rint(dy * invL[1]);
     dz -= L[2] * rint(dz * invL[2]);
     return {dx, dy, dz};
   }
+  __device__ __forceinline__ V3<double> vec(const Self& s, int j) const { return vec_of(s, fetch(j)); }
 };
 
 template <> struct PosView<float> {
   const uint4* q;
   float unit[3];                 // L / 2^32
   struct Self { uint4 q; };
+  using Rec = uint4;
   __device__ __forceinline__ Self self(int i) const { return {q[i]}; }
-  __device__ __forceinline__ V3<float> vec(const Self& s, int j) const {
-    const uint4 o = q[j];
+  __device__ __forceinline__ Rec fetch(int j) const { return q[j]; }
+  // the .w word of o is not read (pass 2 passes posg records, which carry g there)
+  __device__ __forceinline__ V3<float> vec_of(const Self& s, const uint4& o) const {
     return {(float)(int)(o.x - s.q.x) * unit[0], (float)(int)(o.y - s.q.y) * unit[1],
             (float)(int)(o.z - s.q.z) * unit[2]};
   }
+  __device__ __forceinline__ V3<float> vec(const Self& s, int j) const { return vec_of(s, q[j]); }
 };
 
 // Fixed-point coordinate of a wrapped position w in [0, L): floor(w / L * 2^32),

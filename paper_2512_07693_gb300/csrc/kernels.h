@@ -38,10 +38,13 @@ struct Args {
   SwP sw;
   PassK<T> k;
   double r_list2, skin_half2, csp_rcut2;
+  double r_e_in2, r_e_mid2;   // list-order bounds: eam_rc^2, (eam_rc + skin + margin)^2
 
   const double* pos;      // caller positions [n][3]
   const int* id;          // caller ids [n]
   int* nnb; int* nbl; int* nbl_tmp; double* pos_ref; uint4* posq; uint4* posq_ref; int* id2idx; int* csp;
+  int* nnb_e;             // entries of the list whose build-time distance is below eam_rc + skin
+  uint4* posg;            // FP32 path: (posq.x, posq.y, posq.z, bits of g), written by pass 1
   int* cell_count; int* cell_atoms;
   uint4* cell_q;          // FP32 path: fixed-point positions of the cell members, cell order
   T* zeta; T* xi_p; T* e_eam; T* g; T* wbar; T* dd; T* lam; T* dlam; T* e_ace;
@@ -52,6 +55,26 @@ struct Args {
   const T* mlp_w;         // learned indicator weights (APIP_MLP_NPARAM, layout of apip.h)
   T ace_rc, ace_rc_lo;    // cutoff of the radial descriptors (the ACE cutoff)
 };
+
+// Entries [s0, s1) of atom i's neighbour list (column-major, stride nmax) with
+// the index fetched two entries and the neighbour's record (load(j)) one entry
+// ahead of the arithmetic f(j, record), so that the gathers of the next entries
+// are in flight while the current one is evaluated.
+template <typename L, typename F>
+__device__ __forceinline__ void walk_list(const int* nb, int nmax, int s0, int s1, L&& load, F&& f) {
+  if (s0 >= s1) return;
+  int j = nb[(size_t)s0 * nmax];
+  auto r = load(j);
+  int jn = s0 + 1 < s1 ? nb[(size_t)(s0 + 1) * nmax] : j;
+  for (int s = s0; s < s1; ++s) {
+    const int jc = j;
+    const auto rc = r;
+    j = jn;
+    r = load(j);
+    jn = s + 2 < s1 ? nb[(size_t)(s + 2) * nmax] : j;
+    f(jc, rc);
+  }
+}
 
 // EAM density and pair terms of one neighbour at distance r < rc (Eq. B1, S7-S8):
 // rho(r) = A exp(-beta (r - r_e)) fc(r), Phi(r) = D [x^2 - 2x] fc(r), x = exp(-alpha (r - r_0)).

@@ -127,8 +127,8 @@ __global__ void k_cell_sort(const int* flags, const int* cell_count, int* cell_a
 }
 
 // One thread per atom: the candidates go to the scratch list in cell order,
-// those beyond the EAM cutoff marked by bit 31; k_nborder then writes the
-// final list.
+// tagged in bits 30-31 by distance class (0: within the EAM cutoff, 1: within
+// the EAM cutoff + skin, 2: beyond); k_nborder then writes the final list.
 template <typename T>
 __global__ void k_nbfill(Args<T> a) {
   if (!a.flags[0]) return;
@@ -179,10 +179,11 @@ __global__ void k_nbfill(Args<T> a) {
       }
     }
   };
-  const T rin2 = a.k.eam_rc2;
+  const T rin2 = T(a.r_e_in2), rmid2 = T(a.r_e_mid2);
   int cnt = 0;
   scan([&](int j, T r2) {
-    if (cnt < a.max_nb) a.nbl_tmp[(size_t)cnt * a.nmax + i] = r2 < rin2 ? j : (int)((unsigned)j | 0x80000000u);
+    const unsigned tag = r2 < rin2 ? 0u : (r2 < rmid2 ? 1u : 2u);
+    if (cnt < a.max_nb) a.nbl_tmp[(size_t)cnt * a.nmax + i] = (int)((unsigned)j | (tag << 30));
     ++cnt;
   });
   if (cnt > a.max_nb) {
@@ -199,22 +200,25 @@ __global__ void k_nbfill(Args<T> a) {
   }
 }
 
-// The final list: the entries within the EAM cutoff (at build time) first, then
-// the rest, each part in cell order, so that the lanes of a warp take the same
-// branches at the same list position in the passes.
-__global__ void k_nborder(const int* flags, const int* nnb, const int* tmp, int* nbl, int n, int nmax) {
+// The final list, by build-time distance class: the entries within the EAM
+// cutoff first, then those within the EAM cutoff + skin (nnb_e counts the two),
+// then the rest, each class in cell order.  The lanes of a warp then take the
+// same branches at the same list position in the passes, and the EAM sums stop
+// at nnb_e: a pair now within the EAM cutoff was within cutoff + skin at the
+// build, since each atom has moved less than skin / 2.
+__global__ void k_nborder(const int* flags, const int* nnb, const int* tmp, int* nbl, int* nnb_e, int n,
+                          int nmax) {
   if (!flags[0]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int cnt = nnb[i];
   int p = 0;
-  for (int s = 0; s < cnt; ++s) {
-    const int e = tmp[(size_t)s * nmax + i];
-    if (e >= 0) nbl[(size_t)(p++) * nmax + i] = e;
-  }
-  for (int s = 0; s < cnt; ++s) {
-    const int e = tmp[(size_t)s * nmax + i];
-    if (e < 0) nbl[(size_t)(p++) * nmax + i] = e & 0x7fffffff;
+  for (unsigned tag = 0; tag < 3; ++tag) {
+    for (int s = 0; s < cnt; ++s) {
+      const unsigned e = (unsigned)tmp[(size_t)s * nmax + i];
+      if ((e >> 30) == tag) nbl[(size_t)(p++) * nmax + i] = (int)(e & 0x3fffffffu);
+    }
+    if (tag == 1) nnb_e[i] = p;
   }
 }
 
@@ -284,8 +288,11 @@ __global__ void k_csp_init(Args<double> a) {
 
 // ------------------------------------------------------------------ pass 1
 // zeta_i and E_i^EAM (Eq. B1, S8), xi'(zeta_i), and g_i = CSP^list_i (Eq. B3).
+// The EAM sums read only the first nnb_e list entries (the pairs that can be
+// within the EAM cutoff).  FP32 path: also writes posg[i] = (posq[i], g_i) for
+// pass 2.
 template <typename T>
-__global__ void __launch_bounds__(kBlock, 8) k_pass1(Args<T> a) {
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_pass1(Args<T> a) {
   __shared__ double sh[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   T e_out = T(0);
@@ -295,22 +302,20 @@ __global__ void __launch_bounds__(kBlock, 8) k_pass1(Args<T> a) {
     const T A = a.k.eam_A, beta = a.k.eam_beta, re = a.k.eam_re, D = a.k.eam_D, alpha = a.k.eam_alpha,
             r0 = a.k.eam_r0;
     Acc<T> zeta, pair;
-    const int cnt = a.nnb[i];
-    const int* nb = a.nbl + i;
-    for (int s = 0; s < cnt; ++s, nb += a.nmax) {
-      const int j = *nb;
-      const auto d = a.pv.vec(si, j);
-      const T r2 = dot3(d, d);
-      if (r2 < rc2) {
-        T r, ir;
-        len_inv(r2, &r, &ir);
-        T dfc;
-        const T fc = ftrans(r, rlo, rc, inv_w, &dfc);
-        const T x = exp(-alpha * (r - r0));
-        zeta.add(A * exp(-beta * (r - re)) * fc);
-        pair.add(D * (x * x - T(2) * x) * fc);
-      }
-    }
+    walk_list(a.nbl + i, a.nmax, 0, a.nnb_e[i], [&](int j) { return a.pv.fetch(j); },
+              [&](int, const auto& o) {
+                const auto d = a.pv.vec_of(si, o);
+                const T r2 = dot3(d, d);
+                if (r2 < rc2) {
+                  T r, ir;
+                  len_inv(r2, &r, &ir);
+                  T dfc;
+                  const T fc = ftrans(r, rlo, rc, inv_w, &dfc);
+                  const T x = exp(-alpha * (r - r0));
+                  zeta.add(A * exp(-beta * (r - re)) * fc);
+                  pair.add(D * (x * x - T(2) * x) * fc);
+                }
+              });
     const T z = zeta.value();
     const T sz = z > T(0) ? sqrt(z) : T(0);
     const T e = -sz + T(0.5) * pair.value();
@@ -322,22 +327,35 @@ __global__ void __launch_bounds__(kBlock, 8) k_pass1(Args<T> a) {
     e_out = e + e_ind;
     T g = T(0);
     if (a.lam_mode == APIP_LAM_PAPER) {
+      // the partner ids and their indices are gathered in two rounds of
+      // independent loads (idx = -1: no partner, -2: id out of range)
+      const int4* pr4 = reinterpret_cast<const int4*>(a.csp + (size_t)i * kCspCap);
+      static_assert(kCspCap == 8, "two int4 rows of partner ids");
+      int idx[kCspCap];
+      {
+        const int4 p0 = pr4[0], p1 = pr4[1];
+        const int pid[kCspCap] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+        for (int k = 0; k < kCspCap; ++k)
+          idx[k] = (k >= a.csp_nnb || pid[k] < 0) ? -1 : (pid[k] >= a.nmax ? -2 : a.id2idx[pid[k]]);
+      }
+      bool bad = false;
       Acc<T> gs;
-      const int* pr = a.csp + (size_t)i * kCspCap;
-      for (int k = 0; 2 * k + 1 < a.csp_nnb; ++k) {
-        const int ia_id = pr[2 * k], ib_id = pr[2 * k + 1];
-        if (ia_id < 0 || ib_id < 0) continue;
-        if (ia_id >= a.nmax || ib_id >= a.nmax) { atomicOr(&a.status[ST_BAD_PARTNER], 1); continue; }
-        const int ia = a.id2idx[ia_id], ib = a.id2idx[ib_id];
-        if (ia < 0 || ib < 0 || ia >= a.n || ib >= a.n) { atomicOr(&a.status[ST_BAD_PARTNER], 1); continue; }
+#pragma unroll
+      for (int k = 0; k < kCspCap / 2; ++k) {
+        const int ia = idx[2 * k], ib = idx[2 * k + 1];
+        if (ia == -1 || ib == -1) continue;
+        if (ia < 0 || ib < 0 || ia >= a.n || ib >= a.n) { bad = true; continue; }
         const auto u1 = a.pv.vec(si, ia);
         const auto u2 = a.pv.vec(si, ib);
         const V3<T> u{u1.x + u2.x, u1.y + u2.y, u1.z + u2.z};
         gs.add(dot3(u, u));
       }
+      if (bad) atomicOr(&a.status[ST_BAD_PARTNER], 1);
       g = gs.value();
     }
     a.g[i] = g;
+    if constexpr (sizeof(T) == 4) a.posg[i] = make_uint4(si.q.x, si.q.y, si.q.z, __float_as_uint(g));
   }
   const double tot = block_sum_t(e_out, sh);
   if (threadIdx.x == 0) a.partials[blockIdx.x] = tot;
@@ -368,22 +386,20 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
     Acc<T> fx, fy, fz;
     wbar.add(T(1));
     if (paper) S.add(a.g[i]);
-    const int cnt = a.nnb[i];
-    const int* nb = a.nbl + i;
-    for (int s = 0; s < cnt; ++s, nb += a.nmax) {
-      const int j = *nb;
-      const auto d = a.pv.vec(si, j);
+    // one neighbour: the switch sums (w-range) and, for the first nnb_e entries,
+    // the EAM force
+    auto term = [&](int j, const V3<T>& d, T gj, T xij, bool eam) {
       const T r2 = dot3(d, d);
       const bool in_w = paper && r2 < rw2;
-      const bool in_e = a.eam_force && r2 < rc2;
-      if (!(in_w || in_e)) continue;
+      const bool in_e = eam && a.eam_force && r2 < rc2;
+      if (!(in_w || in_e)) return;
       T r, ir;
       len_inv(r2, &r, &ir);
       if (in_w) {
         T dw;
         const T w = ftrans(r, rwlo, rw, rw_inv, &dw);
         wbar.add(w);
-        S.add(a.g[j] * w);
+        S.add(gj * w);
       }
       if (in_e) {
         T dfc;
@@ -392,11 +408,28 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
         const T drho = er * (dfc - beta * fc);
         const T x = exp(-alpha * (r - r0));
         const T dphi = D * (T(2) * alpha * (x - x * x) * fc + (x * x - T(2) * x) * dfc);
-        const T sc = ((xi_i + a.xi_p[j]) * drho + dphi) * ir;
+        const T sc = ((xi_i + xij) * drho + dphi) * ir;
         fx.add(sc * d.x);
         fy.add(sc * d.y);
         fz.add(sc * d.z);
       }
+    };
+    // neighbour records, fetched one entry ahead: FP32 the posg entry (fixed-point
+    // position, g in .w) and, within nnb_e, xi'_j; FP64 the position
+    const int cnt = a.nnb[i], cnt_e = a.nnb_e[i];
+    if constexpr (sizeof(T) == 4) {
+      struct RecE { uint4 o; float xi; };
+      walk_list(a.nbl + i, a.nmax, 0, cnt_e, [&](int j) { return RecE{a.posg[j], a.xi_p[j]}; },
+                [&](int j, const RecE& e) { term(j, a.pv.vec_of(si, e.o), __uint_as_float(e.o.w), e.xi, true); });
+      if (paper)
+        walk_list(a.nbl + i, a.nmax, cnt_e, cnt, [&](int j) { return a.posg[j]; },
+                  [&](int j, const uint4& o) { term(j, a.pv.vec_of(si, o), __uint_as_float(o.w), T(0), false); });
+    } else {
+      walk_list(a.nbl + i, a.nmax, 0, cnt_e, [&](int j) { return a.pv.fetch(j); },
+                [&](int j, const auto& o) { term(j, a.pv.vec_of(si, o), paper ? a.g[j] : T(0), a.xi_p[j], true); });
+      if (paper)
+        walk_list(a.nbl + i, a.nmax, cnt_e, cnt, [&](int j) { return a.pv.fetch(j); },
+                  [&](int j, const auto& o) { term(j, a.pv.vec_of(si, o), a.g[j], T(0), false); });
     }
     T dv = T(0), dl = T(0), wb = T(1);
     if (paper) {
@@ -626,7 +659,7 @@ template <typename T> void launch_neighbors(const Args<T>& a, int ncell, cudaStr
   k_cell_sort<<<nblocks(ncell), kBlock, 0, s>>>(a.flags, a.cell_count, a.cell_atoms, ncell, a.cell_cap,
                                                  sizeof(T) == 4 ? a.posq : nullptr, sizeof(T) == 4 ? a.cell_q : nullptr);
   k_nbfill<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
-  k_nborder<<<nblocks(a.n), kBlock, 0, s>>>(a.flags, a.nnb, a.nbl_tmp, a.nbl, a.n, a.nmax);
+  k_nborder<<<nblocks(a.n), kBlock, 0, s>>>(a.flags, a.nnb, a.nbl_tmp, a.nbl, a.nnb_e, a.n, a.nmax);
 }
 
 void launch_csp_init(const Args<double>& a, cudaStream_t s) {

@@ -139,7 +139,8 @@ __device__ __forceinline__ void mlp_backward_z(const T* __restrict__ w, const T*
 }
 
 // Pass 1 of the learned switch: EAM density, energy and xi' (as k_pass1) and
-// g_i = MLP(G_i).  Weights are staged in shared memory per block.
+// g_i = MLP(G_i), also into posg[i] in the FP32 path.  Weights are staged in
+// shared memory per block.
 template <typename T>
 __global__ void __launch_bounds__(128) k_pass1_learned(Args<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -188,7 +189,9 @@ __global__ void __launch_bounds__(128) k_pass1_learned(Args<T> a) {
     const T e_ind = ind_energy(a, i);   // the external indenter, if any
     if (a.e_atom) a.e_atom[i] = (double)e + (double)e_ind;
     e_out = (double)e + (double)e_ind;
-    a.g[i] = mlp_forward<T>(w, G, nullptr);
+    const T g = mlp_forward<T>(w, G, nullptr);
+    a.g[i] = g;
+    if constexpr (sizeof(T) == 4) a.posg[i] = make_uint4(si.q.x, si.q.y, si.q.z, __float_as_uint(g));
   }
   const double tot = block_sum(e_out, sh);
   if (threadIdx.x == 0) a.partials[blockIdx.x] = tot;
