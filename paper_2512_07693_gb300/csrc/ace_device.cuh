@@ -326,9 +326,9 @@ __device__ __forceinline__ double pair_forces(const Args<T>& a, const AceDev<T>&
     if (in_e) {
       T dfc;
       const T fc = ftrans(r, rcE_lo, rcE, rcE_inv, &dfc);
-      const T er = a.k.eam_A * exp(-a.k.eam_beta * (r - a.k.eam_re));
+      const T er = a.k.eam_A * fexp(-a.k.eam_beta * (r - a.k.eam_re));
       const T drho = er * (dfc - a.k.eam_beta * fc);
-      const T x = exp(-a.k.eam_alpha * (r - a.k.eam_r0));
+      const T x = fexp(-a.k.eam_alpha * (r - a.k.eam_r0));
       const T dphi = a.k.eam_D * (T(2) * a.k.eam_alpha * (x - x * x) * fc + (x * x - T(2) * x) * dfc);
       sr -= g.lam[k] * (g.xi[k] * drho + T(0.5) * dphi);
     }

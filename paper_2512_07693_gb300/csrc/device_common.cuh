@@ -46,6 +46,13 @@ __device__ __forceinline__ T ftrans_c(T x, T lo, T hi, T inv_w, T* deriv) {
   return T(0.0625) * q * q * q * (T(8) + t * (T(9) + T(3) * t));
 }
 
+// exp(x) for the EAM terms: in float32 the hardware exponential (__expf;
+// relative error ~1e-6 for the |x| < 10 of the EAM arguments, far below the
+// float32 path's tolerances), in float64 the correctly rounded exp.
+template <typename T> __device__ __forceinline__ T fexp(T x);
+template <> __device__ __forceinline__ float fexp<float>(float x) { return __expf(x); }
+template <> __device__ __forceinline__ double fexp<double>(double x) { return exp(x); }
+
 // Running sum with Kahan compensation in FP32; plain in FP64.
 template <typename T> struct Acc {
   T s = T(0), c = T(0);

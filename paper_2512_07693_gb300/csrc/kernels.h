@@ -82,8 +82,8 @@ template <typename T>
 __device__ __forceinline__ void eam_terms(const PassK<T>& k, T r, T* rho, T* phi) {
   T dfc;
   const T fc = ftrans(r, k.eam_rc_lo, k.eam_rc, k.eam_inv_w, &dfc);
-  const T x = exp(-k.eam_alpha * (r - k.eam_r0));
-  *rho = k.eam_A * exp(-k.eam_beta * (r - k.eam_re)) * fc;
+  const T x = fexp(-k.eam_alpha * (r - k.eam_r0));
+  *rho = k.eam_A * fexp(-k.eam_beta * (r - k.eam_re)) * fc;
   *phi = k.eam_D * (x * x - T(2) * x) * fc;
 }
 

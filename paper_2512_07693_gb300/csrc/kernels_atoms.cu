@@ -311,8 +311,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_pass1(Args<T
                   len_inv(r2, &r, &ir);
                   T dfc;
                   const T fc = ftrans(r, rlo, rc, inv_w, &dfc);
-                  const T x = exp(-alpha * (r - r0));
-                  zeta.add(A * exp(-beta * (r - re)) * fc);
+                  const T x = fexp(-alpha * (r - r0));
+                  zeta.add(A * fexp(-beta * (r - re)) * fc);
                   pair.add(D * (x * x - T(2) * x) * fc);
                 }
               });
@@ -404,9 +404,9 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
       if (in_e) {
         T dfc;
         const T fc = ftrans(r, rlo, rc, inv_w, &dfc);
-        const T er = A * exp(-beta * (r - re));
+        const T er = A * fexp(-beta * (r - re));
         const T drho = er * (dfc - beta * fc);
-        const T x = exp(-alpha * (r - r0));
+        const T x = fexp(-alpha * (r - r0));
         const T dphi = D * (T(2) * alpha * (x - x * x) * fc + (x * x - T(2) * x) * dfc);
         const T sc = ((xi_i + xij) * drho + dphi) * ir;
         fx.add(sc * d.x);
