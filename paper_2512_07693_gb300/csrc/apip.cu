@@ -216,7 +216,9 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.e_ace = as<T>(c->e_ace);
   a.cvec = c->cvec; a.ace_list = c->ace_list; a.counts = c->counts; a.flags = c->flags; a.status = c->status;
   a.partials = c->partials;
-  a.n_part_p1 = nblk(n);
+  // one energy partial per pass-1 block, ahead of the ACE blocks' partials
+  a.n_part_p1 = p.lam_mode == APIP_LAM_LEARNED ? (int)std::max<int64_t>(1, (n + kLearnedBlock - 1) / kLearnedBlock)
+                                               : nblk(n);
   a.force = force;
   a.e_atom = e_atom;
   a.mlp_w = as<T>(c->mlp_w);
@@ -517,7 +519,9 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->counts, sizeof(int) * 4);
   APIP_ALLOC(ctx->flags, sizeof(int) * 4);
   APIP_ALLOC(ctx->status, sizeof(int) * ST_COUNT);
-  const int p1 = nblk(n_atoms_max);
+  // pass-1 partials: the most blocks either pass 1 launches (the learned one has
+  // smaller blocks)
+  const int p1 = (int)std::max<int64_t>(nblk(n_atoms_max), (n_atoms_max + kLearnedBlock - 1) / kLearnedBlock);
   APIP_ALLOC(ctx->partials, sizeof(double) * (p1 + ctx->ace_blocks));
   APIP_ALLOC(ctx->thermo_part, sizeof(double) * 4 * p1);
   APIP_ALLOC(ctx->e_scratch, sizeof(double) * 2);

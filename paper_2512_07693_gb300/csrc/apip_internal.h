@@ -16,6 +16,7 @@ constexpr int kNmaxCap = 8;    // largest n_max
 constexpr int kLmaxCap = 4;    // largest l_max
 constexpr int kCspCap = 8;     // largest csp_nnb
 constexpr int kBlock = 256;    // threads per block of the all-atom passes
+constexpr int kLearnedBlock = 128;   // threads per block of pass 1 with the learned switch
 constexpr int kAceWarps = 8;               // warps per ACE block
 constexpr int kAceThreads = 32 * kAceWarps;
 

@@ -142,7 +142,7 @@ __device__ __forceinline__ void mlp_backward_z(const T* __restrict__ w, const T*
 // g_i = MLP(G_i), also into posg[i] in the FP32 path.  Weights are staged in
 // shared memory per block.
 template <typename T>
-__global__ void __launch_bounds__(128) k_pass1_learned(Args<T> a) {
+__global__ void __launch_bounds__(kLearnedBlock) k_pass1_learned(Args<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* w = reinterpret_cast<T*>(smem_raw);
   __shared__ double sh[32];
@@ -358,7 +358,7 @@ __global__ void k_adam(float* p, const float* g, float* m, float* v, int t, floa
 template <typename T> void launch_pass1_learned(const Args<T>& a, cudaStream_t s) {
   const size_t bytes = sizeof(T) * APIP_MLP_NPARAM;
   cudaFuncSetAttribute(k_pass1_learned<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k_pass1_learned<T><<<(a.n + 127) / 128, 128, bytes, s>>>(a);
+  k_pass1_learned<T><<<(a.n + kLearnedBlock - 1) / kLearnedBlock, kLearnedBlock, bytes, s>>>(a);
 }
 
 template <typename T> void launch_mlp_force(const Args<T>& a, cudaStream_t s) {

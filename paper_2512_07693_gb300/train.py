@@ -84,3 +84,96 @@ def train(G, y, epochs=20, batch=65536, lr=1e-3, seed=7, prm=None, log_every=0):
         history.append(float(loss.item()))
     holder.close()
     return p, history
+
+
+def _energies(prm, s, lam_mode, params=None):
+    """Per-atom energies, lam, E^EAM and d of one configuration (float32 path)."""
+    import torch
+    dev = torch.device("cuda")
+    n = len(s["pos"])
+    pos = torch.tensor(s["pos"], dtype=torch.float64, device=dev)
+    ids = torch.arange(n, dtype=torch.int32, device=dev)
+    types = torch.zeros(n, dtype=torch.int32, device=dev)
+    box = [float(b) for b in s["box"]]
+    m = apip.Apip(prm, n, precision="fp32", lam_mode=lam_mode)
+    if lam_mode == "paper":
+        m.init_csp_pairs(pos, box, ids)
+    if lam_mode == "learned":
+        m.set_mlp(params)
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    e = torch.empty(n, dtype=torch.float64, device=dev)
+    m.energy_forces(pos, box, types, ids, F, e_atom_out=e)
+    m.sync()
+    out = (e.cpu().numpy(), m.field("lam", n).cpu().numpy(), m.field("e_eam", n).cpu().numpy(),
+           m.field("d", n).cpu().numpy())
+    m.close()
+    return out
+
+
+def compare_switches(prm, params, ref, configs, cells=10):
+    """On held-out configurations: the RMS over atoms of the adaptive energy error
+    against the precise model, bulk offset removed, -(1 - lam_i)(dE_i - dE^(0)),
+    for the paper's switch and for the learned switch with its window placed at
+    the same ACE fraction x."""
+    rows = []
+    for k in configs:
+        s = W.training_config(k, cells=cells)
+        e_prec, _, e_eam, _ = _energies(prm, s, "const1")
+        dE = e_prec - e_eam
+        _, lam_p, _, _ = _energies(prm, s, "paper")
+        x = float((lam_p > 0).mean())
+        wide = dict(prm, switch=dict(prm["switch"], d_lo=-1e3, d_hi=1e3))
+        d = _energies(wide, s, "learned", params)[3]
+        lo = float(np.quantile(d, 1.0 - x))
+        tuned = dict(prm, switch=dict(prm["switch"], d_lo=lo, d_hi=lo + 0.25 * float(np.std(d))))
+        lam_l = _energies(tuned, s, "learned", params)[1]
+        rows.append(dict(config=k, temp=s["temp"], x_paper=x, x_learned=float((lam_l > 0).mean()),
+                         rms_paper=float(np.sqrt(np.mean(((1 - lam_p) * (dE - ref)) ** 2))),
+                         rms_learned=float(np.sqrt(np.mean(((1 - lam_l) * (dE - ref)) ** 2)))))
+    return rows
+
+
+def main():
+    """The learned-indicator training workload: label generation on n_configs
+    2000-site crystals with point defects, then Adam epochs; prints a JSON summary
+    and saves the float32 weights."""
+    import argparse
+    import json
+    import time
+    import torch
+    from . import build
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--configs", type=int, default=50000)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=65536)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--out", default="mlp_weights.npy")
+    ap.add_argument("--held-out", type=int, default=8, help="configurations for the switch comparison")
+    args = ap.parse_args()
+    build.build()
+    prm = W.config("vacancy2k", apip.apip_ace_basis_size)["prm"]
+    torch.cuda.synchronize()
+    t0 = time.time()
+    G, y, ref = make_dataset(prm, args.configs)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    params, hist = train(G, y, epochs=args.epochs, batch=args.batch, lr=args.lr, prm=prm)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    np.save(args.out, params.cpu().numpy())
+    n_atoms = int(len(y))
+    del G, y
+    held = [k for k in range(10 ** 6, 10 ** 6 + 400) if W.training_config(k)["temp"] < 700.0][:args.held_out]
+    rows = compare_switches(prm, params, ref, held)
+    print(json.dumps({
+        "configs": args.configs, "atoms": n_atoms, "epochs": args.epochs, "batch": args.batch,
+        "label_and_descriptor_s": t1 - t0, "training_s": t2 - t1,
+        "label_atoms_per_s": n_atoms / (t1 - t0), "training_atom_epochs_per_s": n_atoms * args.epochs / (t2 - t1),
+        "loss_per_epoch": hist, "dE0": ref,
+        "switch_comparison": rows,
+        "mean_rms_paper": float(np.mean([r["rms_paper"] for r in rows])),
+        "mean_rms_learned": float(np.mean([r["rms_learned"] for r in rows]))}))
+
+
+if __name__ == "__main__":
+    main()

@@ -138,6 +138,36 @@ def crack_slab(nx=200, ny=100, nz=50, opening=2.0, vacuum=15.0, sigma=0.03,
     return _finish(pos, vel, box, surface=surface)
 
 
+def indent_slab(nx=160, ny=160, nz=78, vacuum=None, sigma=0.03, temp=300.0, seed=6, radius=40.0,
+                speed=0.1, k=10.0, depth=0.0, contact_margin=10.0):
+    """bcc slab (free surfaces normal to z, ``vacuum`` A of empty space, by default
+    2 radius + 15 A so that no periodic image of the sphere reaches the slab's
+    bottom) under a
+    spherical indenter of ``radius`` A and stiffness ``k`` eV/A^3 whose centre sits
+    on the slab's axis at ``radius - depth`` above the top surface and moves down
+    (-z) at ``speed`` A/ps.  ``surface_pin`` marks the atoms within 3 A of the
+    bottom surface, and those within 3 A of the top surface farther than
+    radius + contact_margin from the indenter axis: they are held at the fast
+    model (a constant-switch subset), so that the precise region is the contact
+    zone and not the whole free surface."""
+    if vacuum is None:
+        vacuum = 2.0 * radius + 15.0
+    pos, box = bcc(nx, ny, nz)
+    z0 = pos[:, 2].copy()
+    pos = displace(pos, sigma, seed)
+    box = box + np.array([0.0, 0.0, vacuum])
+    pos[:, 2] += 0.5 * vacuum
+    vel = maxwell(len(pos), temp, seed + 1000)
+    ztop = z0.max() + 0.5 * vacuum
+    axis = np.array([0.5 * box[0], 0.5 * box[1]])
+    lateral = np.sqrt(np.sum((pos[:, :2] - axis) ** 2, axis=1))
+    top = z0 > z0.max() - 3.0
+    pin = (z0 < 3.0) | (top & (lateral > radius + contact_margin))
+    center = np.array([axis[0], axis[1], ztop + radius - depth])
+    return _finish(pos, vel, box, surface_pin=pin,
+                   indenter=dict(center=center, velocity=np.array([0.0, 0.0, -speed]), radius=radius, k=k))
+
+
 def training_config(k, cells=10, base_seed=5):
     """Training configuration k of the learned-indicator data set: a bcc cells^3
     crystal (2000 sites for cells = 10) with one to three random point defects
@@ -171,6 +201,11 @@ def config(name, n_basis_fn, scale=None):
                   atoms of the two free z-surfaces to the fast model (lam = 0, a
                   constant-switch subset of Appendix B; NaN elsewhere), so that the
                   precise region is the crack
+      indent4m  : 160 x 160 x 78 cell slab (3 993 600 atoms), 300 K, under a
+                  spherical indenter (R = 40 A, k = 10 eV/A^3, 0.1 A/ps) that
+                  starts touching the top surface; ACE n_max 6, l_max 3, nu <= 3;
+                  FP32; 5000 NVE steps.  ``lam_fixed`` pins the bottom surface
+                  and the top surface outside the contact zone to lam = 0
     """
     switch = {}
     if name == "vacancy2k":
@@ -194,6 +229,13 @@ def config(name, n_basis_fn, scale=None):
             s = crack_slab(nx=2 * scale, ny=scale, nz=scale // 2 + 1)
         nm, lm, nu, seed = 8, 4, 4, 2
         s.update(dt=0.001, steps=100, precision="fp32", lam_fixed=np.where(s["surface"], 0.0, np.nan))
+    elif name == "indent4m":
+        if scale is None:
+            s = indent_slab()
+        else:   # a smaller slab and a proportionally smaller sphere
+            s = indent_slab(nx=scale, ny=scale, nz=max(scale // 2, 8), radius=40.0 * scale / 160.0)
+        nm, lm, nu, seed = 6, 3, 3, 2
+        s.update(dt=0.001, steps=5000, precision="fp32", lam_fixed=np.where(s["surface_pin"], 0.0, np.nan))
     else:
         raise KeyError(name)
     prm = dict(precise_adds_eam=True, eam=dict(EAM), switch=dict(SWITCH, **switch), csp=dict(CSP),

@@ -64,6 +64,11 @@ def test_learned_switch_parity(prec, tolF, tolE):
         np.testing.assert_allclose(g["g"], o["g"], atol=10 * dg)
         budget = tolE + dg * np.abs(o["dlam"] * (o["e_ace"] - o["e_eam"]))
         assert np.all(np.abs(g["e_atom"] - o["e_atom"]) <= budget)
+    # the total is the sum of every atom's energy: one partial per block of the
+    # learned pass 1 (its blocks are smaller than the other passes')
+    n = len(s["pos"])
+    assert abs(g["E"] - g["e_atom"].sum()) <= (1e-9 if prec == "fp64" else 1e-6) * n
+    assert abs(g["E"] - o["E"]) <= (1e-9 * n if prec == "fp64" else float(np.sum(budget)))
 
 
 def _ap_energy_error(s, prm, lam_mode, params=None):
