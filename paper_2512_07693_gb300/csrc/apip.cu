@@ -77,7 +77,7 @@ void free_all(apip_ctx* c) {
   void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nnb_e, c->posg, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->counts, c->flags, c->status, c->partials, c->thermo_part,
-                  c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_ws};
+                  c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_frag, c->mlp_ws};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -217,11 +217,13 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.cvec = c->cvec; a.ace_list = c->ace_list; a.counts = c->counts; a.flags = c->flags; a.status = c->status;
   a.partials = c->partials;
   // one energy partial per pass-1 block, ahead of the ACE blocks' partials
-  a.n_part_p1 = p.lam_mode == APIP_LAM_LEARNED ? (int)std::max<int64_t>(1, (n + kLearnedBlock - 1) / kLearnedBlock)
-                                               : nblk(n);
+  if (p.lam_mode != APIP_LAM_LEARNED) a.n_part_p1 = nblk(n);
+  else if (sizeof(T) == 4) a.n_part_p1 = learned_tc_blocks(n, c->learned_slots);
+  else a.n_part_p1 = (int)std::max<int64_t>(1, (n + kLearnedBlock - 1) / kLearnedBlock);
   a.force = force;
   a.e_atom = e_atom;
   a.mlp_w = as<T>(c->mlp_w);
+  a.mlp_frag = static_cast<const uint2*>(c->mlp_frag);
   a.ace_rc = T(p.ace_rc);
   a.ace_rc_lo = T(p.ace_rc - p.ace_rc_width);
   return a;
@@ -527,6 +529,12 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->e_scratch, sizeof(double) * 2);
   APIP_ALLOC(ctx->ind_acc, sizeof(double) * 3);
   APIP_ALLOC(ctx->mlp_w, es * APIP_MLP_NPARAM);
+  if (p->precision == APIP_FP32) {
+    APIP_ALLOC(ctx->mlp_frag, mlp_frag_bytes());
+    ctx->learned_slots = learned_tc_slots();
+    cudaGetLastError();
+    if (ctx->learned_slots < 1 && p->lam_mode == APIP_LAM_LEARNED) return fail_create(cudaErrorInvalidConfiguration);
+  }
   // ACE tables: one buffer, sub-arrays 256-byte aligned
   const bool f32 = p->precision == APIP_FP32;
   std::vector<unsigned char> host;
@@ -754,7 +762,10 @@ apip_status apip_set_mlp(apip_ctx* ctx, const float* params, void* stream) {
   if (!ctx) return APIP_ERR_ARG;
   if (!params) return fail(ctx, APIP_ERR_ARG, "params must not be NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  if (ctx->p.precision == APIP_FP32) launch_cast_params<float>(params, as<float>(ctx->mlp_w), s);
+  if (ctx->p.precision == APIP_FP32) {
+    launch_cast_params<float>(params, as<float>(ctx->mlp_w), s);
+    launch_mlp_frags(as<float>(ctx->mlp_w), ctx->mlp_frag, s);
+  }
   else launch_cast_params<double>(params, as<double>(ctx->mlp_w), s);
   const apip_status st = launch_status(ctx);
   if (st == APIP_OK) ctx->mlp_ready = true;

@@ -53,6 +53,7 @@ struct Args {
   double* force;          // caller force [n][3]
   double* e_atom;         // caller per-atom energy [n] or null
   const T* mlp_w;         // learned indicator weights (APIP_MLP_NPARAM, layout of apip.h)
+  const uint2* mlp_frag;  // FP32 path: the hidden layers' weights as split bfloat16 mma fragments
   T ace_rc, ace_rc_lo;    // cutoff of the radial descriptors (the ACE cutoff)
 };
 
@@ -154,6 +155,12 @@ template <typename T> void launch_pass1_learned(const Args<T>& a, cudaStream_t s
 template <typename T> void launch_mlp_force(const Args<T>& a, cudaStream_t s);
 template <typename T> void launch_descriptors(const Args<T>& a, uint16_t* out, cudaStream_t s);
 template <typename T> void launch_cast_params(const float* src, T* dst, cudaStream_t s);
+// FP32 learned pass 1 on the tensor cores: resident blocks on the device, blocks
+// for n atoms, the weight fragments (from the float32 weights) and their size
+int learned_tc_slots();
+int learned_tc_blocks(int n, int slots);
+void launch_mlp_frags(const float* w, void* frag, cudaStream_t s);
+size_t mlp_frag_bytes();
 void launch_mlp_loss_grad(const uint16_t* desc, const float* y, int batch, const float* params, float* grad,
                           float* loss, float* ws, cudaStream_t s);
 size_t mlp_workspace_floats(int batch);

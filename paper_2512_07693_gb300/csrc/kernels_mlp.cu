@@ -19,9 +19,10 @@ constexpr int oW1 = 0, oB1 = oW1 + kW * kIn, oW2 = oB1 + kW, oB2 = oW2 + kW * kW
 static_assert(oB4 + 1 == APIP_MLP_NPARAM, "parameter layout");
 constexpr double kMu0 = 1.5, kDmu = (5.0 - 1.5) / (kIn - 1), kEta = 1.0 / (2.0 * 0.15 * 0.15), kSin = 0.25;
 
-template <typename T> __device__ __forceinline__ T silu(T z) { return z / (T(1) + exp(-z)); }
+// SiLU and its derivative (float32: the hardware exponential, as for the EAM terms)
+template <typename T> __device__ __forceinline__ T silu(T z) { return z / (T(1) + fexp(-z)); }
 template <typename T> __device__ __forceinline__ T silu_d(T z) {
-  const T s = T(1) / (T(1) + exp(-z));
+  const T s = T(1) / (T(1) + fexp(-z));
   return s * (T(1) + z * (T(1) - s));
 }
 
@@ -197,6 +198,250 @@ __global__ void __launch_bounds__(kLearnedBlock) k_pass1_learned(Args<T> a) {
   if (threadIdx.x == 0) a.partials[blockIdx.x] = tot;
 }
 
+// ------------------------------------------------ pass 1, learned, float32
+// The network on the tensor cores: mma.sync m16n8k16 with bfloat16 operands and
+// float32 accumulation, a warp per tile of 32 atoms (two 16-row tiles).  Float32
+// accuracy from bfloat16 products: every operand x is split as
+// x = x_hi + x_mid + x_lo (each part the bfloat16 rounding of what the previous
+// parts leave, 8 significant bits each, so 24 in all), and a product is the sum of
+// the six part products whose orders add to at most 2 (hi hi, hi mid, mid hi,
+// hi lo, mid mid, lo hi); the three dropped ones are below 2^-24 of the product.
+// Part products are exact in float32 and accumulate in float32.
+//
+// Fragment layouts (PTX ISA, mma.m16n8k16 .bf16): with g = lane / 4, t = lane % 4,
+// A (16 x 16, row-major) regs a0 = A[g][2t, 2t+1], a1 = A[g+8][2t, 2t+1],
+// a2 = A[g][2t+8, 2t+9], a3 = A[g+8][2t+8, 2t+9]; B (16 x 8, k x n) regs
+// b0 = B[2t, 2t+1][g], b1 = B[2t+8, 2t+9][g]; C (16 x 8) c0 = C[g][2t],
+// c1 = C[g][2t+1], c2 = C[g+8][2t], c3 = C[g+8][2t+1]; the lower column sits in
+// the low 16 bits of a pair.  The C fragments of n-tiles 2kb and 2kb+1 of one
+// layer are the A fragment of k-block kb of the next: activations stay in
+// registers from layer to layer.
+
+// uint2 offsets of the layers within a split: layer 1 (2 k-blocks), 2 and 3 (4 each)
+constexpr int kTcOff1 = 0, kTcOff2 = 2 * 8 * 32, kTcOff3 = kTcOff2 + 4 * 8 * 32;
+constexpr int kTcSplit = kTcOff3 + 4 * 8 * 32;                              // 2560 uint2 per split
+constexpr int kTcFrag = 3 * kTcSplit;                                       // hi, mid, lo
+constexpr int kTcWarps = 8;
+constexpr int kTcXs = 36;        // staging row stride (floats) of the layer-1 input
+constexpr int kTcBias = 3 * kW + kW + 4;   // b1, b2, b3, w4, b4 (+ pad)
+
+__device__ __forceinline__ uint32_t bf2(float lo_col, float hi_col) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo_col, hi_col);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// (x, y) -> the hi, mid, lo bfloat16 pairs of the three-way split.
+__device__ __forceinline__ void split3(float x, float y, uint32_t& hi, uint32_t& mid, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+  const float2 hf = __bfloat1622float2(h);
+  const float rx = x - hf.x, ry = y - hf.y;     // exact
+  const __nv_bfloat162 m = __floats2bfloat162_rn(rx, ry);
+  const float2 mf = __bfloat1622float2(m);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  mid = *reinterpret_cast<const uint32_t*>(&m);
+  lo = bf2(rx - mf.x, ry - mf.y);
+}
+
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint2 b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
+// One k-block of a layer for all 8 n-tiles: acc[nt] += A_kb W^T, A given as its
+// three parts (4 regs each), the weights' fragments from shared memory (layer
+// offset lo_off, k-block kb); small part products first.
+__device__ __forceinline__ void tc_kblock(float (*acc)[4], const uint32_t* ah, const uint32_t* am, const uint32_t* al,
+                                          const uint2* sf, int lo_off, int kb, int lane) {
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int f = lo_off + (kb * 8 + nt) * 32 + lane;
+    const uint2 wh = sf[f], wm = sf[kTcSplit + f], wl = sf[2 * kTcSplit + f];
+    mma_bf16(acc[nt], am, wm);
+    mma_bf16(acc[nt], ah, wl);
+    mma_bf16(acc[nt], al, wh);
+    mma_bf16(acc[nt], ah, wm);
+    mma_bf16(acc[nt], am, wh);
+    mma_bf16(acc[nt], ah, wh);
+  }
+}
+
+// acc (layer output, 8 n-tiles) -> bias + SiLU in place.
+__device__ __forceinline__ void tc_bias_silu(float (*acc)[4], const float* b, int t) {
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[nt][q] = silu(acc[nt][q] + b[8 * nt + 2 * t + (q & 1)]);
+}
+
+// A 64-wide hidden layer: out = in W^T (in holds the previous activations).
+__device__ __forceinline__ void tc_hidden(float (*in)[4], float (*out)[4], const uint2* sf, int lo_off, int lane) {
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[nt][q] = 0.f;
+#pragma unroll
+  for (int kb = 0; kb < 4; ++kb) {
+    uint32_t ah[4], am[4], al[4];
+    split3(in[2 * kb][0], in[2 * kb][1], ah[0], am[0], al[0]);
+    split3(in[2 * kb][2], in[2 * kb][3], ah[1], am[1], al[1]);
+    split3(in[2 * kb + 1][0], in[2 * kb + 1][1], ah[2], am[2], al[2]);
+    split3(in[2 * kb + 1][2], in[2 * kb + 1][3], ah[3], am[3], al[3]);
+    tc_kblock(out, ah, am, al, sf, lo_off, kb, lane);
+  }
+}
+
+// The fragments of the split weights: thread f of kTcFrag writes uint2 f
+// (split, layer, k-block, n-tile, lane) from the float32 weights.
+__global__ void k_mlp_frags(const float* __restrict__ w, uint2* __restrict__ frag) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= kTcFrag) return;
+  const int sp = f / kTcSplit, r = f % kTcSplit;
+  const int layer = r < kTcOff2 ? 0 : (r < kTcOff3 ? 1 : 2);
+  const int q = r - (layer == 0 ? kTcOff1 : (layer == 1 ? kTcOff2 : kTcOff3));
+  const int lane = q % 32, nt = (q / 32) % 8, kb = q / 256;
+  const int K = layer == 0 ? kIn : kW;
+  const float* W = w + (layer == 0 ? oW1 : (layer == 1 ? oW2 : oW3));
+  const int n = 8 * nt + lane / 4, k0 = 16 * kb + 2 * (lane % 4);
+  uint32_t v[2];
+  for (int h = 0; h < 2; ++h) {
+    uint32_t p[3];
+    split3(W[n * K + k0 + 8 * h], W[n * K + k0 + 8 * h + 1], p[0], p[1], p[2]);
+    v[h] = p[sp];
+  }
+  frag[f] = make_uint2(v[0], v[1]);
+}
+
+// Pass 1 with the learned switch, float32: as k_pass1_learned (EAM density,
+// energy, xi'; descriptors; g = MLP(G)) with the network on the tensor cores.
+// Persistent blocks of 8 warps; warp w of block b takes the tiles of 32 atoms
+// b * 8 + w, + 8 gridDim, ...; one energy partial per block.
+__global__ void __launch_bounds__(kTcWarps * 32) k_pass1_learned_tc(Args<float> a, const uint2* __restrict__ frag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint2* sf = reinterpret_cast<uint2*>(smem_raw);
+  float* sb = reinterpret_cast<float*>(sf + kTcFrag);
+  float* sx = sb + kTcBias;
+  __shared__ double sh[32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
+  for (int k = tid; k < kTcFrag / 2; k += blockDim.x)
+    reinterpret_cast<uint4*>(sf)[k] = reinterpret_cast<const uint4*>(frag)[k];
+  for (int k = tid; k < kW; k += blockDim.x) {
+    sb[k] = a.mlp_w[oB1 + k];
+    sb[kW + k] = a.mlp_w[oB2 + k];
+    sb[2 * kW + k] = a.mlp_w[oB3 + k];
+    sb[3 * kW + k] = a.mlp_w[oW4 + k];
+  }
+  if (tid == 0) sb[4 * kW] = a.mlp_w[oB4];
+  __syncthreads();
+  float* xs = sx + warp * (32 * kTcXs + 32);   // [32][kTcXs] layer-1 input, then g of the 32 atoms
+  float* gs = xs + 32 * kTcXs;
+  const float rcE2 = a.k.eam_rc2;
+  const float rc2 = a.ace_rc * a.ace_rc, inv_w = 1.f / (a.ace_rc - a.ace_rc_lo);
+  double e_out = 0.0;
+  const int ntiles = (a.n + 31) / 32;
+  for (int tile = blockIdx.x * kTcWarps + warp; tile < ntiles; tile += gridDim.x * kTcWarps) {
+    const int i = tile * 32 + lane;
+    const bool act = i < a.n;
+    float G[kIn];
+#pragma unroll
+    for (int m = 0; m < kIn; ++m) G[m] = 0.f;
+    if (act) {
+      const auto si = a.pv.self(i);
+      Acc<float> zeta, pair;
+      walk_list(a.nbl + i, a.nmax, 0, a.nnb[i], [&](int j) { return a.pv.fetch(j); },
+                [&](int, const uint4& o) {
+                  const auto d = a.pv.vec_of(si, o);
+                  const float r2 = dot3(d, d);
+                  if (!(r2 < rc2) && !(r2 < rcE2)) return;
+                  const float r = sqrtf(r2);
+                  if (r2 < rcE2) {
+                    float rho, phi;
+                    eam_terms(a.k, r, &rho, &phi);
+                    zeta.add(rho);
+                    pair.add(phi);
+                  }
+                  if (r2 < rc2) {
+                    float dfc;
+                    const float fc = ftrans(r, a.ace_rc_lo, a.ace_rc, inv_w, &dfc);
+                    float ph[kIn];
+                    features<float, false>(r, fc, dfc, ph, nullptr);
+#pragma unroll
+                    for (int m = 0; m < kIn; ++m) G[m] += ph[m];
+                  }
+                });
+      const float zz = zeta.value();
+      const float sz = zz > 0.f ? sqrtf(zz) : 0.f;
+      const float e = -sz + 0.5f * pair.value();
+      a.zeta[i] = zz;
+      a.xi_p[i] = zz > 0.f ? -0.5f / sz : 0.f;
+      a.e_eam[i] = e;
+      const float e_ind = ind_energy(a, i);   // the external indenter, if any
+      if (a.e_atom) a.e_atom[i] = (double)e + (double)e_ind;
+      e_out += (double)e + (double)e_ind;
+    }
+#pragma unroll
+    for (int m = 0; m < kIn; ++m) xs[lane * kTcXs + m] = float(kSin) * G[m];
+    __syncwarp();
+#pragma unroll 1
+    for (int mt = 0; mt < 2; ++mt) {
+      const int r0 = 16 * mt + gq, r1 = r0 + 8;
+      float h1[8][4], h2[8][4];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) h1[nt][q] = 0.f;
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb) {
+        const int c = 16 * kb + 2 * tq;
+        uint32_t ah[4], am[4], al[4];
+        split3(xs[r0 * kTcXs + c], xs[r0 * kTcXs + c + 1], ah[0], am[0], al[0]);
+        split3(xs[r1 * kTcXs + c], xs[r1 * kTcXs + c + 1], ah[1], am[1], al[1]);
+        split3(xs[r0 * kTcXs + c + 8], xs[r0 * kTcXs + c + 9], ah[2], am[2], al[2]);
+        split3(xs[r1 * kTcXs + c + 8], xs[r1 * kTcXs + c + 9], ah[3], am[3], al[3]);
+        tc_kblock(h1, ah, am, al, sf, kTcOff1, kb, lane);
+      }
+      tc_bias_silu(h1, sb, tq);
+      tc_hidden(h1, h2, sf, kTcOff2, lane);
+      tc_bias_silu(h2, sb + kW, tq);
+      tc_hidden(h2, h1, sf, kTcOff3, lane);
+      // output: g = b4 + sum_j w4_j SiLU(z3_j + b3_j), rows r0 (q = 0, 1) and r1 (q = 2, 3)
+      float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int col = 8 * nt + 2 * tq + (q & 1);
+          const float v = sb[3 * kW + col] * silu(h1[nt][q] + sb[2 * kW + col]);
+          if (q < 2) p0 += v; else p1 += v;
+        }
+      p0 += __shfl_xor_sync(0xffffffffu, p0, 1);
+      p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
+      p0 += __shfl_xor_sync(0xffffffffu, p0, 2);
+      p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
+      if (tq == 0) {
+        gs[r0] = sb[4 * kW] + p0;
+        gs[r1] = sb[4 * kW] + p1;
+      }
+    }
+    __syncwarp();
+    if (act) {
+      const float g = gs[lane];
+      a.g[i] = g;
+      const uint4 q = a.posq[i];
+      a.posg[i] = make_uint4(q.x, q.y, q.z, __float_as_uint(g));
+    }
+    __syncwarp();   // xs and gs are rewritten by the next tile
+  }
+  const double tot = block_sum(e_out, sh);
+  if (tid == 0) a.partials[blockIdx.x] = tot;
+}
+
+size_t tc_smem_bytes() {
+  return sizeof(uint2) * kTcFrag + sizeof(float) * (kTcBias + kTcWarps * (32 * kTcXs + 32));
+}
+
 // -grad sum_k c_k g_k for the atoms with c_k != 0 (learned counterpart of
 // k_csp_force): dG_km = c_k dg_k/dG_km by back-propagation, then for each
 // neighbour j: v = sum_m dG_km phi_m'(r_kj), F_j -= v e_kj, F_k += v e_kj.
@@ -355,11 +600,42 @@ __global__ void k_adam(float* p, const float* g, float* m, float* v, int t, floa
 
 }  // namespace
 
+// float64: the per-thread network, one 128-atom block per partial; float32: the
+// tensor-core kernel on a.n_part_p1 persistent blocks (learned_tc_grid)
 template <typename T> void launch_pass1_learned(const Args<T>& a, cudaStream_t s) {
-  const size_t bytes = sizeof(T) * APIP_MLP_NPARAM;
-  cudaFuncSetAttribute(k_pass1_learned<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k_pass1_learned<T><<<(a.n + kLearnedBlock - 1) / kLearnedBlock, kLearnedBlock, bytes, s>>>(a);
+  if constexpr (sizeof(T) == 4) {
+    const size_t bytes = tc_smem_bytes();
+    cudaFuncSetAttribute(k_pass1_learned_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    k_pass1_learned_tc<<<a.n_part_p1, kTcWarps * 32, bytes, s>>>(a, a.mlp_frag);
+  } else {
+    const size_t bytes = sizeof(T) * APIP_MLP_NPARAM;
+    cudaFuncSetAttribute(k_pass1_learned<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    k_pass1_learned<T><<<(a.n + kLearnedBlock - 1) / kLearnedBlock, kLearnedBlock, bytes, s>>>(a);
+  }
 }
+
+int learned_tc_slots() {
+  const size_t bytes = tc_smem_bytes();
+  if (cudaFuncSetAttribute(k_pass1_learned_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    return 0;
+  int occ = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass1_learned_tc, kTcWarps * 32, bytes) != cudaSuccess)
+    return 0;
+  return occ * sms;
+}
+
+int learned_tc_blocks(int n, int slots) {
+  const int need = (n + kTcWarps * 32 - 1) / (kTcWarps * 32);
+  return need < 1 ? 1 : (need < slots ? need : slots);
+}
+
+void launch_mlp_frags(const float* w, void* frag, cudaStream_t s) {
+  k_mlp_frags<<<(kTcFrag + 255) / 256, 256, 0, s>>>(w, reinterpret_cast<uint2*>(frag));
+}
+
+size_t mlp_frag_bytes() { return sizeof(uint2) * kTcFrag; }
 
 template <typename T> void launch_mlp_force(const Args<T>& a, cudaStream_t s) {
   k_mlp_force<T><<<(a.n + 127) / 128, 128, 0, s>>>(a);
