@@ -76,7 +76,7 @@ void free_all(apip_ctx* c) {
   c->prof_pool.clear();
   void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nnb_e, c->posg, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
-                  c->cvec, c->ace_list, c->counts, c->flags, c->status, c->partials, c->thermo_part,
+                  c->cvec, c->ace_list, c->clist, c->counts, c->flags, c->status, c->partials, c->thermo_part,
                   c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_frag, c->mlp_ws};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -214,7 +214,7 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.zeta = as<T>(c->zeta); a.xi_p = as<T>(c->xi_p); a.e_eam = as<T>(c->e_eam); a.g = as<T>(c->g);
   a.wbar = as<T>(c->wbar); a.dd = as<T>(c->dd); a.lam = as<T>(c->lam); a.dlam = as<T>(c->dlam);
   a.e_ace = as<T>(c->e_ace);
-  a.cvec = c->cvec; a.ace_list = c->ace_list; a.counts = c->counts; a.flags = c->flags; a.status = c->status;
+  a.cvec = c->cvec; a.ace_list = c->ace_list; a.clist = c->clist; a.counts = c->counts; a.flags = c->flags; a.status = c->status;
   a.partials = c->partials;
   // one energy partial per pass-1 block, ahead of the ACE blocks' partials
   if (p.lam_mode != APIP_LAM_LEARNED) a.n_part_p1 = nblk(n);
@@ -518,6 +518,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   for (void** q : per_atom) APIP_ALLOC(*q, es * N);
   APIP_ALLOC(ctx->cvec, sizeof(double) * N);
   APIP_ALLOC(ctx->ace_list, sizeof(int) * N);
+  if (p->lam_mode == APIP_LAM_LEARNED) APIP_ALLOC(ctx->clist, sizeof(int) * N);
   APIP_ALLOC(ctx->counts, sizeof(int) * 4);
   APIP_ALLOC(ctx->flags, sizeof(int) * 4);
   APIP_ALLOC(ctx->status, sizeof(int) * ST_COUNT);

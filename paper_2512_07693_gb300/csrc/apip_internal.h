@@ -155,6 +155,7 @@ struct apip_ctx {
   void* e_ace = nullptr;
   double* cvec = nullptr;      // [nmax] grad-lambda CSP coefficients (kept zero between calls)
   int* ace_list = nullptr;     // [nmax]
+  int* clist = nullptr;        // [nmax] learned switch: atoms with a grad-lambda coefficient
   int* counts = nullptr;       // [4]: |P|, scratch
   int* flags = nullptr;        // [4]: need_rebuild
   int* status = nullptr;       // [ST_COUNT]

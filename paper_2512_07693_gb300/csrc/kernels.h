@@ -49,6 +49,7 @@ struct Args {
   uint4* cell_q;          // FP32 path: fixed-point positions of the cell members, cell order
   T* zeta; T* xi_p; T* e_eam; T* g; T* wbar; T* dd; T* lam; T* dlam; T* e_ace;
   double* cvec; int* ace_list; int* counts; int* flags; int* status;
+  int* clist;             // learned switch: the atoms with cvec != 0 (counts[1] of them)
   double* partials; int n_part_p1;
   double* force;          // caller force [n][3]
   double* e_atom;         // caller per-atom energy [n] or null

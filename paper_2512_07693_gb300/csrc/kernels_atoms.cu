@@ -74,7 +74,7 @@ __device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, dou
 template <typename T>
 __global__ void k_prep(Args<T> a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) a.counts[0] = 0;
+  if (i == 0) a.counts[0] = a.counts[1] = 0;
   if (i >= a.n) return;
   prep_atom(a, i, a.pos[3 * i], a.pos[3 * i + 1], a.pos[3 * i + 2]);
 }
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* 
                                                    double dt, double* thermo_part) {
   __shared__ double sh4[4 * 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0 && mode != 2) a.counts[0] = 0;
+  if (i == 0 && mode != 2) a.counts[0] = a.counts[1] = 0;
   double ke = 0.0, p[3] = {0.0, 0.0, 0.0};
   if (i < a.n) {
     const double im = inv_mass[i];

@@ -445,12 +445,10 @@ size_t tc_smem_bytes() {
 // -grad sum_k c_k g_k for the atoms with c_k != 0 (learned counterpart of
 // k_csp_force): dG_km = c_k dg_k/dG_km by back-propagation, then for each
 // neighbour j: v = sum_m dG_km phi_m'(r_kj), F_j -= v e_kj, F_k += v e_kj.
+// Here for one atom k of the compacted list; resets c_k.
 template <typename T>
-__global__ void __launch_bounds__(128) k_mlp_force(Args<T> a) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= a.n) return;
+__device__ __forceinline__ void mlp_force_atom(const Args<T>& a, int k) {
   const double c = a.cvec[k];
-  if (c == 0.0) return;
   a.cvec[k] = 0.0;
   T G[kIn];
   descriptors_of(a, k, G);
@@ -490,6 +488,27 @@ __global__ void __launch_bounds__(128) k_mlp_force(Args<T> a) {
   }
 #pragma unroll
   for (int q = 0; q < 3; ++q) atomicAdd(&a.force[3 * k + q], fk[q]);
+}
+
+// The atoms with c_k != 0 in warp-ballot order (counts[1] of them), so that the
+// force kernel's warps are full: c is nonzero only near the transition region.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cvec_compact(Args<T> a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool pred = i < a.n && a.cvec[i] != 0.0;
+  const unsigned mask = __ballot_sync(0xffffffffu, pred);
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0 && mask) base = atomicAdd(&a.counts[1], __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (pred) a.clist[base + __popc(mask & ((1u << lane) - 1u))] = i;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_mlp_force(Args<T> a) {
+  const int count = a.counts[1];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x)
+    mlp_force_atom(a, a.clist[q]);
 }
 
 template <typename T>
@@ -638,7 +657,10 @@ void launch_mlp_frags(const float* w, void* frag, cudaStream_t s) {
 size_t mlp_frag_bytes() { return sizeof(uint2) * kTcFrag; }
 
 template <typename T> void launch_mlp_force(const Args<T>& a, cudaStream_t s) {
-  k_mlp_force<T><<<(a.n + 127) / 128, 128, 0, s>>>(a);
+  k_cvec_compact<T><<<(a.n + 255) / 256, 256, 0, s>>>(a);
+  int blocks = (a.n + 127) / 128;   // the list holds at most n atoms; a grid-stride loop covers it
+  if (blocks > 2048) blocks = 2048;
+  k_mlp_force<T><<<blocks, 128, 0, s>>>(a);
 }
 
 template <typename T> void launch_descriptors(const Args<T>& a, uint16_t* out, cudaStream_t s) {
