@@ -222,7 +222,8 @@ constexpr int kTcOff1 = 0, kTcOff2 = 2 * 8 * 32, kTcOff3 = kTcOff2 + 4 * 8 * 32;
 constexpr int kTcSplit = kTcOff3 + 4 * 8 * 32;                              // 2560 uint2 per split
 constexpr int kTcFrag = 3 * kTcSplit;                                       // hi, mid, lo
 constexpr int kTcWarps = 8;
-constexpr int kTcXs = 36;        // staging row stride (floats) of the layer-1 input
+constexpr int kTcXs = 33;        // staging row stride (floats) of the layer-1 input: odd, so that
+                                 // lanes adding at nearby Gaussian indices hit different banks
 constexpr int kTcBias = 3 * kW + kW + 4;   // b1, b2, b3, w4, b4 (+ pad)
 
 __device__ __forceinline__ uint32_t bf2(float lo_col, float hi_col) {
@@ -252,20 +253,18 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint2 b) {
 
 // One k-block of a layer for all 8 n-tiles: acc[nt] += A_kb W^T, A given as its
 // three parts (4 regs each), the weights' fragments from shared memory (layer
-// offset lo_off, k-block kb); small part products first.
+// offset lo_off, k-block kb); small part products first.  Product-major order:
+// consecutive mma instructions update different n-tiles, so they overlap
+// instead of waiting on one accumulator.
 __device__ __forceinline__ void tc_kblock(float (*acc)[4], const uint32_t* ah, const uint32_t* am, const uint32_t* al,
                                           const uint2* sf, int lo_off, int kb, int lane) {
+  const uint2* f = sf + lo_off + kb * 8 * 32 + lane;
+  const uint32_t* const as[6] = {am, ah, al, ah, am, ah};
+  constexpr int ws[6] = {1, 2, 0, 1, 0, 0};   // weight part: 0 hi, 1 mid, 2 lo
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const int f = lo_off + (kb * 8 + nt) * 32 + lane;
-    const uint2 wh = sf[f], wm = sf[kTcSplit + f], wl = sf[2 * kTcSplit + f];
-    mma_bf16(acc[nt], am, wm);
-    mma_bf16(acc[nt], ah, wl);
-    mma_bf16(acc[nt], al, wh);
-    mma_bf16(acc[nt], ah, wm);
-    mma_bf16(acc[nt], am, wh);
-    mma_bf16(acc[nt], ah, wh);
-  }
+  for (int p = 0; p < 6; ++p)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) mma_bf16(acc[nt], as[p], f[ws[p] * kTcSplit + nt * 32]);
 }
 
 // acc (layer output, 8 n-tiles) -> bias + SiLU in place.
@@ -314,6 +313,31 @@ __global__ void k_mlp_frags(const float* __restrict__ w, uint2* __restrict__ fra
   frag[f] = make_uint2(v[0], v[1]);
 }
 
+// Adds phi_m(r) (fc folded in) to row[m] for the Gaussians within kWin spacings
+// of the nearest one, |r - mu_m| < 8.5 dmu = 0.96 A; the others are below
+// exp(-eta (8.5 dmu)^2) = 1.3e-9 of the largest, under float32 rounding of the
+// sum.  Same ratio recurrence as features() outward from the nearest Gaussian.
+constexpr int kWin = 8;
+__device__ __forceinline__ void add_features_window(float r, float fc, float kappa, float* row) {
+  const float dmu = float(kDmu), eta = float(kEta);
+  int m0 = __float2int_rn((r - float(kMu0)) / dmu);
+  m0 = m0 < 0 ? 0 : (m0 > kIn - 1 ? kIn - 1 : m0);
+  const float x0 = r - (float(kMu0) + float(m0) * dmu);
+  const float base = -eta * dmu * dmu, slope = 2.f * eta * dmu * x0;
+  const float e0 = __expf(-eta * x0 * x0) * fc;
+  float rho = __expf(base + slope), sig = __expf(base - slope), up = e0, dn = e0;
+  row[m0] += e0;
+#pragma unroll
+  for (int k = 1; k <= kWin; ++k) {
+    up *= rho;
+    rho *= kappa;
+    dn *= sig;
+    sig *= kappa;
+    if (m0 + k < kIn) row[m0 + k] += up;
+    if (m0 - k >= 0) row[m0 - k] += dn;
+  }
+}
+
 // Pass 1 with the learned switch, float32: as k_pass1_learned (EAM density,
 // energy, xi'; descriptors; g = MLP(G)) with the network on the tensor cores.
 // Persistent blocks of 8 warps; warp w of block b takes the tiles of 32 atoms
@@ -339,14 +363,15 @@ __global__ void __launch_bounds__(kTcWarps * 32) k_pass1_learned_tc(Args<float> 
   float* gs = xs + 32 * kTcXs;
   const float rcE2 = a.k.eam_rc2;
   const float rc2 = a.ace_rc * a.ace_rc, inv_w = 1.f / (a.ace_rc - a.ace_rc_lo);
+  const float kappa = __expf(-2.f * float(kEta) * float(kDmu) * float(kDmu));
+  float* xrow = xs + lane * kTcXs;   // this lane's atom: descriptors accumulate here
   double e_out = 0.0;
   const int ntiles = (a.n + 31) / 32;
   for (int tile = blockIdx.x * kTcWarps + warp; tile < ntiles; tile += gridDim.x * kTcWarps) {
     const int i = tile * 32 + lane;
     const bool act = i < a.n;
-    float G[kIn];
 #pragma unroll
-    for (int m = 0; m < kIn; ++m) G[m] = 0.f;
+    for (int m = 0; m < kIn; ++m) xrow[m] = 0.f;
     if (act) {
       const auto si = a.pv.self(i);
       Acc<float> zeta, pair;
@@ -365,10 +390,7 @@ __global__ void __launch_bounds__(kTcWarps * 32) k_pass1_learned_tc(Args<float> 
                   if (r2 < rc2) {
                     float dfc;
                     const float fc = ftrans(r, a.ace_rc_lo, a.ace_rc, inv_w, &dfc);
-                    float ph[kIn];
-                    features<float, false>(r, fc, dfc, ph, nullptr);
-#pragma unroll
-                    for (int m = 0; m < kIn; ++m) G[m] += ph[m];
+                    add_features_window(r, fc, kappa, xrow);
                   }
                 });
       const float zz = zeta.value();
@@ -382,7 +404,7 @@ __global__ void __launch_bounds__(kTcWarps * 32) k_pass1_learned_tc(Args<float> 
       e_out += (double)e + (double)e_ind;
     }
 #pragma unroll
-    for (int m = 0; m < kIn; ++m) xs[lane * kTcXs + m] = float(kSin) * G[m];
+    for (int m = 0; m < kIn; ++m) xrow[m] *= float(kSin);
     __syncwarp();
 #pragma unroll 1
     for (int mt = 0; mt < 2; ++mt) {
