@@ -74,7 +74,7 @@ void free_all(apip_ctx* c) {
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   c->prof_pending.clear();
   c->prof_pool.clear();
-  void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nnb_e, c->posg, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
+  void* ptrs[] = {c->cell_count, c->cell_used, c->cell_atoms, c->cell_q, c->nnb, c->nnb_e, c->posg, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->clist, c->counts, c->flags, c->status, c->partials, c->thermo_part,
                   c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_frag, c->mlp_ws};
@@ -131,12 +131,16 @@ apip_status set_geometry(apip_ctx* ctx, const double* box, cudaStream_t s) {
   }
   if (ncell > ctx->ncell_alloc) {
     if (ctx->cell_count) cudaFree(ctx->cell_count);
+    if (ctx->cell_used) cudaFree(ctx->cell_used);
     if (ctx->cell_atoms) cudaFree(ctx->cell_atoms);
     if (ctx->cell_q) cudaFree(ctx->cell_q);
     ctx->cell_count = nullptr;
+    ctx->cell_used = nullptr;
     ctx->cell_atoms = nullptr;
     ctx->cell_q = nullptr;
     APIP_CK(cudaMalloc(&ctx->cell_count, sizeof(int) * ncell));
+    APIP_CK(cudaMemsetAsync(ctx->cell_count, 0, sizeof(int) * ncell, s));
+    APIP_CK(cudaMalloc(&ctx->cell_used, sizeof(int) * ncell));
     APIP_CK(cudaMalloc(&ctx->cell_atoms, sizeof(int) * (size_t)ncell * ctx->p.cell_cap));
     if (ctx->p.precision == APIP_FP32)
       APIP_CK(cudaMalloc(&ctx->cell_q, sizeof(uint4) * (size_t)ncell * ctx->p.cell_cap));
@@ -210,6 +214,7 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.nnb_e = c->nnb_e; a.posg = c->posg;
   a.nnb = c->nnb; a.nbl = c->nbl; a.nbl_tmp = c->nbl_tmp; a.pos_ref = c->pos_ref; a.posq = c->posq; a.posq_ref = c->posq_ref;
   a.id2idx = c->id2idx; a.csp = c->csp; a.cell_count = c->cell_count; a.cell_atoms = c->cell_atoms;
+  a.cell_used = c->cell_used;
   a.cell_q = c->cell_q;
   a.zeta = as<T>(c->zeta); a.xi_p = as<T>(c->xi_p); a.e_eam = as<T>(c->e_eam); a.g = as<T>(c->g);
   a.wbar = as<T>(c->wbar); a.dd = as<T>(c->dd); a.lam = as<T>(c->lam); a.dlam = as<T>(c->dlam);
@@ -319,7 +324,7 @@ void pass1(const Args<T>& a, cudaStream_t s) {
 // The force pipeline after prep (or after the drift of a Verlet step).
 template <typename T>
 void force_pipeline(apip_ctx* c, Args<T>& a, cudaStream_t s) {
-  { Phase ph(c, APIP_PHASE_NEIGHBOR, 5, s); launch_neighbors<T>(a, c->ncell, s); }
+  { Phase ph(c, APIP_PHASE_NEIGHBOR, 3, s); launch_neighbors<T>(a, c->ncell, s); }
   { Phase ph(c, APIP_PHASE_PASS1, 1, s); pass1<T>(a, s); }
   { Phase ph(c, APIP_PHASE_PASS2, 1, s); launch_pass2<T>(a, s); if (a.force_mix) launch_fm_buffer<T>(a, s); }
   { Phase ph(c, APIP_PHASE_ACE, 1, s); const AceDev<T> t = ace_dev<T>(c);

@@ -46,6 +46,7 @@ struct Args {
   int* nnb_e;             // entries of the list whose build-time distance is below eam_rc + skin
   uint4* posg;            // FP32 path: (posq.x, posq.y, posq.z, bits of g), written by pass 1
   int* cell_count; int* cell_atoms;
+  int* cell_used;         // atoms per cell (at most cell_cap) of the last list build
   uint4* cell_q;          // FP32 path: fixed-point positions of the cell members, cell order
   T* zeta; T* xi_p; T* e_eam; T* g; T* wbar; T* dd; T* lam; T* dlam; T* e_ace;
   double* cvec; int* ace_list; int* counts; int* flags; int* status;

@@ -80,11 +80,9 @@ __global__ void k_prep(Args<T> a) {
 }
 
 // ------------------------------------------------------------ neighbour list
-__global__ void k_cell_clear(const int* flags, int* cell_count, int ncell) {
-  if (!flags[0]) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < ncell) cell_count[c] = 0;
-}
+// Three launches per list build (binning, per-cell sort, fill), each returning at
+// once when no build is due: cell_count is zero before a build (zeroed on
+// allocation and by the sort, which hands the counts on in cell_used).
 
 template <typename T>
 __global__ void k_bin(Args<T> a) {
@@ -109,12 +107,14 @@ __global__ void k_bin(Args<T> a) {
 // over neighbours) does not depend on the order of the binning atomics; in the
 // FP32 path also copy the members' fixed-point positions into cell order, so
 // that the list build streams them without an index indirection.
-__global__ void k_cell_sort(const int* flags, const int* cell_count, int* cell_atoms, int ncell, int cap,
+__global__ void k_cell_sort(const int* flags, int* cell_count, int* cell_used, int* cell_atoms, int ncell, int cap,
                             const uint4* posq, uint4* cell_q) {
   if (!flags[0]) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
   const int cnt = min(cell_count[c], cap);
+  cell_used[c] = cnt;
+  cell_count[c] = 0;
   int* v = cell_atoms + (size_t)c * cap;
   for (int k = 1; k < cnt; ++k) {
     const int x = v[k];
@@ -128,7 +128,10 @@ __global__ void k_cell_sort(const int* flags, const int* cell_count, int* cell_a
 
 // One thread per atom: the candidates go to the scratch list in cell order,
 // tagged in bits 30-31 by distance class (0: within the EAM cutoff, 1: within
-// the EAM cutoff + skin, 2: beyond); k_nborder then writes the final list.
+// the EAM cutoff + skin, 2: beyond); the same thread then writes the final list
+// class by class.  The passes' EAM sums stop at nnb_e: a pair now within the EAM
+// cutoff was within cutoff + skin at the build, since each atom has moved less
+// than skin / 2.
 template <typename T>
 __global__ void k_nbfill(Args<T> a) {
   if (!a.flags[0]) return;
@@ -148,7 +151,7 @@ __global__ void k_nbfill(Args<T> a) {
         for (int dx = -1; dx <= 1; ++dx) {
           const int cx = (c[0] + dx + a.geo.nc[0]) % a.geo.nc[0];
           const int cell = (cz * a.geo.nc[1] + cy) * a.geo.nc[0] + cx;
-          const int m = min(a.cell_count[cell], a.cell_cap);
+          const int m = a.cell_used[cell];
           const int* v = a.cell_atoms + (size_t)cell * a.cell_cap;
           if constexpr (sizeof(T) == 4) {
             // float comparison against r_list^2 rounded up: the list holds every pair
@@ -190,35 +193,25 @@ __global__ void k_nbfill(Args<T> a) {
     atomicOr(&a.status[ST_NB_OVERFLOW], 1);
     atomicMax(&a.status[ST_MAX_NNB], cnt);
   }
-  a.nnb[i] = min(cnt, a.max_nb);
+  const int kept = min(cnt, a.max_nb);
+  a.nnb[i] = kept;
+  // the final list, by build-time distance class: the entries within the EAM
+  // cutoff first, then those within the EAM cutoff + skin (nnb_e counts the two),
+  // then the rest, each class in cell order (this thread's own scratch entries)
+  int p = 0;
+  for (unsigned tag = 0; tag < 3; ++tag) {
+    for (int s = 0; s < kept; ++s) {
+      const unsigned e = (unsigned)a.nbl_tmp[(size_t)s * a.nmax + i];
+      if ((e >> 30) == tag) a.nbl[(size_t)(p++) * a.nmax + i] = (int)(e & 0x3fffffffu);
+    }
+    if (tag == 1) a.nnb_e[i] = p;
+  }
   if (sizeof(T) == 4) {
     a.posq_ref[i] = a.posq[i];
   } else {
     a.pos_ref[3 * i] = a.pos[3 * i];
     a.pos_ref[3 * i + 1] = a.pos[3 * i + 1];
     a.pos_ref[3 * i + 2] = a.pos[3 * i + 2];
-  }
-}
-
-// The final list, by build-time distance class: the entries within the EAM
-// cutoff first, then those within the EAM cutoff + skin (nnb_e counts the two),
-// then the rest, each class in cell order.  The lanes of a warp then take the
-// same branches at the same list position in the passes, and the EAM sums stop
-// at nnb_e: a pair now within the EAM cutoff was within cutoff + skin at the
-// build, since each atom has moved less than skin / 2.
-__global__ void k_nborder(const int* flags, const int* nnb, const int* tmp, int* nbl, int* nnb_e, int n,
-                          int nmax) {
-  if (!flags[0]) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int cnt = nnb[i];
-  int p = 0;
-  for (unsigned tag = 0; tag < 3; ++tag) {
-    for (int s = 0; s < cnt; ++s) {
-      const unsigned e = (unsigned)tmp[(size_t)s * nmax + i];
-      if ((e >> 30) == tag) nbl[(size_t)(p++) * nmax + i] = (int)(e & 0x3fffffffu);
-    }
-    if (tag == 1) nnb_e[i] = p;
   }
 }
 
@@ -654,12 +647,10 @@ template <typename T> void launch_prep(const Args<T>& a, cudaStream_t s) {
 }
 
 template <typename T> void launch_neighbors(const Args<T>& a, int ncell, cudaStream_t s) {
-  k_cell_clear<<<nblocks(ncell), kBlock, 0, s>>>(a.flags, a.cell_count, ncell);
   k_bin<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
-  k_cell_sort<<<nblocks(ncell), kBlock, 0, s>>>(a.flags, a.cell_count, a.cell_atoms, ncell, a.cell_cap,
+  k_cell_sort<<<nblocks(ncell), kBlock, 0, s>>>(a.flags, a.cell_count, a.cell_used, a.cell_atoms, ncell, a.cell_cap,
                                                  sizeof(T) == 4 ? a.posq : nullptr, sizeof(T) == 4 ? a.cell_q : nullptr);
   k_nbfill<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
-  k_nborder<<<nblocks(a.n), kBlock, 0, s>>>(a.flags, a.nnb, a.nbl_tmp, a.nbl, a.nnb_e, a.n, a.nmax);
 }
 
 void launch_csp_init(const Args<double>& a, cudaStream_t s) {
