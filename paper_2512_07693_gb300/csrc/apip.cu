@@ -126,6 +126,10 @@ apip_status set_geometry(apip_ctx* ctx, const double* box, cudaStream_t s) {
     g.cs[k] = box[k] / g.nc[k];
     g.invL[k] = 1.0 / box[k];
     g.inv_unit[k] = 4294967296.0 / box[k];
+    int x = 0;
+    const double f = std::frexp(g.inv_unit[k], &x);   // f in [0.5, 1): f 2^64 is an exact integer
+    g.unit_m[k] = (unsigned long long)std::ldexp(f, 64);
+    g.unit_s[k] = x - 64;
     g.unit[k] = (float)(box[k] / 4294967296.0);
     ncell *= g.nc[k];
   }
@@ -166,7 +170,7 @@ void set_ind_center(Args<T>& a, const Geo& g, const double c[3]) {
     a.ind_c[k] = c[k];
     double w = c[k] - g.L[k] * std::floor(c[k] * g.invL[k]);
     if (w >= g.L[k]) w -= g.L[k];
-    q[k] = (unsigned)((unsigned long long)(w * g.inv_unit[k]) & 0xffffffffull);
+    q[k] = fixed_coord(w, g.unit_m[k], g.unit_s[k]);
   }
   a.ind_q = make_uint4(q[0], q[1], q[2], 0u);
 }

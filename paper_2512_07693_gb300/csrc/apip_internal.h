@@ -38,7 +38,9 @@ struct Geo {
   double cs[3];         // cell edges (>= r_list)
   double invL[3];       // 1 / L
   int nc[3];            // cells per axis (>= 3)
-  double inv_unit[3];   // 2^32 / L (FP32 path fixed-point coordinates)
+  double inv_unit[3];   // 2^32 / L (FP32 path fixed-point coordinates) = unit_m 2^unit_s,
+  unsigned long long unit_m[3];   // unit_m left-aligned (top bit set)
+  int unit_s[3];
   float unit[3];        // L / 2^32
 };
 

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "apip_internal.h"
 
@@ -131,10 +132,26 @@ template <> struct PosView<float> {
   __device__ __forceinline__ V3<float> vec(const Self& s, int j) const { return vec_of(s, q[j]); }
 };
 
-// Fixed-point coordinate of a wrapped position w in [0, L): floor(w / L * 2^32),
-// with w = L (a rounding edge) mapping to 0, its periodic image.
-__device__ __forceinline__ unsigned int fixed_coord(double w, double inv_unit) {
-  return (unsigned int)((unsigned long long)(w * inv_unit) & 0xffffffffull);
+// Fixed-point coordinate of a wrapped position w in [0, L): floor(w 2^32 / L)
+// mod 2^32 (w = L, a rounding edge, maps to 0, its periodic image), in integer
+// arithmetic.  With w = m 2^(e - 1086) (m the 53-bit significand left-aligned in
+// 64 bits, e the biased exponent) and 2^32 / L = M 2^s (M left-aligned, s from the
+// host), the exact product is m M 2^(e - 1086 + s): its floor is the high 64 bits
+// of m M shifted right by 1022 - e - s, the low 64 bits adding less than one unit.
+// This keeps the per-atom conversion off the float64 pipe, slow on this GPU.
+__host__ __device__ __forceinline__ unsigned int fixed_coord(double w, unsigned long long M, int s) {
+  unsigned long long b;
+  memcpy(&b, &w, sizeof(b));
+  const int e = (int)(b >> 52);   // w >= 0: no sign bit
+  const int sh = 1022 - e - s;
+  if (e == 0 || sh < 0 || sh >= 64) return 0u;
+  const unsigned long long m = ((b & 0xfffffffffffffull) | 0x10000000000000ull) << 11;
+#ifdef __CUDA_ARCH__
+  const unsigned long long hi = __umul64hi(m, M);
+#else
+  const unsigned long long hi = (unsigned long long)(((unsigned __int128)m * M) >> 64);
+#endif
+  return (unsigned int)((hi >> sh) & 0xffffffffull);
 }
 
 template <typename T>

@@ -56,7 +56,7 @@ __device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, dou
     unsigned int q[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-      q[k] = fixed_coord(wrapped ? xs[k] : wrap1(xs[k], a.geo.L[k], a.geo.invL[k]), a.geo.inv_unit[k]);
+      q[k] = fixed_coord(wrapped ? xs[k] : wrap1(xs[k], a.geo.L[k], a.geo.invL[k]), a.geo.unit_m[k], a.geo.unit_s[k]);
     a.posq[i] = make_uint4(q[0], q[1], q[2], 0u);
     const uint4 r = a.posq_ref[i];
     const float ex = (float)(int)(q[0] - r.x) * a.geo.unit[0], ey = (float)(int)(q[1] - r.y) * a.geo.unit[1],
@@ -545,7 +545,7 @@ __global__ void k_final(const double* partials, int n_part, double* e_total, dou
       double ts = 0.0, tc = 0.0;
       for (int k = threadIdx.x; k < n_tb; k += blockDim.x) neumaier(ts, tc, thermo_part[4 * k + q]);
       const double tt = block_sum(ts, sh) + block_sum(tc, sh);
-      if (threadIdx.x == 0) thermo_slot[1 + q] = tt;
+      if (threadIdx.x == 0) thermo_slot[1 + q] = q == 0 ? 0.5 * tt : tt;   // partials hold 2 E_kin
     }
   }
 }
@@ -556,7 +556,7 @@ __global__ void k_thermo_final(const double* thermo_part, int n_tb, double* ther
     double ts = 0.0, tc = 0.0;
     for (int k = threadIdx.x; k < n_tb; k += blockDim.x) neumaier(ts, tc, thermo_part[4 * k + q]);
     const double tt = block_sum(ts, sh) + block_sum(tc, sh);
-    if (threadIdx.x == 0) thermo_slot[1 + q] = tt;
+    if (threadIdx.x == 0) thermo_slot[1 + q] = q == 0 ? 0.5 * tt : tt;   // partials hold 2 E_kin
   }
 }
 
@@ -564,14 +564,14 @@ __global__ void k_thermo_final(const double* thermo_part, int n_tb, double* ther
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* pos, double* vel,
                                                    const double* force, const double* inv_mass,
-                                                   double dt, double* thermo_part) {
+                                                   double dt, double half_dt, double* thermo_part) {
   __shared__ double sh4[4 * 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && mode != 2) a.counts[0] = a.counts[1] = 0;
-  double ke = 0.0, p[3] = {0.0, 0.0, 0.0};
+  double ke = 0.0, p[3] = {0.0, 0.0, 0.0};   // ke: 2 E_kin of the atom (v . p; halved after the sums)
   if (i < a.n) {
     const double im = inv_mass[i];
-    const double h = 0.5 * dt * im;
+    const double h = half_dt * im;
     double v[3], x[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) v[q] = vel[3 * i + q] + h * force[3 * i + q];
@@ -580,9 +580,9 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* 
       // error ~1e-7 on each atom's E_kin and momentum) in the float32 path, where
       // a float64 division per atom would cost more than the rest of the kernel
       const double mass = sizeof(T) == 8 ? 1.0 / im : (double)(1.0f / (float)im);
-      ke = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * mass;
 #pragma unroll
       for (int q = 0; q < 3; ++q) p[q] = v[q] * mass;
+      ke = v[0] * p[0] + v[1] * p[1] + v[2] * p[2];
     }
     if (mode == 1) {
 #pragma unroll
@@ -717,7 +717,7 @@ void launch_thermo_final(const double* thermo_part, int n_tblocks, double* therm
 template <typename T> void launch_verlet(const Args<T>& a, int mode, double* pos, double* vel,
                                          const double* force, const double* inv_mass, double dt,
                                          double* thermo_part, cudaStream_t s) {
-  k_verlet<T><<<nblocks(a.n), kBlock, 0, s>>>(a, mode, pos, vel, force, inv_mass, dt, thermo_part);
+  k_verlet<T><<<nblocks(a.n), kBlock, 0, s>>>(a, mode, pos, vel, force, inv_mass, dt, 0.5 * dt, thermo_part);
 }
 
 template <typename T> void launch_get_field(const Args<T>& a, int field, void* dst, cudaStream_t s) {
