@@ -35,6 +35,11 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2, written between timed steps
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# DRAM bytes (read + write) per launch of the step's dominant kernels on this
+# workload, from one ncu capture of the current kernels (profiles/*_void250k.md);
+# the pass-1 and pass-2 figures are per launch, the Verlet one per half-step launch
+NCU_TRAFFIC = {"ace": 3.283456e6, "pass2": 69.677568e6 + 1.855232e6, "pass1": 65.648640e6 + 1.427456e6,
+               "prep": 13.948672e6}
 
 
 def parse():
@@ -339,7 +344,8 @@ def run_ours(args):
         traffic_alg = per_atom * n
         achieved = traffic_alg / (dom_ms * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "algorithmic_bytes_per_launch": traffic_alg,
+                "frac": achieved / hbm, "traffic": NCU_TRAFFIC.get(dom) if args.cells is None else None,
+                "algorithmic_bytes_per_launch": traffic_alg,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}
     else:
         nb_rc = nb_rc_ace
@@ -348,7 +354,8 @@ def run_ours(args):
         peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
         achieved = fl / (dom_ms * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "algorithmic_flops_per_launch": fl,
+                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom) if args.cells is None else None,
+                "traffic_unit": "DRAM bytes per launch (ncu)", "algorithmic_flops_per_launch": fl,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
 
     out = {
