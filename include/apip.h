@@ -107,7 +107,7 @@ typedef struct apip_params {
      n_max in [1, 8], l_max in [0, 4], nu_max in [1, 4], n_max (l_max+1)^2 <= 254. */
   int32_t ace_n_max, ace_l_max, ace_nu_max;
   int32_t ace_group;         /* compacted atoms per ACE thread block, or 0 = automatic.
-                                Body order <= 3 (streamed): 4 or 32 (automatic: 4 for the
+                                Body order <= 3 (streamed): 4, 8 or 32 (automatic: 8 for the
                                 paper and learned switches, 32 for constant lam).  Body
                                 order 4 (pool): 1, 2, 4 or 8 (automatic: the largest whose
                                 two per-atom pools leave room for two resident blocks per

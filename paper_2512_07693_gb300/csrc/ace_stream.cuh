@@ -348,6 +348,7 @@ template <typename T, typename K>
 int stream_dispatch(const Args<T>* a, const AceDev<T>& t, int blocks, cudaStream_t s, bool query) {
   switch (t.group) {
     case 32: return stream_k<T, K, 32>(a, t, blocks, s, query);
+    case 8: return stream_k<T, K, 8>(a, t, blocks, s, query);
     case 4: return stream_k<T, K, 4>(a, t, blocks, s, query);
     default: return 0;
   }

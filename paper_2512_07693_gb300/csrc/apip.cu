@@ -468,8 +468,10 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->dev);
   // atoms per ACE block.  Pool kernel: the largest group whose pools leave room
   // for two resident blocks per SM, else the largest that fits.  Streamed
-  // kernel: 4 atoms per block for the adaptive switches (few compacted atoms,
-  // spread over many blocks), 32 for constant lam (every atom compacted).
+  // kernel: 8 atoms per block for the adaptive switches (a few thousand
+  // compacted atoms fill the resident blocks in one round; 4 per block took two
+  // rounds and 28 % longer on the 249 k-atom void crystal), 32 for constant lam
+  // (every atom compacted).
   {
     const bool f32 = p->precision == APIP_FP32;
     auto occ_of = [&](int g) {
@@ -487,8 +489,8 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
       occ = occ_of(group);   // 0 for a group the kernel does not provide
     } else if (streamed) {
       const bool adaptive = p->lam_mode == APIP_LAM_PAPER || p->lam_mode == APIP_LAM_LEARNED;
-      const int order_a[2] = {4, 32}, order_c[2] = {32, 4};
-      for (int q = 0; q < 2 && occ == 0; ++q) {
+      const int order_a[3] = {8, 4, 32}, order_c[3] = {32, 8, 4};
+      for (int q = 0; q < 3 && occ == 0; ++q) {
         group = adaptive ? order_a[q] : order_c[q];
         occ = occ_of(group);
       }

@@ -67,7 +67,8 @@ def _check(s, prec="fp64", **kw):
     return g, o
 
 
-@pytest.mark.parametrize("prec,group", [("fp64", 0), ("fp64", 32), ("fp32", 0), ("fp32", 4), ("fp32", 32)])
+@pytest.mark.parametrize("prec,group", [("fp64", 0), ("fp64", 32), ("fp64", 4), ("fp32", 0), ("fp32", 4),
+                                        ("fp32", 8), ("fp32", 32)])
 def test_mixed_system_parity(prec, group):
     """Body order 3 (the streamed kernel); group = compacted atoms per ACE thread
     block (0: automatic)."""
@@ -275,7 +276,7 @@ def test_error_paths():
     # kernel does not provide, and pools that exceed shared memory (the crack
     # basis in float64: 2 atoms x 2 pools x 13188 values x 8 bytes = 422 KB)
     with pytest.raises(apip.ApipError) as e:
-        apip.Apip(s["prm"], n, precision="fp64", ace_group=8)
+        apip.Apip(s["prm"], n, precision="fp64", ace_group=2)
     assert e.value.status == apip.APIP_ERR_ARG
     crack = dict(s["prm"], ace=W.ace_params(8, 4, 4, 2, nbasis(8, 4, 4)))
     with pytest.raises(apip.ApipError) as e:
