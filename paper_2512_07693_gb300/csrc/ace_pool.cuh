@@ -28,6 +28,7 @@ __host__ __device__ inline size_t ace_pool_smem(int npool) {
 
 template <typename T, typename K, int LMAX, int KA>
 __global__ void __launch_bounds__(kAceThreads) k_ace_pool(Args<T> a, AceDev<T> t) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ AceGroup<T, KA> g;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -171,7 +172,7 @@ template <typename T, typename K, int LMAX, int KA>
 void launch_pool_lk(const Args<T>& a, const AceDev<T>& t, int blocks, cudaStream_t s) {
   const size_t bytes = ace_pool_smem<T, LMAX, KA>(t.npool);
   cudaFuncSetAttribute(k_ace_pool<T, K, LMAX, KA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k_ace_pool<T, K, LMAX, KA><<<blocks, kAceThreads, bytes, s>>>(a, t);
+  launch_pdl(k_ace_pool<T, K, LMAX, KA>, blocks, kAceThreads, bytes, s, a, t);
 }
 
 // Resident blocks per SM for this pool size (0 if it does not fit).

@@ -182,6 +182,7 @@ __device__ __forceinline__ void coupling_dispatch(const uint4& cp, const T* Ak, 
 
 template <typename T, typename K, int LMAX, int NAT>
 __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev<T> t) {
+  pdl_begin();
   static_assert(NAT <= 32 && 32 % NAT == 0, "a warp holds whole slices");
   constexpr int NS = kAceThreads / NAT;
   constexpr bool PRIV = stream_private<T, LMAX>();
@@ -310,7 +311,7 @@ template <typename T, typename K, int LMAX, int NAT>
 void launch_stream_lk(const Args<T>& a, const AceDev<T>& t, int blocks, cudaStream_t s) {
   const size_t bytes = ace_stream_smem<T, LMAX, NAT>(t.nA);
   cudaFuncSetAttribute(k_ace_stream<T, K, LMAX, NAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k_ace_stream<T, K, LMAX, NAT><<<blocks, kAceThreads, bytes, s>>>(a, t);
+  launch_pdl(k_ace_stream<T, K, LMAX, NAT>, blocks, kAceThreads, bytes, s, a, t);
 }
 
 template <typename T, typename K, int LMAX, int NAT>

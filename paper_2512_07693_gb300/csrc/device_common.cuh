@@ -14,6 +14,16 @@ namespace apip {
 
 template <typename T> struct V3 { T x, y, z; };
 
+// Programmatic dependent launch.  The kernels of the force pipeline are launched
+// so that the next kernel in the stream may be scheduled while this one finishes
+// (launch_pdl).  Each calls pdl_begin() before its first memory access: it waits
+// until the previous kernel has completed and its writes are visible, then lets
+// its own dependent launch begin.  Waits end when the previous grid ends.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ T dot3(const V3<T>& a, const V3<T>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 

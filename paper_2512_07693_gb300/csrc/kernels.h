@@ -124,6 +124,24 @@ __device__ __forceinline__ T ind_energy(const Args<T>& a, int i) {
   return a.ind_K / T(3) * gap * gap * gap;
 }
 
+// Launch with programmatic stream serialization (the kernel must start with
+// pdl_begin()).
+template <typename... KArgs, typename... Act>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Act&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<Act&&>(args)...);
+}
+
 template <typename T> Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n,
                                         double* force, double* e_atom);
 

@@ -73,6 +73,7 @@ __device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, dou
 
 template <typename T>
 __global__ void k_prep(Args<T> a) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) a.counts[0] = a.counts[1] = 0;
   if (i >= a.n) return;
@@ -86,6 +87,7 @@ __global__ void k_prep(Args<T> a) {
 
 template <typename T>
 __global__ void k_bin(Args<T> a) {
+  pdl_begin();
   if (!a.flags[0]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
@@ -109,6 +111,7 @@ __global__ void k_bin(Args<T> a) {
 // that the list build streams them without an index indirection.
 __global__ void k_cell_sort(const int* flags, int* cell_count, int* cell_used, int* cell_atoms, int ncell, int cap,
                             const uint4* posq, uint4* cell_q) {
+  pdl_begin();
   if (!flags[0]) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
@@ -134,6 +137,7 @@ __global__ void k_cell_sort(const int* flags, int* cell_count, int* cell_used, i
 // than skin / 2.
 template <typename T>
 __global__ void k_nbfill(Args<T> a) {
+  pdl_begin();
   if (!a.flags[0]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
@@ -286,6 +290,7 @@ __global__ void k_csp_init(Args<double> a) {
 // pass 2.
 template <typename T>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_pass1(Args<T> a) {
+  pdl_begin();
   __shared__ double sh[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   T e_out = T(0);
@@ -361,6 +366,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_pass1(Args<T
 // and warp-ballot compaction of {i : lam_i > 0} into ace_list.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = i < a.n;
   T lam = T(0);
@@ -483,6 +489,7 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
 // Indenter work by the midpoint rule over one step (dt > 0), or just the shift of
 // the last (sum F).v (dt = 0, a plain force evaluation).
 __global__ void k_ind_work(double* acc, double dt) {
+  pdl_begin();
   acc[0] += 0.5 * dt * (acc[1] + acc[2]);
   acc[1] = acc[2];
   acc[2] = 0.0;
@@ -493,6 +500,7 @@ __global__ void k_ind_work(double* acc, double dt) {
 // c_j = sum_k Et_k w(r_kj) was accumulated by the ACE kernel; resets c_j.
 template <typename T>
 __global__ void k_csp_force(Args<T> a) {
+  pdl_begin();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.n) return;
   const double c = a.cvec[j];
@@ -530,6 +538,7 @@ __device__ __forceinline__ void neumaier(double& s, double& c, double v) {
 __global__ void k_final(const double* partials, int n_part, double* e_total, double* e_pot_slot,
                         const double* thermo_part, int n_tb, double* thermo_slot, int* flags,
                         const int* counts, int64_t* n_ace_out) {
+  pdl_begin();
   __shared__ double sh[32];
   double s = 0.0, c = 0.0;
   for (int k = threadIdx.x; k < n_part; k += blockDim.x) neumaier(s, c, partials[k]);
@@ -551,6 +560,7 @@ __global__ void k_final(const double* partials, int n_part, double* e_total, dou
 }
 
 __global__ void k_thermo_final(const double* thermo_part, int n_tb, double* thermo_slot) {
+  pdl_begin();
   __shared__ double sh[32];
   for (int q = 0; q < 4; ++q) {
     double ts = 0.0, tc = 0.0;
@@ -565,6 +575,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* pos, double* vel,
                                                    const double* force, const double* inv_mass,
                                                    double dt, double half_dt, double* thermo_part) {
+  pdl_begin();
   __shared__ double sh4[4 * 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && mode != 2) a.counts[0] = a.counts[1] = 0;
@@ -643,14 +654,14 @@ inline int nblocks(int n, int b = kBlock) { return (n + b - 1) / b > 0 ? (n + b 
 
 // ---------------------------------------------------------------- launchers
 template <typename T> void launch_prep(const Args<T>& a, cudaStream_t s) {
-  k_prep<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+  launch_pdl(k_prep<T>, nblocks(a.n), kBlock, 0, s, a);
 }
 
 template <typename T> void launch_neighbors(const Args<T>& a, int ncell, cudaStream_t s) {
-  k_bin<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
-  k_cell_sort<<<nblocks(ncell), kBlock, 0, s>>>(a.flags, a.cell_count, a.cell_used, a.cell_atoms, ncell, a.cell_cap,
+  launch_pdl(k_bin<T>, nblocks(a.n), kBlock, 0, s, a);
+  launch_pdl(k_cell_sort, nblocks(ncell), kBlock, 0, s, a.flags, a.cell_count, a.cell_used, a.cell_atoms, ncell, a.cell_cap,
                                                  sizeof(T) == 4 ? a.posq : nullptr, sizeof(T) == 4 ? a.cell_q : nullptr);
-  k_nbfill<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+  launch_pdl(k_nbfill<T>, nblocks(a.n), kBlock, 0, s, a);
 }
 
 void launch_csp_init(const Args<double>& a, cudaStream_t s) {
@@ -658,7 +669,7 @@ void launch_csp_init(const Args<double>& a, cudaStream_t s) {
 }
 
 template <typename T> void launch_pass1(const Args<T>& a, cudaStream_t s) {
-  k_pass1<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+  launch_pdl(k_pass1<T>, nblocks(a.n), kBlock, 0, s, a);
 }
 
 // Force mixing: the precise model's forces on the atoms with lam > 0 need E^prec
@@ -666,6 +677,7 @@ template <typename T> void launch_pass1(const Args<T>& a, cudaStream_t s) {
 // to the compacted list after pass 2.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_fm_buffer(Args<T> a) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool pred = false;
   if (i < a.n && a.lam[i] == T(0)) {
@@ -689,35 +701,35 @@ __global__ void __launch_bounds__(kBlock) k_fm_buffer(Args<T> a) {
   if (pred) a.ace_list[base + __popc(mask & ((1u << lane) - 1u))] = i;
 }
 
-void launch_ind_work(double* acc, double dt, cudaStream_t s) { k_ind_work<<<1, 1, 0, s>>>(acc, dt); }
+void launch_ind_work(double* acc, double dt, cudaStream_t s) { launch_pdl(k_ind_work, 1, 1, 0, s, acc, dt); }
 
 template <typename T> void launch_fm_buffer(const Args<T>& a, cudaStream_t s) {
-  k_fm_buffer<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+  launch_pdl(k_fm_buffer<T>, nblocks(a.n), kBlock, 0, s, a);
 }
 
 template <typename T> void launch_pass2(const Args<T>& a, cudaStream_t s) {
-  k_pass2<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+  launch_pdl(k_pass2<T>, nblocks(a.n), kBlock, 0, s, a);
 }
 
 template <typename T> void launch_csp_force(const Args<T>& a, cudaStream_t s) {
-  k_csp_force<T><<<nblocks(a.n), kBlock, 0, s>>>(a);
+  launch_pdl(k_csp_force<T>, nblocks(a.n), kBlock, 0, s, a);
 }
 
 void launch_final(double* partials, int n_part, double* e_total, double* e_pot_slot,
                   const double* thermo_part, int n_tblocks, double* thermo_slot, int* flags,
                   const int* counts, int64_t* n_ace_out, cudaStream_t s) {
-  k_final<<<1, 256, 0, s>>>(partials, n_part, e_total, e_pot_slot, thermo_part, n_tblocks, thermo_slot,
+  launch_pdl(k_final, 1, 256, 0, s, partials, n_part, e_total, e_pot_slot, thermo_part, n_tblocks, thermo_slot,
                             flags, counts, n_ace_out);
 }
 
 void launch_thermo_final(const double* thermo_part, int n_tblocks, double* thermo_slot, cudaStream_t s) {
-  k_thermo_final<<<1, 256, 0, s>>>(thermo_part, n_tblocks, thermo_slot);
+  launch_pdl(k_thermo_final, 1, 256, 0, s, thermo_part, n_tblocks, thermo_slot);
 }
 
 template <typename T> void launch_verlet(const Args<T>& a, int mode, double* pos, double* vel,
                                          const double* force, const double* inv_mass, double dt,
                                          double* thermo_part, cudaStream_t s) {
-  k_verlet<T><<<nblocks(a.n), kBlock, 0, s>>>(a, mode, pos, vel, force, inv_mass, dt, 0.5 * dt, thermo_part);
+  launch_pdl(k_verlet<T>, nblocks(a.n), kBlock, 0, s, a, mode, pos, vel, force, inv_mass, dt, 0.5 * dt, thermo_part);
 }
 
 template <typename T> void launch_get_field(const Args<T>& a, int field, void* dst, cudaStream_t s) {

@@ -144,6 +144,7 @@ __device__ __forceinline__ void mlp_backward_z(const T* __restrict__ w, const T*
 // shared memory per block.
 template <typename T>
 __global__ void __launch_bounds__(kLearnedBlock) k_pass1_learned(Args<T> a) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* w = reinterpret_cast<T*>(smem_raw);
   __shared__ double sh[32];
@@ -343,6 +344,7 @@ __device__ __forceinline__ void add_features_window(float r, float fc, float kap
 // Persistent blocks of 8 warps; warp w of block b takes the tiles of 32 atoms
 // b * 8 + w, + 8 gridDim, ...; one energy partial per block.
 __global__ void __launch_bounds__(kTcWarps * 32) k_pass1_learned_tc(Args<float> a, const uint2* __restrict__ frag) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint2* sf = reinterpret_cast<uint2*>(smem_raw);
   float* sb = reinterpret_cast<float*>(sf + kTcFrag);
@@ -516,6 +518,7 @@ __device__ __forceinline__ void mlp_force_atom(const Args<T>& a, int k) {
 // force kernel's warps are full: c is nonzero only near the transition region.
 template <typename T>
 __global__ void __launch_bounds__(256) k_cvec_compact(Args<T> a) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool pred = i < a.n && a.cvec[i] != 0.0;
   const unsigned mask = __ballot_sync(0xffffffffu, pred);
@@ -528,6 +531,7 @@ __global__ void __launch_bounds__(256) k_cvec_compact(Args<T> a) {
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_mlp_force(Args<T> a) {
+  pdl_begin();
   const int count = a.counts[1];
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x)
     mlp_force_atom(a, a.clist[q]);
@@ -647,11 +651,11 @@ template <typename T> void launch_pass1_learned(const Args<T>& a, cudaStream_t s
   if constexpr (sizeof(T) == 4) {
     const size_t bytes = tc_smem_bytes();
     cudaFuncSetAttribute(k_pass1_learned_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    k_pass1_learned_tc<<<a.n_part_p1, kTcWarps * 32, bytes, s>>>(a, a.mlp_frag);
+    launch_pdl(k_pass1_learned_tc, a.n_part_p1, kTcWarps * 32, bytes, s, a, a.mlp_frag);
   } else {
     const size_t bytes = sizeof(T) * APIP_MLP_NPARAM;
     cudaFuncSetAttribute(k_pass1_learned<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    k_pass1_learned<T><<<(a.n + kLearnedBlock - 1) / kLearnedBlock, kLearnedBlock, bytes, s>>>(a);
+    launch_pdl(k_pass1_learned<T>, (a.n + kLearnedBlock - 1) / kLearnedBlock, kLearnedBlock, bytes, s, a);
   }
 }
 
@@ -679,10 +683,10 @@ void launch_mlp_frags(const float* w, void* frag, cudaStream_t s) {
 size_t mlp_frag_bytes() { return sizeof(uint2) * kTcFrag; }
 
 template <typename T> void launch_mlp_force(const Args<T>& a, cudaStream_t s) {
-  k_cvec_compact<T><<<(a.n + 255) / 256, 256, 0, s>>>(a);
+  launch_pdl(k_cvec_compact<T>, (a.n + 255) / 256, 256, 0, s, a);
   int blocks = (a.n + 127) / 128;   // the list holds at most n atoms; a grid-stride loop covers it
   if (blocks > 2048) blocks = 2048;
-  k_mlp_force<T><<<blocks, 128, 0, s>>>(a);
+  launch_pdl(k_mlp_force<T>, blocks, 128, 0, s, a);
 }
 
 template <typename T> void launch_descriptors(const Args<T>& a, uint16_t* out, cudaStream_t s) {
