@@ -38,8 +38,8 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes (read + write) per launch of the step's dominant kernels on this
 # workload, from one ncu capture of the current kernels (profiles/*_void250k.md);
 # the pass-1 and pass-2 figures are per launch, the Verlet one per half-step launch
-NCU_TRAFFIC = {"ace": 3.37152e6, "pass2": 69.677568e6 + 1.855232e6, "pass1": 65.648640e6 + 1.427456e6,
-               "prep": 13.948672e6}
+NCU_TRAFFIC = {"ace": 3.370752e6, "pass2": 69.671680e6 + 1.681664e6, "pass1": 65.648128e6 + 1.270016e6,
+               "prep": 13.949184e6}
 
 
 def parse():
