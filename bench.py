@@ -67,6 +67,21 @@ def dist_env():
     return rank, world, local
 
 
+def job_ms(torch, total_ms, world, device):
+    """The job's timed total: the maximum over the ranks (all-reduce MAX); each rank
+    runs an independent replica, so the job ends with its slowest rank."""
+    if world <= 1:
+        return total_ms
+    tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt)
+
+
+def job_value(world, n_atoms, steps, total_ms):
+    """Whole-job atom-steps/s: the atom-steps of all ranks over the job's time."""
+    return world * n_atoms * steps / (total_ms * 1e-3)
+
+
 # ------------------------------------------------------------------ oracle
 def oracle_sample(steps_budget_s, target_s):
     """Time the FP64 CPU oracle on a shrunken copy of the workload recipe
@@ -241,12 +256,8 @@ def run_ours(args):
     clk = clocks_start()
     per = timed_steps(torch, m, t, box, args.steps, flush, thermo)
     clocks = clocks_stop(clk, local)
-    total_ms = sum(per)
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt)
-    value = world * n * args.steps / (total_ms * 1e-3)
+    total_ms = job_ms(torch, sum(per), world, "cuda")
+    value = job_value(world, n, args.steps, total_ms)
     th = thermo.cpu().numpy()
     H = (th[:, 0] + th[:, 1]) / n
     tps = np.arange(args.steps) * 0.001
