@@ -51,8 +51,9 @@ typedef enum {
   APIP_ERR_STATE = 5,        /* call order: apip_init_csp_pairs must precede calls that use
                                 the paper's switch */
   APIP_ERR_SIZE = 6,         /* input larger than a fixed-capacity entry point can hold */
-  APIP_ERR_TIMEOUT = 7       /* a device-side wait (asynchronous table copy) exceeded its
-                                iteration limit; the results of that call are invalid */
+  APIP_ERR_TIMEOUT = 7       /* reserved: a device-side wait exceeded its iteration limit.
+                                No kernel of this version waits on another, so no call
+                                returns it */
 } apip_status;
 
 enum { APIP_FP64 = 0, APIP_FP32 = 1 };
