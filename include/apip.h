@@ -162,6 +162,17 @@ apip_status apip_build_neighbors(apip_ctx* ctx, const double* pos, const double 
 apip_status apip_init_csp_pairs(apip_ctx* ctx, const double* pos, const double box[3],
                                 const int32_t* id, int64_t n, void* stream);
 
+/* Restore the CSP^list partner ids of a run (Appendix B: detected once, then fixed
+ * by ID), for a context that resumes it from a checkpoint instead of detecting
+ * them again at the resumed configuration.  partner_ids (device, int32
+ * [n][csp_nnb], caller-owned, -1 for no partner) as apip_get_field
+ * (APIP_FIELD_CSP) returns them; row i belongs to the atom at index i of the
+ * positions of later calls.  Copied on the stream; the paper's switch may be used
+ * afterwards.  Partner ids that are not present are reported by apip_sync
+ * (APIP_ERR_BAD_INPUT).  Errors: APIP_ERR_ARG (n outside [0, n_atoms_max], NULL
+ * pointer), APIP_ERR_CUDA. */
+apip_status apip_set_csp_pairs(apip_ctx* ctx, const int32_t* partner_ids, int64_t n, void* stream);
+
 /* Switch only (Eq. 2, Eq. 6): writes lam (ACE weight) and dlam = d lam/d d_i for
  * every atom (float64, optional, may be NULL) and the number of atoms with lam > 0
  * (the compacted precise + transition set) to *n_ace_out (device int64, may be NULL). */

@@ -61,6 +61,7 @@ def _load():
         "apip_destroy": (ctypes.c_int, [_vp]),
         "apip_build_neighbors": (ctypes.c_int, [_vp, _vp, P(_c_double), _vp, _c_int64, _vp]),
         "apip_init_csp_pairs": (ctypes.c_int, [_vp, _vp, P(_c_double), _vp, _c_int64, _vp]),
+        "apip_set_csp_pairs": (ctypes.c_int, [_vp, _vp, _c_int64, _vp]),
         "apip_switch": (ctypes.c_int, [_vp, _vp, P(_c_double), _vp, _vp, _c_int64, _vp, _vp, _vp, _vp]),
         "apip_energy_forces": (ctypes.c_int, [_vp, _vp, P(_c_double), _vp, _vp, _c_int64, _vp, _vp, _vp, _vp]),
         "apip_verlet_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, P(_c_double), _vp, _vp, _c_int64, _c_double,
@@ -141,6 +142,10 @@ def apip_build_neighbors(ctx, pos, box, id, n, stream=None):
 
 def apip_init_csp_pairs(ctx, pos, box, id, n, stream=None):
     _check(ctx, lib.apip_init_csp_pairs(ctx, _ptr(pos), _box(box), _ptr(id), int(n), _stream(stream)))
+
+
+def apip_set_csp_pairs(ctx, partner_ids, n, stream=None):
+    _check(ctx, lib.apip_set_csp_pairs(ctx, _ptr(partner_ids), int(n), _stream(stream)))
 
 
 def apip_switch(ctx, pos, box, type, id, n, lam_out=None, dlam_out=None, n_ace_out=None, stream=None):
@@ -321,6 +326,11 @@ class Apip:
 
     def init_csp_pairs(self, pos, box, ids, stream=None):
         apip_init_csp_pairs(self.ctx, pos, box, ids, pos.shape[0], stream)
+
+    def set_csp_pairs(self, partner_ids, stream=None):
+        """Restore saved partner ids (int32 [n][csp_nnb] device tensor)."""
+        self._csp_saved = partner_ids   # kept alive until the copy on the stream has run
+        apip_set_csp_pairs(self.ctx, partner_ids, partner_ids.shape[0], stream)
 
     def build_neighbors(self, pos, box, ids, stream=None):
         apip_build_neighbors(self.ctx, pos, box, ids, pos.shape[0], stream)

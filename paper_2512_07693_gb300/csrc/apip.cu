@@ -699,6 +699,16 @@ apip_status apip_init_csp_pairs(apip_ctx* ctx, const double* pos, const double b
   return st;
 }
 
+apip_status apip_set_csp_pairs(apip_ctx* ctx, const int32_t* partner_ids, int64_t n, void* stream) {
+  if (!ctx) return APIP_ERR_ARG;
+  if (n < 0 || n > ctx->nmax) return fail(ctx, APIP_ERR_ARG, "n must be in [0, n_atoms_max]");
+  if (n > 0 && !partner_ids) return fail(ctx, APIP_ERR_ARG, "partner_ids must not be NULL");
+  if (n > 0) launch_set_csp(partner_ids, ctx->csp, (int)n, ctx->p.csp_nnb, (cudaStream_t)stream);
+  const apip_status st = launch_status(ctx);
+  if (st == APIP_OK) ctx->csp_ready = true;
+  return st;
+}
+
 apip_status apip_switch(apip_ctx* ctx, const double* pos, const double box[3], const int32_t* type,
                         const int32_t* id, int64_t n, double* lam_out, double* dlam_out, int64_t* n_ace_out,
                         void* stream) {

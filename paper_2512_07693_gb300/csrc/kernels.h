@@ -149,6 +149,7 @@ template <typename T> Args<T> make_args(apip_ctx* c, const double* pos, const in
 template <typename T> void launch_prep(const Args<T>& a, cudaStream_t s);
 template <typename T> void launch_neighbors(const Args<T>& a, int ncell, cudaStream_t s);
 void launch_csp_init(const Args<double>& a, cudaStream_t s);
+void launch_set_csp(const int32_t* src, int* dst, int n, int nnb, cudaStream_t s);
 template <typename T> void launch_pass1(const Args<T>& a, cudaStream_t s);
 template <typename T> void launch_pass2(const Args<T>& a, cudaStream_t s);
 // force mixing: append to the compacted list every atom with lam = 0 that has a

@@ -283,6 +283,14 @@ __global__ void k_csp_init(Args<double> a) {
   }
 }
 
+// Restored partner ids: row i (kCspCap entries) from src[i * nnb .. + nnb), -1 beyond.
+__global__ void k_set_csp(const int32_t* src, int* dst, int n, int nnb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+#pragma unroll
+  for (int k = 0; k < kCspCap; ++k) dst[(size_t)i * kCspCap + k] = k < nnb ? src[(size_t)i * nnb + k] : -1;
+}
+
 // ------------------------------------------------------------------ pass 1
 // zeta_i and E_i^EAM (Eq. B1, S8), xi'(zeta_i), and g_i = CSP^list_i (Eq. B3).
 // The EAM sums read only the first nnb_e list entries (the pairs that can be
@@ -662,6 +670,10 @@ template <typename T> void launch_neighbors(const Args<T>& a, int ncell, cudaStr
   launch_pdl(k_cell_sort, nblocks(ncell), kBlock, 0, s, a.flags, a.cell_count, a.cell_used, a.cell_atoms, ncell, a.cell_cap,
                                                  sizeof(T) == 4 ? a.posq : nullptr, sizeof(T) == 4 ? a.cell_q : nullptr);
   launch_pdl(k_nbfill<T>, nblocks(a.n), kBlock, 0, s, a);
+}
+
+void launch_set_csp(const int32_t* src, int* dst, int n, int nnb, cudaStream_t s) {
+  k_set_csp<<<nblocks(n), kBlock, 0, s>>>(src, dst, n, nnb);
 }
 
 void launch_csp_init(const Args<double>& a, cudaStream_t s) {
