@@ -71,3 +71,32 @@ def test_void250k_full_size_sampled_atoms_fp32():
         assert abs(e[i] - o["e_atom"][k]) <= 1e-5, (i, e[i], o["e_atom"][k])
         err = np.abs(F[i] - o["F"][k]).max()
         assert err <= 2e-4, (i, lam[i], err)
+
+
+def test_void250k_fp32_against_fp64_all_atoms():
+    """Every atom of the full crystal: the float32 path (the benchmarked one)
+    against the float64 path, which the parity tests pin to the oracle at 1e-9 eV/A,
+    within the float32 tolerances (2e-4 eV/A, 1e-5 eV per atom)."""
+    torch = torch_cuda()
+    from paper_2512_07693_gb300 import apip
+    s = W.config("void250k", apip.apip_ace_basis_size)
+    n = len(s["pos"])
+    t = to_dev(torch, s)
+    box = [float(x) for x in s["box"]]
+    out = {}
+    for prec in ("fp32", "fp64"):
+        m = apip.Apip(s["prm"], n, precision=prec, lam_mode="paper", max_nb=80, cell_cap=48)
+        m.init_csp_pairs(t["pos"], box, t["ids"])
+        F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        e = torch.empty(n, dtype=torch.float64, device="cuda")
+        m.energy_forces(t["pos"], box, t["types"], t["ids"], F, e)
+        m.sync()
+        out[prec] = (F.cpu().numpy(), e.cpu().numpy(), m.field("lam", n).cpu().numpy())
+        m.close()
+    F32, e32, l32 = out["fp32"]
+    F64, e64, l64 = out["fp64"]
+    assert int((l64 > 0).sum()) > 1000
+    assert np.abs(F32 - F64).max() <= 2e-4
+    assert np.abs(e32 - e64).max() <= 1e-5
+    assert np.abs(l32 - l64).max() <= 1e-5
+    assert np.abs(F64.sum(axis=0)).max() < 1e-9                  # Newton's third law in float64
