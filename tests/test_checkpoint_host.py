@@ -1,0 +1,53 @@
+"""Checkpoint files on the host (no GPU): what save writes is what load returns,
+and resume hands the saved partners and indenter centre to the context."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2512_07693_gb300 import checkpoint
+
+
+class _Model:
+    """Stands in for apip.Apip: the calls checkpoint makes, recorded."""
+
+    def __init__(self, csp=None, centre=(1.0, 2.0, 3.0), work=0.5):
+        self.csp, self.centre, self.work = csp, centre, work
+        self.calls = []
+
+    def field(self, name, n):
+        assert name == "csp"
+        return torch.tensor(self.csp, dtype=torch.int64)
+
+    def indenter_state(self):
+        return list(self.centre), self.work
+
+    def set_csp_pairs(self, partners):
+        self.calls.append(("csp", partners.cpu().numpy()))
+
+    def set_indenter(self, centre, velocity, radius, k):
+        self.calls.append(("ind", np.asarray(centre), np.asarray(velocity), radius, k))
+
+
+def test_save_load_resume_round_trip(tmp_path):
+    rng = np.random.default_rng(0)
+    n = 7
+    t = dict(pos=torch.tensor(rng.normal(size=(n, 3))), vel=torch.tensor(rng.normal(size=(n, 3))),
+             ids=torch.arange(n, dtype=torch.int32), types=torch.zeros(n, dtype=torch.int32),
+             inv_mass=torch.full((n,), 0.1, dtype=torch.float64))
+    csp = rng.integers(-1, n, size=(n, 8))
+    m = _Model(csp=csp)
+    path = str(tmp_path / "c.npz")
+    checkpoint.save(path, m, t, [10.0, 11.0, 12.0], 42, csp=True, indenter=True)
+    ck = checkpoint.load(path)
+    for k in checkpoint.STATE:
+        np.testing.assert_array_equal(ck[k], t[k].numpy())
+    assert ck["csp"].dtype == np.int32
+    m2 = _Model()
+    t2, box, step, work = checkpoint.resume(m2, ck, device="cpu",
+                                            indenter=dict(velocity=[0, 0, -0.1], radius=4.0, k=10.0))
+    assert step == 42 and box == [10.0, 11.0, 12.0] and work == 0.5
+    np.testing.assert_array_equal(t2["pos"].numpy(), t["pos"].numpy())
+    (kind, parts), ind = m2.calls
+    assert kind == "csp" and np.array_equal(parts, csp)
+    assert ind[0] == "ind" and np.allclose(ind[1], [1.0, 2.0, 3.0]) and ind[3] == 4.0
