@@ -158,19 +158,20 @@ apip_status apip_build_neighbors(apip_ctx* ctx, const double* pos, const double 
 /* Detect the CSP^list opposite-neighbour pairs once (t = 0, Appendix B, Eq. B3):
  * for each atom the csp_nnb nearest neighbours within csp_rcut (ties by ID) are
  * paired greedily by ascending |r_ia + r_ib|^2.  Partner IDs are kept for the
- * rest of the context's life. */
+ * rest of the context's life, by atom ID, so the atoms may be reordered in later
+ * calls. */
 apip_status apip_init_csp_pairs(apip_ctx* ctx, const double* pos, const double box[3],
                                 const int32_t* id, int64_t n, void* stream);
 
 /* Restore the CSP^list partner ids of a run (Appendix B: detected once, then fixed
  * by ID), for a context that resumes it from a checkpoint instead of detecting
  * them again at the resumed configuration.  partner_ids (device, int32
- * [n][csp_nnb], caller-owned, -1 for no partner) as apip_get_field
- * (APIP_FIELD_CSP) returns them; row i belongs to the atom at index i of the
- * positions of later calls.  Copied on the stream; the paper's switch may be used
- * afterwards.  Partner ids that are not present are reported by apip_sync
- * (APIP_ERR_BAD_INPUT).  Errors: APIP_ERR_ARG (n outside [0, n_atoms_max], NULL
- * pointer), APIP_ERR_CUDA. */
+ * [n][csp_nnb], caller-owned, -1 for no partner): row k holds the partners of the
+ * atom whose id is k, for ids 0 .. n-1, as apip_get_field (APIP_FIELD_CSP)
+ * returns them.  Copied on the stream; the paper's
+ * switch may be used afterwards.  Partner ids that are not present are reported
+ * by apip_sync (APIP_ERR_BAD_INPUT).  Errors: APIP_ERR_ARG (n outside
+ * [0, n_atoms_max], NULL pointer), APIP_ERR_CUDA. */
 apip_status apip_set_csp_pairs(apip_ctx* ctx, const int32_t* partner_ids, int64_t n, void* stream);
 
 /* Switch only (Eq. 2, Eq. 6): writes lam (ACE weight) and dlam = d lam/d d_i for
@@ -234,7 +235,8 @@ const char* apip_last_error(apip_ctx* ctx);
  *                         (unordered; only the first count entries are defined)
  *   APIP_FIELD_NNB      : int64 dst, neighbours per atom (within cutoff + skin)
  *   APIP_FIELD_NBLIST   : int64 dst [n][max_nb], neighbour indices (-1 padded)
- *   APIP_FIELD_CSP      : int64 dst [n][csp_nnb], partner IDs (-1 = none) */
+ *   APIP_FIELD_CSP      : int64 dst [n][csp_nnb], partner IDs (-1 = none); row k holds
+ *                         the partners of the atom whose id is k */
 enum {
   APIP_FIELD_G = 0, APIP_FIELD_D = 1, APIP_FIELD_WBAR = 2, APIP_FIELD_LAM = 3,
   APIP_FIELD_DLAM = 4, APIP_FIELD_E_EAM = 5, APIP_FIELD_E_ACE = 6, APIP_FIELD_ZETA = 7,

@@ -328,7 +328,7 @@ class Apip:
         apip_init_csp_pairs(self.ctx, pos, box, ids, pos.shape[0], stream)
 
     def set_csp_pairs(self, partner_ids, stream=None):
-        """Restore saved partner ids (int32 [n][csp_nnb] device tensor)."""
+        """Restore saved partner ids (int32 [n][csp_nnb] device tensor, row k for atom id k)."""
         self._csp_saved = partner_ids   # kept alive until the copy on the stream has run
         apip_set_csp_pairs(self.ctx, partner_ids, partner_ids.shape[0], stream)
 

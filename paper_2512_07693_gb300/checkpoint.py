@@ -22,8 +22,9 @@ def save(path, model, t, box, step, csp=True, indenter=False):
     arrays = {k: t[k].detach().cpu().numpy() for k in STATE}
     arrays["box"] = np.asarray(box, dtype=np.float64)
     arrays["step"] = np.int64(step)
-    if csp:
-        arrays["csp"] = model.field("csp", n).cpu().numpy().astype(np.int32)
+    if csp:   # rows by atom id, for every id in use
+        rows = int(arrays["ids"].max()) + 1 if n else 0
+        arrays["csp"] = model.field("csp", rows).cpu().numpy().astype(np.int32)
     if indenter:
         centre, work = model.indenter_state()
         arrays["ind_centre"] = np.asarray(centre, dtype=np.float64)
@@ -44,7 +45,7 @@ def resume(model, ck, device="cuda", indenter=None):
     (apip_energy_forces) before the next Verlet step."""
     import torch
     t = {k: torch.tensor(ck[k], device=device) for k in STATE}
-    if "csp" in ck:
+    if "csp" in ck:   # rows by atom id, as the library keeps them
         model.set_csp_pairs(torch.tensor(ck["csp"], dtype=torch.int32, device=device).contiguous())
     work = 0.0
     if indenter is not None and "ind_centre" in ck:

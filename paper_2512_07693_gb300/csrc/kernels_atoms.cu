@@ -260,7 +260,9 @@ __global__ void k_csp_init(Args<double> a) {
     }
     r2s[p] = r2; ids[p] = idj; rv[p][0] = dx; rv[p][1] = dy; rv[p][2] = dz;
   }
-  int* out = a.csp + (size_t)i * kCspCap;
+  const int idv = a.id[i];   // rows are kept by atom id, so atoms may be reordered later
+  if (idv < 0 || idv >= a.nmax) return;   // reported by prep (ST_BAD_INPUT)
+  int* out = a.csp + (size_t)idv * kCspCap;
   for (int k = 0; k < kCspCap; ++k) out[k] = -1;
   bool used[kCspCap];
   for (int k = 0; k < kCspCap; ++k) used[k] = false;
@@ -283,7 +285,8 @@ __global__ void k_csp_init(Args<double> a) {
   }
 }
 
-// Restored partner ids: row i (kCspCap entries) from src[i * nnb .. + nnb), -1 beyond.
+// Restored partner ids: the row of atom id i (kCspCap entries) from
+// src[i * nnb .. + nnb), -1 beyond.
 __global__ void k_set_csp(const int32_t* src, int* dst, int n, int nnb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -335,11 +338,14 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_pass1(Args<T
     if (a.lam_mode == APIP_LAM_PAPER) {
       // the partner ids and their indices are gathered in two rounds of
       // independent loads (idx = -1: no partner, -2: id out of range)
-      const int4* pr4 = reinterpret_cast<const int4*>(a.csp + (size_t)i * kCspCap);
+      const int idv = a.id[i];   // the partner row of this atom's id (an invalid id: reported
+      const bool idok = idv >= 0 && idv < a.nmax;   // by prep, no partners here)
+      const int4* pr4 = reinterpret_cast<const int4*>(a.csp + (size_t)(idok ? idv : 0) * kCspCap);
       static_assert(kCspCap == 8, "two int4 rows of partner ids");
       int idx[kCspCap];
       {
-        const int4 p0 = pr4[0], p1 = pr4[1];
+        const int4 none = make_int4(-1, -1, -1, -1);
+        const int4 p0 = idok ? pr4[0] : none, p1 = idok ? pr4[1] : none;
         const int pid[kCspCap] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
 #pragma unroll
         for (int k = 0; k < kCspCap; ++k)
@@ -515,7 +521,9 @@ __global__ void k_csp_force(Args<T> a) {
   if (c == 0.0) return;
   a.cvec[j] = 0.0;
   const auto sj = a.pv.self(j);
-  const int* pr = a.csp + (size_t)j * kCspCap;
+  const int idj = a.id[j];
+  if (idj < 0 || idj >= a.nmax) return;   // reported by prep (ST_BAD_INPUT)
+  const int* pr = a.csp + (size_t)idj * kCspCap;
   double fj[3] = {0.0, 0.0, 0.0};
   for (int k = 0; 2 * k + 1 < a.csp_nnb; ++k) {
     const int ia_id = pr[2 * k], ib_id = pr[2 * k + 1];
@@ -650,6 +658,7 @@ __global__ void k_get_field(Args<T> a, int field, void* dst) {
         di[(size_t)i * a.max_nb + s] = s < a.nnb[i] ? (long long)a.nbl[(size_t)s * a.nmax + i] : -1;
       break;
     case APIP_FIELD_CSP:
+      // row i: the partners of the atom whose id is i (the rows are kept by id)
       for (int s = 0; s < a.csp_nnb; ++s) di[(size_t)i * a.csp_nnb + s] = a.csp[(size_t)i * kCspCap + s];
       break;
     default: break;

@@ -17,7 +17,7 @@ class _Model:
 
     def field(self, name, n):
         assert name == "csp"
-        return torch.tensor(self.csp, dtype=torch.int64)
+        return torch.tensor(self.csp[:n], dtype=torch.int64)
 
     def indenter_state(self):
         return list(self.centre), self.work
@@ -51,3 +51,23 @@ def test_save_load_resume_round_trip(tmp_path):
     (kind, parts), ind = m2.calls
     assert kind == "csp" and np.array_equal(parts, csp)
     assert ind[0] == "ind" and np.allclose(ind[1], [1.0, 2.0, 3.0]) and ind[3] == 4.0
+
+
+
+def test_partner_rows_cover_every_id_in_use(tmp_path):
+    """The partner rows are saved by atom id for every id in use (ids need not be
+    0 .. n-1 in order) and handed back unchanged."""
+    n = 5
+    ids = np.array([3, 0, 6, 1, 2], dtype=np.int32)
+    csp = np.arange(7 * 8).reshape(7, 8) % n
+    t = dict(pos=torch.zeros((n, 3), dtype=torch.float64), vel=torch.zeros((n, 3), dtype=torch.float64),
+             ids=torch.tensor(ids), types=torch.zeros(n, dtype=torch.int32),
+             inv_mass=torch.ones(n, dtype=torch.float64))
+    path = str(tmp_path / "p.npz")
+    checkpoint.save(path, _Model(csp=csp), t, [9.0, 9.0, 9.0], 3)
+    ck = checkpoint.load(path)
+    assert ck["csp"].shape == (7, 8)
+    m = _Model()
+    checkpoint.resume(m, ck, device="cpu")
+    (_, rows), = m.calls
+    np.testing.assert_array_equal(rows, csp)

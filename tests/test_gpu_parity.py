@@ -5,7 +5,7 @@ sets, CSP pairs and the compacted ACE set exact."""
 import numpy as np
 import pytest
 
-from gpu_helpers import run_gpu, run_oracle, torch_cuda
+from gpu_helpers import run_gpu, run_oracle, to_dev, torch_cuda
 from oracle import ace
 from oracle.neighbors import pairs
 from paper_2512_07693_gb300 import workloads as W
@@ -287,3 +287,34 @@ def test_error_paths():
     m.energy_forces(t["pos"][:0], box, t["types"][:0], t["ids"][:0], F[:0], e_total_out=E)
     m.sync()
     assert float(E.cpu()[0]) == 0.0
+
+
+def test_atoms_reordered_after_pair_detection():
+    """The CSP^list partners are kept by atom id: after the pairs are detected, the
+    same atoms passed in another order give the same energies and forces, permuted."""
+    torch = torch_cuda()
+    from paper_2512_07693_gb300 import apip
+    s = W.vacancy_crystal(cells=6, sigma=0.06, seed=21)
+    nb = nbasis(6, 3, 3)
+    prm = dict(precise_adds_eam=True, eam=dict(W.EAM), csp=dict(W.CSP),
+               switch=dict(W.SWITCH, d_lo=0.25, d_hi=0.9), ace=W.ace_params(6, 3, 3, 2, nb))
+    n = len(s["pos"])
+    m = apip.Apip(prm, n, precision="fp64")
+    t = to_dev(torch, s)
+    box = [float(x) for x in s["box"]]
+    m.init_csp_pairs(t["pos"], box, t["ids"])
+    out = []
+    perm = np.random.default_rng(5).permutation(n)
+    for order in (np.arange(n), perm):
+        o = torch.tensor(order, device="cuda")
+        F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        e = torch.empty(n, dtype=torch.float64, device="cuda")
+        m.energy_forces(t["pos"][o].contiguous(), box, t["types"][o].contiguous(), t["ids"][o].contiguous(), F, e)
+        m.sync()
+        out.append((F.cpu().numpy(), e.cpu().numpy(), m.field("dlam", n).cpu().numpy()))
+    m.close()
+    (F0, e0, dl0), (F1, e1, dl1) = out
+    assert np.count_nonzero(dl0) > 10
+    assert np.abs(F1 - F0[perm]).max() < 1e-10
+    assert np.abs(e1 - e0[perm]).max() < 1e-10
+    np.testing.assert_allclose(dl1, dl0[perm], atol=1e-12)
