@@ -127,8 +127,8 @@ typedef struct apip_params {
   int32_t nb_pad;
   /* neighbour list: cutoff = max(eam_rc, ace_rc, sw_r_w) + skin */
   double skin;
-  int32_t max_nb;            /* neighbour capacity per atom (<= 256) */
-  int32_t cell_cap;          /* atom capacity per cell (<= 256) */
+  int32_t max_nb;            /* neighbour capacity per atom (1 .. 1024) */
+  int32_t cell_cap;          /* atom capacity per cell (1 .. 1024) */
   int32_t mixing;            /* APIP_MIX_ENERGY or APIP_MIX_FORCE */
 } apip_params;
 
@@ -150,7 +150,9 @@ apip_status apip_destroy(apip_ctx* ctx);
 
 /* Build the cell-binned neighbour list (cutoff + skin) for the n atoms at pos.
  * Normally not needed: the force calls rebuild on their own when an atom has
- * moved more than skin/2 since the last build.  Paper: distances only (main text
+ * moved more than skin/2 since the last build, when the box changes, and when n
+ * differs from the n of the last build (any n in [0, n_atoms_max] may be passed to
+ * each call).  Paper: distances only (main text
  * after Eq. 5); the list itself is an implementation device. */
 apip_status apip_build_neighbors(apip_ctx* ctx, const double* pos, const double box[3],
                                  const int32_t* id, int64_t n, void* stream);
@@ -318,6 +320,9 @@ apip_status apip_mlp_adam(apip_ctx* ctx, float* params, const float* grad, float
  * library routine.
  *  - The first call on each device looks up the array's device address (with that
  *    device current) and caches it; make that first call before any stream capture.
+ *    The cached address belongs to the device's primary context: after
+ *    cudaDeviceReset (or anything else that destroys that context) it is stale,
+ *    so do not call this entry point again in a process that has reset the device.
  *  - All calls share the one array.  Each call writes every partial it reads, so
  *    nothing needs clearing between calls, but calls that overlap on the GPU (on
  *    different streams, or from different host threads) race on the partials and

@@ -157,6 +157,15 @@ apip_status set_geometry(apip_ctx* ctx, const double* box, cudaStream_t s) {
   return APIP_OK;
 }
 
+// A call with another atom count than the last list build needs a new list: the
+// old one holds indices of atoms that may be gone (n shrank) or misses the new
+// atoms (n grew).  Marks the list for rebuild on the stream.
+void mark_atom_count(apip_ctx* c, int n, cudaStream_t s) {
+  if (n == c->built_n) return;
+  cudaMemsetAsync(c->flags, 0xff, sizeof(int), s);
+  c->built_n = n;
+}
+
 }  // namespace
 
 namespace apip {
@@ -348,6 +357,7 @@ apip_status energy_forces_t(apip_ctx* c, const double* pos, const int32_t* id, i
                             double* e_atom, double* e_total, cudaStream_t s) {
   Args<T> a = make_args<T>(c, pos, id, n, force, e_atom);
   set_view<T>(a, c);
+  mark_atom_count(c, n, s);
   { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_prep<T>(a, s); }
   force_pipeline<T>(c, a, s);
   Phase ph(c, APIP_PHASE_REDUCE, 1, s);
@@ -363,6 +373,7 @@ apip_status switch_t(apip_ctx* c, const double* pos, const int32_t* id, int n, d
   Args<T> a = make_args<T>(c, pos, id, n, nullptr, nullptr);
   set_view<T>(a, c);
   a.eam_force = 0;
+  mark_atom_count(c, n, s);
   launch_prep<T>(a, s);
   launch_neighbors<T>(a, c->ncell, s);
   pass1<T>(a, s);
@@ -379,6 +390,7 @@ apip_status neighbors_t(apip_ctx* c, const double* pos, const int32_t* id, int n
   set_view<T>(a, c);
   launch_prep<T>(a, s);
   cudaMemsetAsync(c->flags, 0xff, sizeof(int), s);
+  c->built_n = n;
   launch_neighbors<T>(a, c->ncell, s);
   cudaMemsetAsync(c->flags, 0, sizeof(int), s);
   return launch_status(c);
@@ -389,6 +401,7 @@ apip_status verlet_t(apip_ctx* c, double* pos, double* vel, double* force, const
                      const int32_t* id, int n, double dt, int steps, double* thermo, cudaStream_t s) {
   Args<T> a = make_args<T>(c, pos, id, n, force, nullptr);
   set_view<T>(a, c);
+  mark_atom_count(c, n, s);
   const int ntb = nblk(n);
   const int n_part = a.n_part_p1 + c->ace_blocks;
   for (int k = 0; k < steps; ++k) {
@@ -651,15 +664,17 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   double norms[(kLmaxCap + 1) * (kLmaxCap + 1)];
   ylm_norms(kLmaxCap, norms);
   const int nn = (kLmaxCap + 1) * (kLmaxCap + 1);
+  // the harmonic norms and Gaunt values are the same for every context: constant
+  // memory of the current device, (re)filled by each apip_create
   if (streamed) {
     std::vector<double> gv(kGauntTotal);
     gaunt_fill(gv.data());
-    if (p->precision == APIP_FP64) ace_stream_set_consts<double>(norms, nn, gv.data());
-    else ace_stream_set_consts<float>(norms, nn, gv.data());
+    e = p->precision == APIP_FP64 ? ace_stream_set_consts<double>(norms, nn, gv.data())
+                                  : ace_stream_set_consts<float>(norms, nn, gv.data());
   } else {
-    if (p->precision == APIP_FP64) ace_pool_set_norms<double>(norms, nn);
-    else ace_pool_set_norms<float>(norms, nn);
+    e = p->precision == APIP_FP64 ? ace_pool_set_norms<double>(norms, nn) : ace_pool_set_norms<float>(norms, nn);
   }
+  if (e != cudaSuccess) return fail_create(e);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail_create(e);
   *out = ctx;
@@ -774,7 +789,7 @@ apip_status apip_sync(apip_ctx* ctx, void* stream) {
   if (st[ST_CELL_OVERFLOW])
     return fail(ctx, APIP_ERR_NB_OVERFLOW, "cell overflow: a cell holds " + std::to_string(st[ST_MAX_CELL]) +
                                               " atoms, cell_cap = " + std::to_string(ctx->p.cell_cap));
-  if (st[ST_TIMEOUT]) return fail(ctx, APIP_ERR_TIMEOUT, "an asynchronous table copy did not complete in time");
+  if (st[ST_TIMEOUT]) return fail(ctx, APIP_ERR_TIMEOUT, "reserved: a bounded device wait gave up");
   if (st[ST_BAD_INPUT]) return fail(ctx, APIP_ERR_BAD_INPUT, "non-finite position or atom id out of range");
   if (st[ST_BAD_PARTNER]) return fail(ctx, APIP_ERR_BAD_INPUT, "a CSP partner id is not present");
   return APIP_OK;
@@ -805,12 +820,14 @@ apip_status apip_descriptors(apip_ctx* ctx, const double* pos, const double box[
   if (ctx->p.precision == APIP_FP32) {
     Args<float> a = make_args<float>(ctx, pos, id, (int)n, nullptr, nullptr);
     set_view<float>(a, ctx);
+    mark_atom_count(ctx, (int)n, s);
     launch_prep<float>(a, s);
     launch_neighbors<float>(a, ctx->ncell, s);
     launch_descriptors<float>(a, desc_bf16, s);
   } else {
     Args<double> a = make_args<double>(ctx, pos, id, (int)n, nullptr, nullptr);
     set_view<double>(a, ctx);
+    mark_atom_count(ctx, (int)n, s);
     launch_prep<double>(a, s);
     launch_neighbors<double>(a, ctx->ncell, s);
     launch_descriptors<double>(a, desc_bf16, s);

@@ -126,6 +126,7 @@ struct apip_ctx {
   double r_list = 0.0;
   apip::Geo geo{};
   bool geo_set = false;
+  int64_t built_n = -1;        // atom count of the last neighbour-list build (or the last call)
   int ncell = 0, ncell_alloc = 0;
   bool csp_ready = false;
   const double* lam_fixed = nullptr;  // caller's per-atom constant lam (NaN = switch)

@@ -64,6 +64,8 @@ __global__ void k_total(const double* partials, int nb, double* out) {
 }
 
 // Device address of g_partials per device, looked up once with that device current.
+// It belongs to the device's primary context and goes stale if that context is
+// destroyed (cudaDeviceReset); the header documents the limit.
 constexpr int kMaxDevices = 64;
 double* g_addr[kMaxDevices] = {};
 std::mutex g_mu;

@@ -94,14 +94,6 @@ template <> __device__ __forceinline__ void len_inv<double>(double r2, double* r
   *ir = 1.0 / *r;
 }
 
-// Plain running sum, for the float32 sums whose rounding (~1e-7 relative over
-// some tens of terms) is far below their tolerance (the switch weights).
-template <typename T> struct Sum {
-  T s = T(0);
-  __device__ __forceinline__ void add(T v) { s += v; }
-  __device__ __forceinline__ T value() const { return s; }
-};
-
 // Positions.  FP64 path: the caller's float64 array, minimum image with rint.
 // FP32 path: each coordinate as a 32-bit fixed-point fraction of the box,
 // q = floor(x_wrapped / L * 2^32).  The unsigned difference q_j - q_i read as a
@@ -141,6 +133,23 @@ template <> struct PosView<float> {
   }
   __device__ __forceinline__ V3<float> vec(const Self& s, int j) const { return vec_of(s, q[j]); }
 };
+
+// The CSP^list vector r_ia + r_ib of atom i's partners a and b (Eq. B3).  FP32
+// path: the two fixed-point separations are added as integers (exact; partners
+// lie far closer than half the box) and converted once, so the nearly cancelling
+// sum keeps the relative precision of its own length.
+__device__ __forceinline__ V3<double> csp_vec(const PosView<double>& pv, const PosView<double>::Self& s, int ia,
+                                              int ib) {
+  const V3<double> u1 = pv.vec(s, ia), u2 = pv.vec(s, ib);
+  return {u1.x + u2.x, u1.y + u2.y, u1.z + u2.z};
+}
+__device__ __forceinline__ V3<float> csp_vec(const PosView<float>& pv, const PosView<float>::Self& s, int ia,
+                                             int ib) {
+  const uint4 qa = pv.q[ia], qb = pv.q[ib];
+  return {(float)(int)((qa.x - s.q.x) + (qb.x - s.q.x)) * pv.unit[0],
+          (float)(int)((qa.y - s.q.y) + (qb.y - s.q.y)) * pv.unit[1],
+          (float)(int)((qa.z - s.q.z) + (qb.z - s.q.z)) * pv.unit[2]};
+}
 
 // Fixed-point coordinate of a wrapped position w in [0, L): floor(w 2^32 / L)
 // mod 2^32 (w = L, a rounding edge, maps to 0, its periodic image), in integer

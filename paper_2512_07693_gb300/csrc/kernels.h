@@ -190,10 +190,10 @@ void launch_mlp_adam(float* p, const float* g, float* m, float* v, int t, float 
 // ACE: body order 4 (kernels_ace_f32.cu, kernels_ace_f64.cu) and body order
 // <= 3 (kernels_ace3_f32.cu, kernels_ace3_f64.cu).  The occupancy queries return
 // resident blocks per SM for ace.group atoms per block (0 if it does not fit).
-template <typename T> void ace_pool_set_norms(const double* norms, int count);
+template <typename T> cudaError_t ace_pool_set_norms(const double* norms, int count);
 template <typename T> void launch_ace_pool(const Args<T>& a, const AceDev<T>& ace, int blocks, cudaStream_t s);
 template <typename T> int ace_pool_occupancy(const AceDev<T>& ace);
-template <typename T> void ace_stream_set_consts(const double* norms, int count, const double* gaunt);
+template <typename T> cudaError_t ace_stream_set_consts(const double* norms, int count, const double* gaunt);
 template <typename T> void launch_ace_stream(const Args<T>& a, const AceDev<T>& ace, int blocks, cudaStream_t s);
 template <typename T> int ace_stream_occupancy(const AceDev<T>& ace);
 

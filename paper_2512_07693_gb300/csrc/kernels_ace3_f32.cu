@@ -1,4 +1,6 @@
 // float instantiation of the body-order <= 3 ACE kernel (ace_stream.cuh).
+#include <vector>
+
 #include "apip_internal.h"
 #include "gaunt_layout.h"
 
@@ -17,13 +19,11 @@ struct Consts {
 
 namespace apip {
 
-template <> void ace_stream_set_consts<float>(const double* norms, int count, const double* gaunt) {
-  float f[(kLmaxCap + 1) * (kLmaxCap + 1)];
-  for (int k = 0; k < count; ++k) f[k] = (float)norms[k];
-  cudaMemcpyToSymbol(c_norm, f, sizeof(float) * count);
-  static float gv[kGauntTotal];
-  for (int e = 0; e < kGauntTotal; ++e) gv[e] = (float)gaunt[e];
-  cudaMemcpyToSymbol(c_gaunt, gv, sizeof(float) * kGauntTotal);
+template <> cudaError_t ace_stream_set_consts<float>(const double* norms, int count, const double* gaunt) {
+  std::vector<float> f(norms, norms + count), gv(gaunt, gaunt + kGauntTotal);
+  const cudaError_t e = cudaMemcpyToSymbol(c_norm, f.data(), sizeof(float) * count);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_gaunt, gv.data(), sizeof(float) * kGauntTotal);
 }
 
 template <> void launch_ace_stream<float>(const Args<float>& a, const AceDev<float>& t, int blocks, cudaStream_t s) {

@@ -1,4 +1,6 @@
 // double instantiation of the body-order <= 3 ACE kernel (ace_stream.cuh).
+#include <vector>
+
 #include "apip_internal.h"
 #include "gaunt_layout.h"
 
@@ -17,13 +19,11 @@ struct Consts {
 
 namespace apip {
 
-template <> void ace_stream_set_consts<double>(const double* norms, int count, const double* gaunt) {
-  double f[(kLmaxCap + 1) * (kLmaxCap + 1)];
-  for (int k = 0; k < count; ++k) f[k] = (double)norms[k];
-  cudaMemcpyToSymbol(c_norm, f, sizeof(double) * count);
-  static double gv[kGauntTotal];
-  for (int e = 0; e < kGauntTotal; ++e) gv[e] = (double)gaunt[e];
-  cudaMemcpyToSymbol(c_gaunt, gv, sizeof(double) * kGauntTotal);
+template <> cudaError_t ace_stream_set_consts<double>(const double* norms, int count, const double* gaunt) {
+  std::vector<double> f(norms, norms + count), gv(gaunt, gaunt + kGauntTotal);
+  const cudaError_t e = cudaMemcpyToSymbol(c_norm, f.data(), sizeof(double) * count);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_gaunt, gv.data(), sizeof(double) * kGauntTotal);
 }
 
 template <> void launch_ace_stream<double>(const Args<double>& a, const AceDev<double>& t, int blocks, cudaStream_t s) {

@@ -14,10 +14,10 @@ struct Consts {
 
 namespace apip {
 
-template <> void ace_pool_set_norms<float>(const double* norms, int count) {
+template <> cudaError_t ace_pool_set_norms<float>(const double* norms, int count) {
   float f[(kLmaxCap + 1) * (kLmaxCap + 1)];
   for (int k = 0; k < count; ++k) f[k] = (float)norms[k];
-  cudaMemcpyToSymbol(c_norm, f, sizeof(float) * count);
+  return cudaMemcpyToSymbol(c_norm, f, sizeof(float) * count);
 }
 
 template <> void launch_ace_pool<float>(const Args<float>& a, const AceDev<float>& t, int blocks, cudaStream_t s) {

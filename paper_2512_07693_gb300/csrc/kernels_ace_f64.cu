@@ -14,10 +14,8 @@ struct Consts {
 
 namespace apip {
 
-template <> void ace_pool_set_norms<double>(const double* norms, int count) {
-  double f[(kLmaxCap + 1) * (kLmaxCap + 1)];
-  for (int k = 0; k < count; ++k) f[k] = (double)norms[k];
-  cudaMemcpyToSymbol(c_norm, f, sizeof(double) * count);
+template <> cudaError_t ace_pool_set_norms<double>(const double* norms, int count) {
+  return cudaMemcpyToSymbol(c_norm, norms, sizeof(double) * count);
 }
 
 template <> void launch_ace_pool<double>(const Args<double>& a, const AceDev<double>& t, int blocks, cudaStream_t s) {

@@ -342,14 +342,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_pass1(Args<T
       const bool idok = idv >= 0 && idv < a.nmax;   // by prep, no partners here)
       const int4* pr4 = reinterpret_cast<const int4*>(a.csp + (size_t)(idok ? idv : 0) * kCspCap);
       static_assert(kCspCap == 8, "two int4 rows of partner ids");
-      int idx[kCspCap];
+      int idx[kCspCap], pid[kCspCap];
       {
         const int4 none = make_int4(-1, -1, -1, -1);
         const int4 p0 = idok ? pr4[0] : none, p1 = idok ? pr4[1] : none;
-        const int pid[kCspCap] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+        const int pr[kCspCap] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
 #pragma unroll
-        for (int k = 0; k < kCspCap; ++k)
-          idx[k] = (k >= a.csp_nnb || pid[k] < 0) ? -1 : (pid[k] >= a.nmax ? -2 : a.id2idx[pid[k]]);
+        for (int k = 0; k < kCspCap; ++k) {
+          pid[k] = pr[k];
+          idx[k] = (k >= a.csp_nnb || pr[k] < 0) ? -1 : (pr[k] >= a.nmax ? -2 : a.id2idx[pr[k]]);
+        }
       }
       bool bad = false;
       Acc<T> gs;
@@ -357,10 +359,13 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_pass1(Args<T
       for (int k = 0; k < kCspCap / 2; ++k) {
         const int ia = idx[2 * k], ib = idx[2 * k + 1];
         if (ia == -1 || ib == -1) continue;
-        if (ia < 0 || ib < 0 || ia >= a.n || ib >= a.n) { bad = true; continue; }
-        const auto u1 = a.pv.vec(si, ia);
-        const auto u2 = a.pv.vec(si, ib);
-        const V3<T> u{u1.x + u2.x, u1.y + u2.y, u1.z + u2.z};
+        // the index must hold that partner now: the id -> index map keeps the
+        // entries of ids that are no longer present
+        if (ia < 0 || ib < 0 || ia >= a.n || ib >= a.n || a.id[ia] != pid[2 * k] || a.id[ib] != pid[2 * k + 1]) {
+          bad = true;
+          continue;
+        }
+        const V3<T> u = csp_vec(a.pv, si, ia, ib);
         gs.add(dot3(u, u));
       }
       if (bad) atomicOr(&a.status[ST_BAD_PARTNER], 1);
@@ -393,9 +398,10 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
     const T A = a.k.eam_A, beta = a.k.eam_beta, re = a.k.eam_re, D = a.k.eam_D, alpha = a.k.eam_alpha,
             r0 = a.k.eam_r0;
     const T xi_i = a.xi_p[i];
-    // the force components keep compensated sums: their rounding decides how well
-    // the float32 path conserves the total momentum; the switch weights do not
-    Sum<T> wbar, S;
+    // compensated sums: the force components' rounding decides how well the float32
+    // path conserves the total momentum; that of w-bar and sum g w moves d, and through
+    // dlam/dd times (E^prec - E^EAM) the energy
+    Acc<T> wbar, S;
     Acc<T> fx, fy, fz;
     wbar.add(T(1));
     if (paper) S.add(a.g[i]);
@@ -529,10 +535,10 @@ __global__ void k_csp_force(Args<T> a) {
     const int ia_id = pr[2 * k], ib_id = pr[2 * k + 1];
     if (ia_id < 0 || ib_id < 0 || ia_id >= a.nmax || ib_id >= a.nmax) continue;
     const int ia = a.id2idx[ia_id], ib = a.id2idx[ib_id];
-    if (ia < 0 || ib < 0 || ia >= a.n || ib >= a.n) continue;
-    const auto u1 = a.pv.vec(sj, ia);
-    const auto u2 = a.pv.vec(sj, ib);
-    const double u[3] = {(double)(u1.x + u2.x), (double)(u1.y + u2.y), (double)(u1.z + u2.z)};
+    // stale map entries (ids no longer present) are reported by pass 1
+    if (ia < 0 || ib < 0 || ia >= a.n || ib >= a.n || a.id[ia] != ia_id || a.id[ib] != ib_id) continue;
+    const V3<T> uv = csp_vec(a.pv, sj, ia, ib);
+    const double u[3] = {(double)uv.x, (double)uv.y, (double)uv.z};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       atomicAdd(&a.force[3 * ia + q], -2.0 * c * u[q]);

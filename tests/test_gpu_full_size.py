@@ -32,7 +32,10 @@ def _cluster(s, i):
     return c, int(np.flatnonzero(keep == i)[0])
 
 
-def test_void250k_full_size_sampled_atoms_fp32():
+@pytest.fixture(scope="module")
+def void250k_fp32():
+    """The whole crystal evaluated once on the GPU (float32 path, bench launch
+    configuration): the workload, forces, per-atom energies, lam and dlam."""
     torch = torch_cuda()
     from paper_2512_07693_gb300 import apip
     s = W.config("void250k", apip.apip_ace_basis_size)
@@ -46,11 +49,14 @@ def test_void250k_full_size_sampled_atoms_fp32():
     e = torch.empty(n, dtype=torch.float64, device="cuda")
     m.energy_forces(t["pos"], box, t["types"], t["ids"], F, e)
     m.sync()
-    F = F.cpu().numpy()
-    e = e.cpu().numpy()
-    lam = m.field("lam", n).cpu().numpy()
-    dlam = m.field("dlam", n).cpu().numpy()
+    out = dict(s=s, F=F.cpu().numpy(), e=e.cpu().numpy(), lam=m.field("lam", n).cpu().numpy(),
+               dlam=m.field("dlam", n).cpu().numpy())
     m.close()
+    return out
+
+
+def test_void250k_full_size_sampled_atoms_fp32(void250k_fp32):
+    s, F, e, lam, dlam = (void250k_fp32[k] for k in ("s", "F", "e", "lam", "dlam"))
     assert np.abs(F.sum(axis=0)).max() < 1e-2     # 249 k atoms, float32 pair terms
     rng = np.random.default_rng(11)
     core = np.flatnonzero(lam == 1.0)
@@ -71,6 +77,43 @@ def test_void250k_full_size_sampled_atoms_fp32():
         assert abs(e[i] - o["e_atom"][k]) <= 1e-5, (i, e[i], o["e_atom"][k])
         err = np.abs(F[i] - o["F"][k]).max()
         assert err <= 2e-4, (i, lam[i], err)
+
+
+SUBBOX_HALF = 16.0     # half edge of the sub-box (A): ~2 100 atoms
+SUBBOX_HALO = 20.0     # every dependency of its atoms' outputs (module docstring)
+SUBBOX_FREE = 10.0     # atoms farther than this from the sub-box do not affect them
+
+
+def test_void250k_subbox_every_atom_fp32(void250k_fp32):
+    """Every atom of a ~2 100-atom cube straddling the void surface (centred on the
+    surface, so it holds precise, transition and fast atoms) against one oracle run
+    on the cube and a 20 A halo.  The halo's outer atoms (farther than 10 A from
+    the cube) neither enter the cube's energies nor, beyond 9.5 A, its forces;
+    the oracle holds them at lam = 0 (a constant-switch subset) so that it does
+    not evaluate ACE on the free surface of the cut-out."""
+    s, F, e, lam = (void250k_fp32[k] for k in ("s", "F", "e", "lam"))
+    centre = 0.5 * s["box"] + np.array([15.0, 0.0, 0.0])
+    d = s["pos"] - centre
+    d -= s["box"] * np.rint(d / s["box"])
+    out = np.maximum(np.abs(d) - SUBBOX_HALF, 0.0)
+    dist = np.sqrt(np.sum(out * out, axis=1))     # distance to the cube, 0 inside
+    inside = np.flatnonzero(dist == 0.0)
+    keep = np.flatnonzero(dist < SUBBOX_HALO)
+    assert 1900 < len(inside) < 2400
+    assert np.any(lam[inside] == 1.0) and np.any((lam[inside] > 0) & (lam[inside] < 1)) and np.any(lam[inside] == 0)
+    box = np.full(3, 2 * (SUBBOX_HALF + SUBBOX_HALO) + 40.0)
+    pos = d[keep] + 0.5 * box
+    c = W._finish(pos, np.zeros_like(pos), box)
+    c["ids"] = s["ids"][keep].copy()
+    c["prm"] = s["prm"]
+    lam_const = np.where(dist[keep] > SUBBOX_FREE, 0.0, np.nan)
+    o = run_oracle(c, lam_const=lam_const)
+    loc = np.searchsorted(keep, inside)
+    assert np.array_equal(keep[loc], inside)
+    np.testing.assert_allclose(lam[inside], o["lam"][loc], atol=1e-5, rtol=0)
+    np.testing.assert_allclose(e[inside], o["e_atom"][loc], atol=1e-5, rtol=0)
+    err = np.abs(F[inside] - o["F"][loc]).max()
+    assert err <= 2e-4, err
 
 
 def test_void250k_fp32_against_fp64_all_atoms():
