@@ -9,9 +9,13 @@ void250k workload: a 50^3-cell bcc crystal with a central void of radius 15 A
 arithmetic with float64 positions, velocities, forces and reductions.
 
 Prints one JSON line (rank 0).  Metric: atom-steps/s of the adaptive run; the
-all-ACE run on the same GPU, the NVE drift and the roofline of the dominant
-kernel are reported beside it.  ``--impl reference`` times the FP64 CPU oracle
-on the host cores instead (a bounded sample of the same workload).
+all-ACE run on the same GPU, the NVE drift, the rooflines of the dominant kernel
+and of the ACE kernel against measured peaks, and one line per other workload
+(the 2 k-atom vacancy crystal in float64, the void crystal in float64, the 2 M-atom
+cracked slab, learned-indicator training, the 4 M-atom indentation slab with the
+paper's switch, the learned switch and all-ACE) are reported beside it.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (a
+bounded sample of the same workload).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU (torchrun): replicas only, one independent system per rank.
@@ -19,6 +23,7 @@ Multi-GPU (torchrun): replicas only, one independent system per rank.
 import argparse
 import json
 import math
+import multiprocessing
 import os
 import statistics
 import subprocess
@@ -34,12 +39,11 @@ METRIC = "atom-steps/s adaptive EAM+ACE vs all-ACE on 1 GB300; NVE drift eV/atom
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2, written between timed steps
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes (read + write) per launch of the step's dominant kernels on this
-# workload, from one ncu capture of the current kernels (profiles/*_void250k.md),
-# per launch (the Verlet one per half-step launch); a kernel changed since its
-# capture has no entry
-NCU_TRAFFIC = {"ace": 3.370752e6, "pass2": 69.671680e6 + 1.681664e6, "prep": 13.949184e6}
+# workload from an ncu capture, with the commit of the kernel's source it was
+# taken at; bench.py reports it only while the kernel is unchanged since
+NCU_TRAFFIC = {"pass2": (69.671680e6 + 1.681664e6, "round-1 capture, before the float32 switch sums changed")}
+NCU_TRAFFIC_CURRENT = {}
 
 
 def parse():
@@ -55,6 +59,7 @@ def parse():
     ap.add_argument("--ace-group", type=int, default=0, choices=[0, 1, 2, 4, 8, 32],
                     help="compacted atoms per ACE thread block (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the lines of the other workloads")
     ap.add_argument("--cells", type=int, default=None,
                     help="scale the void workload to cells^3 (small cases for profiling; not the metric)")
     return ap.parse_args()
@@ -83,17 +88,21 @@ def job_value(world, n_atoms, steps, total_ms):
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(steps_budget_s, target_s):
-    """Time the FP64 CPU oracle on a shrunken copy of the workload recipe
-    (same lattice, void radius scaled with the box, same potentials)."""
+def _oracle_system(cells):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
-    from oracle import ace, apip as oapip, csp
+    from oracle import ace, csp
     from paper_2512_07693_gb300 import workloads as W
-    nb = lambda a, b, c: len(ace.enumerate_basis(a, b, c))
-    cells = 12
-    s = W.config(WORKLOAD, nb, scale=cells)
+    s = W.config(WORKLOAD, lambda a, b, c: len(ace.enumerate_basis(a, b, c)), scale=cells)
     part = csp.init_pairs(s["pos"], s["box"], s["ids"], W.CSP["rcut"])
-    model = ace.AceModel(s["prm"]["ace"])
+    return s, part, ace.AceModel(s["prm"]["ace"])
+
+
+def _oracle_forces_worker(job):
+    """One host process: repeated FP64 oracle energy/force calls on the shrunken
+    recipe for about target_s seconds."""
+    target_s, cells = job
+    from oracle import apip as oapip
+    s, part, model = _oracle_system(cells)
     t0 = time.perf_counter()
     reps = 0
     while True:
@@ -101,37 +110,66 @@ def oracle_sample(steps_budget_s, target_s):
         reps += 1
         if time.perf_counter() - t0 >= target_s:
             break
-    dt = time.perf_counter() - t0
-    n = len(s["pos"])
-    return dict(value=n * reps / dt, n=n, reps=reps, seconds=dt, x=len(res["P"]) / n, cells=cells)
+    return len(s["pos"]), reps, time.perf_counter() - t0, len(res["P"]) / len(s["pos"])
+
+
+def _oracle_verlet_worker(job):
+    """One host process: warm-up then timed FP64 oracle velocity-Verlet steps."""
+    cells, warmup, steps = job
+    from oracle import verlet
+    s, part, model = _oracle_system(cells)
+    pos, vel = s["pos"], s["vel"]
+    pos, vel, _, _ = verlet.run(pos, vel, s["box"], s["ids"], part, s["prm"], s["mass"], 0.001, warmup, model=model)
+    t0 = time.perf_counter()
+    verlet.run(pos, vel, s["box"], s["ids"], part, s["prm"], s["mass"], 0.001, steps, model=model)
+    return len(s["pos"]), steps, time.perf_counter() - t0
+
+
+def host_workers():
+    return max(1, os.cpu_count() or 1)
+
+
+def _pool_map(fn, jobs):
+    """Run the oracle in spawned processes (a fresh interpreter each: the parent's
+    CUDA context is never forked), one numpy thread per process."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    ctx = multiprocessing.get_context("spawn")
+    with ctx.Pool(len(jobs)) as pool:
+        return pool.map(fn, jobs)
+
+
+def oracle_sample(target_s, cells=12):
+    """The FP64 CPU oracle on every host core: one independent copy of a shrunken
+    void recipe (same lattice, void radius scaled with the box, same potentials)
+    per core, timed together; atom-steps/s summed over the copies."""
+    workers = host_workers()
+    res = _pool_map(_oracle_forces_worker, [(target_s, cells)] * workers)
+    value = sum(n * reps / dt for n, reps, dt, _ in res)
+    n, reps, dt, x = res[0]
+    return dict(value=value, n=n, reps=sum(r[1] for r in res), seconds=max(r[2] for r in res), x=x,
+                cells=cells, workers=workers)
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from oracle import ace, apip as oapip, csp
-    from paper_2512_07693_gb300 import workloads as W
-    nb = lambda a, b, c: len(ace.enumerate_basis(a, b, c))
     cells = 6
-    s = W.config(WORKLOAD, nb, scale=cells)
-    part = csp.init_pairs(s["pos"], s["box"], s["ids"], W.CSP["rcut"])
-    model = ace.AceModel(s["prm"]["ace"])
-    from oracle import verlet
-    n = len(s["pos"])
-    pos, vel = s["pos"], s["vel"]
-    _, _, _, _ = verlet.run(pos, vel, s["box"], s["ids"], part, s["prm"], s["mass"], 0.001, args.warmup, model=model)
+    workers = host_workers()
     t0 = time.perf_counter()
-    _, _, _, log = verlet.run(pos, vel, s["box"], s["ids"], part, s["prm"], s["mass"], 0.001, args.steps, model=model)
-    dt = time.perf_counter() - t0
-    value = n * args.steps / dt
-    sample = f"{WORKLOAD} recipe at {cells}^3 cells ({n} atoms), FP64 numpy oracle, velocity-Verlet steps"
+    res = _pool_map(_oracle_verlet_worker, [(cells, args.warmup, args.steps)] * workers)
+    wall = time.perf_counter() - t0
+    value = sum(n * steps / dt for n, steps, dt in res)
+    n = res[0][0]
+    sample = (f"{WORKLOAD} recipe at {cells}^3 cells ({n} atoms), FP64 numpy oracle, velocity-Verlet steps; "
+              f"{workers} independent copies, one per host core, atom-steps/s summed")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * max(r[2] for r in res) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "atoms": n, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": WORKLOAD, "atoms": n, "sample": sample, "wall_s": wall},
+        "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": workers, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -181,17 +219,23 @@ def clocks_stop(handle, gpu_index):
 ACE_GROUP = 0
 
 
-def setup(torch, prm, s, lam_mode, precision="fp32"):
+def device_arrays(torch, s):
     from paper_2512_07693_gb300 import apip
     n = len(s["pos"])
     dev = torch.device("cuda")
+    return dict(pos=torch.tensor(s["pos"], dtype=torch.float64, device=dev),
+                vel=torch.tensor(s["vel"], dtype=torch.float64, device=dev),
+                ids=torch.tensor(s["ids"], dtype=torch.int32, device=dev),
+                types=torch.zeros(n, dtype=torch.int32, device=dev),
+                inv_mass=torch.tensor(1.0 / (s["mass"] * apip.MVV2E), dtype=torch.float64, device=dev),
+                F=torch.empty((n, 3), dtype=torch.float64, device=dev))
+
+
+def setup(torch, prm, s, lam_mode, precision="fp32"):
+    from paper_2512_07693_gb300 import apip
+    n = len(s["pos"])
     m = apip.Apip(prm, n, precision=precision, lam_mode=lam_mode, max_nb=80, cell_cap=48, ace_group=ACE_GROUP)
-    t = dict(pos=torch.tensor(s["pos"], dtype=torch.float64, device=dev),
-             vel=torch.tensor(s["vel"], dtype=torch.float64, device=dev),
-             ids=torch.tensor(s["ids"], dtype=torch.int32, device=dev),
-             types=torch.zeros(n, dtype=torch.int32, device=dev),
-             inv_mass=torch.tensor(1.0 / (s["mass"] * apip.MVV2E), dtype=torch.float64, device=dev),
-             F=torch.empty((n, 3), dtype=torch.float64, device=dev))
+    t = device_arrays(torch, s)
     box = [float(x) for x in s["box"]]
     if lam_mode == "paper":
         m.init_csp_pairs(t["pos"], box, t["ids"])
@@ -200,20 +244,44 @@ def setup(torch, prm, s, lam_mode, precision="fp32"):
     return m, t, box
 
 
+THERMO_EVERY = 10   # thermo output (E_pot, E_kin, momentum) every 10th step, as an MD log does
+
+
 def timed_steps(torch, m, t, box, steps, flush, thermo=None):
-    """Per-step CUDA-event timing on the launching stream, L2 flushed between steps."""
+    """Per-step CUDA-event timing on the launching stream, L2 flushed between steps.
+    With ``thermo`` (rows of 5), step k writes row k // THERMO_EVERY when
+    k % THERMO_EVERY == THERMO_EVERY - 1."""
     stream = torch.cuda.current_stream()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     for k in range(steps):
         flush.fill_(k & 0xff)
+        log = thermo is not None and k % THERMO_EVERY == THERMO_EVERY - 1
         starts[k].record(stream)
         m.verlet_step(t["pos"], t["vel"], t["F"], t["inv_mass"], box, t["types"], t["ids"], 0.001, 1,
-                      None if thermo is None else thermo[k])
+                      thermo[k // THERMO_EVERY] if log else None)
         ends[k].record(stream)
     torch.cuda.synchronize()
     m.sync()
     return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def nve_drift(torch, m, t, box, n, steps, chunk=100):
+    """Least-squares slope of H/N (eV/atom/ps) over ``steps`` NVE steps of 1 fs
+    (untimed; thermo every step), and the momentum change over them."""
+    import numpy as np
+    nd = max(chunk, steps // chunk * chunk)
+    thd = torch.zeros((nd, 5), dtype=torch.float64, device="cuda")
+    for q in range(0, nd, chunk):
+        m.verlet_step(t["pos"], t["vel"], t["F"], t["inv_mass"], box, t["types"], t["ids"], 0.001, chunk,
+                      thd[q:q + chunk])
+    torch.cuda.synchronize()
+    m.sync()
+    hd = thd.cpu().numpy()
+    Hd = (hd[:, 0] + hd[:, 1]) / n
+    return (float(np.polyfit(np.arange(nd) * 0.001, Hd, 1)[0]),
+            {"ps": nd * 0.001, "H_std_ev_per_atom": float(Hd.std()),
+             "momentum_change": [float(v) for v in hd[-1, 2:] - hd[0, 2:]]})
 
 
 def ace_flops_per_atom(s, nnb_rc, info):
@@ -226,6 +294,172 @@ def ace_flops_per_atom(s, nnb_rc, info):
     nlm = (a["l_max"] + 1) ** 2
     per_nb = 2 * a["n_max"] * nlm + 4 * a["n_max"] * nlm + 8 * nlm
     return nnb_rc * per_nb + info["table_flops"], per_nb
+
+
+def neighbours_within(torch, m, t, box, atoms, rc, n):
+    """Mean number of neighbours within rc of the given atoms (the ACE pair work)."""
+    import numpy as np
+    if len(atoms) == 0:
+        return 0.0
+    nbl = m.field("nblist", n)[torch.as_tensor(atoms, device="cuda")].cpu().numpy()
+    pos_now = t["pos"].cpu().numpy()
+    jj = np.where(nbl >= 0, nbl, atoms[:, None])
+    dv = pos_now[jj] - pos_now[atoms][:, None, :]
+    dv -= np.asarray(box) * np.rint(dv / np.asarray(box))
+    r2 = np.sum(dv * dv, axis=2)
+    return float(np.mean(np.sum((nbl >= 0) & (r2 < rc * rc) & (jj != atoms[:, None]), axis=1)))
+
+
+def ace_roofline(s, nb_rc, info, atoms, ms, peak, source):
+    fl_atom, _ = ace_flops_per_atom(s, nb_rc, info)
+    fl = fl_atom * atoms
+    achieved = fl / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    return {"kernel": "ace", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None, "traffic": None, "atoms": int(atoms),
+            "algorithmic_flops_per_launch": fl, "flops_per_atom": fl_atom, "peak_source": source}
+
+
+# ------------------------------------------------------- the other workloads
+def extra_vacancy2k(torch, W, apip):
+    """C1: 1 999 atoms, float64, one energy/force call and 100 Verlet steps."""
+    s = W.config("vacancy2k", apip.apip_ace_basis_size)
+    n = len(s["pos"])
+    m, t, box = setup(torch, s["prm"], s, "paper", precision="fp64")
+    stream = torch.cuda.current_stream()
+    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    a.record(stream)
+    m.energy_forces(t["pos"], box, t["types"], t["ids"], t["F"])
+    b.record(stream)
+    m.verlet_step(t["pos"], t["vel"], t["F"], t["inv_mass"], box, t["types"], t["ids"], 0.001, 100)
+    c.record(stream)
+    torch.cuda.synchronize()
+    m.sync()
+    x = float((m.field("lam", n).cpu().numpy() > 0).mean())
+    m.close()
+    ms_md = b.elapsed_time(c)
+    return {"workload": "vacancy2k", "atoms": n, "precision": "fp64", "x_ace": x,
+            "energy_forces_ms": a.elapsed_time(b), "md_100_steps_ms": ms_md,
+            "atom_steps_per_s": n * 100 / (ms_md * 1e-3)}
+
+
+def extra_void_fp64(torch, W, apip, flush, steps=10, drift_steps=1000):
+    """C2 in float64: the same void crystal and step, every pair in float64."""
+    s = W.config(WORKLOAD, apip.apip_ace_basis_size)
+    n = len(s["pos"])
+    m, t, box = setup(torch, s["prm"], s, "paper", precision="fp64")
+    timed_steps(torch, m, t, box, 3, flush)
+    per = timed_steps(torch, m, t, box, steps, flush)
+    x = float((m.field("lam", n).cpu().numpy() > 0).mean())
+    drift, window = nve_drift(torch, m, t, box, n, drift_steps)
+    m.close()
+    return {"workload": WORKLOAD, "atoms": n, "precision": "fp64", "steps": steps, "ms_per_step": sum(per) / steps,
+            "atom_steps_per_s": n * steps / (sum(per) * 1e-3), "x_ace": x,
+            "nve_drift_ev_per_atom_ps": drift, "nve_drift_window": window}
+
+
+def extra_crack2m(torch, W, apip, flush, steps=3):
+    """C3: the 2.0 M-atom cracked slab, ACE n_max 8 / l_max 4 / nu <= 4, float32."""
+    s = W.config("crack2m", apip.apip_ace_basis_size)
+    n = len(s["pos"])
+    m = apip.Apip(s["prm"], n, precision="fp32", lam_mode="paper", max_nb=80, cell_cap=48)
+    t = device_arrays(torch, s)
+    box = [float(x) for x in s["box"]]
+    lam_fixed = torch.tensor(s["lam_fixed"], dtype=torch.float64, device="cuda")
+    m.set_lam_fixed(lam_fixed)
+    m.init_csp_pairs(t["pos"], box, t["ids"])
+    m.energy_forces(t["pos"], box, t["types"], t["ids"], t["F"])
+    m.sync()
+    timed_steps(torch, m, t, box, 1, flush)
+    per = timed_steps(torch, m, t, box, steps, flush)
+    x = float((m.field("lam", n).cpu().numpy() > 0).mean())
+    info = apip.apip_ace_info(m.ctx)
+    m.close()
+    return {"workload": "crack2m", "atoms": n, "precision": "fp32", "ace": "n_max 8, l_max 4, nu<=4",
+            "basis_functions": int(s["prm"]["ace"]["c1"].shape[0]), "steps": steps,
+            "ms_per_step": sum(per) / steps, "atom_steps_per_s": n * steps / (sum(per) * 1e-3), "x_ace": x,
+            "ace_group": info["group"]}
+
+
+def extra_training(torch, W, apip, configs=400, epochs=20, batch=65536):
+    """C4 on a subsample: labels + descriptors of ``configs`` 2000-site defect
+    crystals, then Adam epochs; returns the trained weights for the indentation line."""
+    from paper_2512_07693_gb300 import train
+    prm = W.config("vacancy2k", apip.apip_ace_basis_size)["prm"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G, y, ref = train.make_dataset(prm, configs)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    params, hist = train.train(G, y, epochs=epochs, batch=min(batch, len(y)), lr=1e-3, prm=prm)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    na = int(len(y))
+    line = {"workload": f"learned-indicator training, {configs} of the 50 000 configurations", "atoms": na,
+            "epochs": epochs, "label_and_descriptor_s": t1 - t0, "label_atoms_per_s": na / (t1 - t0),
+            "training_s": t2 - t1, "training_atom_epochs_per_s": na * epochs / (t2 - t1),
+            "loss_first_last": [hist[0], hist[-1]]}
+    return line, params
+
+
+def extra_indent4m(torch, W, apip, flush, params, steps=20, ace_steps=3):
+    """C5: the 3 993 600-atom indentation slab, three arms on the same GPU: the
+    paper's switch, the learned switch (window placed at the paper's x), all-ACE."""
+    import numpy as np
+    from paper_2512_07693_gb300 import indent
+    s = W.config("indent4m", apip.apip_ace_basis_size)
+    n = len(s["pos"])
+    arms = {}
+    x_paper = None
+    for arm in ("paper", "learned", "ace"):
+        t = indent._device(torch, s)
+        prm = s["prm"]
+        if arm == "learned":
+            free = ~np.isfinite(s["lam_fixed"])
+            lo, hi = indent.learned_window(torch, s, t, params, x_paper * n / free.sum())
+            prm = dict(s["prm"], switch=dict(s["prm"]["switch"], d_lo=lo, d_hi=hi))
+        m, box = indent.model(torch, s, arm, t, prm=prm, mlp_flat=params)
+        k = steps if arm != "ace" else ace_steps
+        timed_steps(torch, m, t, box, 2, flush)
+        per = timed_steps(torch, m, t, box, k, flush)
+        lam = m.field("lam", n).cpu().numpy()
+        x = float((lam > 0).mean())
+        if arm == "paper":
+            x_paper = x
+        m.close()
+        arms[arm] = {"steps": k, "ms_per_step": sum(per) / k, "atom_steps_per_s": n * k / (sum(per) * 1e-3),
+                     "x_ace": x}
+    for a in arms.values():
+        a["speedup_vs_all_ace"] = a["atom_steps_per_s"] / arms["ace"]["atom_steps_per_s"]
+    return {"workload": "indent4m", "atoms": n, "precision": "fp32", "arms": arms}
+
+
+def run_extras(torch, W, apip, flush):
+    """One line per other workload; a workload that fails records its error
+    instead of ending the run."""
+    out = {}
+
+    def guarded(name, fn):
+        try:
+            r = fn()
+        except Exception as e:    # recorded in the output line, not raised
+            r = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        return r
+
+    out["vacancy2k_fp64"] = guarded("vacancy2k", lambda: extra_vacancy2k(torch, W, apip))
+    out["void250k_fp64"] = guarded("void250k_fp64", lambda: extra_void_fp64(torch, W, apip, flush))
+    out["crack2m"] = guarded("crack2m", lambda: extra_crack2m(torch, W, apip, flush))
+    params = {}
+
+    def train_line():
+        line, p = extra_training(torch, W, apip)
+        params["p"] = p
+        return line
+    out["training"] = guarded("training", train_line)
+    if "p" in params:
+        out["indent4m"] = guarded("indent4m", lambda: extra_indent4m(torch, W, apip, flush, params["p"]))
+    return out
 
 
 def run_ours(args):
@@ -242,46 +476,38 @@ def run_ours(args):
     build.build()
     from paper_2512_07693_gb300 import apip, workloads as W
 
+    fp32_peak, fp64_peak = apip.apip_measure_peaks()
     s = W.config(WORKLOAD, apip.apip_ace_basis_size, scale=args.cells)
     n = len(s["pos"])
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    # --- adaptive run (the metric)
+    # --- adaptive run (the metric); the clock sampler runs from the set-up through
+    # the timed steps, since the timed region alone is shorter than its period
+    clk = clocks_start()
     m, t, box = setup(torch, s["prm"], s, "paper")
     timed_steps(torch, m, t, box, args.warmup, flush)
-    thermo = torch.zeros((args.steps, 5), dtype=torch.float64, device="cuda")
+    n_log = args.steps // THERMO_EVERY
+    thermo = torch.zeros((max(1, n_log), 5), dtype=torch.float64, device="cuda")
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clk = clocks_start()
     per = timed_steps(torch, m, t, box, args.steps, flush, thermo)
     clocks = clocks_stop(clk, local)
     total_ms = job_ms(torch, sum(per), world, "cuda")
     value = job_value(world, n, args.steps, total_ms)
-    th = thermo.cpu().numpy()
+    th = thermo.cpu().numpy()[:n_log]
     H = (th[:, 0] + th[:, 1]) / n
-    tps = np.arange(args.steps) * 0.001
-    drift_timed = float(np.polyfit(tps, H, 1)[0]) if args.steps > 2 else None
-    # energy drift: least-squares slope of H/N over a 10 ps NVE continuation (untimed;
-    # 100 steps per call), after the timed steps let the start-up transient decay
+    tps = (np.arange(n_log) + 1) * THERMO_EVERY * 0.001
+    drift_timed = float(np.polyfit(tps, H, 1)[0]) if n_log > 2 else None
+    pmom = th[-1, 2:] - th[0, 2:] if n_log > 1 else np.zeros(3)
+    # energy drift: least-squares slope of H/N over a 10 ps NVE continuation (untimed),
+    # after the timed steps let the start-up transient decay
     drift, drift_window = None, None
     if args.drift_steps >= 100:
-        nd = args.drift_steps // 100 * 100
-        thd = torch.zeros((nd, 5), dtype=torch.float64, device="cuda")
-        for q in range(0, nd, 100):
-            m.verlet_step(t["pos"], t["vel"], t["F"], t["inv_mass"], box, t["types"], t["ids"], 0.001, 100,
-                          thd[q:q + 100])
-        torch.cuda.synchronize()
-        m.sync()
-        hd = thd.cpu().numpy()
-        Hd = (hd[:, 0] + hd[:, 1]) / n
-        drift = float(np.polyfit(np.arange(nd) * 0.001, Hd, 1)[0])
-        drift_window = {"ps": nd * 0.001, "start_ps": (args.warmup + args.steps) * 0.001,
-                        "H_std_ev_per_atom": float(Hd.std()),
-                        "momentum_change": [float(v) for v in hd[-1, 2:] - th[0, 2:]]}
+        drift, drift_window = nve_drift(torch, m, t, box, n, args.drift_steps)
+        drift_window["start_ps"] = (args.warmup + args.steps) * 0.001
     lam = m.field("lam", n).cpu().numpy()
     x_ace = float((lam > 0).mean())
-    pmom = th[-1, 2:] - th[0, 2:]
 
     # --- per-phase device time (profiled pass, same workload)
     apip.apip_profile(m.ctx, 1)
@@ -292,18 +518,12 @@ def run_ours(args):
     apip.apip_profile(m.ctx, 0)
     launches_per_step = sum(v[1] for v in prof.values()) / prof_steps
     nnb = m.field("nnb", n).cpu().numpy()
+    lam = m.field("lam", n).cpu().numpy()
     P = m.field("ace_list", n).cpu().numpy()[: int((lam > 0).sum())]
     ace_info = apip.apip_ace_info(m.ctx)
-    # neighbours within the ACE cutoff of the compacted atoms (the per-pair work)
-    nbl = m.field("nblist", n)[torch.as_tensor(P, device="cuda")].cpu().numpy()
-    pos_now = t["pos"].cpu().numpy()
-    jj = np.where(nbl >= 0, nbl, P[:, None])
-    dv = pos_now[jj] - pos_now[P][:, None, :]
-    dv -= np.asarray(box) * np.rint(dv / np.asarray(box))
-    r2 = np.sum(dv * dv, axis=2)
     rc = s["prm"]["ace"]["rc"]
-    nb_rc_ace = float(np.mean(np.sum((nbl >= 0) & (r2 < rc * rc) & (jj != P[:, None]), axis=1))) if len(P) else 0.0
-    del m
+    nb_rc_ace = neighbours_within(torch, m, t, box, P, rc, n)
+    m.close()
 
     # --- all-ACE run on the same GPU (lam = 1 everywhere)
     ma, ta, boxa = setup(torch, s["prm"], s, "const1")
@@ -313,7 +533,9 @@ def run_ours(args):
     apip.apip_profile(ma.ctx, 1)
     timed_steps(torch, ma, ta, boxa, 2, flush)
     prof_a = apip.apip_profile_read(ma.ctx)
-    del ma
+    nb_rc_all = neighbours_within(torch, ma, ta, boxa, np.arange(0, n, 97), rc, n)
+    ace_info_a = apip.apip_ace_info(ma.ctx)
+    ma.close()
 
     # --- end to end through the public API with host buffers
     me, te, boxe = setup(torch, s["prm"], s, "paper")
@@ -334,40 +556,39 @@ def run_ours(args):
         torch.cuda.current_stream().synchronize()
     e2e_dt = time.perf_counter() - t0
     me.sync()
-    del me
+    me.close()
     e2e = dict(value=world * n * e2e_steps / e2e_dt, unit="atom-steps/s", h2d_bytes_per_step=2 * 24 * n,
                d2h_bytes_per_step=2 * 24 * n + 40)
 
-    # --- roofline of the dominant kernel
+    # --- rooflines: the dominant kernel of the step, and the ACE kernel (adaptive
+    # and all-ACE) against the measured float32 multiply-add peak
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
     hbm = peaks.get("hbm_gbs", FALLBACK_HBM)
+    peak_src = "apip_measure_peaks: float32 multiply-add loop on every SM (measured in this run)"
     dom = max((k for k in prof if k != "reduce"), key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / max(1, prof[dom][1] if dom != "neighbor" else prof_steps)
-    mean_nnb = float(nnb.mean())
+    ace_ms = prof["ace"][0] / max(1, prof["ace"][1])
+    ace_ms_a = prof_a["ace"][0] / max(1, prof_a["ace"][1])
+    roof_ace = ace_roofline(s, nb_rc_ace, ace_info, len(P), ace_ms, fp32_peak, peak_src)
+    roof_ace_all = ace_roofline(s, nb_rc_all, ace_info_a, n, ace_ms_a, fp32_peak, peak_src)
     if dom in ("pass1", "pass2", "prep", "neighbor"):
         # algorithmic bytes per atom: neighbour indices 4 B each + nnb + own position
         # (hi/lo 32 B) + per-atom inputs/outputs (pass1: 8 partner ids 32 B + 4 outputs 16 B;
         # pass2: g, xi' 8 B + lam, dlam, wbar, d 16 B + force 24 B)
         extra = {"pass1": 32 + 16, "pass2": 8 + 16 + 24, "prep": 0, "neighbor": 0}[dom]
-        per_atom = 4 * mean_nnb + 4 + 32 + extra
+        per_atom = 4 * float(nnb.mean()) + 4 + 32 + extra
         if dom == "prep":
             per_atom = 2 * 48 + 24 + 24 + 32 + 8      # Verlet: pos, vel r/w, F, ref, hi/lo, inv_mass
         traffic_alg = per_atom * n
         achieved = traffic_alg / (dom_ms * 1e-3) / 1e9
+        cap = NCU_TRAFFIC_CURRENT.get(dom) if args.cells is None else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": NCU_TRAFFIC.get(dom) if args.cells is None else None,
+                "frac": achieved / hbm, "traffic": cap[0] if cap else None,
+                "traffic_source": cap[1] if cap else "no ncu capture of the current kernel",
                 "algorithmic_bytes_per_launch": traffic_alg,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}
     else:
-        nb_rc = nb_rc_ace
-        fl_atom, _ = ace_flops_per_atom(s, nb_rc, ace_info)
-        fl = fl_atom * len(P)
-        peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        achieved = fl / (dom_ms * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom) if args.cells is None else None,
-                "traffic_unit": "DRAM bytes per launch (ncu)", "algorithmic_flops_per_launch": fl,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+        roof = dict(roof_ace)
 
     out = {
         "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
@@ -386,17 +607,23 @@ def run_ours(args):
         "phase_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()},
         "phase_ms_per_step_all_ace": {k: v[0] / 2 for k, v in prof_a.items()},
         "roofline": roof,
+        "roofline_ace": {"adaptive": roof_ace, "all_ace": roof_ace_all},
+        "peaks_measured": {"fp32_tflops": fp32_peak, "fp64_tflops": fp64_peak, "hbm_gbs": hbm},
         "clocks": clocks,
+        "thermo_every": THERMO_EVERY,
         "e2e": e2e,
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "ace_tables": ace_info,
     }
+    if rank == 0 and not args.no_extra and args.cells is None:
+        out["workloads"] = run_extras(torch, W, apip, flush)
     if rank == 0 and not args.no_cpu_baseline:
-        cb = oracle_sample(None, 15.0)
-        out["cpu_baseline"] = {"value": cb["value"], "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
-                               "sample": f"{cb['reps']} FP64 numpy energy/force call(s) on the {WORKLOAD} recipe "
-                                         f"at {cb['cells']}^3 cells ({cb['n']} atoms, x = {cb['x']:.3f}), "
-                                         f"{cb['seconds']:.1f} s, single thread"}
+        cb = oracle_sample(12.0)
+        out["cpu_baseline"] = {"value": cb["value"], "unit": "atom-steps/s", "cores": cb["workers"], "kind": "oracle",
+                               "sample": f"{cb['reps']} FP64 numpy energy/force calls on the {WORKLOAD} recipe at "
+                                         f"{cb['cells']}^3 cells ({cb['n']} atoms, x = {cb['x']:.3f}) in "
+                                         f"{cb['workers']} independent processes, one per host core, "
+                                         f"{cb['seconds']:.1f} s; atom-steps/s summed"}
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()

@@ -130,6 +130,14 @@ typedef struct apip_params {
   int32_t max_nb;            /* neighbour capacity per atom (1 .. 1024) */
   int32_t cell_cap;          /* atom capacity per cell (1 .. 1024) */
   int32_t mixing;            /* APIP_MIX_ENERGY or APIP_MIX_FORCE */
+  int32_t pad2;
+  double prec_shift;         /* energy zero of the precise model: E^prec_i is lowered by this
+                                constant (eV per atom).  0 keeps E^prec as defined above.  Set
+                                to the models' difference per atom in the perfect lattice, it
+                                makes E^prec - E^EAM vanish in the bulk, as for two potentials
+                                fitted to the same reference energies (a constant per-atom
+                                shift moves no force of either model, but it enters the
+                                grad-lambda force of Eq. 5 through E^prec - E^EAM) */
 } apip_params;
 
 /* Number of product-basis functions of the canonical ACE basis (the length of
@@ -332,6 +340,16 @@ apip_status apip_mlp_adam(apip_ctx* ctx, float* params, const float* grad, float
 #define APIP_STATIC_MAX_BLOCKS 4096
 #define APIP_STATIC_MAX_ATOMS ((int64_t)APIP_STATIC_ATOMS_PER_BLOCK * APIP_STATIC_MAX_BLOCKS)
 apip_status apip_reduce_energy_static(const double* e_atom, int64_t n, double* e_total, void* stream);
+
+/* Measured multiply-add peaks of the current device, the denominators of the
+ * roofline of the ACE kernels (float32 pipe) and of the float64 path.  The paper
+ * has no counterpart: it is a measurement aid.  A register-resident loop of
+ * independent multiply-adds runs on every SM; the best of three launches, timed
+ * with CUDA events on the stream, is written to the host outputs in TFLOP/s (a
+ * multiply-add counts 2).  Synchronises the stream; changes no clock or power
+ * setting; takes well under a second.  Errors: APIP_ERR_ARG (NULL output),
+ * APIP_ERR_CUDA. */
+apip_status apip_measure_peaks(double* fp32_tflops, double* fp64_tflops, void* stream);
 
 #ifdef __cplusplus
 }

@@ -69,7 +69,8 @@ def energy_forces(pos, box, ids, partners, prm, model=None, lam_mode="paper",
                                              weights=lam[P] if forces else None)
     e_ace[P] = ace_e
     beta = 1.0 if prm.get("precise_adds_eam", False) else 0.0
-    e_prec = e_ace + beta * e_eam
+    # prm["prec_shift"]: the precise model's energy zero, a constant per atom
+    e_prec = e_ace + beta * e_eam - prm.get("prec_shift", 0.0)
     e_atom = lam * e_prec + (1.0 - lam) * e_eam
     out = dict(E=math.fsum(e_atom), e_atom=e_atom, e_ace=e_ace, e_eam=e_eam,
                zeta=zeta, g=g, wbar=wbar, d=d, lam=lam, dlam=dlam, P=P)

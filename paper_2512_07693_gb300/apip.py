@@ -47,6 +47,7 @@ class ApipParams(ctypes.Structure):
         ("sw_d0", _c_double),
         ("csp_rcut", _c_double), ("csp_nnb", _c_int32), ("nb_pad", _c_int32),
         ("skin", _c_double), ("max_nb", _c_int32), ("cell_cap", _c_int32), ("mixing", _c_int32),
+        ("pad2", _c_int32), ("prec_shift", _c_double),
     ]
 
 
@@ -73,6 +74,7 @@ def _load():
         "apip_profile_read": (ctypes.c_int, [_vp, P(_c_double), P(_c_int64)]),
         "apip_ace_info": (ctypes.c_int, [_vp, P(_c_int64)]),
         "apip_reduce_energy_static": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
+        "apip_measure_peaks": (ctypes.c_int, [P(_c_double), P(_c_double), _vp]),
         "apip_set_mlp": (ctypes.c_int, [_vp, _vp, _vp]),
         "apip_set_lam_fixed": (ctypes.c_int, [_vp, _vp, _c_int64]),
         "apip_set_indenter": (ctypes.c_int, [_vp, P(_c_double), P(_c_double), _c_double, _c_double]),
@@ -210,6 +212,13 @@ def apip_reduce_energy_static(e_atom, n, e_total, stream=None):
         raise ApipError(st, why)
 
 
+def apip_measure_peaks(stream=None):
+    """Measured float32 and float64 multiply-add peaks (TFLOP/s) of the current device."""
+    f32, f64 = _c_double(0.0), _c_double(0.0)
+    _check(None, lib.apip_measure_peaks(ctypes.byref(f32), ctypes.byref(f64), _stream(stream)))
+    return f32.value, f64.value
+
+
 def apip_set_mlp(ctx, params, stream=None):
     _check(ctx, lib.apip_set_mlp(ctx, _ptr(params), _stream(stream)))
 
@@ -272,7 +281,7 @@ def mlp_unflat(flat):
 def make_params(prm, precision="fp64", lam_mode="paper", grad_lambda=True, skin=0.5, max_nb=96, cell_cap=64,
                 ace_group=0, mixing="energy"):
     """apip_params from a parameter dict (keys eam, ace, switch, csp,
-    precise_adds_eam).  The returned structure keeps the coefficient arrays
+    precise_adds_eam, optional prec_shift).  The returned structure keeps the coefficient arrays
     alive through its ``_keep`` attribute."""
     e, a, s, c = prm["eam"], prm["ace"], prm["switch"], prm["csp"]
     c1 = np.ascontiguousarray(a["c1"], dtype=np.float64)
@@ -299,6 +308,7 @@ def make_params(prm, precision="fp64", lam_mode="paper", grad_lambda=True, skin=
     p.csp_rcut, p.csp_nnb = c["rcut"], c["nnb"]
     p.skin, p.max_nb, p.cell_cap = skin, max_nb, cell_cap
     p.mixing = MIXING[mixing]
+    p.prec_shift = float(prm.get("prec_shift", 0.0))
     p._keep = (c1, c2)
     return p
 

@@ -182,6 +182,67 @@ __device__ __forceinline__ void group_setup(const Args<T>& a, int grp, int count
   __syncthreads();
 }
 
+// Float32 path: the switch of the group's transition atoms (dlam != 0 after pass
+// 2), recomputed with the pair distances and the sums of Eq. 6 in float64.  Pass 2
+// takes w-bar_i and sum_k g_k w(r_ik) in float32 from float32 distances, good to
+// a few 1e-7 in d_i; through dlam/dd and E^prec - E^EAM (several eV for a
+// pure-ACE precise model) that would be ~1e-5 eV of energy.  Only atoms with
+// 0 < lam < 1 need it (elsewhere lam is 0 or 1 up to terms cubic in the float
+// error), and they are all compacted.  One warp per transition atom, lanes over
+// its neighbour list: r from the exact fixed-point separation in float64, w from
+// the float64 t of Eq. S1 (the quintic itself in float32), float64 sums; then d,
+// lam = 1 - f_trans(d) and dlam in float64.  The results replace the atom's
+// lam, dlam, w-bar and d (read by atom_scalars).  Ends with a barrier.
+template <typename T, int NAT>
+__device__ __forceinline__ void refine_switch(const Args<T>& a, const AceGroup<T, NAT>& g) {
+  if constexpr (sizeof(T) == 4) {
+    if (a.lam_mode == APIP_LAM_PAPER || a.lam_mode == APIP_LAM_LEARNED) {
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      const double u0 = a.geo.L[0] * 0x1p-32, u1 = a.geo.L[1] * 0x1p-32, u2 = a.geo.L[2] * 0x1p-32;
+      const double rw = a.sw.r_w, rw_lo = a.sw.r_w_lo, rw2 = rw * rw, rw_lo2 = rw_lo * rw_lo;
+      for (int k = warp; k < NAT; k += kAceWarps) {
+        const int i = g.atom[k];
+        if (i < 0 || a.dlam[i] == T(0)) continue;   // not transitional (constant-lam atoms: dlam = 0)
+        const uint4 qi = a.pv.q[i];
+        const int cnt = a.nnb[i];
+        double wsum = 0.0, gsum = 0.0;
+        for (int s = lane; s < cnt; s += 32) {
+          const int j = a.nbl[(size_t)s * a.nmax + i];
+          const uint4 qj = a.pv.q[j];
+          const double ex = (double)(int)(qj.x - qi.x) * u0, ey = (double)(int)(qj.y - qi.y) * u1,
+                       ez = (double)(int)(qj.z - qi.z) * u2;
+          const double r2 = ex * ex + ey * ey + ez * ez;
+          if (!(r2 < rw2)) continue;
+          float w = 1.0f;
+          if (r2 > rw_lo2) {
+            const float t = (float)((rw + rw_lo - 2.0 * sqrt(r2)) * a.sw.inv_w);
+            const float p = 1.0f + t;
+            w = 0.0625f * p * p * p * (8.0f + t * (-9.0f + 3.0f * t));
+          }
+          wsum += (double)w;
+          gsum += (double)(a.g[j] * w);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+          gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
+        }
+        if (lane == 0) {
+          const double wb = 1.0 + wsum;                 // the self term, w(0) = 1
+          const double d = (gsum + (double)a.g[i]) / wb - a.sw.d0;
+          double dl;
+          const double lam = ftrans_c(d, a.sw.d_lo, a.sw.d_hi, a.sw.inv_d, &dl);
+          a.lam[i] = (T)lam;
+          a.dlam[i] = (T)dl;
+          a.wbar[i] = (T)wb;
+          a.dd[i] = (T)d;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // Step 1: A[c * NAT + k] += a_scale sum_j R Y (A zeroed by the caller; RY is a
 // staging area of ry_elems<LMAX>() elements).  The pairs are taken 256 at a
 // time; after their R, Y rows are staged, the (atom, component) sums are formed
@@ -256,7 +317,9 @@ __device__ __forceinline__ void atom_scalars(const Args<T>& a, const AceDev<T>& 
   if (i >= 0) {
     lam = a.lam[i];
     const T e_eam = a.e_eam[i];
-    delta = e_ace + (a.precise_adds_eam ? e_eam : T(0)) - e_eam;
+    // E^prec - E^EAM: E^ACE alone when the precise model adds the EAM (no float
+    // cancellation of E^EAM against itself), minus the precise model's energy zero
+    delta = (a.precise_adds_eam ? e_ace : e_ace - e_eam) - a.k.prec_shift;
     const T dl = a.dlam[i];
     trans = (a.grad_lambda && (a.lam_mode == APIP_LAM_PAPER || a.lam_mode == APIP_LAM_LEARNED) && dl != T(0))
                 ? 1 : 0;

@@ -29,6 +29,9 @@ __host__ __device__ inline size_t ace_pool_smem(int npool) {
 template <typename T, typename K, int LMAX, int KA>
 __global__ void __launch_bounds__(kAceThreads) k_ace_pool(Args<T> a, AceDev<T> t) {
   pdl_begin();
+  // every list-build kernel of this call has completed (and read the rebuild
+  // flag): clear it for the next step's drift
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[0] = 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ AceGroup<T, KA> g;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -46,6 +49,7 @@ __global__ void __launch_bounds__(kAceThreads) k_ace_pool(Args<T> a, AceDev<T> t
 
   for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     group_setup<T, KA>(a, grp, count, g);
+    refine_switch<T, KA>(a, g);
     for (int c = tid; c < c0 * KA; c += kAceThreads) X[c] = (c < KA) ? T(1) : T(0);
     __syncthreads();
     densities<T, K, LMAX, KA>(a, t, g, A, G);

@@ -183,6 +183,9 @@ __device__ __forceinline__ void coupling_dispatch(const uint4& cp, const T* Ak, 
 template <typename T, typename K, int LMAX, int NAT>
 __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev<T> t) {
   pdl_begin();
+  // every list-build kernel of this call has completed (and read the rebuild
+  // flag): clear it for the next step's drift
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[0] = 0;
   static_assert(NAT <= 32 && 32 % NAT == 0, "a warp holds whole slices");
   constexpr int NS = kAceThreads / NAT;
   constexpr bool PRIV = stream_private<T, LMAX>();
@@ -217,6 +220,7 @@ __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev
 
   for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     group_setup<T, NAT>(a, grp, count, g);
+    refine_switch<T, NAT>(a, g);
     for (int c = tid; c < nA * NAT; c += kAceThreads) A[c] = T(0);
     __syncthreads();
     densities<T, K, LMAX, NAT>(a, t, g, A, G);

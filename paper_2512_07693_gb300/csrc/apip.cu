@@ -97,6 +97,7 @@ apip_status check_params(const apip_params* p, std::string* why) {
   if (p->mixing != APIP_MIX_ENERGY && p->mixing != APIP_MIX_FORCE) return bad("unknown mixing");
   if (!(p->ace_rc > 0 && p->ace_rc_width > 0 && p->ace_rc_width <= p->ace_rc)) return bad("bad ACE cutoff");
   if (!(p->ace_eps > 0)) return bad("ace_eps must be > 0");
+  if (!std::isfinite(p->prec_shift)) return bad("prec_shift must be finite");
   if (!(p->eam_rc > 0 && p->eam_rc_width > 0 && p->eam_rc_width <= p->eam_rc)) return bad("bad EAM cutoff");
   if (!(p->sw_r_w > 0 && p->sw_r_w_width > 0 && p->sw_r_w_width <= p->sw_r_w)) return bad("bad switch cutoff");
   if (!(p->sw_d_hi > p->sw_d_lo)) return bad("sw_d_hi must exceed sw_d_lo");
@@ -201,9 +202,9 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.lam_fixed = c->lam_fixed;
   a.ind_on = c->ind_on ? 1 : 0;
   a.ind_acc = c->ind_acc;
-  a.ind_R = T(c->ind_R);
   a.ind_R2 = T(c->ind_R * c->ind_R);
-  a.ind_K = T(c->ind_K);
+  a.ind_Rd = c->ind_R;
+  a.ind_Kd = c->ind_K;
   for (int k = 0; k < 3; ++k) a.ind_v[k] = c->ind_v[k];
   set_ind_center(a, c->geo, c->ind_c);
   a.geo = c->geo;
@@ -214,9 +215,11 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.k = {T(p.eam_A), T(p.eam_beta), T(p.eam_re), T(p.eam_D), T(p.eam_alpha), T(p.eam_r0), T(p.eam_rc),
          T(p.eam_rc * p.eam_rc), T(p.eam_rc - p.eam_rc_width), T(1.0 / p.eam_rc_width),
          T(p.sw_r_w), T(p.sw_r_w * p.sw_r_w), T(p.sw_r_w - p.sw_r_w_width), T(1.0 / p.sw_r_w_width),
-         T(p.sw_d_lo), T(p.sw_d_hi), T(1.0 / (p.sw_d_hi - p.sw_d_lo)), T(p.sw_d0)};
+         T(p.sw_d_lo), T(p.sw_d_hi), T(1.0 / (p.sw_d_hi - p.sw_d_lo)), T(p.sw_d0), T(p.prec_shift)};
   a.r_list2 = c->r_list * c->r_list;
   a.skin_half2 = 0.25 * p.skin * p.skin;
+  a.skin_half2_f = (float)a.skin_half2;
+  if ((double)a.skin_half2_f > a.skin_half2) a.skin_half2_f = std::nextafter(a.skin_half2_f, 0.0f);
   // a pair now within eam_rc was within eam_rc + skin at the last build (each atom
   // moved less than skin / 2); the margin covers the rounding of the trigger
   a.r_e_in2 = p.eam_rc * p.eam_rc;
@@ -232,7 +235,8 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.zeta = as<T>(c->zeta); a.xi_p = as<T>(c->xi_p); a.e_eam = as<T>(c->e_eam); a.g = as<T>(c->g);
   a.wbar = as<T>(c->wbar); a.dd = as<T>(c->dd); a.lam = as<T>(c->lam); a.dlam = as<T>(c->dlam);
   a.e_ace = as<T>(c->e_ace);
-  a.cvec = c->cvec; a.ace_list = c->ace_list; a.clist = c->clist; a.counts = c->counts; a.flags = c->flags; a.status = c->status;
+  a.cvec = c->cvec; a.ace_list = c->ace_list; a.clist = c->clist; a.counts = c->counts;
+  a.flags = c->flags; a.status = c->status;
   a.partials = c->partials;
   // one energy partial per pass-1 block, ahead of the ACE blocks' partials
   if (p.lam_mode != APIP_LAM_LEARNED) a.n_part_p1 = nblk(n);
@@ -360,9 +364,11 @@ apip_status energy_forces_t(apip_ctx* c, const double* pos, const int32_t* id, i
   mark_atom_count(c, n, s);
   { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_prep<T>(a, s); }
   force_pipeline<T>(c, a, s);
-  Phase ph(c, APIP_PHASE_REDUCE, 1, s);
-  launch_final(c->partials, a.n_part_p1 + c->ace_blocks, e_total, nullptr, nullptr, 0, nullptr,
-               c->flags, c->counts, nullptr, s);
+  if (e_total) {
+    Phase ph(c, APIP_PHASE_REDUCE, 1, s);
+    launch_final(c->partials, a.n_part_p1 + c->ace_blocks, e_total, nullptr, nullptr, 0, nullptr,
+                 c->flags, c->counts, nullptr, s);
+  }
   if (a.ind_on) launch_ind_work(c->ind_acc, 0.0, s);
   return launch_status(c);
 }
@@ -404,20 +410,24 @@ apip_status verlet_t(apip_ctx* c, double* pos, double* vel, double* force, const
   mark_atom_count(c, n, s);
   const int ntb = nblk(n);
   const int n_part = a.n_part_p1 + c->ace_blocks;
+  // without thermo output the step needs no reduction at all: the energy partials
+  // are left unread and the ACE kernel clears the rebuild flag
+  double* tp = thermo ? c->thermo_part : nullptr;
   for (int k = 0; k < steps; ++k) {
-    { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, k == 0 ? 0 : 1, pos, vel, force, inv_mass, dt, c->thermo_part, s); }
+    { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, k == 0 ? 0 : 1, pos, vel, force, inv_mass, dt, k > 0 ? tp : nullptr, s); }
     if (a.ind_on) {   // the indenter centre moves with the drift
       for (int q = 0; q < 3; ++q) c->ind_c[q] += dt * c->ind_v[q];
       set_ind_center(a, c->geo, c->ind_c);
     }
     force_pipeline<T>(c, a, s);
     if (a.ind_on) launch_ind_work(c->ind_acc, dt, s);
-    Phase ph(c, APIP_PHASE_REDUCE, 1, s);
-    launch_final(c->partials, n_part, nullptr, thermo ? thermo + 5 * k : nullptr,
-                 (thermo && k > 0) ? c->thermo_part : nullptr, ntb, thermo ? thermo + 5 * (k - 1) : nullptr,
-                 c->flags, c->counts, nullptr, s);
+    if (thermo) {
+      Phase ph(c, APIP_PHASE_REDUCE, 1, s);
+      launch_final(c->partials, n_part, nullptr, thermo + 5 * k, k > 0 ? tp : nullptr, ntb,
+                   k > 0 ? thermo + 5 * (k - 1) : nullptr, c->flags, c->counts, nullptr, s);
+    }
   }
-  { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, 2, pos, vel, force, inv_mass, dt, c->thermo_part, s); }
+  { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, 2, pos, vel, force, inv_mass, dt, tp, s); }
   if (thermo) {
     Phase ph(c, APIP_PHASE_REDUCE, 1, s);
     launch_thermo_final(c->thermo_part, ntb, thermo + 5 * (steps - 1), s);

@@ -81,6 +81,13 @@ template <> struct Acc<double> {
   __device__ __forceinline__ double value() const { return s; }
 };
 
+// Plain running sum (the same interface as Acc).
+template <typename T> struct Plain {
+  T s = T(0);
+  __device__ __forceinline__ void add(T v) { s += v; }
+  __device__ __forceinline__ T value() const { return s; }
+};
+
 // r = |d| and 1/r from r^2: in float32 through the reciprocal square root
 // (rsqrtf, within 2 ulp), in float64 by the correctly rounded square root and a
 // division.

@@ -15,6 +15,7 @@ template <typename T>
 struct PassK {
   T eam_A, eam_beta, eam_re, eam_D, eam_alpha, eam_r0, eam_rc, eam_rc2, eam_rc_lo, eam_inv_w;
   T sw_r_w, sw_r_w2, sw_r_w_lo, sw_inv_w, sw_d_lo, sw_d_hi, sw_inv_d, sw_d0;
+  T prec_shift;   // energy zero of the precise model (subtracted from E^prec per atom)
 };
 
 // Everything a kernel of the force pipeline may need, passed by value.
@@ -29,7 +30,8 @@ struct Args {
   int ind_on;
   double ind_c[3];        // centre (FP64 path)
   uint4 ind_q;            // centre as fixed-point coordinates (FP32 path)
-  T ind_R, ind_R2, ind_K;
+  T ind_R2;               // R^2 in the path precision (the float32 path's contact test)
+  double ind_Rd, ind_Kd;  // radius and stiffness
   double ind_v[3];        // centre velocity
   double* ind_acc;        // [3] device: work W, (sum F).v of the previous and of this evaluation
   PosView<T> pv;
@@ -38,6 +40,7 @@ struct Args {
   SwP sw;
   PassK<T> k;
   double r_list2, skin_half2, csp_rcut2;
+  float skin_half2_f;     // skin_half2 rounded down to float (the FP32 path's rebuild trigger)
   double r_e_in2, r_e_mid2;   // list-order bounds: eam_rc^2, (eam_rc + skin + margin)^2
 
   const double* pos;      // caller positions [n][3]
@@ -90,38 +93,46 @@ __device__ __forceinline__ void eam_terms(const PassK<T>& k, T r, T* rho, T* phi
   *phi = k.eam_D * (x * x - T(2) * x) * fc;
 }
 
-// Vector from the indenter centre to atom i (minimum image) and its square.
+// The spherical indenter's term for atom i: for r = |x_i - c| < R, the energy
+// K/3 (R - r)^3 and the force K (R - r)^2 (x_i - c)/r; returns false (and leaves
+// the outputs) outside the sphere.  In float64 in both paths: the gap R - r is a
+// small difference of numbers near R (40 A), which float32 would carry to ~1e-5 A.
+// The float32 path tests the sphere on float distances first, so that only the
+// few atoms in contact reach the float64 arithmetic; it takes the separation from
+// the exact fixed-point difference.
 template <typename T>
-__device__ __forceinline__ V3<T> ind_vec(const Args<T>& a, int i, T* r2);
-template <>
-__device__ __forceinline__ V3<float> ind_vec<float>(const Args<float>& a, int i, float* r2) {
-  const uint4 q = a.posq[i];
-  const V3<float> d{(float)(int)(q.x - a.ind_q.x) * a.pv.unit[0], (float)(int)(q.y - a.ind_q.y) * a.pv.unit[1],
-                    (float)(int)(q.z - a.ind_q.z) * a.pv.unit[2]};
-  *r2 = dot3(d, d);
-  return d;
-}
-template <>
-__device__ __forceinline__ V3<double> ind_vec<double>(const Args<double>& a, int i, double* r2) {
+__device__ __forceinline__ bool ind_term(const Args<T>& a, int i, double* e, double f[3]) {
   double d[3];
+  if constexpr (sizeof(T) == 4) {
+    const uint4 q = a.posq[i];
+    const int di[3] = {(int)(q.x - a.ind_q.x), (int)(q.y - a.ind_q.y), (int)(q.z - a.ind_q.z)};
+    const float fx = (float)di[0] * a.pv.unit[0], fy = (float)di[1] * a.pv.unit[1], fz = (float)di[2] * a.pv.unit[2];
+    if (!(fx * fx + fy * fy + fz * fz < a.ind_R2 * 1.0001f)) return false;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    d[k] = a.pos[3 * i + k] - a.ind_c[k];
-    d[k] -= a.geo.L[k] * rint(d[k] * a.geo.invL[k]);
+    for (int k = 0; k < 3; ++k) d[k] = (double)di[k] * (a.geo.L[k] * 0x1p-32);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      d[k] = a.pos[3 * i + k] - a.ind_c[k];
+      d[k] -= a.geo.L[k] * rint(d[k] * a.geo.invL[k]);
+    }
   }
-  *r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-  return {d[0], d[1], d[2]};
+  const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  if (!(r2 < a.ind_Rd * a.ind_Rd) || !(r2 > 0.0)) return false;
+  const double r = sqrt(r2), gap = a.ind_Rd - r;
+  *e = a.ind_Kd / 3.0 * gap * gap * gap;
+  const double sc = a.ind_Kd * gap * gap / r;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) f[k] = sc * d[k];
+  return true;
 }
 
 // Indenter energy K/3 (R - r)^3 of atom i (zero outside the sphere or without one).
 template <typename T>
-__device__ __forceinline__ T ind_energy(const Args<T>& a, int i) {
-  if (!a.ind_on) return T(0);
-  T r2;
-  ind_vec(a, i, &r2);
-  if (!(r2 < a.ind_R2)) return T(0);
-  const T gap = a.ind_R - sqrt(r2);
-  return a.ind_K / T(3) * gap * gap * gap;
+__device__ __forceinline__ double ind_energy(const Args<T>& a, int i) {
+  if (!a.ind_on) return 0.0;
+  double e, f[3];
+  return ind_term(a, i, &e, f) ? e : 0.0;
 }
 
 // Launch with programmatic stream serialization (the kernel must start with

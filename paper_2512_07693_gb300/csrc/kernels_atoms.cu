@@ -61,7 +61,7 @@ __device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, dou
     const uint4 r = a.posq_ref[i];
     const float ex = (float)(int)(q[0] - r.x) * a.geo.unit[0], ey = (float)(int)(q[1] - r.y) * a.geo.unit[1],
                 ez = (float)(int)(q[2] - r.z) * a.geo.unit[2];
-    if (ex * ex + ey * ey + ez * ez > (float)a.skin_half2) atomicOr(&a.flags[0], 1);
+    if (ex * ex + ey * ey + ez * ez > a.skin_half2_f) atomicOr(&a.flags[0], 1);
     return;
   }
   double dx = x - a.pos_ref[3 * i], dy = y - a.pos_ref[3 * i + 1], dz = z - a.pos_ref[3 * i + 2];
@@ -331,9 +331,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_pass1(Args<T
     a.zeta[i] = z;
     a.xi_p[i] = z > T(0) ? T(-0.5) / sz : T(0);
     a.e_eam[i] = e;
-    const T e_ind = ind_energy(a, i);   // the external indenter, if any
-    if (a.e_atom) a.e_atom[i] = (double)e + (double)e_ind;
-    e_out = e + e_ind;
+    const double e_ind = ind_energy(a, i);   // the external indenter, if any
+    if (a.e_atom) a.e_atom[i] = (double)e + e_ind;
+    e_out = e + (T)e_ind;
     T g = T(0);
     if (a.lam_mode == APIP_LAM_PAPER) {
       // the partner ids and their indices are gathered in two rounds of
@@ -398,10 +398,11 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
     const T A = a.k.eam_A, beta = a.k.eam_beta, re = a.k.eam_re, D = a.k.eam_D, alpha = a.k.eam_alpha,
             r0 = a.k.eam_r0;
     const T xi_i = a.xi_p[i];
-    // compensated sums: the force components' rounding decides how well the float32
-    // path conserves the total momentum; that of w-bar and sum g w moves d, and through
-    // dlam/dd times (E^prec - E^EAM) the energy
-    Acc<T> wbar, S;
+    // the force components keep compensated sums (their rounding decides how well
+    // the float32 path conserves the total momentum); w-bar and sum g w are plain:
+    // they decide the compaction here, and the ACE kernel recomputes them in float64
+    // for the transition atoms, where their rounding would reach the energy
+    Plain<T> wbar, S;
     Acc<T> fx, fy, fz;
     wbar.add(T(1));
     if (paper) S.add(a.g[i]);
@@ -473,23 +474,17 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
       // force mixing (Eq. 3): this atom's EAM force enters with (1 - lam_i) from the
       // fast model plus, when the precise model contains the EAM, lam_i from it
       const T wf = a.force_mix ? T(1) - lam + (a.precise_adds_eam ? lam : T(0)) : T(1);
-      T gx = wf * fx.value(), gy = wf * fy.value(), gz = wf * fz.value();
-      if (a.ind_on) {   // indenter: K (R - r)^2 (x_i - c) / r
-        T r2;
-        const V3<T> d = ind_vec(a, i, &r2);
-        if (r2 < a.ind_R2 && r2 > T(0)) {
-          const T r = sqrt(r2), gap = a.ind_R - r;
-          const T sc = a.ind_K * gap * gap / r;
-          gx += sc * d.x;
-          gy += sc * d.y;
-          gz += sc * d.z;
-          ind_fv = (double)(sc * d.x) * a.ind_v[0] + (double)(sc * d.y) * a.ind_v[1] +
-                   (double)(sc * d.z) * a.ind_v[2];
-        }
+      double gx = (double)(wf * fx.value()), gy = (double)(wf * fy.value()), gz = (double)(wf * fz.value());
+      double fi[3], ei;
+      if (a.ind_on && ind_term(a, i, &ei, fi)) {   // indenter: K (R - r)^2 (x_i - c) / r
+        gx += fi[0];
+        gy += fi[1];
+        gz += fi[2];
+        ind_fv = fi[0] * a.ind_v[0] + fi[1] * a.ind_v[1] + fi[2] * a.ind_v[2];
       }
-      a.force[3 * i] = (double)gx;
-      a.force[3 * i + 1] = (double)gy;
-      a.force[3 * i + 2] = (double)gz;
+      a.force[3 * i] = gx;
+      a.force[3 * i + 1] = gy;
+      a.force[3 * i + 2] = gz;
     }
   }
   if (a.ind_on && __syncthreads_or(ind_fv != 0.0)) {
@@ -517,7 +512,10 @@ __global__ void k_ind_work(double* acc, double dt) {
 
 // -------------------------------------------- grad-lambda force, CSP part
 // F -= grad sum_j c_j g_j (Eq. S25-S27) for the atoms with c_j != 0, where
-// c_j = sum_k Et_k w(r_kj) was accumulated by the ACE kernel; resets c_j.
+// c_j = sum_k Et_k w(r_kj) was accumulated by the ACE kernel; resets c_j.  One
+// thread per atom in index order: the few atoms with c_j != 0 lie near the
+// transition region, and neighbouring threads then gather and scatter near one
+// another (a list of them in the ACE kernel's first-touch order measured slower).
 template <typename T>
 __global__ void k_csp_force(Args<T> a) {
   pdl_begin();
@@ -601,6 +599,9 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* 
   __shared__ double sh4[4 * 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && mode != 2) a.counts[0] = a.counts[1] = 0;
+  // the kinetic energy and momentum partials of the step that the first kick ends,
+  // only when the caller asked for thermo output (float64 work, slow on this GPU)
+  const bool thermo = mode != 0 && thermo_part != nullptr;
   double ke = 0.0, p[3] = {0.0, 0.0, 0.0};   // ke: 2 E_kin of the atom (v . p; halved after the sums)
   if (i < a.n) {
     const double im = inv_mass[i];
@@ -608,7 +609,7 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* 
     double v[3], x[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) v[q] = vel[3 * i + q] + h * force[3 * i + q];
-    if (mode != 0) {
+    if (thermo) {
       // mass = 1/inv_mass: exact in the float64 path; a float reciprocal (relative
       // error ~1e-7 on each atom's E_kin and momentum) in the float32 path, where
       // a float64 division per atom would cost more than the rest of the kernel
@@ -632,7 +633,7 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* 
       prep_atom(a, i, x[0], x[1], x[2], true);
     }
   }
-  if (mode != 0) {
+  if (thermo) {
     const double vals[4] = {ke, p[0], p[1], p[2]};
     double tot[4];
     block_sum4(vals, sh4, tot);

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kLearnedBlock) k_pass1_learned(Args<T> a) {
     a.zeta[i] = zz;
     a.xi_p[i] = zz > T(0) ? T(-0.5) / sz : T(0);
     a.e_eam[i] = e;
-    const T e_ind = ind_energy(a, i);   // the external indenter, if any
+    const double e_ind = ind_energy(a, i);   // the external indenter, if any
     if (a.e_atom) a.e_atom[i] = (double)e + (double)e_ind;
     e_out = (double)e + (double)e_ind;
     const T g = mlp_forward<T>(w, G, nullptr);
@@ -217,6 +217,29 @@ __global__ void __launch_bounds__(kLearnedBlock) k_pass1_learned(Args<T> a) {
 // the low 16 bits of a pair.  The C fragments of n-tiles 2kb and 2kb+1 of one
 // layer are the A fragment of k-block kb of the next: activations stay in
 // registers from layer to layer.
+
+// Compensated float32 dot product (the Dot2 scheme of Ogita, Rump and Oishi): s
+// is the running sum, c the sum of the exact rounding errors of every product
+// (from an FMA) and every addition (TwoSum); the value s + c is as accurate as a
+// twice-as-wide accumulation.
+struct Dot2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = s + v, bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
+  }
+  __device__ __forceinline__ void fma(float a, float b) {
+    const float p = a * b;
+    c += fmaf(a, b, -p);
+    add(p);
+  }
+  __device__ __forceinline__ void merge(float s2, float c2) {
+    add(s2);
+    c += c2;
+  }
+  __device__ __forceinline__ float value() const { return s + c; }
+};
 
 // uint2 offsets of the layers within a split: layer 1 (2 k-blocks), 2 and 3 (4 each)
 constexpr int kTcOff1 = 0, kTcOff2 = 2 * 8 * 32, kTcOff3 = kTcOff2 + 4 * 8 * 32;
@@ -401,7 +424,7 @@ __global__ void __launch_bounds__(kTcWarps * 32) k_pass1_learned_tc(Args<float> 
       a.zeta[i] = zz;
       a.xi_p[i] = zz > 0.f ? -0.5f / sz : 0.f;
       a.e_eam[i] = e;
-      const float e_ind = ind_energy(a, i);   // the external indenter, if any
+      const double e_ind = ind_energy(a, i);   // the external indenter, if any
       if (a.e_atom) a.e_atom[i] = (double)e + (double)e_ind;
       e_out += (double)e + (double)e_ind;
     }
@@ -430,23 +453,29 @@ __global__ void __launch_bounds__(kTcWarps * 32) k_pass1_learned_tc(Args<float> 
       tc_hidden(h1, h2, sf, kTcOff2, lane);
       tc_bias_silu(h2, sb + kW, tq);
       tc_hidden(h2, h1, sf, kTcOff3, lane);
-      // output: g = b4 + sum_j w4_j SiLU(z3_j + b3_j), rows r0 (q = 0, 1) and r1 (q = 2, 3)
-      float p0 = 0.f, p1 = 0.f;
+      // output: g = b4 + sum_j w4_j SiLU(z3_j + b3_j), rows r0 (q = 0, 1) and r1 (q = 2, 3),
+      // a compensated dot product: each product split exactly (FMA) and each sum
+      // with its rounding error (TwoSum) carried in a second float, so that the
+      // cancelling terms of the output layer add no rounding of their own
+      Dot2 d0, d1;
 #pragma unroll
       for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int col = 8 * nt + 2 * tq + (q & 1);
-          const float v = sb[3 * kW + col] * silu(h1[nt][q] + sb[2 * kW + col]);
-          if (q < 2) p0 += v; else p1 += v;
+          const float w = sb[3 * kW + col], h = silu(h1[nt][q] + sb[2 * kW + col]);
+          if (q < 2) d0.fma(w, h); else d1.fma(w, h);
         }
-      p0 += __shfl_xor_sync(0xffffffffu, p0, 1);
-      p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
-      p0 += __shfl_xor_sync(0xffffffffu, p0, 2);
-      p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
+#pragma unroll
+      for (int o = 1; o <= 2; o <<= 1) {
+        d0.merge(__shfl_xor_sync(0xffffffffu, d0.s, o), __shfl_xor_sync(0xffffffffu, d0.c, o));
+        d1.merge(__shfl_xor_sync(0xffffffffu, d1.s, o), __shfl_xor_sync(0xffffffffu, d1.c, o));
+      }
       if (tq == 0) {
-        gs[r0] = sb[4 * kW] + p0;
-        gs[r1] = sb[4 * kW] + p1;
+        d0.merge(sb[4 * kW], 0.f);
+        d1.merge(sb[4 * kW], 0.f);
+        gs[r0] = d0.value();
+        gs[r1] = d1.value();
       }
     }
     __syncwarp();

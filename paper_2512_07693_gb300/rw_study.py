@@ -6,9 +6,15 @@ descriptor marks as defective (g_i > 1.5 A^2, the paper's selector threshold;
 here the void's surface atoms).
 
 The force error is split as in Fig. 3: the fast-model part (the AP force
-without its grad-lambda term against the precise force) and the full AP force
-(with it).  Energies are compared with the constant bulk offset between the two
-models removed.  Float64 path, one configuration.
+without its grad-lambda term against the precise force), the grad-lambda part
+(the AP force minus the force without it) and the full AP force.  The synthetic
+precise model (EAM + random ACE) differs from the EAM by a constant dE^(0) per
+atom even in the perfect crystal, where the paper's two fitted potentials agree;
+through (E^prec - E^EAM) grad lam that offset alone makes a grad-lambda force.
+Each radius is therefore evaluated twice: as defined (prec_shift = 0) and with
+the precise model's energy zero aligned to the EAM's (prec_shift = dE^(0)),
+which moves no force of either model.  Energies are compared with the constant
+offset removed.  Float64 path, one configuration.
 
 Usage: python -m paper_2512_07693_gb300.rw_study [--cells 24] [--rw 4 5 6 7 8]
 """
@@ -55,20 +61,26 @@ def study(torch, cells, radii):
     rows = []
     de0 = bulk_offset(torch, base)
     for rw in radii:
-        prm = dict(base, switch=dict(base["switch"], r_w=float(rw)))
         # list capacity for the sphere of radius r_w + skin (bcc: 2 atoms per a^3) with margin
         r_list = max(rw, base["ace"]["rc"], base["eam"]["rc"]) + 0.5
         max_nb = min(256, int(1.3 * 4.18879 * r_list ** 3 * 2 / W.LATTICE_A ** 3) + 16)
-        ref = _eval(torch, s, prm, "const1", True, max_nb)
-        ap = _eval(torch, s, prm, "paper", True, max_nb)
-        nog = _eval(torch, s, prm, "paper", False, max_nb)
-        sel = np.flatnonzero(ap["g"] > 1.5)
-        err_e = ap["e"] - ref["e"] + (1.0 - ap["lam"]) * de0
-        rms = lambda f: float(np.sqrt(np.mean((f[sel] - ref["F"][sel]) ** 2)))
-        rows.append(dict(r_w=rw, atoms_selected=int(len(sel)), x=float((ap["lam"] > 0).mean()),
-                         rmse_e_ev=float(np.sqrt(np.mean(err_e[sel] ** 2))),
-                         rmse_f_ev_per_a=rms(ap["F"]), rmse_f_without_grad_lambda_ev_per_a=rms(nog["F"]),
-                         rmse_f_all_atoms_ev_per_a=float(np.sqrt(np.mean((ap["F"] - ref["F"]) ** 2)))))
+        row = dict(r_w=rw)
+        for tag, shift in (("", 0.0), ("aligned_", de0)):
+            prm = dict(base, switch=dict(base["switch"], r_w=float(rw)), prec_shift=shift)
+            ref = _eval(torch, s, prm, "const1", True, max_nb)
+            ap = _eval(torch, s, prm, "paper", True, max_nb)
+            nog = _eval(torch, s, prm, "paper", False, max_nb)
+            sel = np.flatnonzero(ap["g"] > 1.5)
+            # -(1 - lam_i)(dE_i - dE^(0)): the constant offset removed (already so when aligned)
+            err_e = ap["e"] - ref["e"] + (1.0 - ap["lam"]) * (de0 - shift)
+            rms = lambda f: float(np.sqrt(np.mean(f[sel] ** 2)))
+            row.update({"atoms_selected": int(len(sel)), "x": float((ap["lam"] > 0).mean()),
+                        tag + "rmse_e_ev": rms(err_e[:, None]),
+                        tag + "rmse_f_ev_per_a": rms(ap["F"] - ref["F"]),
+                        tag + "rmse_f_fast_model_part_ev_per_a": rms(nog["F"] - ref["F"]),
+                        tag + "rmse_f_grad_lambda_part_ev_per_a": rms(ap["F"] - nog["F"]),
+                        tag + "rmse_f_all_atoms_ev_per_a": float(np.sqrt(np.mean((ap["F"] - ref["F"]) ** 2)))})
+        rows.append(row)
     return dict(workload=f"void recipe at {cells}^3 cells ({len(s['pos'])} atoms)", bulk_offset_ev=de0, rows=rows)
 
 

@@ -57,18 +57,14 @@ def test_learned_switch_parity(prec, tolF, tolE):
         np.testing.assert_allclose(g["lam"], o["lam"], atol=1e-12)
         np.testing.assert_allclose(g["e_atom"], o["e_atom"], atol=tolE)
     else:
-        # float32 g carries ~1e-6 relative rounding from the 10 k multiply-adds of the
-        # network; through the switch it moves lam by |dlam/dd| * dg, and the energy
-        # by that times |E^prec - E^EAM|: the per-atom bar is 1e-5 eV plus that budget
-        dg = 1e-6 * np.abs(o["g"]).max()
-        np.testing.assert_allclose(g["g"], o["g"], atol=10 * dg)
-        budget = tolE + dg * np.abs(o["dlam"] * (o["e_ace"] - o["e_eam"]))
-        assert np.all(np.abs(g["e_atom"] - o["e_atom"]) <= budget)
+        # float32 g: ~1e-6 of its range from the network's multiply-adds
+        np.testing.assert_allclose(g["g"], o["g"], atol=1e-5 * np.abs(o["g"]).max())
+        np.testing.assert_allclose(g["e_atom"], o["e_atom"], atol=tolE, rtol=0)
     # the total is the sum of every atom's energy: one partial per block of the
     # learned pass 1 (its blocks are smaller than the other passes')
     n = len(s["pos"])
     assert abs(g["E"] - g["e_atom"].sum()) <= (1e-9 if prec == "fp64" else 1e-6) * n
-    assert abs(g["E"] - o["E"]) <= (1e-9 * n if prec == "fp64" else float(np.sum(budget)))
+    assert abs(g["E"] - o["E"]) <= tolE * n
 
 
 def _ap_energy_error(s, prm, lam_mode, params=None):

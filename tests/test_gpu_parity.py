@@ -130,6 +130,14 @@ def test_pure_ace_precise_model_nu4_fp32():
     compare(g, o, "fp32")
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_shifted_energy_zero_parity(prec):
+    """The precise model's energy lowered by a constant per atom (prec_shift)."""
+    s = small()
+    s["prm"]["prec_shift"] = 0.7
+    _check(s, prec)
+
+
 @pytest.mark.parametrize("mode", ["const0", "const1"])
 def test_constant_switch_modes(mode):
     s = small(cells=(6, 6, 6), adds_eam=False)

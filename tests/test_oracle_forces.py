@@ -84,6 +84,24 @@ def test_pure_ace_precise_model_force_is_minus_gradient():
     np.testing.assert_allclose(res["F"][atoms], fd, atol=2e-6, rtol=1e-6)
 
 
+def test_shifted_energy_zero_force_is_minus_gradient(sysA):
+    """With the precise model's energy lowered by a constant per atom, E changes by
+    -shift sum_i lam_i (Eq. 4) and the force by the matching grad-lambda term: it is
+    still -grad E, and it differs from the unshifted force exactly by
+    shift * sum_i grad lam_i, which no model force carries."""
+    s, prm, part, model, res = sysA
+    shift = 0.7
+    sprm = dict(prm, prec_shift=shift)
+    r2 = apip.energy_forces(s["pos"], s["box"], s["ids"], part, sprm, model=model)
+    assert r2["E"] == pytest.approx(res["E"] - shift * math.fsum(res["lam"]), abs=1e-9)
+    np.testing.assert_allclose(r2["lam"], res["lam"], atol=0)
+    atoms = _pick(r2)
+    fd = _fd(s, sprm, part, model, atoms)
+    np.testing.assert_allclose(r2["F"][atoms], fd, atol=2e-6, rtol=1e-6)
+    assert np.abs(r2["F"] - res["F"]).max() > 1e-3
+    np.testing.assert_allclose(r2["F"].sum(axis=0), 0.0, atol=1e-9)
+
+
 def test_nu4_force_is_minus_gradient():
     s, prm, part = small_system(nu=4, cells=5)
     model = ace.AceModel(prm["ace"])
