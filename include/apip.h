@@ -259,7 +259,7 @@ apip_status apip_get_field(apip_ctx* ctx, int32_t field, void* dst, int64_t n, v
  * writes the accumulated device milliseconds and launch counts per phase since
  * the last read into the host arrays ms[APIP_PHASE_COUNT] and
  * launches[APIP_PHASE_COUNT], and resets them.  Phases: PREP (position
- * preparation or Verlet kernels), NEIGHBOR (the four conditional neighbour-list
+ * preparation or Verlet kernels), NEIGHBOR (the two conditional neighbour-list
  * kernels), PASS1, PASS2, ACE, CSP (CSP part of grad-lambda), REDUCE. */
 enum {
   APIP_PHASE_PREP = 0, APIP_PHASE_NEIGHBOR = 1, APIP_PHASE_PASS1 = 2, APIP_PHASE_PASS2 = 3,

@@ -182,54 +182,100 @@ __device__ __forceinline__ void group_setup(const Args<T>& a, int grp, int count
   __syncthreads();
 }
 
+// Float-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2): the
+// error-free sum (Knuth's TwoSum) and product (an FMA gives the rounding error of
+// a product exactly), written with the _rn intrinsics, which the compiler never
+// contracts or reorders.
+struct FF { float hi, lo; };
+__device__ __forceinline__ FF ff_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bp = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp))};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const FF s = ff_sum(a.hi, b.hi);
+  return ff_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ FF ff_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+// The separation of two fixed-point coordinates in float-float: the exact
+// integer difference d (split as d_h + d_l, d_h = d with its low 8 bits cleared,
+// both exact in float) times the grid unit u = u_hi + u_lo.
+__device__ __forceinline__ FF ff_coord(int d, float u_hi, float u_lo) {
+  const int dh = d & ~0xff;
+  const float h = (float)dh, l = (float)(d - dh);
+  const FF p = ff_prod(h, u_hi);
+  const float small = __fmaf_rn(h, u_lo, __fmaf_rn(l, u_hi, __fmul_rn(l, u_lo)));
+  return ff_sum(p.hi, __fadd_rn(p.lo, small));
+}
+
 // Float32 path: the switch of the group's transition atoms (dlam != 0 after pass
-// 2), recomputed with the pair distances and the sums of Eq. 6 in float64.  Pass 2
-// takes w-bar_i and sum_k g_k w(r_ik) in float32 from float32 distances, good to
-// a few 1e-7 in d_i; through dlam/dd and E^prec - E^EAM (several eV for a
-// pure-ACE precise model) that would be ~1e-5 eV of energy.  Only atoms with
-// 0 < lam < 1 need it (elsewhere lam is 0 or 1 up to terms cubic in the float
-// error), and they are all compacted.  One warp per transition atom, lanes over
-// its neighbour list: r from the exact fixed-point separation in float64, w from
-// the float64 t of Eq. S1 (the quintic itself in float32), float64 sums; then d,
-// lam = 1 - f_trans(d) and dlam in float64.  The results replace the atom's
-// lam, dlam, w-bar and d (read by atom_scalars).  Ends with a barrier.
+// 2), recomputed with accurate pair distances and sums of Eq. 6.  Pass 2 takes
+// w-bar_i and sum_k g_k w(r_ik) in float32 from float32 distances, whose
+// reciprocal square root is biased at ~1e-7; through dlam/dd and E^prec - E^EAM
+// (several eV for a pure-ACE precise model) that would be ~1e-5 eV of energy.
+// Only atoms with 0 < lam < 1 need it (elsewhere lam is 0 or 1 up to terms cubic
+// in the float error), and they are all compacted.  One warp per transition atom,
+// lanes over its neighbour list: r in float-float from the exact fixed-point
+// separation (error-free squares and sums, a correctly rounded square root and one
+// correction), the t of Eq. S1 in float-float, the quintic in float32, the sums in
+// float-float; then d, lam = 1 - f_trans(d) and dlam in float64 (a few operations
+// per atom).  The results replace the atom's lam, dlam, w-bar and d (read by
+// atom_scalars).  Ends with a barrier.
 template <typename T, int NAT>
 __device__ __forceinline__ void refine_switch(const Args<T>& a, const AceGroup<T, NAT>& g) {
   if constexpr (sizeof(T) == 4) {
     if (a.lam_mode == APIP_LAM_PAPER || a.lam_mode == APIP_LAM_LEARNED) {
       const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      const double u0 = a.geo.L[0] * 0x1p-32, u1 = a.geo.L[1] * 0x1p-32, u2 = a.geo.L[2] * 0x1p-32;
-      const double rw = a.sw.r_w, rw_lo = a.sw.r_w_lo, rw2 = rw * rw, rw_lo2 = rw_lo * rw_lo;
+      const SwFF& sw = a.swff;
       for (int k = warp; k < NAT; k += kAceWarps) {
         const int i = g.atom[k];
         if (i < 0 || a.dlam[i] == T(0)) continue;   // not transitional (constant-lam atoms: dlam = 0)
         const uint4 qi = a.pv.q[i];
         const int cnt = a.nnb[i];
-        double wsum = 0.0, gsum = 0.0;
+        FF wsum{0.f, 0.f}, gsum{0.f, 0.f};
         for (int s = lane; s < cnt; s += 32) {
           const int j = a.nbl[(size_t)s * a.nmax + i];
           const uint4 qj = a.pv.q[j];
-          const double ex = (double)(int)(qj.x - qi.x) * u0, ey = (double)(int)(qj.y - qi.y) * u1,
-                       ez = (double)(int)(qj.z - qi.z) * u2;
-          const double r2 = ex * ex + ey * ey + ez * ez;
-          if (!(r2 < rw2)) continue;
-          float w = 1.0f;
-          if (r2 > rw_lo2) {
-            const float t = (float)((rw + rw_lo - 2.0 * sqrt(r2)) * a.sw.inv_w);
-            const float p = 1.0f + t;
-            w = 0.0625f * p * p * p * (8.0f + t * (-9.0f + 3.0f * t));
+          const FF x = ff_coord((int)(qj.x - qi.x), sw.u_hi[0], sw.u_lo[0]);
+          const FF y = ff_coord((int)(qj.y - qi.y), sw.u_hi[1], sw.u_lo[1]);
+          const FF z = ff_coord((int)(qj.z - qi.z), sw.u_hi[2], sw.u_lo[2]);
+          // r^2: exact squares of the high parts plus the cross terms
+          FF r2 = ff_prod(x.hi, x.hi);
+          r2.lo = __fmaf_rn(2.f * x.hi, x.lo, r2.lo);
+          FF t2 = ff_prod(y.hi, y.hi);
+          t2.lo = __fmaf_rn(2.f * y.hi, y.lo, t2.lo);
+          r2 = ff_add(r2, t2);
+          t2 = ff_prod(z.hi, z.hi);
+          t2.lo = __fmaf_rn(2.f * z.hi, z.lo, t2.lo);
+          r2 = ff_add(r2, t2);
+          if (!(r2.hi < sw.rw2)) continue;
+          float w = 1.f;
+          if (r2.hi > sw.rw_lo2) {
+            // r = sqrt(r2): the rounded root r_h leaves r2 - r_h^2 exact (FMA)
+            const float rh = __fsqrt_rn(r2.hi);
+            const float rl = __fdividef(__fadd_rn(__fmaf_rn(-rh, rh, r2.hi), r2.lo), 2.f * rh);
+            // t = (r_w + r_w_lo - 2r) / width: c_hi - 2 r_h is exact (Sterbenz)
+            // (clamped: the bounds above are rounded outwards)
+            const float t = fminf(1.f, fmaxf(-1.f, __fmul_rn(__fadd_rn(__fsub_rn(sw.c_hi, 2.f * rh),
+                                                                         __fsub_rn(sw.c_lo, 2.f * rl)),
+                                                               sw.inv_w)));
+            const float p = 1.f + t;
+            w = 0.0625f * p * p * p * (8.f + t * (-9.f + 3.f * t));
           }
-          wsum += (double)w;
-          gsum += (double)(a.g[j] * w);
+          wsum = ff_add(wsum, FF{w, 0.f});
+          gsum = ff_add(gsum, ff_prod(a.g[j], w));
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-          gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
+          wsum = ff_add(wsum, FF{__shfl_xor_sync(0xffffffffu, wsum.hi, o), __shfl_xor_sync(0xffffffffu, wsum.lo, o)});
+          gsum = ff_add(gsum, FF{__shfl_xor_sync(0xffffffffu, gsum.hi, o), __shfl_xor_sync(0xffffffffu, gsum.lo, o)});
         }
         if (lane == 0) {
-          const double wb = 1.0 + wsum;                 // the self term, w(0) = 1
-          const double d = (gsum + (double)a.g[i]) / wb - a.sw.d0;
+          const double wb = 1.0 + ((double)wsum.hi + (double)wsum.lo);   // the self term, w(0) = 1
+          const double d = ((double)gsum.hi + (double)gsum.lo + (double)a.g[i]) / wb - a.sw.d0;
           double dl;
           const double lam = ftrans_c(d, a.sw.d_lo, a.sw.d_hi, a.sw.inv_d, &dl);
           a.lam[i] = (T)lam;

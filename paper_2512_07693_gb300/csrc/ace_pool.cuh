@@ -29,9 +29,9 @@ __host__ __device__ inline size_t ace_pool_smem(int npool) {
 template <typename T, typename K, int LMAX, int KA>
 __global__ void __launch_bounds__(kAceThreads) k_ace_pool(Args<T> a, AceDev<T> t) {
   pdl_begin();
-  // every list-build kernel of this call has completed (and read the rebuild
-  // flag): clear it for the next step's drift
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[0] = 0;
+  // every list-build kernel of this call has completed: block 0 clears the
+  // trigger (and, after a build, the binning counts) for the next step
+  if (blockIdx.x == 0) end_list_build(a.flags, a.cell_count, a.ncell);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ AceGroup<T, KA> g;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;

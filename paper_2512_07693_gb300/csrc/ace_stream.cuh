@@ -183,9 +183,9 @@ __device__ __forceinline__ void coupling_dispatch(const uint4& cp, const T* Ak, 
 template <typename T, typename K, int LMAX, int NAT>
 __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev<T> t) {
   pdl_begin();
-  // every list-build kernel of this call has completed (and read the rebuild
-  // flag): clear it for the next step's drift
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[0] = 0;
+  // every list-build kernel of this call has completed: block 0 clears the
+  // trigger (and, after a build, the binning counts) for the next step
+  if (blockIdx.x == 0) end_list_build(a.flags, a.cell_count, a.ncell);
   static_assert(NAT <= 32 && 32 % NAT == 0, "a warp holds whole slices");
   constexpr int NS = kAceThreads / NAT;
   constexpr bool PRIV = stream_private<T, LMAX>();

@@ -74,7 +74,7 @@ void free_all(apip_ctx* c) {
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   c->prof_pending.clear();
   c->prof_pool.clear();
-  void* ptrs[] = {c->cell_count, c->cell_used, c->cell_atoms, c->cell_q, c->nnb, c->nnb_e, c->posg, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
+  void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nnb_e, c->posg, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->clist, c->counts, c->flags, c->status, c->partials, c->thermo_part,
                   c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_frag, c->mlp_ws};
@@ -136,16 +136,13 @@ apip_status set_geometry(apip_ctx* ctx, const double* box, cudaStream_t s) {
   }
   if (ncell > ctx->ncell_alloc) {
     if (ctx->cell_count) cudaFree(ctx->cell_count);
-    if (ctx->cell_used) cudaFree(ctx->cell_used);
     if (ctx->cell_atoms) cudaFree(ctx->cell_atoms);
     if (ctx->cell_q) cudaFree(ctx->cell_q);
     ctx->cell_count = nullptr;
-    ctx->cell_used = nullptr;
     ctx->cell_atoms = nullptr;
     ctx->cell_q = nullptr;
     APIP_CK(cudaMalloc(&ctx->cell_count, sizeof(int) * ncell));
     APIP_CK(cudaMemsetAsync(ctx->cell_count, 0, sizeof(int) * ncell, s));
-    APIP_CK(cudaMalloc(&ctx->cell_used, sizeof(int) * ncell));
     APIP_CK(cudaMalloc(&ctx->cell_atoms, sizeof(int) * (size_t)ncell * ctx->p.cell_cap));
     if (ctx->p.precision == APIP_FP32)
       APIP_CK(cudaMalloc(&ctx->cell_q, sizeof(uint4) * (size_t)ncell * ctx->p.cell_cap));
@@ -216,6 +213,21 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
          T(p.eam_rc * p.eam_rc), T(p.eam_rc - p.eam_rc_width), T(1.0 / p.eam_rc_width),
          T(p.sw_r_w), T(p.sw_r_w * p.sw_r_w), T(p.sw_r_w - p.sw_r_w_width), T(1.0 / p.sw_r_w_width),
          T(p.sw_d_lo), T(p.sw_d_hi), T(1.0 / (p.sw_d_hi - p.sw_d_lo)), T(p.sw_d0), T(p.prec_shift)};
+  for (int k = 0; k < 3; ++k) {
+    const double u = c->geo.L[k] / 4294967296.0;
+    a.swff.u_hi[k] = (float)u;
+    a.swff.u_lo[k] = (float)(u - (double)a.swff.u_hi[k]);
+  }
+  {
+    const double cc = p.sw_r_w + (p.sw_r_w - p.sw_r_w_width);
+    a.swff.c_hi = (float)cc;
+    a.swff.c_lo = (float)(cc - (double)a.swff.c_hi);
+    a.swff.inv_w = (float)(1.0 / p.sw_r_w_width);
+    // the float-float r^2 is compared on its high part: bounds rounded outwards, so
+    // that every pair of the taper is evaluated (beyond r_w, w = 0 exactly)
+    a.swff.rw2 = std::nextafter((float)(p.sw_r_w * p.sw_r_w), INFINITY);
+    a.swff.rw_lo2 = std::nextafter((float)((p.sw_r_w - p.sw_r_w_width) * (p.sw_r_w - p.sw_r_w_width)), 0.0f);
+  }
   a.r_list2 = c->r_list * c->r_list;
   a.skin_half2 = 0.25 * p.skin * p.skin;
   a.skin_half2_f = (float)a.skin_half2;
@@ -230,7 +242,7 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.nnb_e = c->nnb_e; a.posg = c->posg;
   a.nnb = c->nnb; a.nbl = c->nbl; a.nbl_tmp = c->nbl_tmp; a.pos_ref = c->pos_ref; a.posq = c->posq; a.posq_ref = c->posq_ref;
   a.id2idx = c->id2idx; a.csp = c->csp; a.cell_count = c->cell_count; a.cell_atoms = c->cell_atoms;
-  a.cell_used = c->cell_used;
+  a.ncell = c->ncell;
   a.cell_q = c->cell_q;
   a.zeta = as<T>(c->zeta); a.xi_p = as<T>(c->xi_p); a.e_eam = as<T>(c->e_eam); a.g = as<T>(c->g);
   a.wbar = as<T>(c->wbar); a.dd = as<T>(c->dd); a.lam = as<T>(c->lam); a.dlam = as<T>(c->dlam);
@@ -341,7 +353,7 @@ void pass1(const Args<T>& a, cudaStream_t s) {
 // The force pipeline after prep (or after the drift of a Verlet step).
 template <typename T>
 void force_pipeline(apip_ctx* c, Args<T>& a, cudaStream_t s) {
-  { Phase ph(c, APIP_PHASE_NEIGHBOR, 3, s); launch_neighbors<T>(a, c->ncell, s); }
+  { Phase ph(c, APIP_PHASE_NEIGHBOR, 2, s); launch_neighbors<T>(a, c->ncell, s); }
   { Phase ph(c, APIP_PHASE_PASS1, 1, s); pass1<T>(a, s); }
   { Phase ph(c, APIP_PHASE_PASS2, 1, s); launch_pass2<T>(a, s); if (a.force_mix) launch_fm_buffer<T>(a, s); }
   { Phase ph(c, APIP_PHASE_ACE, 1, s); const AceDev<T> t = ace_dev<T>(c);
@@ -367,7 +379,7 @@ apip_status energy_forces_t(apip_ctx* c, const double* pos, const int32_t* id, i
   if (e_total) {
     Phase ph(c, APIP_PHASE_REDUCE, 1, s);
     launch_final(c->partials, a.n_part_p1 + c->ace_blocks, e_total, nullptr, nullptr, 0, nullptr,
-                 c->flags, c->counts, nullptr, s);
+                 c->flags, c->counts, nullptr, c->cell_count, c->ncell, s);
   }
   if (a.ind_on) launch_ind_work(c->ind_acc, 0.0, s);
   return launch_status(c);
@@ -386,7 +398,8 @@ apip_status switch_t(apip_ctx* c, const double* pos, const int32_t* id, int n, d
   launch_pass2<T>(a, s);
   if (lam_out) launch_get_field<T>(a, APIP_FIELD_LAM, lam_out, s);
   if (dlam_out) launch_get_field<T>(a, APIP_FIELD_DLAM, dlam_out, s);
-  launch_final(c->partials, 0, nullptr, nullptr, nullptr, 0, nullptr, c->flags, c->counts, n_ace_out, s);
+  launch_final(c->partials, 0, nullptr, nullptr, nullptr, 0, nullptr, c->flags, c->counts, n_ace_out, c->cell_count,
+               c->ncell, s);
   return launch_status(c);
 }
 
@@ -398,6 +411,7 @@ apip_status neighbors_t(apip_ctx* c, const double* pos, const int32_t* id, int n
   cudaMemsetAsync(c->flags, 0xff, sizeof(int), s);
   c->built_n = n;
   launch_neighbors<T>(a, c->ncell, s);
+  cudaMemsetAsync(c->cell_count, 0, sizeof(int) * c->ncell, s);
   cudaMemsetAsync(c->flags, 0, sizeof(int), s);
   return launch_status(c);
 }
@@ -424,7 +438,7 @@ apip_status verlet_t(apip_ctx* c, double* pos, double* vel, double* force, const
     if (thermo) {
       Phase ph(c, APIP_PHASE_REDUCE, 1, s);
       launch_final(c->partials, n_part, nullptr, thermo + 5 * k, k > 0 ? tp : nullptr, ntb,
-                   k > 0 ? thermo + 5 * (k - 1) : nullptr, c->flags, c->counts, nullptr, s);
+                   k > 0 ? thermo + 5 * (k - 1) : nullptr, c->flags, c->counts, nullptr, c->cell_count, c->ncell, s);
     }
   }
   { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, 2, pos, vel, force, inv_mass, dt, tp, s); }
@@ -842,6 +856,7 @@ apip_status apip_descriptors(apip_ctx* ctx, const double* pos, const double box[
     launch_neighbors<double>(a, ctx->ncell, s);
     launch_descriptors<double>(a, desc_bf16, s);
   }
+  APIP_CK(cudaMemsetAsync(ctx->cell_count, 0, sizeof(int) * ctx->ncell, s));
   APIP_CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int), s));
   return launch_status(ctx);
 }

@@ -138,8 +138,7 @@ struct apip_ctx {
   std::vector<double> ace_c1, ace_c2;
 
   // neighbour structures
-  int* cell_count = nullptr;   // binning counters, zero outside a list build
-  int* cell_used = nullptr;    // atoms per cell of the last build
+  int* cell_count = nullptr;   // binning counters, zero outside a list build (read by the fill)
   uint4* cell_q = nullptr;     // FP32 path: posq of the cell members in cell order
   int* cell_atoms = nullptr;
   int* nnb = nullptr;

@@ -18,6 +18,13 @@ struct PassK {
   T prec_shift;   // energy zero of the precise model (subtracted from E^prec per atom)
 };
 
+// Float-float constants of the float32 switch refinement: the grid unit L / 2^32
+// per axis, r_w + r_w_lo, and the float bounds of the taper.
+struct SwFF {
+  float u_hi[3], u_lo[3];
+  float c_hi, c_lo, inv_w, rw2, rw_lo2;
+};
+
 // Everything a kernel of the force pipeline may need, passed by value.
 template <typename T>
 struct Args {
@@ -38,6 +45,7 @@ struct Args {
   Geo geo;
   EamP eam;
   SwP sw;
+  SwFF swff;
   PassK<T> k;
   double r_list2, skin_half2, csp_rcut2;
   float skin_half2_f;     // skin_half2 rounded down to float (the FP32 path's rebuild trigger)
@@ -48,8 +56,8 @@ struct Args {
   int* nnb; int* nbl; int* nbl_tmp; double* pos_ref; uint4* posq; uint4* posq_ref; int* id2idx; int* csp;
   int* nnb_e;             // entries of the list whose build-time distance is below eam_rc + skin
   uint4* posg;            // FP32 path: (posq.x, posq.y, posq.z, bits of g), written by pass 1
-  int* cell_count; int* cell_atoms;
-  int* cell_used;         // atoms per cell (at most cell_cap) of the last list build
+  int* cell_count; int* cell_atoms;   // binning counts (zero outside a build) and members
+  int ncell;
   uint4* cell_q;          // FP32 path: fixed-point positions of the cell members, cell order
   T* zeta; T* xi_p; T* e_eam; T* g; T* wbar; T* dd; T* lam; T* dlam; T* e_ace;
   double* cvec; int* ace_list; int* counts; int* flags; int* status;
@@ -61,6 +69,18 @@ struct Args {
   const uint2* mlp_frag;  // FP32 path: the hidden layers' weights as split bfloat16 mma fragments
   T ace_rc, ace_rc_lo;    // cutoff of the radial descriptors (the ACE cutoff)
 };
+
+// Ends a call's use of the list-build trigger, by one whole block, after every
+// kernel that reads the trigger or the binning counts has completed: after a
+// build (trigger set) the counts are cleared for the next build, then the
+// trigger.
+__device__ __forceinline__ void end_list_build(int* flags, int* cell_count, int ncell) {
+  const int built = flags[0];
+  __syncthreads();
+  if (built)
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) cell_count[c] = 0;
+  if (threadIdx.x == 0) flags[0] = 0;
+}
 
 // Entries [s0, s1) of atom i's neighbour list (column-major, stride nmax) with
 // the index fetched two entries and the neighbour's record (load(j)) one entry
@@ -171,7 +191,7 @@ void launch_ind_work(double* acc, double dt, cudaStream_t s);
 template <typename T> void launch_csp_force(const Args<T>& a, cudaStream_t s);
 void launch_final(double* partials, int n_part, double* e_total, double* e_pot_slot,
                   const double* thermo_part, int n_tblocks, double* thermo_slot, int* flags,
-                  const int* counts, int64_t* n_ace_out, cudaStream_t s);
+                  const int* counts, int64_t* n_ace_out, int* cell_count, int ncell, cudaStream_t s);
 template <typename T> void launch_get_field(const Args<T>& a, int field, void* dst, cudaStream_t s);
 void launch_fill_const_list(int* list, int* counts, int n, cudaStream_t s);
 

@@ -81,10 +81,30 @@ __global__ void k_prep(Args<T> a) {
 }
 
 // ------------------------------------------------------------ neighbour list
-// Three launches per list build (binning, per-cell sort, fill), each returning at
-// once when no build is due: cell_count is zero before a build (zeroed on
-// allocation and by the sort, which hands the counts on in cell_used).
+// Two launches per list build (binning, fill), each returning at once when no
+// build is due: cell_count is zero before a build (zeroed on allocation, and after
+// each build by end_list_build, which also clears the trigger).
 
+// The cell of atom i: FP32 path from its fixed-point coordinates (integer
+// arithmetic, floor(q nc / 2^32)), FP64 path from the wrapped position.
+template <typename T>
+__device__ __forceinline__ void atom_cell(const Args<T>& a, int i, int c[3]) {
+  if constexpr (sizeof(T) == 4) {
+    const uint4 q = a.posq[i];
+    const unsigned qq[3] = {q.x, q.y, q.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[k] = (int)(((unsigned long long)qq[k] * (unsigned)a.geo.nc[k]) >> 32);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      c[k] = cell_of(wrap1(a.pos[3 * i + k], a.geo.L[k], a.geo.invL[k]), a.geo.L[k], a.geo.nc[k]);
+  }
+}
+
+// Binning: each atom takes a slot of its cell (the order of the slots follows
+// the atomics, so neighbour order within a cell is not fixed; every sum over
+// neighbours is order-independent up to rounding); FP32 path: the member's
+// fixed-point position is copied into cell order for the fill.
 template <typename T>
 __global__ void k_bin(Args<T> a) {
   pdl_begin();
@@ -92,41 +112,16 @@ __global__ void k_bin(Args<T> a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   int c[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-    c[k] = cell_of(wrap1(a.pos[3 * i + k], a.geo.L[k], a.geo.invL[k]), a.geo.L[k], a.geo.nc[k]);
+  atom_cell(a, i, c);
   const int cell = (c[2] * a.geo.nc[1] + c[1]) * a.geo.nc[0] + c[0];
   const int slot = atomicAdd(&a.cell_count[cell], 1);
   if (slot < a.cell_cap) {
     a.cell_atoms[cell * a.cell_cap + slot] = i;
+    if constexpr (sizeof(T) == 4) a.cell_q[(size_t)cell * a.cell_cap + slot] = a.posq[i];
   } else {
     atomicOr(&a.status[ST_CELL_OVERFLOW], 1);
     atomicMax(&a.status[ST_MAX_CELL], slot + 1);
   }
-}
-
-// Order each cell by atom index so that neighbour order (and thus every sum
-// over neighbours) does not depend on the order of the binning atomics; in the
-// FP32 path also copy the members' fixed-point positions into cell order, so
-// that the list build streams them without an index indirection.
-__global__ void k_cell_sort(const int* flags, int* cell_count, int* cell_used, int* cell_atoms, int ncell, int cap,
-                            const uint4* posq, uint4* cell_q) {
-  pdl_begin();
-  if (!flags[0]) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  const int cnt = min(cell_count[c], cap);
-  cell_used[c] = cnt;
-  cell_count[c] = 0;
-  int* v = cell_atoms + (size_t)c * cap;
-  for (int k = 1; k < cnt; ++k) {
-    const int x = v[k];
-    int m = k - 1;
-    while (m >= 0 && v[m] > x) { v[m + 1] = v[m]; --m; }
-    v[m + 1] = x;
-  }
-  if (cell_q)
-    for (int k = 0; k < cnt; ++k) cell_q[(size_t)c * cap + k] = posq[v[k]];
 }
 
 // One thread per atom: the candidates go to the scratch list in cell order,
@@ -142,9 +137,7 @@ __global__ void k_nbfill(Args<T> a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   int c[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-    c[k] = cell_of(wrap1(a.pos[3 * i + k], a.geo.L[k], a.geo.invL[k]), a.geo.L[k], a.geo.nc[k]);
+  atom_cell(a, i, c);
   const auto si = a.pv.self(i);
   // calls f(j, r^2) for every atom j != i within r_list, in cell order
   auto scan = [&](auto&& f) {
@@ -155,7 +148,7 @@ __global__ void k_nbfill(Args<T> a) {
         for (int dx = -1; dx <= 1; ++dx) {
           const int cx = (c[0] + dx + a.geo.nc[0]) % a.geo.nc[0];
           const int cell = (cz * a.geo.nc[1] + cy) * a.geo.nc[0] + cx;
-          const int m = a.cell_used[cell];
+          const int m = min(a.cell_count[cell], a.cell_cap);
           const int* v = a.cell_atoms + (size_t)cell * a.cell_cap;
           if constexpr (sizeof(T) == 4) {
             // float comparison against r_list^2 rounded up: the list holds every pair
@@ -557,8 +550,9 @@ __device__ __forceinline__ void neumaier(double& s, double& c, double v) {
 
 __global__ void k_final(const double* partials, int n_part, double* e_total, double* e_pot_slot,
                         const double* thermo_part, int n_tb, double* thermo_slot, int* flags,
-                        const int* counts, int64_t* n_ace_out) {
+                        const int* counts, int64_t* n_ace_out, int* cell_count, int ncell) {
   pdl_begin();
+  end_list_build(flags, cell_count, ncell);
   __shared__ double sh[32];
   double s = 0.0, c = 0.0;
   for (int k = threadIdx.x; k < n_part; k += blockDim.x) neumaier(s, c, partials[k]);
@@ -566,7 +560,6 @@ __global__ void k_final(const double* partials, int n_part, double* e_total, dou
   if (threadIdx.x == 0) {
     if (e_total) *e_total = tot;
     if (e_pot_slot) *e_pot_slot = tot;
-    flags[0] = 0;
     if (n_ace_out) *n_ace_out = (int64_t)counts[0];
   }
   if (thermo_part) {
@@ -682,9 +675,8 @@ template <typename T> void launch_prep(const Args<T>& a, cudaStream_t s) {
 }
 
 template <typename T> void launch_neighbors(const Args<T>& a, int ncell, cudaStream_t s) {
+  (void)ncell;
   launch_pdl(k_bin<T>, nblocks(a.n), kBlock, 0, s, a);
-  launch_pdl(k_cell_sort, nblocks(ncell), kBlock, 0, s, a.flags, a.cell_count, a.cell_used, a.cell_atoms, ncell, a.cell_cap,
-                                                 sizeof(T) == 4 ? a.posq : nullptr, sizeof(T) == 4 ? a.cell_q : nullptr);
   launch_pdl(k_nbfill<T>, nblocks(a.n), kBlock, 0, s, a);
 }
 
@@ -745,9 +737,9 @@ template <typename T> void launch_csp_force(const Args<T>& a, cudaStream_t s) {
 
 void launch_final(double* partials, int n_part, double* e_total, double* e_pot_slot,
                   const double* thermo_part, int n_tblocks, double* thermo_slot, int* flags,
-                  const int* counts, int64_t* n_ace_out, cudaStream_t s) {
+                  const int* counts, int64_t* n_ace_out, int* cell_count, int ncell, cudaStream_t s) {
   launch_pdl(k_final, 1, 256, 0, s, partials, n_part, e_total, e_pot_slot, thermo_part, n_tblocks, thermo_slot,
-                            flags, counts, n_ace_out);
+                            flags, counts, n_ace_out, cell_count, ncell);
 }
 
 void launch_thermo_final(const double* thermo_part, int n_tblocks, double* thermo_slot, cudaStream_t s) {
