@@ -16,6 +16,14 @@ difference of the two models.  Readings (none of this is in the paper):
                perfect 0 K lattice (the energy analogue of the reference d^(0) of Eq. 6)
   loss         mean over the batch of (g_i - y_i)^2
   optimiser    Adam (Kingma & Ba 2015): lr 1e-3, beta1 0.9, beta2 0.999, eps 1e-8
+  training     "BF16 inputs, FP32 accumulate" (the workload): every matrix product of
+               the training step takes its operands rounded to bfloat16 (round to
+               nearest even) -- the weights W1, W2, W3, the activations x0, h1, h2,
+               h3 and the back-propagated gradients dz1, dz2, dz3, dg -- and sums
+               exactly; the elementwise steps (bias, SiLU, its derivative, the
+               output layer's dot product g = w4 . h3 + b4 and the loss) are not
+               rounded (``loss_and_grads_bf16``).  Inference (the switch and its
+               forces) keeps the plain float64 definition above.
 """
 import numpy as np
 
@@ -100,6 +108,40 @@ def loss_and_grads(p, G, y):
     loss = float(np.mean(r * r))
     grads = backward(p, cache, 2.0 * r / len(y))
     return loss, grads
+
+
+def bf16(x):
+    """Round to the nearest bfloat16 (ties to even) through float32, as float64."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def loss_and_grads_bf16(p, G, y):
+    """Loss and weight gradients of one training step with bfloat16 GEMM operands
+    (module docstring): the same chain as forward/backward, each matrix product's
+    inputs rounded to bfloat16.  Bias gradients are sums of the rounded dz; the
+    output layer's weight gradient pairs the rounded dg with the rounded h3."""
+    x0 = S_IN * np.asarray(G, dtype=np.float64)          # G holds bfloat16 values; 0.25 G is exact
+    W1, W2, W3 = bf16(p["W1"]), bf16(p["W2"]), bf16(p["W3"])
+    z1 = x0 @ W1.T + p["b1"]
+    h1 = bf16(silu(z1))
+    z2 = h1 @ W2.T + p["b2"]
+    h2 = bf16(silu(z2))
+    z3 = h2 @ W3.T + p["b3"]
+    h3 = silu(z3)
+    g = h3 @ p["w4"] + p["b4"]
+    r = g - y
+    loss = float(np.mean(r * r))
+    dg = 2.0 * r / len(y)
+    d3 = bf16(np.outer(dg, p["w4"]) * silu_deriv(z3))
+    d2 = bf16((d3 @ W3) * silu_deriv(z2))
+    d1 = bf16((d2 @ W2) * silu_deriv(z1))
+    dgb, h3b = bf16(dg), bf16(h3)
+    out = {"W3": d3.T @ h2, "b3": d3.sum(axis=0), "W2": d2.T @ h1, "b2": d2.sum(axis=0),
+           "W1": d1.T @ x0, "b1": d1.sum(axis=0), "w4": h3b.T @ dgb, "b4": float(np.sum(dgb))}
+    return loss, out
 
 
 def adam_step(p, grads, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):

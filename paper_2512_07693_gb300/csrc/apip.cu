@@ -813,7 +813,7 @@ apip_status apip_sync(apip_ctx* ctx, void* stream) {
   if (st[ST_CELL_OVERFLOW])
     return fail(ctx, APIP_ERR_NB_OVERFLOW, "cell overflow: a cell holds " + std::to_string(st[ST_MAX_CELL]) +
                                               " atoms, cell_cap = " + std::to_string(ctx->p.cell_cap));
-  if (st[ST_TIMEOUT]) return fail(ctx, APIP_ERR_TIMEOUT, "reserved: a bounded device wait gave up");
+  if (st[ST_TIMEOUT]) return fail(ctx, APIP_ERR_TIMEOUT, "a bounded device wait gave up (the tensor-core training kernel's wait for its matrix products)");
   if (st[ST_BAD_INPUT]) return fail(ctx, APIP_ERR_BAD_INPUT, "non-finite position or atom id out of range");
   if (st[ST_BAD_PARTNER]) return fail(ctx, APIP_ERR_BAD_INPUT, "a CSP partner id is not present");
   return APIP_OK;
@@ -874,7 +874,8 @@ apip_status apip_mlp_loss_grad(apip_ctx* ctx, const uint16_t* desc_bf16, const f
     APIP_CK(cudaMalloc(&ctx->mlp_ws, sizeof(float) * need));
     ctx->mlp_ws_cap = need;
   }
-  launch_mlp_loss_grad(desc_bf16, y, (int)batch, params, grad_out, loss_out, ctx->mlp_ws, (cudaStream_t)stream);
+  launch_mlp_loss_grad(desc_bf16, y, (int)batch, params, grad_out, loss_out, ctx->mlp_ws, ctx->status,
+                       (cudaStream_t)stream);
   return launch_status(ctx);
 }
 

@@ -582,82 +582,7 @@ __global__ void k_cast_params(const float* src, T* dst) {
   if (k < APIP_MLP_NPARAM) dst[k] = (T)src[k];
 }
 
-// ---------------------------------------------------------------- training
-// Per sample: forward (z -> ws_z), loss term, back-propagation to d (-> ws_d).
-__global__ void __launch_bounds__(128) k_train_fwd_bwd(const __nv_bfloat16* __restrict__ desc,
-                                                       const float* __restrict__ y, int batch,
-                                                       const float* __restrict__ params, float* ws_z,
-                                                       float* ws_d, float* dg_out, float* loss_part) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* w = reinterpret_cast<float*>(smem_raw);
-  __shared__ double sh[32];
-  for (int k = threadIdx.x; k < APIP_MLP_NPARAM; k += blockDim.x) w[k] = params[k];
-  __syncthreads();
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  double l = 0.0;
-  if (s < batch) {
-    float G[kIn];
-#pragma unroll
-    for (int m = 0; m < kIn; ++m) G[m] = __bfloat162float(desc[(size_t)s * kIn + m]);
-    float* z = ws_z + (size_t)s * 3 * kW;
-    float* d = ws_d + (size_t)s * 3 * kW;
-    const float g = mlp_forward<float>(w, G, z);
-    const float r = g - y[s];
-    l = (double)r * (double)r;
-    const float dg = 2.0f * r / (float)batch;
-    dg_out[s] = dg;
-    mlp_backward_z<float>(w, z, dg, d);
-  }
-  const double tot = block_sum(l, sh);
-  if (threadIdx.x == 0) loss_part[blockIdx.x] = tot;
-}
-
-// Weight gradients: one thread per parameter, summed over a chunk of samples,
-// chunks combined with atomics into grad (zeroed beforehand).
-__global__ void k_train_wgrad(const __nv_bfloat16* __restrict__ desc, int batch, const float* __restrict__ ws_z,
-                              const float* __restrict__ ws_d, const float* __restrict__ dg, float* grad,
-                              int chunk) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= APIP_MLP_NPARAM) return;
-  const int s0 = blockIdx.y * chunk, s1 = min(batch, s0 + chunk);
-  float acc = 0.0f;
-  if (p < oB1) {                          // W1[j][k]: d1_j x0_k
-    const int j = (p - oW1) / kIn, k = (p - oW1) % kIn;
-    for (int s = s0; s < s1; ++s)
-      acc += ws_d[(size_t)s * 3 * kW + j] * (float)kSin * __bfloat162float(desc[(size_t)s * kIn + k]);
-  } else if (p < oW2) {                   // b1[j]
-    const int j = p - oB1;
-    for (int s = s0; s < s1; ++s) acc += ws_d[(size_t)s * 3 * kW + j];
-  } else if (p < oB2) {                   // W2[j][k]: d2_j h1_k
-    const int j = (p - oW2) / kW, k = (p - oW2) % kW;
-    for (int s = s0; s < s1; ++s) acc += ws_d[(size_t)s * 3 * kW + kW + j] * silu(ws_z[(size_t)s * 3 * kW + k]);
-  } else if (p < oW3) {                   // b2[j]
-    const int j = p - oB2;
-    for (int s = s0; s < s1; ++s) acc += ws_d[(size_t)s * 3 * kW + kW + j];
-  } else if (p < oB3) {                   // W3[j][k]: d3_j h2_k
-    const int j = (p - oW3) / kW, k = (p - oW3) % kW;
-    for (int s = s0; s < s1; ++s)
-      acc += ws_d[(size_t)s * 3 * kW + 2 * kW + j] * silu(ws_z[(size_t)s * 3 * kW + kW + k]);
-  } else if (p < oW4) {                   // b3[j]
-    const int j = p - oB3;
-    for (int s = s0; s < s1; ++s) acc += ws_d[(size_t)s * 3 * kW + 2 * kW + j];
-  } else if (p < oB4) {                   // w4[j]: dg h3_j
-    const int j = p - oW4;
-    for (int s = s0; s < s1; ++s) acc += dg[s] * silu(ws_z[(size_t)s * 3 * kW + 2 * kW + j]);
-  } else {                                // b4
-    for (int s = s0; s < s1; ++s) acc += dg[s];
-  }
-  atomicAdd(&grad[p], acc);
-}
-
-__global__ void k_train_loss(const float* loss_part, int nb, int batch, float* loss_out) {
-  __shared__ double sh[32];
-  double s = 0.0;
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) s += loss_part[k];
-  const double tot = block_sum(s, sh);
-  if (threadIdx.x == 0) *loss_out = (float)(tot / batch);
-}
-
+// ------------------------------------------------------------------ Adam
 __global__ void k_adam(float* p, const float* g, float* m, float* v, int t, float lr) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= APIP_MLP_NPARAM) return;
@@ -725,26 +650,6 @@ template <typename T> void launch_descriptors(const Args<T>& a, uint16_t* out, c
 template <typename T> void launch_cast_params(const float* src, T* dst, cudaStream_t s) {
   k_cast_params<T><<<(APIP_MLP_NPARAM + 255) / 256, 256, 0, s>>>(src, dst);
 }
-
-void launch_mlp_loss_grad(const uint16_t* desc, const float* y, int batch, const float* params, float* grad,
-                          float* loss, float* ws, cudaStream_t s) {
-  const int nb = (batch + 127) / 128;
-  float* ws_z = ws;
-  float* ws_d = ws + (size_t)batch * 3 * kW;
-  float* dg = ws_d + (size_t)batch * 3 * kW;
-  float* loss_part = dg + batch;
-  const size_t bytes = sizeof(float) * APIP_MLP_NPARAM;
-  cudaFuncSetAttribute(k_train_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  const __nv_bfloat16* d = reinterpret_cast<const __nv_bfloat16*>(desc);
-  k_train_fwd_bwd<<<nb, 128, bytes, s>>>(d, y, batch, params, ws_z, ws_d, dg, loss_part);
-  cudaMemsetAsync(grad, 0, sizeof(float) * APIP_MLP_NPARAM, s);
-  const int chunk = 256;
-  dim3 grid((APIP_MLP_NPARAM + 255) / 256, (batch + chunk - 1) / chunk);
-  k_train_wgrad<<<grid, 256, 0, s>>>(d, batch, ws_z, ws_d, dg, grad, chunk);
-  k_train_loss<<<1, 256, 0, s>>>(loss_part, nb, batch, loss);
-}
-
-size_t mlp_workspace_floats(int batch) { return (size_t)batch * (6 * kW + 1) + (batch + 127) / 128; }
 
 void launch_mlp_adam(float* p, const float* g, float* m, float* v, int t, float lr, cudaStream_t s) {
   k_adam<<<(APIP_MLP_NPARAM + 255) / 256, 256, 0, s>>>(p, g, m, v, t, lr);

@@ -159,7 +159,8 @@ def test_training_gradient_and_adam_match_oracle():
     G = _bf16(rng.uniform(0, 6, (B, 32)))
     y = rng.uniform(0, 0.5, B).astype(np.float32)
     w = f32(W.mlp_params(9))
-    loss_ref, grads_ref = mlp.loss_and_grads(w, G, y.astype(np.float64))
+    # the training step's reading: bfloat16 GEMM operands, float32 accumulation
+    loss_ref, grads_ref = mlp.loss_and_grads_bf16(w, G, y.astype(np.float64))
     flat = torch.tensor(apip.mlp_flat(w), device="cuda")
     Gd = torch.tensor(G.astype(np.float32), device="cuda").to(torch.bfloat16).contiguous()
     yd = torch.tensor(y, device="cuda")

@@ -124,3 +124,38 @@ def test_learned_switch_force_is_minus_gradient():
                                     forces=False)["E"]
             assert res["F"][a, c] == pytest.approx(-(ep - em) / (2 * h), abs=2e-6)
     assert np.abs(res["F"].sum(axis=0)).max() < 1e-10
+
+
+def test_bf16_rounding_matches_library():
+    """The oracle's bfloat16 rounding against torch's (round to nearest even)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.normal(0, 1, 4000), rng.normal(0, 1e-3, 1000) * 1e3, [0.0, -0.0, 1.0, 3.0, 1e-30]])
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(mlp.bf16(x), ref)
+
+
+def test_bf16_training_step_is_the_exact_chain_without_rounding(monkeypatch):
+    """With the bfloat16 rounding replaced by the identity, the mixed-precision
+    training step is the exact loss and gradient (same chain, no term dropped)."""
+    p = W.mlp_params(4)
+    G, y = _rand_batch(seed=1)
+    loss, grads = mlp.loss_and_grads(p, G, y)
+    monkeypatch.setattr(mlp, "bf16", lambda x: np.asarray(x, dtype=np.float64))
+    loss_b, grads_b = mlp.loss_and_grads_bf16(p, G, y)
+    assert loss_b == pytest.approx(loss, rel=1e-14)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3", "w4"):
+        np.testing.assert_allclose(grads_b[k], grads[k], rtol=1e-12, atol=1e-15)
+    assert grads_b["b4"] == pytest.approx(grads["b4"], rel=1e-12)
+
+
+def test_bf16_training_step_is_close_to_the_exact_one():
+    """bfloat16 operands move each gradient by a few bfloat16 roundings (2^-9)."""
+    p = W.mlp_params(4)
+    G, y = _rand_batch(seed=1)
+    loss, grads = mlp.loss_and_grads(p, G, y)
+    loss_b, grads_b = mlp.loss_and_grads_bf16(p, G, y)
+    assert loss_b == pytest.approx(loss, rel=2e-2)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3", "w4"):
+        scale = np.abs(grads[k]).max()
+        np.testing.assert_allclose(grads_b[k], grads[k], atol=3e-2 * scale)
