@@ -10,8 +10,9 @@
 // pre-activations stay float32 in tensor memory, the master weights and Adam
 // are float32.
 //
-// A CTA of 128 threads (one per sample of a 128-sample tile, which is also its
-// tensor-memory lane) loops over tiles.  Per tile, with D = A B^T on the tensor
+// A CTA of 256 threads loops over 128-sample tiles: sample r of a tile is
+// tensor-memory lane r, read by warp r / 32 (lanes) and warp r / 32 + 4, which
+// take the first and the second half of each layer's 64 columns.  Per tile, with D = A B^T on the tensor
 // cores (M = 128 rows of A, N rows of B, K the shared dimension):
 //   z1 = x0 W1^T, z2 = h1 W2^T, z3 = h2 W3^T                (forward, M = samples)
 //   dh2 = dz3 W3, dh1 = dz2 W2                              (back-propagation)
@@ -48,7 +49,8 @@ constexpr int oW1 = 0, oB1 = oW1 + kW * kIn, oW2 = oB1 + kW, oB2 = oW2 + kW * kW
               oB3 = oW3 + kW * kW, oW4 = oB3 + kW, oB4 = oW4 + kW;
 static_assert(oB4 + 1 == APIP_MLP_NPARAM, "parameter layout");
 constexpr float kSin = 0.25f;
-constexpr int kS = 128;       // samples per tile = threads per CTA = tensor-memory lanes
+constexpr int kS = 128;       // samples per tile = tensor-memory lanes
+constexpr int kT = 256;       // threads per CTA: two per sample
 
 // shared-memory operands (byte offsets; every one a multiple of 1024)
 constexpr int sX0 = 0;                        // [128][32]  A of layer 1
@@ -65,8 +67,8 @@ constexpr int sAW = sBW + kNB * kS * 2;       // [128][128] A of the W3 / W2 gra
 constexpr int kNB1 = kIn + kW + 16;           // 112 rows: x0^T, h3^T, a row of ones, zeros
 constexpr int sB1 = sAW + kS * kS * 2;        // [112][128] B of the W1 / w4 gradients
 constexpr int sA1 = sB1 + kNB1 * kS * 2;      // [128][128] A of the W1 / w4 gradients: dz1^T, dg, zeros
-constexpr int sF = sA1 + kS * kS * 2;         // float32: b1, b2, b3, w4, b4
-constexpr int kSmem = sF + (4 * kW + 4) * 4;
+constexpr int sF = sA1 + kS * kS * 2;         // float32: b1, b2, b3, w4, b4 (4 kW + 4), y, g partials (3 kS)
+constexpr int kSmem = sF + (4 * kW + 4 + 3 * kS) * 4;
 static_assert(sW1 % 1024 == 0 && sH1 % 1024 == 0 && sBW % 1024 == 0 && sAW % 1024 == 0 && sB1 % 1024 == 0 &&
                   sA1 % 1024 == 0 && sF % 16 == 0,
               "operand alignment");
@@ -82,6 +84,19 @@ __device__ __forceinline__ int core(int r, int k, int K) {
 
 __device__ __forceinline__ void put(unsigned char* base, int r, int k, int K, float v) {
   *reinterpret_cast<__nv_bfloat16*>(base + core(r, k, K)) = __float2bfloat16_rn(v);
+}
+
+// Eight consecutive elements (r, k0 .. k0 + 7) of a row, k0 a multiple of 8: one
+// 16-byte store (they form one row of a core matrix).
+__device__ __forceinline__ void put8(unsigned char* base, int r, int k0, int K, const float* v) {
+  uint4 w;
+  uint32_t* u = reinterpret_cast<uint32_t*>(&w);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+    u[q] = *reinterpret_cast<const uint32_t*>(&p);
+  }
+  *reinterpret_cast<uint4*>(base + core(r, k0, K)) = w;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -154,7 +169,9 @@ __device__ __forceinline__ void tld16(uint32_t addr, float* v) {
   for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-__device__ __forceinline__ float sig(float z) { return 1.f / (1.f + __expf(-z)); }
+// The logistic function (hardware exponential and approximate division: a few
+// ulp, far below the bfloat16 rounding of the GEMM operands it feeds).
+__device__ __forceinline__ float sig(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
 
 // Operands written by the threads are made visible to the tensor cores, and the
 // threads' tensor-memory reads are ordered before the next MMA.
@@ -165,36 +182,41 @@ __device__ __forceinline__ void to_mma() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(kS, 1)
+__global__ void __launch_bounds__(kT, 1)
     k_train_tc(const __nv_bfloat16* __restrict__ desc, const float* __restrict__ y, int batch,
                const float* __restrict__ params, float* __restrict__ grad, double* loss_acc, int* status) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_holder;
   __shared__ int failed;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int r = 32 * quarter + lane;            // this thread's sample row (tensor-memory lane)
+  const int c0 = 32 * half;                     // its half of a layer's 64 columns
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
                  "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   // weights (bfloat16 operands) and the constant rows
-  for (int e = tid; e < kW * kIn; e += kS) put(sm + sW1, e / kIn, e % kIn, kIn, params[oW1 + e]);
-  for (int e = tid; e < kW * kW; e += kS) {
-    const int r = e / kW, k = e % kW;
-    put(sm + sW2, r, k, kW, params[oW2 + e]);
-    put(sm + sW3, r, k, kW, params[oW3 + e]);
-    put(sm + sW2t, k, r, kW, params[oW2 + e]);
-    put(sm + sW3t, k, r, kW, params[oW3 + e]);
+  for (int e = tid; e < kW * kIn; e += kT) put(sm + sW1, e / kIn, e % kIn, kIn, params[oW1 + e]);
+  for (int e = tid; e < kW * kW; e += kT) {
+    const int rr = e / kW, k = e % kW;
+    put(sm + sW2, rr, k, kW, params[oW2 + e]);
+    put(sm + sW3, rr, k, kW, params[oW3 + e]);
+    put(sm + sW2t, k, rr, kW, params[oW2 + e]);
+    put(sm + sW3t, k, rr, kW, params[oW3 + e]);
   }
-  for (int e = tid; e < 16 * kS; e += kS) {
-    const int r = e / kS, s = e % kS;
-    put(sm + sBW, 2 * kW + r, s, kS, r == 0 ? 1.f : 0.f);
-    put(sm + sB1, kIn + kW + r, s, kS, r == 0 ? 1.f : 0.f);
+  for (int e = tid; e < 16 * kS; e += kT) {
+    const int rr = e / kS, ss = e % kS;
+    put(sm + sBW, 2 * kW + rr, ss, kS, rr == 0 ? 1.f : 0.f);
+    put(sm + sB1, kIn + kW + rr, ss, kS, rr == 0 ? 1.f : 0.f);
   }
-  for (int e = tid; e < 63 * kS; e += kS) put(sm + sA1, kW + 1 + e / kS, e % kS, kS, 0.f);
+  for (int e = tid; e < 63 * kS; e += kT) put(sm + sA1, kW + 1 + e / kS, e % kS, kS, 0.f);
   float* fb = reinterpret_cast<float*>(sm + sF);
-  for (int k = tid; k < kW; k += kS) {
+  float* ys = fb + 4 * kW + 4;                  // y of the tile's samples
+  float* gp = ys + kS;                          // [2][kS] partial sums of the output layer
+  for (int k = tid; k < kW; k += kT) {
     fb[k] = params[oB1 + k];
     fb[kW + k] = params[oB2 + k];
     fb[2 * kW + k] = params[oB3 + k];
@@ -208,7 +230,7 @@ __global__ void __launch_bounds__(kS, 1)
   }
   to_mma();
   const uint32_t tm = tmem_holder;
-  const uint32_t lane_addr = tm + ((uint32_t)(32 * warp) << 16);   // this warp's quarter of the lanes
+  const uint32_t lane_addr = tm + ((uint32_t)(32 * quarter) << 16);   // this warp's quarter of the lanes
   const float b4 = fb[4 * kW];
   const float inv_batch = 1.f / (float)batch;
   uint32_t phase = 0;
@@ -229,116 +251,127 @@ __global__ void __launch_bounds__(kS, 1)
     __syncthreads();
     return failed == 0;
   };
-
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int s = tile * kS + tid;
-    const bool valid = s < batch;
-    // inputs: x0 = 0.25 G (exact in bfloat16), row tid of the layer-1 A and column tid of the W1-gradient B
-    {
-      const uint4* src = reinterpret_cast<const uint4*>(desc + (size_t)(valid ? s : 0) * kIn);
+  // one layer's epilogue over this thread's 32 columns: f(column, z) -> value
+  // stored in row r of the A operand `rowbuf` (may be null) and, transposed, in
+  // rows tbase + column of `tbuf`
+  // (tbase + c0 and c0 are multiples of 8: the addresses are a per-thread base
+  // plus compile-time offsets)
+  auto epilogue = [&](uint32_t col, unsigned char* rowbuf, unsigned char* tbuf, int tbase, auto&& f) {
+    unsigned char* tb = tbuf + core(tbase + c0, r, kS);
+    unsigned char* rb = rowbuf ? rowbuf + core(r, c0, kW) : nullptr;
 #pragma unroll
-      for (int q = 0; q < kIn / 8; ++q) {
-        uint4 v = valid ? src[q] : make_uint4(0u, 0u, 0u, 0u);
-        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&v);
+    for (int c = 0; c < 32; c += 16) {
+      float z[16], o[16];
+      tld16(lane_addr + col + c0 + c, z);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const float x = kSin * __bfloat162float(h[e]);
-          put(sm + sX0, tid, 8 * q + e, kIn, x);
-          put(sm + sB1, 8 * q + e, tid, kS, x);
+      for (int q = 0; q < 16; ++q) {
+        o[q] = f(c0 + c + q, z[q]);
+        const int j = c + q;
+        *reinterpret_cast<__nv_bfloat16*>(tb + (j >> 3) * (kS * 16) + (j & 7) * 16) = __float2bfloat16_rn(o[q]);
+      }
+      if (rb) {
+#pragma unroll
+        for (int h8 = 0; h8 < 2; ++h8) {
+          uint4 w;
+          uint32_t* u = reinterpret_cast<uint32_t*>(&w);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 p = __floats2bfloat162_rn(o[8 * h8 + 2 * q], o[8 * h8 + 2 * q + 1]);
+            u[q] = *reinterpret_cast<const uint32_t*>(&p);
+          }
+          *reinterpret_cast<uint4*>(rb + ((c + 8 * h8) >> 3) * 128) = w;
         }
       }
     }
-    const float yv = valid ? y[s] : 0.f;
+  };
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int s = tile * kS + r;
+    const bool valid = s < batch;
+    // inputs: x0 = 0.25 G (exact in bfloat16), features 16 half .. of row r of the
+    // layer-1 A and of column r of the W1-gradient B
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(desc + (size_t)(valid ? s : 0) * kIn) + 2 * half;
+      float x[16];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const uint4 v = valid ? src[q] : make_uint4(0u, 0u, 0u, 0u);
+        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          x[8 * q + e] = kSin * __bfloat162float(h[e]);
+          put(sm + sB1, 16 * half + 8 * q + e, r, kS, x[8 * q + e]);
+        }
+      }
+      put8(sm + sX0, r, 16 * half, kIn, x);
+      put8(sm + sX0, r, 16 * half + 8, kIn, x + 8);
+      if (half == 0) ys[r] = valid ? y[s] : 0.f;
+    }
     to_mma();
     if (!run([&] { mma(tm, cZ1, sm + sX0, sm + sW1, kIn, kW, false); })) break;
     // layer 1: h1 = silu(z1 + b1) -> A of layer 2 and rows 64.. of the W-gradient B (h1^T)
-    for (int c = 0; c < kW; c += 16) {
-      float z[16];
-      tld16(lane_addr + cZ1 + c, z);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float zz = z[q] + fb[c + q];
-        const float h = zz * sig(zz);
-        put(sm + sH1, tid, c + q, kW, h);
-        put(sm + sBW, kW + c + q, tid, kS, h);
-      }
-    }
+    epilogue(cZ1, sm + sH1, sm + sBW, kW, [&](int c, float z) {
+      const float zz = z + fb[c];
+      return zz * sig(zz);
+    });
     to_mma();
     if (!run([&] { mma(tm, cZ2, sm + sH1, sm + sW2, kW, kW, false); })) break;
     // layer 2: h2 -> A of layer 3 and rows 0.. of the W-gradient B (h2^T)
-    for (int c = 0; c < kW; c += 16) {
-      float z[16];
-      tld16(lane_addr + cZ2 + c, z);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float zz = z[q] + fb[kW + c + q];
-        const float h = zz * sig(zz);
-        put(sm + sH2, tid, c + q, kW, h);
-        put(sm + sBW, c + q, tid, kS, h);
-      }
-    }
+    epilogue(cZ2, sm + sH2, sm + sBW, 0, [&](int c, float z) {
+      const float zz = z + fb[kW + c];
+      return zz * sig(zz);
+    });
     to_mma();
     if (!run([&] { mma(tm, cZ3, sm + sH2, sm + sW3, kW, kW, false); })) break;
-    // layer 3 and the output: g = w4 . h3 + b4; h3^T -> rows 32.. of the W1-gradient B
-    float g = b4;
-    for (int c = 0; c < kW; c += 16) {
-      float z[16];
-      tld16(lane_addr + cZ3 + c, z);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float zz = z[q] + fb[2 * kW + c + q];
-        const float h = zz * sig(zz);
-        g = fmaf(fb[3 * kW + c + q], h, g);
-        put(sm + sB1, kIn + c + q, tid, kS, h);
-      }
+    // layer 3 and the output: g = w4 . h3 + b4, its two halves summed through
+    // shared memory; h3^T -> rows 32.. of the W1-gradient B
+    float gh = 0.f;
+    epilogue(cZ3, nullptr, sm + sB1, kIn, [&](int c, float z) {
+      const float zz = z + fb[2 * kW + c];
+      const float h = zz * sig(zz);
+      gh = fmaf(fb[3 * kW + c], h, gh);
+      return h;
+    });
+    gp[half * kS + r] = gh;
+    __syncthreads();
+    const float g = b4 + gp[r] + gp[kS + r];
+    const float res = valid ? g - ys[r] : 0.f;
+    if (half == 0) {
+      loss += (double)res * (double)res;
+      put(sm + sA1, kW, r, kS, 2.f * res * inv_batch);   // row 64 of the W1-gradient A: dg
     }
-    const float r = valid ? g - yv : 0.f;
-    loss += (double)r * (double)r;
-    const float dg = 2.f * r * inv_batch;
-    put(sm + sA1, kW, tid, kS, dg);   // row 64 of the W1-gradient A: the output layer's gradient
-    // dz3 = dg w4 silu'(z3) -> A of dh2 (in the h1 buffer) and rows 0.. of the W-gradient A (dz3^T)
-    for (int c = 0; c < kW; c += 16) {
-      float z[16];
-      tld16(lane_addr + cZ3 + c, z);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float zz = z[q] + fb[2 * kW + c + q];
-        const float sg = sig(zz);
-        const float d = dg * fb[3 * kW + c + q] * (sg * (1.f + zz * (1.f - sg)));
-        put(sm + sH1, tid, c + q, kW, d);
-        put(sm + sAW, c + q, tid, kS, d);
-      }
-    }
+    const float dg = 2.f * res * inv_batch;
+    // dz3 = dg w4 silu'(z3) -> A of dh2 (the h1 buffer) and rows 0.. of the W-gradient A (dz3^T)
+    epilogue(cZ3, sm + sH1, sm + sAW, 0, [&](int c, float z) {
+      const float zz = z + fb[2 * kW + c];
+      const float sg = sig(zz);
+      return dg * fb[3 * kW + c] * (sg * (1.f + zz * (1.f - sg)));
+    });
     to_mma();
     if (!run([&] { mma(tm, cDH, sm + sH1, sm + sW3t, kW, kW, false); })) break;
-    // dz2 = dh2 silu'(z2) -> A of dh1 (in the h2 buffer) and rows 64.. of the W-gradient A
-    for (int c = 0; c < kW; c += 16) {
-      float dh[16], z[16];
-      tld16(lane_addr + cDH + c, dh);
-      tld16(lane_addr + cZ2 + c, z);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float zz = z[q] + fb[kW + c + q];
+    // dz2 = dh2 silu'(z2) -> A of dh1 (the h2 buffer) and rows 64.. of the W-gradient A
+    {
+      float zs[32];
+      tld16(lane_addr + cZ2 + c0, zs);
+      tld16(lane_addr + cZ2 + c0 + 16, zs + 16);
+      epilogue(cDH, sm + sH2, sm + sAW, kW, [&](int c, float dh) {
+        const float zz = zs[c - c0] + fb[kW + c];
         const float sg = sig(zz);
-        const float d = valid ? dh[q] * (sg * (1.f + zz * (1.f - sg))) : 0.f;
-        put(sm + sH2, tid, c + q, kW, d);
-        put(sm + sAW, kW + c + q, tid, kS, d);
-      }
+        return valid ? dh * (sg * (1.f + zz * (1.f - sg))) : 0.f;
+      });
     }
     to_mma();
     if (!run([&] { mma(tm, cDH, sm + sH2, sm + sW2t, kW, kW, false); })) break;
     // dz1 = dh1 silu'(z1) -> rows 0.. of the W1-gradient A
-    for (int c = 0; c < kW; c += 16) {
-      float dh[16], z[16];
-      tld16(lane_addr + cDH + c, dh);
-      tld16(lane_addr + cZ1 + c, z);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float zz = z[q] + fb[c + q];
+    {
+      float zs[32];
+      tld16(lane_addr + cZ1 + c0, zs);
+      tld16(lane_addr + cZ1 + c0 + 16, zs + 16);
+      epilogue(cDH, nullptr, sm + sA1, 0, [&](int c, float dh) {
+        const float zz = zs[c - c0] + fb[c];
         const float sg = sig(zz);
-        const float d = valid ? dh[q] * (sg * (1.f + zz * (1.f - sg))) : 0.f;
-        put(sm + sA1, c + q, tid, kS, d);
-      }
+        return valid ? dh * (sg * (1.f + zz * (1.f - sg))) : 0.f;
+      });
     }
     to_mma();
     const bool acc = !first;
@@ -349,46 +382,50 @@ __global__ void __launch_bounds__(kS, 1)
       break;
     first = false;
   }
-  // the accumulated gradients, lane m = row m of the two gradient products
+  // the accumulated gradients: lane m = row m of the two gradient products, this
+  // thread's half of the columns (the loads are warp-wide: every branch below is
+  // uniform across a warp)
   if (!first && failed == 0) {
-    const int m = tid;
+    const int m = r;
     float v[16];
-    if (m < kW) {
-      for (int c = 0; c < kW; c += 16) {          // dW3[m][.]
-        tld16(lane_addr + cW32 + c, v);
-        for (int q = 0; q < 16; ++q) atomicAdd(&grad[oW3 + m * kW + c + q], v[q]);
+    if (quarter < 2) {                            // rows 0 .. 63: dW3, dW1, db3, db1
+      for (int c = 0; c < 32; c += 16) {
+        tld16(lane_addr + cW32 + c0 + c, v);
+        for (int q = 0; q < 16; ++q) atomicAdd(&grad[oW3 + m * kW + c0 + c + q], v[q]);
       }
-      for (int c = 0; c < kIn; c += 16) {         // dW1[m][.]
-        tld16(lane_addr + cW1 + c, v);
-        for (int q = 0; q < 16; ++q) atomicAdd(&grad[oW1 + m * kIn + c + q], v[q]);
-      }
-      tld16(lane_addr + cW32 + 2 * kW, v);
-      atomicAdd(&grad[oB3 + m], v[0]);
-      tld16(lane_addr + cW1 + kIn + kW, v);
-      atomicAdd(&grad[oB1 + m], v[0]);
-    } else {
-      const int j = m - kW;
-      for (int c = 0; c < kW; c += 16) {          // dW2[j][.]
-        tld16(lane_addr + cW32 + kW + c, v);
-        for (int q = 0; q < 16; ++q) atomicAdd(&grad[oW2 + j * kW + c + q], v[q]);
-      }
-      tld16(lane_addr + cW32 + 2 * kW, v);
-      atomicAdd(&grad[oB2 + j], v[0]);
-      // dw4, db4: row 64, lane 0 of warp 2; the loads are warp-wide (.sync.aligned),
-      // so the whole warp executes them and lane 0 keeps the values
-      if (warp == kW / 32) {
-        for (int c = 0; c < kW; c += 16) {
-          tld16(lane_addr + cW1 + kIn + c, v);
-          if (m == kW)
-            for (int q = 0; q < 16; ++q) atomicAdd(&grad[oW4 + c + q], v[q]);
-        }
+      tld16(lane_addr + cW1 + 16 * half, v);
+      for (int q = 0; q < 16; ++q) atomicAdd(&grad[oW1 + m * kIn + 16 * half + q], v[q]);
+      if (half == 0) {
+        tld16(lane_addr + cW32 + 2 * kW, v);
+        atomicAdd(&grad[oB3 + m], v[0]);
         tld16(lane_addr + cW1 + kIn + kW, v);
-        if (m == kW) atomicAdd(&grad[oB4], v[0]);
+        atomicAdd(&grad[oB1 + m], v[0]);
+      }
+    } else {                                      // rows 64 .. 127: dW2, db2; row 64 also dw4, db4
+      const int j = m - kW;
+      for (int c = 0; c < 32; c += 16) {
+        tld16(lane_addr + cW32 + kW + c0 + c, v);
+        for (int q = 0; q < 16; ++q) atomicAdd(&grad[oW2 + j * kW + c0 + c + q], v[q]);
+      }
+      if (half == 0) {
+        tld16(lane_addr + cW32 + 2 * kW, v);
+        atomicAdd(&grad[oB2 + j], v[0]);
+      }
+      if (quarter == 2) {
+        for (int c = 0; c < 32; c += 16) {
+          tld16(lane_addr + cW1 + kIn + c0 + c, v);
+          if (m == kW)
+            for (int q = 0; q < 16; ++q) atomicAdd(&grad[oW4 + c0 + c + q], v[q]);
+        }
+        if (half == 0) {
+          tld16(lane_addr + cW1 + kIn + kW, v);
+          if (m == kW) atomicAdd(&grad[oB4], v[0]);
+        }
       }
     }
   }
   for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
-  if ((tid & 31) == 0) atomicAdd(loss_acc, loss);
+  if (lane == 0 && loss != 0.0) atomicAdd(loss_acc, loss);
   if (failed) {
     if (tid == 0) atomicOr(&status[ST_TIMEOUT], 1);
     wait_phase(&bar, phase ^ 1u);   // the MMAs in flight, once more (bounded)
@@ -420,7 +457,7 @@ void launch_mlp_loss_grad(const uint16_t* desc, const float* y, int batch, const
   const int ntiles = (batch + kS - 1) / kS;
   const int grid = ntiles < sms ? ntiles : sms;   // one CTA per SM (512 tensor-memory columns each)
   cudaFuncSetAttribute(k_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-  k_train_tc<<<grid, kS, kSmem, s>>>(reinterpret_cast<const __nv_bfloat16*>(desc), y, batch, params, grad, acc,
+  k_train_tc<<<grid, kT, kSmem, s>>>(reinterpret_cast<const __nv_bfloat16*>(desc), y, batch, params, grad, acc,
                                      status);
   k_train_loss_tc<<<1, 1, 0, s>>>(acc, batch, loss);
 }

@@ -57,7 +57,8 @@ def make_dataset(prm, n_configs, cells=10, base_seed=5, precision="fp32"):
 
 
 def train(G, y, epochs=20, batch=65536, lr=1e-3, seed=7, prm=None, log_every=0):
-    """Adam on mean squared error; returns (float32 parameter tensor, losses per epoch)."""
+    """Adam on mean squared error; returns (float32 parameter tensor, losses): the
+    loss on the first batch before training, then after each epoch."""
     import torch
     dev = G.device
     ctx_prm = prm if prm is not None else W.config("vacancy2k", apip.apip_ace_basis_size, scale=6)["prm"]
@@ -71,7 +72,8 @@ def train(G, y, epochs=20, batch=65536, lr=1e-3, seed=7, prm=None, log_every=0):
     batch = min(batch, n)
     nb = n // batch
     t = 0
-    history = []
+    apip.apip_mlp_loss_grad(holder.ctx, G[:batch], y[:batch], batch, p, grad, loss)
+    history = [float(loss.item())]
     for ep in range(epochs):
         acc = 0.0
         for b in range(nb):

@@ -102,7 +102,7 @@ def test_trained_indicator_beats_csp_at_equal_ace_fraction():
     prm = W.config("vacancy2k", apip.apip_ace_basis_size)["prm"]
     G, y, ref = train.make_dataset(prm, n_configs=60, cells=10)
     params, hist = train.train(G, y, epochs=20, batch=4096, lr=1e-3, prm=prm)
-    assert hist[-1] < 0.5 * hist[0]
+    assert len(hist) == 21 and hist[-1] < 0.5 * hist[0]   # against the untrained network
     rms = {"paper": [], "learned": []}
     held_out = [k for k in range(1000, 1100) if W.training_config(k, cells=10)["temp"] < 700.0][:4]
     for k in held_out:
