@@ -299,10 +299,15 @@ apip_status apip_ace_info(apip_ctx* ctx, int64_t* out);
  *   into the context; required before APIP_LAM_LEARNED calls (APIP_ERR_STATE otherwise).
  * apip_descriptors: the 32 radial descriptors of every atom as bfloat16 (round to
  *   nearest even), desc_bf16 device [n][32] (training inputs).
- * apip_mlp_loss_grad: for a batch of descriptors (bfloat16 [batch][32]) and labels
- *   y (float32 [batch]): *loss_out = mean (g - y)^2 and grad_out[APIP_MLP_NPARAM]
- *   its gradient with respect to params (all device, float32 accumulation).  The
- *   context keeps a workspace of 1.5 KiB per sample, grown on demand.
+ * apip_mlp_loss_grad: for a batch of descriptors (bfloat16 [batch][32], rows
+ *   contiguous, the start 16-byte aligned: it is read by TMA; APIP_ERR_ARG
+ *   otherwise) and labels y (float32 [batch]): *loss_out = mean (g - y)^2 and
+ *   grad_out[APIP_MLP_NPARAM]
+ *   its gradient with respect to params (all device; bfloat16 GEMM operands,
+ *   float32 accumulation).  The gradient is the same bit for bit on every call with
+ *   the same inputs (no atomics: per-CTA sums added in a fixed order).  The context
+ *   keeps a workspace of about 42 KiB per SM of the device, allocated on the first
+ *   call.
  * apip_mlp_adam: one Adam update (beta1 0.9, beta2 0.999, eps 1e-8, bias
  *   corrected, step t >= 1) of params with grad; m and v are the moment arrays. */
 apip_status apip_set_mlp(apip_ctx* ctx, const float* params, void* stream);

@@ -874,8 +874,9 @@ apip_status apip_mlp_loss_grad(apip_ctx* ctx, const uint16_t* desc_bf16, const f
     APIP_CK(cudaMalloc(&ctx->mlp_ws, sizeof(float) * need));
     ctx->mlp_ws_cap = need;
   }
-  launch_mlp_loss_grad(desc_bf16, y, (int)batch, params, grad_out, loss_out, ctx->mlp_ws, ctx->status,
-                       (cudaStream_t)stream);
+  if (!launch_mlp_loss_grad(desc_bf16, y, (int)batch, params, grad_out, loss_out, ctx->mlp_ws, ctx->status,
+                            (cudaStream_t)stream))
+    return fail(ctx, APIP_ERR_ARG, "desc_bf16 not 16-byte aligned, or no TMA descriptor for it");
   return launch_status(ctx);
 }
 

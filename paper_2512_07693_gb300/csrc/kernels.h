@@ -214,8 +214,9 @@ int learned_tc_blocks(int n, int slots);
 void launch_mlp_frags(const float* w, void* frag, cudaStream_t s);
 size_t mlp_frag_bytes();
 // training on the tensor cores (kernels_train_tc.cu); a bounded wait that gives up
-// sets status[ST_TIMEOUT]
-void launch_mlp_loss_grad(const uint16_t* desc, const float* y, int batch, const float* params, float* grad,
+// sets status[ST_TIMEOUT].  False (nothing launched) when desc is not 16-byte
+// aligned or its TMA descriptor cannot be made.
+bool launch_mlp_loss_grad(const uint16_t* desc, const float* y, int batch, const float* params, float* grad,
                           float* loss, float* ws, int* status, cudaStream_t s);
 size_t mlp_workspace_floats(int batch);
 void launch_mlp_adam(float* p, const float* g, float* m, float* v, int t, float lr, cudaStream_t s);

@@ -8,34 +8,50 @@
 // bfloat16 and sums in float32; the elementwise steps (bias, SiLU and its
 // derivative, the output layer's dot product, the loss) are float32, the
 // pre-activations stay float32 in tensor memory, the master weights and Adam
-// are float32.
+// are float32.  The factor 0.25 of the inputs is moved onto W1 (bfloat16
+// scaling by a power of two is exact, so every product is unchanged) and onto
+// the W1 gradient at the end; the layer-1 operand is then G itself.
 //
-// A CTA of 256 threads loops over 128-sample tiles: sample r of a tile is
-// tensor-memory lane r, read by warp r / 32 (lanes) and warp r / 32 + 4, which
-// take the first and the second half of each layer's 64 columns.  Per tile, with D = A B^T on the tensor
-// cores (M = 128 rows of A, N rows of B, K the shared dimension):
-//   z1 = x0 W1^T, z2 = h1 W2^T, z3 = h2 W3^T                (forward, M = samples)
-//   dh2 = dz3 W3, dh1 = dz2 W2                              (back-propagation)
-//   [dW3 | dW2 | db3 db2] += [dz3^T ; dz2^T] [h2^T ; h1^T ; 1]^T   (one M = 128, N = 144 product
-//                                      whose diagonal blocks are the two gradients)
-//   [dW1 | dw4 | db1 db4] += [dz1^T ; dg] [x0^T ; h3^T ; 1]^T        (M = 128, N = 112)
-// the sample dimension being K of the last two, accumulated over the CTA's tiles
-// in tensor memory and added to the global gradient once at the end.  A row of
-// ones in B turns a column of D into the bias gradient.
+// A CTA of 512 threads loops over 128-sample tiles (a persistent grid of one CTA
+// per SM).  Sample r of a tile is tensor-memory lane r; warp w reads lanes
+// 32 (w % 4) .. + 31 and owns columns 16 (w / 4) .. + 15 of each 64-wide layer.
+// Per tile, with D = A B^T on the tensor cores (M = 128 rows of A, N rows of B):
+//   z1 = G (W1/4)^T, z2 = h1 W2^T, z3 = h2 W3^T           (forward, M = samples)
+//   dh2 = dz3 W3, dh1 = dz2 W2                          (back-propagation)
+//   [dW3 | dW2 | db3 db2] += [dz3 ; dz2]^T [h2 | h1 | 1]  (M = 128, N = 144, K = samples;
+//                                                       the diagonal blocks are the gradients)
+//   [dW1 | db1] += dz1^T [G | 1]                         (M = 128 of which 64 are used, N = 48)
+// The forward epilogues leave silu'(z) in the tensor-memory columns of z for the
+// back-propagation.  The gradient products accumulate over the CTA's tiles in
+// tensor memory; the output layer's gradient (dw4, db4) is summed by the
+// threads.  Each CTA writes its sums once and a second kernel adds the CTAs'
+// sums in a fixed order, so the gradient is the same bit for bit on every call.
 //
-// Tensor-memory loads (tcgen05.ld ... .sync.aligned) are executed by whole warps,
-// each warp reading its own quarter of the lanes (rows), never under a branch
-// that splits a warp.
+// Operand layout ("chunk-major", no swizzle): an operand with 128 samples is
+// stored as 8-feature chunks of 128 x 16 bytes, element (sample s, feature f) at
+//   (f / 8) * 2048 + s * 16 + (f % 8) * 2.
+// Read as a K-major operand (samples = M, features = K) its core matrices are 8
+// samples x 16 bytes, the K-adjacent ones 2048 bytes apart (leading byte offset)
+// and the 8-sample groups 128 bytes apart (stride byte offset).  Read as an
+// MN-major operand (features = M or N, samples = K) its core matrices are 8
+// samples x 8 features: the 8-sample groups (along K) 128 bytes apart (leading
+// byte offset) and the 8-feature groups 2048 bytes apart (stride byte offset).
+// So every activation a thread writes once, row by row, serves both the next
+// layer's product and the transposed gradient product; nothing is transposed.
+// The weights are stored the same way with 64 rows (chunks of 1024 bytes): K-major
+// for the forward products and, the same bytes read MN-major, transposed for the
+// back-propagation.  The per-tile inputs G arrive by TMA (four 8 x 128 boxes,
+// zero-filled past the batch), double-buffered: the next tile's load is in flight
+// while this tile computes.
 //
-// Operands live in shared memory in the no-swizzle K-major core-matrix layout:
-// element (r, k) of an R x K bfloat16 matrix at byte
-//   (r / 8) * (16 K) + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
-// i.e. 8-row x 16-byte core matrices, the K-adjacent ones 128 bytes apart (the
-// descriptor's leading byte offset) and the 8-row groups 16 K bytes apart (its
-// stride byte offset).  One thread issues the MMAs and commits them to an
-// mbarrier; every thread waits on it (a bounded wait: on time-out the kernel
-// records ST_TIMEOUT, waits once more for the MMAs in flight, frees its tensor
-// memory and returns).
+// Tensor-memory loads and stores (tcgen05.ld / st ... .sync.aligned) are executed
+// by whole warps, each warp on its own quarter of the lanes, never under a branch
+// that splits a warp.  One thread issues the MMAs and the copies; MMAs are
+// committed to an mbarrier that every thread waits on.  Every wait is bounded
+// (two seconds): on time-out the kernel records ST_TIMEOUT, waits once more for
+// the MMAs and copies in flight, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -48,80 +64,100 @@ constexpr int kIn = APIP_MLP_IN, kW = APIP_MLP_WIDTH;
 constexpr int oW1 = 0, oB1 = oW1 + kW * kIn, oW2 = oB1 + kW, oB2 = oW2 + kW * kW, oW3 = oB2 + kW,
               oB3 = oW3 + kW * kW, oW4 = oB3 + kW, oB4 = oW4 + kW;
 static_assert(oB4 + 1 == APIP_MLP_NPARAM, "parameter layout");
+static_assert(kIn == 32 && kW == 64, "the tile layout below is written for a 32-64-64-64-1 network");
 constexpr float kSin = 0.25f;
-constexpr int kS = 128;       // samples per tile = tensor-memory lanes
-constexpr int kT = 256;       // threads per CTA: two per sample
+constexpr int kS = 128;                 // samples per tile = tensor-memory lanes
+constexpr int kT = 512;                 // threads per CTA: four per sample
+constexpr int kC = 16;                  // columns of a 64-wide layer per thread
+constexpr int kChunk = kS * 16;         // bytes of an 8-feature chunk of a 128-sample operand
 
-// shared-memory operands (byte offsets; every one a multiple of 1024)
-constexpr int sX0 = 0;                        // [128][32]  A of layer 1
-constexpr int sW1 = sX0 + kS * kIn * 2;       // [64][32]   B of layer 1
-constexpr int sW2 = sW1 + kW * kIn * 2;       // [64][64]   B of layer 2
-constexpr int sW3 = sW2 + kW * kW * 2;        // [64][64]   B of layer 3
-constexpr int sW2t = sW3 + kW * kW * 2;       // [64][64]   W2^T, B of dh1
-constexpr int sW3t = sW2t + kW * kW * 2;      // [64][64]   W3^T, B of dh2
-constexpr int sH1 = sW3t + kW * kW * 2;       // [128][64]  h1 (A of layer 2), then dz3 (A of dh2)
-constexpr int sH2 = sH1 + kS * kW * 2;        // [128][64]  h2 (A of layer 3), then dz2 (A of dh1)
-constexpr int kNB = 2 * kW + 16;              // 144 rows: h2^T, h1^T, a row of ones, zeros
-constexpr int sBW = sH2 + kS * kW * 2;        // [144][128] B of the W3 / W2 gradients
-constexpr int sAW = sBW + kNB * kS * 2;       // [128][128] A of the W3 / W2 gradients: dz3^T, dz2^T
-constexpr int kNB1 = kIn + kW + 16;           // 112 rows: x0^T, h3^T, a row of ones, zeros
-constexpr int sB1 = sAW + kS * kS * 2;        // [112][128] B of the W1 / w4 gradients
-constexpr int sA1 = sB1 + kNB1 * kS * 2;      // [128][128] A of the W1 / w4 gradients: dz1^T, dg, zeros
-constexpr int sF = sA1 + kS * kS * 2;         // float32: b1, b2, b3, w4, b4 (4 kW + 4), y, g partials (3 kS)
-constexpr int kSmem = sF + (4 * kW + 4 + 3 * kS) * 4;
-static_assert(sW1 % 1024 == 0 && sH1 % 1024 == 0 && sBW % 1024 == 0 && sAW % 1024 == 0 && sB1 % 1024 == 0 &&
-                  sA1 % 1024 == 0 && sF % 16 == 0,
-              "operand alignment");
+// shared memory (byte offsets)
+constexpr int kXBuf = 6 * kChunk;       // G (4 chunks, by TMA), a chunk of ones, a chunk of zeros
+constexpr int sX = 0;                   // two input buffers
+constexpr int sWt1 = sX + 2 * kXBuf;    // W1 / 4: [4 K-chunks][64 rows][16 B]
+constexpr int sWt2 = sWt1 + kW * kIn * 2;
+constexpr int sWt3 = sWt2 + kW * kW * 2;
+constexpr int sFp = sWt3 + kW * kW * 2; // float32 b1, b2, b3, w4, b4, 3 pad
+constexpr int kNF = 4 * kW + 4;
+constexpr int sGp = sFp + kNF * 4;      // float32 [4][128]: the output layer's partial sums
+constexpr int sH2 = 48 * 1024;          // h2 | h1 | ones | zeros: B of the big gradient product
+constexpr int sH1 = sH2 + 8 * kChunk;
+constexpr int sOnes = sH1 + 8 * kChunk;
+constexpr int sDZ1 = sOnes + 2 * kChunk;  // dz1 | dz3 | dz2: A of the W1 gradient (16 chunks from dz1),
+constexpr int sDZ3 = sDZ1 + 8 * kChunk;   //   A of the big gradient product (dz3 | dz2),
+constexpr int sDZ2 = sDZ3 + 8 * kChunk;   //   A of dh2 (dz3) and of dh1 (dz2)
+constexpr int kSmem = sDZ2 + 8 * kChunk;
+constexpr int kImage = sGp - sWt1;      // bytes copied from the weight image (weights and floats)
+static_assert(sGp + kS * 4 * 4 <= sH2, "shared-memory map");
+static_assert(sWt1 % 1024 == 0 && sH2 % 1024 == 0 && sDZ1 % 1024 == 0 && kImage % 16 == 0, "alignment");
 static_assert(kSmem <= 227 * 1024, "shared memory");
 
 // tensor-memory columns (512 allocated: one CTA per SM)
-constexpr uint32_t cZ1 = 0, cZ2 = 64, cZ3 = 128, cDH = 192, cW32 = 256, cW1 = cW32 + kNB;
-static_assert(cW1 + kNB1 <= 512, "tensor memory");
+constexpr uint32_t cZ1 = 0, cZ2 = 64, cZ3 = 128, cDH = 192, cW32 = 256, cW1 = 400;
+constexpr int kNB = 2 * kW + 16, kNB1 = kIn + 16;
+static_assert(cW32 + kNB <= cW1 && cW1 + kNB1 <= 512, "tensor memory");
 
-__device__ __forceinline__ int core(int r, int k, int K) {
-  return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+// element (row, k) of a chunk-major operand with `rows` rows
+__host__ __device__ constexpr int chunk_off(int row, int k, int rows) {
+  return (k >> 3) * (rows * 16) + row * 16 + (k & 7) * 2;
 }
 
-__device__ __forceinline__ void put(unsigned char* base, int r, int k, int K, float v) {
-  *reinterpret_cast<__nv_bfloat16*>(base + core(r, k, K)) = __float2bfloat16_rn(v);
-}
-
-// Eight consecutive elements (r, k0 .. k0 + 7) of a row, k0 a multiple of 8: one
-// 16-byte store (they form one row of a core matrix).
-__device__ __forceinline__ void put8(unsigned char* base, int r, int k0, int K, const float* v) {
-  uint4 w;
-  uint32_t* u = reinterpret_cast<uint32_t*>(&w);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-    u[q] = *reinterpret_cast<const uint32_t*>(&p);
+// The weight operands (bfloat16, chunk-major, 64 rows) and the float32 biases
+// and output weights: the bytes sWt1 .. sGp of a CTA's shared memory.
+__global__ void k_train_image(const float* __restrict__ params, unsigned char* __restrict__ image) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < kW * kIn)
+    *reinterpret_cast<__nv_bfloat16*>(image + chunk_off(e / kIn, e % kIn, kW)) =
+        __float2bfloat16_rn(kSin * params[oW1 + e]);
+  if (e < kW * kW) {
+    const int o = chunk_off(e / kW, e % kW, kW);
+    *reinterpret_cast<__nv_bfloat16*>(image + (sWt2 - sWt1) + o) = __float2bfloat16_rn(params[oW2 + e]);
+    *reinterpret_cast<__nv_bfloat16*>(image + (sWt3 - sWt1) + o) = __float2bfloat16_rn(params[oW3 + e]);
   }
-  *reinterpret_cast<uint4*>(base + core(r, k0, K)) = w;
+  float* fb = reinterpret_cast<float*>(image + (sFp - sWt1));
+  if (e < kW) {
+    fb[e] = params[oB1 + e];
+    fb[kW + e] = params[oB2 + e];
+    fb[2 * kW + e] = params[oB3 + e];
+    fb[3 * kW + e] = params[oW4 + e];
+  }
+  if (e < 4) fb[4 * kW + e] = e == 0 ? params[oB4] : 0.f;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Shared-memory matrix descriptor: start address, leading byte offset 128
-// (K-adjacent core matrices), stride byte offset 16 K (8-row groups), the
-// descriptor version of this tensor-core generation, no swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, int K) {
-  return (uint64_t)((addr >> 4) & 0x3fff) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(((uint32_t)K * 16) >> 4) << 32) |
-         ((uint64_t)1 << 46);
+// An operand for the tensor cores: its shared-memory start, the leading and
+// stride byte offsets of its descriptor, and the bytes to advance per K = 16.
+struct Opnd {
+  uint32_t addr, lbo, sbo, kstep;
+};
+// 128-sample operands: K-major (samples = M) and MN-major (samples = K)
+__device__ __forceinline__ Opnd act_k(const unsigned char* p) { return {smem_u32(p), 2048u, 128u, 4096u}; }
+__device__ __forceinline__ Opnd act_mn(const unsigned char* p) { return {smem_u32(p), 128u, 2048u, 256u}; }
+// 64-row weights: K-major (forward) and MN-major (the transpose, back-propagation)
+__device__ __forceinline__ Opnd wt_k(const unsigned char* p) { return {smem_u32(p), 1024u, 128u, 2048u}; }
+__device__ __forceinline__ Opnd wt_mn(const unsigned char* p) { return {smem_u32(p), 128u, 1024u, 256u}; }
+
+// Shared-memory matrix descriptor: start address, leading and stride byte
+// offsets, the descriptor version of this tensor-core generation, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3fff) | ((uint64_t)((lbo >> 4) & 0x3fff) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3fff) << 32) | ((uint64_t)1 << 46);
 }
 
-// Instruction descriptor, kind::f16: float32 D, bfloat16 A and B, both K-major, M = 128.
-__host__ __device__ constexpr uint32_t idesc(int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// Instruction descriptor, kind::f16: float32 D, bfloat16 A and B, M = 128; bits
+// 15 / 16 select an MN-major A / B.
+__device__ __forceinline__ uint32_t idesc(int N, bool a_mn, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
 // D (tensor memory, column d) (+)= A B^T over K, in K = 16 steps (one thread).
-__device__ __forceinline__ void mma(uint32_t tmem, uint32_t d, const unsigned char* A, const unsigned char* B, int K,
-                                    int N, bool accumulate) {
-  const uint32_t a0 = smem_u32(A), b0 = smem_u32(B), id = idesc(N);
+__device__ __forceinline__ void mma(uint32_t tmem, uint32_t d, Opnd A, Opnd B, int K, uint32_t id, bool accumulate) {
   for (int kk = 0; kk < K / 16; ++kk) {
-    const uint64_t ad = sdesc(a0 + kk * 256, K), bd = sdesc(b0 + kk * 256, K);
+    const uint64_t ad = sdesc(A.addr + kk * A.kstep, A.lbo, A.sbo), bd = sdesc(B.addr + kk * B.kstep, B.lbo, B.sbo);
     const uint32_t acc = (accumulate || kk > 0) ? 1u : 0u;
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -137,7 +173,7 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
 
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
 
@@ -156,6 +192,20 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
   }
 }
 
+// G rows 128 tile .. + 127 into an input buffer: four boxes of 8 features x 128
+// samples (TMA; rows past the batch read as zeros), completing on `bar`.
+__device__ __forceinline__ void load_tile(const CUtensorMap* map, unsigned char* dst, uint64_t* bar, int tile) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(4 * kChunk)
+               : "memory");
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst + c * kChunk)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(8 * c), "r"(tile * kS), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // 16 consecutive float32 columns of this thread's tensor-memory lane.
 __device__ __forceinline__ void tld16(uint32_t addr, float* v) {
   uint32_t r[16];
@@ -169,12 +219,44 @@ __device__ __forceinline__ void tld16(uint32_t addr, float* v) {
   for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// ... and the reverse: 16 float32 values into this thread's lane.
+__device__ __forceinline__ void tst16(uint32_t addr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          addr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Sixteen float32 values as bfloat16 into row r of a chunk-major operand at
+// column c0 (a multiple of 8): two 16-byte stores.
+__device__ __forceinline__ void put16(unsigned char* base, int r, int c0, const float* v) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint4 w;
+    uint32_t* u = reinterpret_cast<uint32_t*>(&w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat162 p = __floats2bfloat162_rn(v[8 * h + 2 * q], v[8 * h + 2 * q + 1]);
+      u[q] = *reinterpret_cast<const uint32_t*>(&p);
+    }
+    *reinterpret_cast<uint4*>(base + chunk_off(r, c0 + 8 * h, kS)) = w;
+  }
+}
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
 // The logistic function (hardware exponential and approximate division: a few
 // ulp, far below the bfloat16 rounding of the GEMM operands it feeds).
 __device__ __forceinline__ float sig(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
 
 // Operands written by the threads are made visible to the tensor cores, and the
-// threads' tensor-memory reads are ordered before the next MMA.
+// threads' tensor-memory accesses are ordered before the next MMA.
 __device__ __forceinline__ void to_mma() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -183,60 +265,81 @@ __device__ __forceinline__ void to_mma() {
 }
 
 __global__ void __launch_bounds__(kT, 1)
-    k_train_tc(const __nv_bfloat16* __restrict__ desc, const float* __restrict__ y, int batch,
-               const float* __restrict__ params, float* __restrict__ grad, double* loss_acc, int* status) {
+    k_train_tc(const __grid_constant__ CUtensorMap gmap, const float* __restrict__ y, int batch,
+               const unsigned char* __restrict__ image, float* __restrict__ part, double* loss_part, int* status) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar, tbar[2];
   __shared__ uint32_t tmem_holder;
   __shared__ int failed;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quarter = warp & 3, half = warp >> 2;
+  const int quarter = warp & 3, cg = warp >> 2;
   const int r = 32 * quarter + lane;            // this thread's sample row (tensor-memory lane)
-  const int c0 = 32 * half;                     // its half of a layer's 64 columns
+  const int c0 = kC * cg;                       // its columns of a 64-wide layer
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
                  "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // weights (bfloat16 operands) and the constant rows
-  for (int e = tid; e < kW * kIn; e += kT) put(sm + sW1, e / kIn, e % kIn, kIn, params[oW1 + e]);
-  for (int e = tid; e < kW * kW; e += kT) {
-    const int rr = e / kW, k = e % kW;
-    put(sm + sW2, rr, k, kW, params[oW2 + e]);
-    put(sm + sW3, rr, k, kW, params[oW3 + e]);
-    put(sm + sW2t, k, rr, kW, params[oW2 + e]);
-    put(sm + sW3t, k, rr, kW, params[oW3 + e]);
-  }
-  for (int e = tid; e < 16 * kS; e += kT) {
-    const int rr = e / kS, ss = e % kS;
-    put(sm + sBW, 2 * kW + rr, ss, kS, rr == 0 ? 1.f : 0.f);
-    put(sm + sB1, kIn + kW + rr, ss, kS, rr == 0 ? 1.f : 0.f);
-  }
-  for (int e = tid; e < 63 * kS; e += kT) put(sm + sA1, kW + 1 + e / kS, e % kS, kS, 0.f);
-  float* fb = reinterpret_cast<float*>(sm + sF);
-  float* ys = fb + 4 * kW + 4;                  // y of the tile's samples
-  float* gp = ys + kS;                          // [2][kS] partial sums of the output layer
-  for (int k = tid; k < kW; k += kT) {
-    fb[k] = params[oB1 + k];
-    fb[kW + k] = params[oB2 + k];
-    fb[2 * kW + k] = params[oB3 + k];
-    fb[3 * kW + k] = params[oW4 + k];
-  }
   if (tid == 0) {
-    fb[4 * kW] = params[oB4];
     failed = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tbar[1])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // the constant chunks (16-byte words): a chunk of ones (feature 0 of every
+  // sample 1, for the bias gradients) and a chunk of zeros, after each input
+  // buffer and after h1
+  {
+    const uint4 one = make_uint4(0x3f80u, 0u, 0u, 0u), zero = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < 2 * kS; e += kT) {
+      const int s = e & (kS - 1), wch = e >> 7;
+      const uint4 v = wch == 0 ? one : zero;
+      *reinterpret_cast<uint4*>(sm + sX + 4 * kChunk + wch * kChunk + s * 16) = v;
+      *reinterpret_cast<uint4*>(sm + sX + kXBuf + 4 * kChunk + wch * kChunk + s * 16) = v;
+      *reinterpret_cast<uint4*>(sm + sOnes + wch * kChunk + s * 16) = v;
+    }
+  }
+  // everything below reads what the previous kernel (the weight image) wrote
+  pdl_begin();
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(image);
+    uint4* dst = reinterpret_cast<uint4*>(sm + sWt1);
+    for (int e = tid; e < kImage / 16; e += kT) dst[e] = src[e];
+  }
+  const int ntiles = (batch + kS - 1) / kS;
+  const int stride = gridDim.x;
+  // input copies (thread 0 only): issued and waited-for counts per buffer; the
+  // k-th copy into a buffer completes phase k of its barrier
+  uint32_t tissued0 = 0, tissued1 = 0, twaited0 = 0, twaited1 = 0;
+  auto tload = [&](int b, int tile) {
+    load_tile(&gmap, sm + sX + b * kXBuf, &tbar[b], tile);
+    ++(b ? tissued1 : tissued0);
+  };
+  auto twait = [&](int b) -> bool {
+    uint32_t& k = b ? twaited1 : twaited0;
+    return wait_phase(&tbar[b], k++ & 1u);
+  };
+  __syncthreads();   // barriers initialised
+  if (tid == 0) {
+    tload(0, blockIdx.x);
+    if (blockIdx.x + stride < ntiles) tload(1, blockIdx.x + stride);
   }
   to_mma();
   const uint32_t tm = tmem_holder;
   const uint32_t lane_addr = tm + ((uint32_t)(32 * quarter) << 16);   // this warp's quarter of the lanes
+  const float* fb = reinterpret_cast<const float*>(sm + sFp);
+  float* gp = reinterpret_cast<float*>(sm + sGp);
   const float b4 = fb[4 * kW];
   const float inv_batch = 1.f / (float)batch;
+  const uint32_t id64 = idesc(kW, false, false), id_bwd = idesc(kW, false, true);
+  const uint32_t id_w32 = idesc(kNB, true, true), id_w1 = idesc(kNB1, true, true);
   uint32_t phase = 0;
   double loss = 0.0;
+  float aw4[kC], ab4 = 0.f;   // this thread's share of dw4 (its columns) and of db4 (cg == 0)
+#pragma unroll
+  for (int q = 0; q < kC; ++q) aw4[q] = 0.f;
   bool first = true;
-  const int ntiles = (batch + kS - 1) / kS;
 
   // one MMA group: issued by thread 0, then every thread waits for it
   auto run = [&](auto&& issue) -> bool {
@@ -251,215 +354,260 @@ __global__ void __launch_bounds__(kT, 1)
     __syncthreads();
     return failed == 0;
   };
-  // one layer's epilogue over this thread's 32 columns: f(column, z) -> value
-  // stored in row r of the A operand `rowbuf` (may be null) and, transposed, in
-  // rows tbase + column of `tbuf`
-  // (tbase + c0 and c0 are multiples of 8: the addresses are a per-thread base
-  // plus compile-time offsets)
-  auto epilogue = [&](uint32_t col, unsigned char* rowbuf, unsigned char* tbuf, int tbase, auto&& f) {
-    unsigned char* tb = tbuf + core(tbase + c0, r, kS);
-    unsigned char* rb = rowbuf ? rowbuf + core(r, c0, kW) : nullptr;
+  // one forward layer's epilogue on this thread's 16 columns: h = silu(z + b)
+  // into row r of `dst`, silu'(z + b) back into the tensor-memory columns of z
+  auto forward = [&](uint32_t col, const float* bias, unsigned char* dst) {
+    float z[kC], d[kC];
+    tld16(lane_addr + col + c0, z);
 #pragma unroll
-    for (int c = 0; c < 32; c += 16) {
-      float z[16], o[16];
-      tld16(lane_addr + col + c0 + c, z);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        o[q] = f(c0 + c + q, z[q]);
-        const int j = c + q;
-        *reinterpret_cast<__nv_bfloat16*>(tb + (j >> 3) * (kS * 16) + (j & 7) * 16) = __float2bfloat16_rn(o[q]);
-      }
-      if (rb) {
-#pragma unroll
-        for (int h8 = 0; h8 < 2; ++h8) {
-          uint4 w;
-          uint32_t* u = reinterpret_cast<uint32_t*>(&w);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const __nv_bfloat162 p = __floats2bfloat162_rn(o[8 * h8 + 2 * q], o[8 * h8 + 2 * q + 1]);
-            u[q] = *reinterpret_cast<const uint32_t*>(&p);
-          }
-          *reinterpret_cast<uint4*>(rb + ((c + 8 * h8) >> 3) * 128) = w;
-        }
-      }
+    for (int q = 0; q < kC; ++q) {
+      const float zz = z[q] + bias[c0 + q];
+      const float sg = sig(zz);
+      d[q] = sg * (1.f + zz * (1.f - sg));
+      z[q] = zz * sg;
     }
+    put16(dst, r, c0, z);
+    tst16(lane_addr + col + c0, d);
+  };
+  // one backward epilogue: dz = dh silu'(z) (zero for samples past the batch)
+  auto backward = [&](uint32_t dcol, unsigned char* dst, bool valid) {
+    float dh[kC], d[kC];
+    tld16(lane_addr + cDH + c0, dh);
+    tld16(lane_addr + dcol + c0, d);
+#pragma unroll
+    for (int q = 0; q < kC; ++q) dh[q] = valid ? dh[q] * d[q] : 0.f;
+    put16(dst, r, c0, dh);
   };
 
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  // layer 1 of the first tile
+  bool ok = run([&] {
+    if (!twait(0)) failed = 1;
+    else mma(tm, cZ1, act_k(sm + sX), wt_k(sm + sWt1), kIn, id64, false);
+  });
+  for (int it = 0; ok; ++it) {
+    const int tile = blockIdx.x + it * stride;
+    if (tile >= ntiles) break;
+    const int b = it & 1;
     const int s = tile * kS + r;
     const bool valid = s < batch;
-    // inputs: x0 = 0.25 G (exact in bfloat16), features 16 half .. of row r of the
-    // layer-1 A and of column r of the W1-gradient B
+    const float yv = valid ? y[s] : 0.f;
+    forward(cZ1, fb, sm + sH1);
+    to_mma();
+    if (!run([&] { mma(tm, cZ2, act_k(sm + sH1), wt_k(sm + sWt2), kW, id64, false); })) break;
+    forward(cZ2, fb + kW, sm + sH2);
+    to_mma();
+    if (!run([&] { mma(tm, cZ3, act_k(sm + sH2), wt_k(sm + sWt3), kW, id64, false); })) break;
+    // layer 3 and the output g = w4 . h3 + b4 (the four column groups' partial sums
+    // through shared memory), then dz3 = dg w4 silu'(z3)
     {
-      const uint4* src = reinterpret_cast<const uint4*>(desc + (size_t)(valid ? s : 0) * kIn) + 2 * half;
-      float x[16];
+      float h3[kC], d3[kC], gh = 0.f;
+      tld16(lane_addr + cZ3 + c0, h3);
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const uint4 v = valid ? src[q] : make_uint4(0u, 0u, 0u, 0u);
-        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&v);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          x[8 * q + e] = kSin * __bfloat162float(h[e]);
-          put(sm + sB1, 16 * half + 8 * q + e, r, kS, x[8 * q + e]);
-        }
+      for (int q = 0; q < kC; ++q) {
+        const float zz = h3[q] + fb[2 * kW + c0 + q];
+        const float sg = sig(zz);
+        d3[q] = sg * (1.f + zz * (1.f - sg));
+        h3[q] = zz * sg;
+        gh = fmaf(fb[3 * kW + c0 + q], h3[q], gh);
       }
-      put8(sm + sX0, r, 16 * half, kIn, x);
-      put8(sm + sX0, r, 16 * half + 8, kIn, x + 8);
-      if (half == 0) ys[r] = valid ? y[s] : 0.f;
+      gp[cg * kS + r] = gh;
+      __syncthreads();
+      const float g = b4 + ((gp[r] + gp[kS + r]) + (gp[2 * kS + r] + gp[3 * kS + r]));
+      const float res = valid ? g - yv : 0.f;
+      const float dg = 2.f * res * inv_batch;
+      const float dgb = bf16r(dg);
+      if (cg == 0) {
+        loss += (double)res * (double)res;
+        ab4 += dgb;
+      }
+#pragma unroll
+      for (int q = 0; q < kC; ++q) {
+        aw4[q] = fmaf(dgb, bf16r(h3[q]), aw4[q]);
+        d3[q] = dg * fb[3 * kW + c0 + q] * d3[q];
+      }
+      put16(sm + sDZ3, r, c0, d3);
     }
     to_mma();
-    if (!run([&] { mma(tm, cZ1, sm + sX0, sm + sW1, kIn, kW, false); })) break;
-    // layer 1: h1 = silu(z1 + b1) -> A of layer 2 and rows 64.. of the W-gradient B (h1^T)
-    epilogue(cZ1, sm + sH1, sm + sBW, kW, [&](int c, float z) {
-      const float zz = z + fb[c];
-      return zz * sig(zz);
-    });
+    if (!run([&] { mma(tm, cDH, act_k(sm + sDZ3), wt_mn(sm + sWt3), kW, id_bwd, false); })) break;
+    backward(cZ2, sm + sDZ2, valid);
     to_mma();
-    if (!run([&] { mma(tm, cZ2, sm + sH1, sm + sW2, kW, kW, false); })) break;
-    // layer 2: h2 -> A of layer 3 and rows 0.. of the W-gradient B (h2^T)
-    epilogue(cZ2, sm + sH2, sm + sBW, 0, [&](int c, float z) {
-      const float zz = z + fb[kW + c];
-      return zz * sig(zz);
-    });
+    if (!run([&] { mma(tm, cDH, act_k(sm + sDZ2), wt_mn(sm + sWt2), kW, id_bwd, false); })) break;
+    backward(cZ1, sm + sDZ1, valid);
     to_mma();
-    if (!run([&] { mma(tm, cZ3, sm + sH2, sm + sW3, kW, kW, false); })) break;
-    // layer 3 and the output: g = w4 . h3 + b4, its two halves summed through
-    // shared memory; h3^T -> rows 32.. of the W1-gradient B
-    float gh = 0.f;
-    epilogue(cZ3, nullptr, sm + sB1, kIn, [&](int c, float z) {
-      const float zz = z + fb[2 * kW + c];
-      const float h = zz * sig(zz);
-      gh = fmaf(fb[3 * kW + c], h, gh);
-      return h;
-    });
-    gp[half * kS + r] = gh;
-    __syncthreads();
-    const float g = b4 + gp[r] + gp[kS + r];
-    const float res = valid ? g - ys[r] : 0.f;
-    if (half == 0) {
-      loss += (double)res * (double)res;
-      put(sm + sA1, kW, r, kS, 2.f * res * inv_batch);   // row 64 of the W1-gradient A: dg
-    }
-    const float dg = 2.f * res * inv_batch;
-    // dz3 = dg w4 silu'(z3) -> A of dh2 (the h1 buffer) and rows 0.. of the W-gradient A (dz3^T)
-    epilogue(cZ3, sm + sH1, sm + sAW, 0, [&](int c, float z) {
-      const float zz = z + fb[2 * kW + c];
-      const float sg = sig(zz);
-      return dg * fb[3 * kW + c] * (sg * (1.f + zz * (1.f - sg)));
-    });
-    to_mma();
-    if (!run([&] { mma(tm, cDH, sm + sH1, sm + sW3t, kW, kW, false); })) break;
-    // dz2 = dh2 silu'(z2) -> A of dh1 (the h2 buffer) and rows 64.. of the W-gradient A
-    {
-      float zs[32];
-      tld16(lane_addr + cZ2 + c0, zs);
-      tld16(lane_addr + cZ2 + c0 + 16, zs + 16);
-      epilogue(cDH, sm + sH2, sm + sAW, kW, [&](int c, float dh) {
-        const float zz = zs[c - c0] + fb[kW + c];
-        const float sg = sig(zz);
-        return valid ? dh * (sg * (1.f + zz * (1.f - sg))) : 0.f;
-      });
-    }
-    to_mma();
-    if (!run([&] { mma(tm, cDH, sm + sH2, sm + sW2t, kW, kW, false); })) break;
-    // dz1 = dh1 silu'(z1) -> rows 0.. of the W1-gradient A
-    {
-      float zs[32];
-      tld16(lane_addr + cZ1 + c0, zs);
-      tld16(lane_addr + cZ1 + c0 + 16, zs + 16);
-      epilogue(cDH, nullptr, sm + sA1, 0, [&](int c, float dh) {
-        const float zz = zs[c - c0] + fb[c];
-        const float sg = sig(zz);
-        return valid ? dh * (sg * (1.f + zz * (1.f - sg))) : 0.f;
-      });
-    }
-    to_mma();
+    // the gradient products of this tile, and layer 1 of the next tile (its input
+    // buffer is the other one; its output columns hold nothing needed any more)
     const bool acc = !first;
-    if (!run([&] {
-          mma(tm, cW32, sm + sAW, sm + sBW, kS, kNB, acc);
-          mma(tm, cW1, sm + sA1, sm + sB1, kS, kNB1, acc);
-        }))
-      break;
+    const bool next = tile + stride < ntiles;
+    ok = run([&] {
+      mma(tm, cW32, act_mn(sm + sDZ3), act_mn(sm + sH2), kS, id_w32, acc);
+      mma(tm, cW1, act_mn(sm + sDZ1), act_mn(sm + sX + b * kXBuf), kS, id_w1, acc);
+      if (next) {
+        if (!twait(b ^ 1)) failed = 1;
+        else mma(tm, cZ1, act_k(sm + sX + (b ^ 1) * kXBuf), wt_k(sm + sWt1), kIn, id64, false);
+      }
+    });
     first = false;
+    // this tile's input buffer is free again: the tile after next goes there
+    if (ok && tid == 0 && tile + 2 * stride < ntiles) tload(b, tile + 2 * stride);
   }
-  // the accumulated gradients: lane m = row m of the two gradient products, this
-  // thread's half of the columns (the loads are warp-wide: every branch below is
-  // uniform across a warp)
-  if (!first && failed == 0) {
+  // this CTA's gradient sums, part[blockIdx.x][parameter]: lane m = row m of the
+  // two gradient products; zero if the CTA had no tile or a wait gave up.  Every
+  // branch below is uniform across a warp.
+  float* out = part + (size_t)blockIdx.x * APIP_MLP_NPARAM;
+  const bool have = !first && failed == 0;
+  {
     const int m = r;
     float v[16];
-    if (quarter < 2) {                            // rows 0 .. 63: dW3, dW1, db3, db1
-      for (int c = 0; c < 32; c += 16) {
-        tld16(lane_addr + cW32 + c0 + c, v);
-        for (int q = 0; q < 16; ++q) atomicAdd(&grad[oW3 + m * kW + c0 + c + q], v[q]);
+    if (quarter < 2) {                            // rows 0 .. 63: dW3, db3; dW1, db1
+      if (have) tld16(lane_addr + cW32 + c0, v);
+      for (int q = 0; q < 16; ++q) out[oW3 + m * kW + c0 + q] = have ? v[q] : 0.f;
+      if (cg < 2) {
+        if (have) tld16(lane_addr + cW1 + c0, v);
+        for (int q = 0; q < 16; ++q) out[oW1 + m * kIn + c0 + q] = have ? kSin * v[q] : 0.f;
+      } else if (cg == 2) {
+        if (have) tld16(lane_addr + cW32 + 2 * kW, v);
+        out[oB3 + m] = have ? v[0] : 0.f;
+      } else {
+        if (have) tld16(lane_addr + cW1 + kIn, v);
+        out[oB1 + m] = have ? v[0] : 0.f;
       }
-      tld16(lane_addr + cW1 + 16 * half, v);
-      for (int q = 0; q < 16; ++q) atomicAdd(&grad[oW1 + m * kIn + 16 * half + q], v[q]);
-      if (half == 0) {
-        tld16(lane_addr + cW32 + 2 * kW, v);
-        atomicAdd(&grad[oB3 + m], v[0]);
-        tld16(lane_addr + cW1 + kIn + kW, v);
-        atomicAdd(&grad[oB1 + m], v[0]);
-      }
-    } else {                                      // rows 64 .. 127: dW2, db2; row 64 also dw4, db4
+    } else {                                      // rows 64 .. 127: dW2, db2
       const int j = m - kW;
-      for (int c = 0; c < 32; c += 16) {
-        tld16(lane_addr + cW32 + kW + c0 + c, v);
-        for (int q = 0; q < 16; ++q) atomicAdd(&grad[oW2 + j * kW + c0 + c + q], v[q]);
-      }
-      if (half == 0) {
-        tld16(lane_addr + cW32 + 2 * kW, v);
-        atomicAdd(&grad[oB2 + j], v[0]);
-      }
-      if (quarter == 2) {
-        for (int c = 0; c < 32; c += 16) {
-          tld16(lane_addr + cW1 + kIn + c0 + c, v);
-          if (m == kW)
-            for (int q = 0; q < 16; ++q) atomicAdd(&grad[oW4 + c0 + c + q], v[q]);
-        }
-        if (half == 0) {
-          tld16(lane_addr + cW1 + kIn + kW, v);
-          if (m == kW) atomicAdd(&grad[oB4], v[0]);
-        }
+      if (have) tld16(lane_addr + cW32 + kW + c0, v);
+      for (int q = 0; q < 16; ++q) out[oW2 + j * kW + c0 + q] = have ? v[q] : 0.f;
+      if (cg == 0) {
+        if (have) tld16(lane_addr + cW32 + 2 * kW, v);
+        out[oB2 + j] = have ? v[0] : 0.f;
       }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
-  if (lane == 0 && loss != 0.0) atomicAdd(loss_acc, loss);
-  if (failed) {
-    if (tid == 0) atomicOr(&status[ST_TIMEOUT], 1);
-    wait_phase(&bar, phase ^ 1u);   // the MMAs in flight, once more (bounded)
+  // dw4, db4 and the loss: warp sums, then the warps in a fixed order
+  {
+    __shared__ float red[kT / 32][kC + 1];
+    __shared__ double lred[kT / 32];
+#pragma unroll
+    for (int q = 0; q < kC; ++q)
+      for (int o = 16; o > 0; o >>= 1) aw4[q] += __shfl_xor_sync(0xffffffffu, aw4[q], o);
+    for (int o = 16; o > 0; o >>= 1) {
+      ab4 += __shfl_xor_sync(0xffffffffu, ab4, o);
+      loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    }
+    if (lane == 0) {
+      for (int q = 0; q < kC; ++q) red[warp][q] = aw4[q];
+      red[warp][kC] = ab4;
+      lred[warp] = loss;
+    }
+    __syncthreads();
+    if (tid < kW) {                               // column tid: the warps 4 (tid / 16) + quarter
+      const int g4 = tid / kC, q = tid % kC;
+      const float t = (red[4 * g4][q] + red[4 * g4 + 1][q]) + (red[4 * g4 + 2][q] + red[4 * g4 + 3][q]);
+      out[oW4 + tid] = have ? t : 0.f;
+    } else if (tid == kW) {
+      const float t = (red[0][kC] + red[1][kC]) + (red[2][kC] + red[3][kC]);
+      out[oB4] = have ? t : 0.f;
+    } else if (tid == kW + 1) {
+      double t = 0.0;
+      for (int w = 0; w < kT / 32; ++w) t += lred[w];
+      loss_part[blockIdx.x] = t;
+    }
+  }
+  if (failed && tid == 0) {
+    atomicOr(&status[ST_TIMEOUT], 1);
+    // the MMAs and input copies still in flight, once more (bounded)
+    wait_phase(&bar, phase ^ 1u);
+    while (twaited0 < tissued0 && twait(0)) {}
+    while (twaited1 < tissued1 && twait(1)) {}
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(512));
 }
 
-__global__ void k_train_loss_tc(const double* loss_acc, int batch, float* loss_out) {
-  *loss_out = (float)(*loss_acc / batch);
+// grad[p] = sum over the CTAs of part[b][p] in a fixed order (eight interleaved
+// partial sums, then those in order); the loss likewise.  32 parameters per block.
+constexpr int kRedWarps = 8;
+__global__ void __launch_bounds__(32 * kRedWarps)
+    k_train_reduce(const float* __restrict__ part, const double* __restrict__ loss_part, int nb, int batch,
+                   float* __restrict__ grad, float* __restrict__ loss_out) {
+  pdl_begin();
+  __shared__ float red[kRedWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + lane;
+  float acc = 0.f;
+  if (p < APIP_MLP_NPARAM)
+    for (int b = w; b < nb; b += kRedWarps) acc += part[(size_t)b * APIP_MLP_NPARAM + p];
+  red[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && p < APIP_MLP_NPARAM) {
+    float t = 0.f;
+    for (int k = 0; k < kRedWarps; ++k) t += red[k][lane];
+    grad[p] = t;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 32) {
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += loss_part[b];
+    *loss_out = (float)(t / batch);
+  }
+}
+
+int train_grid_max() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+size_t loss_floats(int g) { return (2 * (size_t)g + 3) / 4 * 4; }
+constexpr size_t kImageFloats = kImage / 4;
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
 }
 
 }  // namespace
 
+// Workspace (floats, from a 16-byte aligned base): the loss partials (float64, one
+// per CTA, padded to 16 bytes), the weight image, the CTAs' gradient sums.
 size_t mlp_workspace_floats(int batch) {
   (void)batch;
-  return 4;   // the float64 loss accumulator
+  const int g = train_grid_max();
+  return loss_floats(g) + kImageFloats + (size_t)g * APIP_MLP_NPARAM;
 }
 
-void launch_mlp_loss_grad(const uint16_t* desc, const float* y, int batch, const float* params, float* grad,
+bool launch_mlp_loss_grad(const uint16_t* desc, const float* y, int batch, const float* params, float* grad,
                           float* loss, float* ws, int* status, cudaStream_t s) {
-  double* acc = reinterpret_cast<double*>(ws);
-  cudaMemsetAsync(grad, 0, sizeof(float) * APIP_MLP_NPARAM, s);
-  cudaMemsetAsync(acc, 0, sizeof(double), s);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  PFN_cuTensorMapEncodeTiled_v12000 encode = encode_tiled();
+  if (!encode || (reinterpret_cast<uintptr_t>(desc) & 15u) != 0) return false;
+  // G as a [batch][32] bfloat16 tensor read in boxes of 8 features x 128 samples
+  CUtensorMap gmap;
+  const cuuint64_t dims[2] = {(cuuint64_t)kIn, (cuuint64_t)batch};
+  const cuuint64_t strides[1] = {(cuuint64_t)kIn * 2};
+  const cuuint32_t box[2] = {8u, (cuuint32_t)kS};
+  const cuuint32_t estr[2] = {1u, 1u};
+  if (encode(&gmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(desc), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  const int gmax = train_grid_max();
+  double* loss_part = reinterpret_cast<double*>(ws);
+  unsigned char* image = reinterpret_cast<unsigned char*>(ws + loss_floats(gmax));
+  float* part = ws + loss_floats(gmax) + kImageFloats;
+  k_train_image<<<(kW * kW + 255) / 256, 256, 0, s>>>(params, image);
   const int ntiles = (batch + kS - 1) / kS;
-  const int grid = ntiles < sms ? ntiles : sms;   // one CTA per SM (512 tensor-memory columns each)
+  const int grid = ntiles < gmax ? ntiles : gmax;   // one CTA per SM (512 tensor-memory columns each)
   cudaFuncSetAttribute(k_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-  k_train_tc<<<grid, kT, kSmem, s>>>(reinterpret_cast<const __nv_bfloat16*>(desc), y, batch, params, grad, acc,
-                                     status);
-  k_train_loss_tc<<<1, 1, 0, s>>>(acc, batch, loss);
+  launch_pdl(k_train_tc, grid, kT, kSmem, s, gmap, y, batch, (const unsigned char*)image, part, loss_part, status);
+  launch_pdl(k_train_reduce, (APIP_MLP_NPARAM + 31) / 32, 32 * kRedWarps, 0, s, (const float*)part,
+             (const double*)loss_part, grid, batch, grad, loss);
+  return true;
 }
 
 }  // namespace apip
