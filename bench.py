@@ -38,6 +38,12 @@ WORKLOAD = "void250k"
 METRIC = "atom-steps/s adaptive EAM+ACE vs all-ACE on 1 GB300; NVE drift eV/atom/ps"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
+FALLBACK_BF16 = 1900.0
+
+
+def measured_peaks():
+    """The measured peaks of this machine's GPUs (empty if the file is absent)."""
+    return json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2, written between timed steps
 # DRAM bytes (read + write) per launch of the step's dominant kernels on this
 # workload from an ncu capture, with the commit of the kernel's source it was
@@ -394,10 +400,23 @@ def extra_training(torch, W, apip, configs=400, epochs=20, batch=65536):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     na = int(len(y))
+    del G, y
+    # the training step alone (loss and gradient, then Adam), device-timed on a
+    # synthetic batch of the same size: its roofline is the bf16 tensor pipe
+    us, tf = train.step_time(batch, steps=50, warmup=5)
+    peaks = measured_peaks()
+    peak = peaks.get("bf16_tflops", FALLBACK_BF16)
     line = {"workload": f"learned-indicator training, {configs} of the 50 000 configurations", "atoms": na,
             "epochs": epochs, "label_and_descriptor_s": t1 - t0, "label_atoms_per_s": na / (t1 - t0),
             "training_s": t2 - t1, "training_atom_epochs_per_s": na * epochs / (t2 - t1),
-            "loss_first_last": [hist[0], hist[-1]]}
+            "loss_first_last": [hist[0], hist[-1]],
+            "step": {"batch": batch, "us_per_step": us, "samples_per_s": batch / (us * 1e-6),
+                     "flop_per_sample": train.FLOP_PER_SAMPLE,
+                     "roofline": {"kernel": "k_train_tc (+ k_train_reduce, k_adam)", "bound": "tensor",
+                                  "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                                  "frac": tf / peak if peak else None, "traffic": None,
+                                  "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured, burst)"
+                                  if "bf16_tflops" in peaks else "fallback"}}}
     return line, params
 
 

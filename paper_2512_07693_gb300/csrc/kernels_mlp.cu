@@ -584,6 +584,7 @@ __global__ void k_cast_params(const float* src, T* dst) {
 
 // ------------------------------------------------------------------ Adam
 __global__ void k_adam(float* p, const float* g, float* m, float* v, int t, float lr) {
+  pdl_begin();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= APIP_MLP_NPARAM) return;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
@@ -652,7 +653,7 @@ template <typename T> void launch_cast_params(const float* src, T* dst, cudaStre
 }
 
 void launch_mlp_adam(float* p, const float* g, float* m, float* v, int t, float lr, cudaStream_t s) {
-  k_adam<<<(APIP_MLP_NPARAM + 255) / 256, 256, 0, s>>>(p, g, m, v, t, lr);
+  launch_pdl(k_adam, (APIP_MLP_NPARAM + 255) / 256, 256, 0, s, p, g, m, v, t, lr);
 }
 
 template void launch_pass1_learned<float>(const Args<float>&, cudaStream_t);

@@ -40,16 +40,18 @@
 // layer's product and the transposed gradient product; nothing is transposed.
 // The weights are stored the same way with 64 rows (chunks of 1024 bytes): K-major
 // for the forward products and, the same bytes read MN-major, transposed for the
-// back-propagation.  The per-tile inputs G arrive by TMA (four 8 x 128 boxes,
-// zero-filled past the batch), double-buffered: the next tile's load is in flight
-// while this tile computes.
+// back-propagation; each CTA converts them from the float32 parameters once.  The
+// per-tile inputs G arrive by TMA (four 8 x 128 boxes, zero-filled past the
+// batch), double-buffered: the next tile's load is in flight while this tile
+// computes.
 //
 // Tensor-memory loads and stores (tcgen05.ld / st ... .sync.aligned) are executed
 // by whole warps, each warp on its own quarter of the lanes, never under a branch
 // that splits a warp.  One thread issues the MMAs and the copies; MMAs are
-// committed to an mbarrier that every thread waits on.  Every wait is bounded
-// (two seconds): on time-out the kernel records ST_TIMEOUT, waits once more for
-// the MMAs and copies in flight, frees its tensor memory and returns.
+// committed to an mbarrier that every thread waits on itself.  Every wait is
+// bounded (two seconds): on time-out the kernel records ST_TIMEOUT, stops issuing,
+// leaves the tile loop at the next CTA barrier, waits once more for the MMAs and
+// copies in flight, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -65,6 +67,7 @@ constexpr int oW1 = 0, oB1 = oW1 + kW * kIn, oW2 = oB1 + kW, oB2 = oW2 + kW * kW
               oB3 = oW3 + kW * kW, oW4 = oB3 + kW, oB4 = oW4 + kW;
 static_assert(oB4 + 1 == APIP_MLP_NPARAM, "parameter layout");
 static_assert(kIn == 32 && kW == 64, "the tile layout below is written for a 32-64-64-64-1 network");
+static_assert((kW * kIn) % 512 == 0 && (kW * kW) % 512 == 0 && 4 * kW + 4 <= 512, "weight conversion");
 constexpr float kSin = 0.25f;
 constexpr int kS = 128;                 // samples per tile = tensor-memory lanes
 constexpr int kT = 512;                 // threads per CTA: four per sample
@@ -87,9 +90,11 @@ constexpr int sDZ1 = sOnes + 2 * kChunk;  // dz1 | dz3 | dz2: A of the W1 gradie
 constexpr int sDZ3 = sDZ1 + 8 * kChunk;   //   A of the big gradient product (dz3 | dz2),
 constexpr int sDZ2 = sDZ3 + 8 * kChunk;   //   A of dh2 (dz3) and of dh1 (dz2)
 constexpr int kSmem = sDZ2 + 8 * kChunk;
-constexpr int kImage = sGp - sWt1;      // bytes copied from the weight image (weights and floats)
 static_assert(sGp + kS * 4 * 4 <= sH2, "shared-memory map");
-static_assert(sWt1 % 1024 == 0 && sH2 % 1024 == 0 && sDZ1 % 1024 == 0 && kImage % 16 == 0, "alignment");
+static_assert(sWt1 % 1024 == 0 && sH2 % 1024 == 0 && sDZ1 % 1024 == 0 && sFp % 16 == 0, "alignment");
+// per-CTA gradient sums in the workspace: the parameters padded to 16 bytes
+constexpr int kPart = (APIP_MLP_NPARAM + 3) / 4 * 4;
+static_assert(oW1 % 4 == 0 && oW2 % 4 == 0 && oW3 % 4 == 0, "16-byte aligned weight rows");
 static_assert(kSmem <= 227 * 1024, "shared memory");
 
 // tensor-memory columns (512 allocated: one CTA per SM)
@@ -100,28 +105,6 @@ static_assert(cW32 + kNB <= cW1 && cW1 + kNB1 <= 512, "tensor memory");
 // element (row, k) of a chunk-major operand with `rows` rows
 __host__ __device__ constexpr int chunk_off(int row, int k, int rows) {
   return (k >> 3) * (rows * 16) + row * 16 + (k & 7) * 2;
-}
-
-// The weight operands (bfloat16, chunk-major, 64 rows) and the float32 biases
-// and output weights: the bytes sWt1 .. sGp of a CTA's shared memory.
-__global__ void k_train_image(const float* __restrict__ params, unsigned char* __restrict__ image) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < kW * kIn)
-    *reinterpret_cast<__nv_bfloat16*>(image + chunk_off(e / kIn, e % kIn, kW)) =
-        __float2bfloat16_rn(kSin * params[oW1 + e]);
-  if (e < kW * kW) {
-    const int o = chunk_off(e / kW, e % kW, kW);
-    *reinterpret_cast<__nv_bfloat16*>(image + (sWt2 - sWt1) + o) = __float2bfloat16_rn(params[oW2 + e]);
-    *reinterpret_cast<__nv_bfloat16*>(image + (sWt3 - sWt1) + o) = __float2bfloat16_rn(params[oW3 + e]);
-  }
-  float* fb = reinterpret_cast<float*>(image + (sFp - sWt1));
-  if (e < kW) {
-    fb[e] = params[oB1 + e];
-    fb[kW + e] = params[oB2 + e];
-    fb[2 * kW + e] = params[oB3 + e];
-    fb[3 * kW + e] = params[oW4 + e];
-  }
-  if (e < 4) fb[4 * kW + e] = e == 0 ? params[oB4] : 0.f;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -266,7 +249,7 @@ __device__ __forceinline__ void to_mma() {
 
 __global__ void __launch_bounds__(kT, 1)
     k_train_tc(const __grid_constant__ CUtensorMap gmap, const float* __restrict__ y, int batch,
-               const unsigned char* __restrict__ image, float* __restrict__ part, double* loss_part, int* status) {
+               const float* __restrict__ params, float* __restrict__ part, double* loss_part, int* status) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t bar, tbar[2];
   __shared__ uint32_t tmem_holder;
@@ -300,13 +283,6 @@ __global__ void __launch_bounds__(kT, 1)
       *reinterpret_cast<uint4*>(sm + sOnes + wch * kChunk + s * 16) = v;
     }
   }
-  // everything below reads what the previous kernel (the weight image) wrote
-  pdl_begin();
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(image);
-    uint4* dst = reinterpret_cast<uint4*>(sm + sWt1);
-    for (int e = tid; e < kImage / 16; e += kT) dst[e] = src[e];
-  }
   const int ntiles = (batch + kS - 1) / kS;
   const int stride = gridDim.x;
   // input copies (thread 0 only): issued and waited-for counts per buffer; the
@@ -320,10 +296,31 @@ __global__ void __launch_bounds__(kT, 1)
     uint32_t& k = b ? twaited1 : twaited0;
     return wait_phase(&tbar[b], k++ & 1u);
   };
-  __syncthreads();   // barriers initialised
+  // everything below may read what the previous kernel wrote
+  pdl_begin();
   if (tid == 0) {
     tload(0, blockIdx.x);
     if (blockIdx.x + stride < ntiles) tload(1, blockIdx.x + stride);
+  }
+  // the weight operands from the float32 parameters (coalesced reads): W1 / 4, W2,
+  // W3 as bfloat16 in the chunk-major layout with 64 rows; biases and w4 as float32
+#pragma unroll
+  for (int k = 0; k < kW * kIn / kT; ++k) {
+    const int e = tid + k * kT;
+    *reinterpret_cast<__nv_bfloat16*>(sm + sWt1 + chunk_off(e / kIn, e % kIn, kW)) =
+        __float2bfloat16_rn(kSin * params[oW1 + e]);
+  }
+#pragma unroll
+  for (int k = 0; k < kW * kW / kT; ++k) {
+    const int e = tid + k * kT;
+    const int o = chunk_off(e / kW, e % kW, kW);
+    *reinterpret_cast<__nv_bfloat16*>(sm + sWt2 + o) = __float2bfloat16_rn(params[oW2 + e]);
+    *reinterpret_cast<__nv_bfloat16*>(sm + sWt3 + o) = __float2bfloat16_rn(params[oW3 + e]);
+  }
+  if (tid < 4 * kW + 4) {
+    const int q = tid / kW, c = tid % kW;
+    const int src = q == 0 ? oB1 : q == 1 ? oB2 : q == 2 ? oB3 : oW4;
+    reinterpret_cast<float*>(sm + sFp)[tid] = tid < 4 * kW ? params[src + c] : (tid == 4 * kW ? params[oB4] : 0.f);
   }
   to_mma();
   const uint32_t tm = tmem_holder;
@@ -341,18 +338,24 @@ __global__ void __launch_bounds__(kT, 1)
   for (int q = 0; q < kC; ++q) aw4[q] = 0.f;
   bool first = true;
 
-  // one MMA group: issued by thread 0, then every thread waits for it
-  auto run = [&](auto&& issue) -> bool {
-    if (tid == 0) {
-      issue();
-      commit(&bar);
+  // one MMA group: issued by thread 0, then every thread waits for it itself (no
+  // CTA barrier: the next step's shared-memory writes touch no operand in use).
+  // After a time-out nothing more is issued; `failed` is read uniformly right
+  // after the CTA barrier of each to_mma(), where the tile loop is left.
+  int fail_par = -1;   // parity of a group this thread saw time out
+  auto run = [&](auto&& issue) {
+    if (!failed) {
+      if (tid == 0) {
+        issue();
+        commit(&bar);
+      }
+      if (!wait_phase(&bar, phase)) {
+        failed = 1;
+        fail_par = (int)phase;
+      }
     }
-    const bool ok = wait_phase(&bar, phase);
     phase ^= 1u;
-    if (!ok) failed = 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    __syncthreads();
-    return failed == 0;
   };
   // one forward layer's epilogue on this thread's 16 columns: h = silu(z + b)
   // into row r of `dst`, silu'(z + b) back into the tensor-memory columns of z
@@ -380,11 +383,11 @@ __global__ void __launch_bounds__(kT, 1)
   };
 
   // layer 1 of the first tile
-  bool ok = run([&] {
+  run([&] {
     if (!twait(0)) failed = 1;
     else mma(tm, cZ1, act_k(sm + sX), wt_k(sm + sWt1), kIn, id64, false);
   });
-  for (int it = 0; ok; ++it) {
+  for (int it = 0;; ++it) {
     const int tile = blockIdx.x + it * stride;
     if (tile >= ntiles) break;
     const int b = it & 1;
@@ -393,10 +396,12 @@ __global__ void __launch_bounds__(kT, 1)
     const float yv = valid ? y[s] : 0.f;
     forward(cZ1, fb, sm + sH1);
     to_mma();
-    if (!run([&] { mma(tm, cZ2, act_k(sm + sH1), wt_k(sm + sWt2), kW, id64, false); })) break;
+    if (failed) break;
+    run([&] { mma(tm, cZ2, act_k(sm + sH1), wt_k(sm + sWt2), kW, id64, false); });
     forward(cZ2, fb + kW, sm + sH2);
     to_mma();
-    if (!run([&] { mma(tm, cZ3, act_k(sm + sH2), wt_k(sm + sWt3), kW, id64, false); })) break;
+    if (failed) break;
+    run([&] { mma(tm, cZ3, act_k(sm + sH2), wt_k(sm + sWt3), kW, id64, false); });
     // layer 3 and the output g = w4 . h3 + b4 (the four column groups' partial sums
     // through shared memory), then dz3 = dg w4 silu'(z3)
     {
@@ -428,17 +433,20 @@ __global__ void __launch_bounds__(kT, 1)
       put16(sm + sDZ3, r, c0, d3);
     }
     to_mma();
-    if (!run([&] { mma(tm, cDH, act_k(sm + sDZ3), wt_mn(sm + sWt3), kW, id_bwd, false); })) break;
+    if (failed) break;
+    run([&] { mma(tm, cDH, act_k(sm + sDZ3), wt_mn(sm + sWt3), kW, id_bwd, false); });
     backward(cZ2, sm + sDZ2, valid);
     to_mma();
-    if (!run([&] { mma(tm, cDH, act_k(sm + sDZ2), wt_mn(sm + sWt2), kW, id_bwd, false); })) break;
+    if (failed) break;
+    run([&] { mma(tm, cDH, act_k(sm + sDZ2), wt_mn(sm + sWt2), kW, id_bwd, false); });
     backward(cZ1, sm + sDZ1, valid);
     to_mma();
+    if (failed) break;
     // the gradient products of this tile, and layer 1 of the next tile (its input
     // buffer is the other one; its output columns hold nothing needed any more)
     const bool acc = !first;
     const bool next = tile + stride < ntiles;
-    ok = run([&] {
+    run([&] {
       mma(tm, cW32, act_mn(sm + sDZ3), act_mn(sm + sH2), kS, id_w32, acc);
       mma(tm, cW1, act_mn(sm + sDZ1), act_mn(sm + sX + b * kXBuf), kS, id_w1, acc);
       if (next) {
@@ -448,22 +456,31 @@ __global__ void __launch_bounds__(kT, 1)
     });
     first = false;
     // this tile's input buffer is free again: the tile after next goes there
-    if (ok && tid == 0 && tile + 2 * stride < ntiles) tload(b, tile + 2 * stride);
+    if (tid == 0 && !failed && tile + 2 * stride < ntiles) tload(b, tile + 2 * stride);
   }
+  __syncthreads();   // `failed` is uniform from here on
   // this CTA's gradient sums, part[blockIdx.x][parameter]: lane m = row m of the
   // two gradient products; zero if the CTA had no tile or a wait gave up.  Every
   // branch below is uniform across a warp.
-  float* out = part + (size_t)blockIdx.x * APIP_MLP_NPARAM;
+  float* out = part + (size_t)blockIdx.x * kPart;
   const bool have = !first && failed == 0;
+  // 16 values of a row as four 16-byte stores (the rows start 16-byte aligned)
+  auto put_row = [&](float* dst, const float* v, float scale) {
+#pragma unroll
+    for (int q = 0; q < 16; q += 4)
+      *reinterpret_cast<float4*>(dst + q) =
+          have ? make_float4(scale * v[q], scale * v[q + 1], scale * v[q + 2], scale * v[q + 3])
+               : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
   {
     const int m = r;
     float v[16];
     if (quarter < 2) {                            // rows 0 .. 63: dW3, db3; dW1, db1
       if (have) tld16(lane_addr + cW32 + c0, v);
-      for (int q = 0; q < 16; ++q) out[oW3 + m * kW + c0 + q] = have ? v[q] : 0.f;
+      put_row(out + oW3 + m * kW + c0, v, 1.f);
       if (cg < 2) {
         if (have) tld16(lane_addr + cW1 + c0, v);
-        for (int q = 0; q < 16; ++q) out[oW1 + m * kIn + c0 + q] = have ? kSin * v[q] : 0.f;
+        put_row(out + oW1 + m * kIn + c0, v, kSin);
       } else if (cg == 2) {
         if (have) tld16(lane_addr + cW32 + 2 * kW, v);
         out[oB3 + m] = have ? v[0] : 0.f;
@@ -474,7 +491,7 @@ __global__ void __launch_bounds__(kT, 1)
     } else {                                      // rows 64 .. 127: dW2, db2
       const int j = m - kW;
       if (have) tld16(lane_addr + cW32 + kW + c0, v);
-      for (int q = 0; q < 16; ++q) out[oW2 + j * kW + c0 + q] = have ? v[q] : 0.f;
+      put_row(out + oW2 + j * kW + c0, v, 1.f);
       if (cg == 0) {
         if (have) tld16(lane_addr + cW32 + 2 * kW, v);
         out[oB2 + j] = have ? v[0] : 0.f;
@@ -514,7 +531,7 @@ __global__ void __launch_bounds__(kT, 1)
   if (failed && tid == 0) {
     atomicOr(&status[ST_TIMEOUT], 1);
     // the MMAs and input copies still in flight, once more (bounded)
-    wait_phase(&bar, phase ^ 1u);
+    if (fail_par >= 0) wait_phase(&bar, (uint32_t)fail_par);
     while (twaited0 < tissued0 && twait(0)) {}
     while (twaited1 < tissued1 && twait(1)) {}
   }
@@ -524,24 +541,39 @@ __global__ void __launch_bounds__(kT, 1)
 }
 
 // grad[p] = sum over the CTAs of part[b][p] in a fixed order (eight interleaved
-// partial sums, then those in order); the loss likewise.  32 parameters per block.
+// partial sums over b, then those in order); the loss likewise.  A block takes 128
+// parameters, a lane four consecutive ones (16-byte loads).
 constexpr int kRedWarps = 8;
 __global__ void __launch_bounds__(32 * kRedWarps)
     k_train_reduce(const float* __restrict__ part, const double* __restrict__ loss_part, int nb, int batch,
                    float* __restrict__ grad, float* __restrict__ loss_out) {
   pdl_begin();
-  __shared__ float red[kRedWarps][32];
+  __shared__ float4 red[kRedWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int p = blockIdx.x * 32 + lane;
-  float acc = 0.f;
-  if (p < APIP_MLP_NPARAM)
-    for (int b = w; b < nb; b += kRedWarps) acc += part[(size_t)b * APIP_MLP_NPARAM + p];
+  const int p = 4 * (blockIdx.x * 32 + lane);   // first of this lane's parameters
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (p < kPart) {
+#pragma unroll 4
+    for (int b = w; b < nb; b += kRedWarps) {
+      const float4 v = *reinterpret_cast<const float4*>(part + (size_t)b * kPart + p);
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+  }
   red[w][lane] = acc;
   __syncthreads();
   if (w == 0 && p < APIP_MLP_NPARAM) {
-    float t = 0.f;
-    for (int k = 0; k < kRedWarps; ++k) t += red[k][lane];
-    grad[p] = t;
+    float t[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < kRedWarps; ++k) {
+      const float4 v = red[k][lane];
+      t[0] += v.x;
+      t[1] += v.y;
+      t[2] += v.z;
+      t[3] += v.w;
+    }
+    for (int q = 0; q < 4 && p + q < APIP_MLP_NPARAM; ++q) grad[p + q] = t[q];
   }
   if (blockIdx.x == 0 && threadIdx.x == 32) {
     double t = 0.0;
@@ -557,7 +589,6 @@ int train_grid_max() {
   return sms > 0 ? sms : 1;
 }
 size_t loss_floats(int g) { return (2 * (size_t)g + 3) / 4 * 4; }
-constexpr size_t kImageFloats = kImage / 4;
 
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime
 PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
@@ -575,11 +606,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
 }  // namespace
 
 // Workspace (floats, from a 16-byte aligned base): the loss partials (float64, one
-// per CTA, padded to 16 bytes), the weight image, the CTAs' gradient sums.
+// per CTA, padded to 16 bytes), then the CTAs' gradient sums (kPart floats each).
 size_t mlp_workspace_floats(int batch) {
   (void)batch;
   const int g = train_grid_max();
-  return loss_floats(g) + kImageFloats + (size_t)g * APIP_MLP_NPARAM;
+  return loss_floats(g) + (size_t)g * kPart;
 }
 
 bool launch_mlp_loss_grad(const uint16_t* desc, const float* y, int batch, const float* params, float* grad,
@@ -598,14 +629,12 @@ bool launch_mlp_loss_grad(const uint16_t* desc, const float* y, int batch, const
     return false;
   const int gmax = train_grid_max();
   double* loss_part = reinterpret_cast<double*>(ws);
-  unsigned char* image = reinterpret_cast<unsigned char*>(ws + loss_floats(gmax));
-  float* part = ws + loss_floats(gmax) + kImageFloats;
-  k_train_image<<<(kW * kW + 255) / 256, 256, 0, s>>>(params, image);
+  float* part = ws + loss_floats(gmax);
   const int ntiles = (batch + kS - 1) / kS;
   const int grid = ntiles < gmax ? ntiles : gmax;   // one CTA per SM (512 tensor-memory columns each)
   cudaFuncSetAttribute(k_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-  launch_pdl(k_train_tc, grid, kT, kSmem, s, gmap, y, batch, (const unsigned char*)image, part, loss_part, status);
-  launch_pdl(k_train_reduce, (APIP_MLP_NPARAM + 31) / 32, 32 * kRedWarps, 0, s, (const float*)part,
+  launch_pdl(k_train_tc, grid, kT, kSmem, s, gmap, y, batch, params, part, loss_part, status);
+  launch_pdl(k_train_reduce, (kPart / 4 + 31) / 32, 32 * kRedWarps, 0, s, (const float*)part,
              (const double*)loss_part, grid, batch, grad, loss);
   return true;
 }

@@ -88,6 +88,47 @@ def train(G, y, epochs=20, batch=65536, lr=1e-3, seed=7, prm=None, log_every=0):
     return p, history
 
 
+# Algorithmic flops of one training sample: the forward products (32*64 + 2*64*64
+# + 64 multiply-adds), the back-propagation to h1 (2*64*64) and the weight
+# gradients (as many as the forward), two flops per multiply-add.
+FLOP_PER_SAMPLE = 2 * ((32 * 64 + 2 * 64 * 64 + 64) * 2 + 2 * 64 * 64)
+
+
+def step_time(batch=65536, steps=50, warmup=5, seed=3):
+    """Device time of one training step (loss and gradient, then Adam) on a batch
+    of seeded synthetic descriptors, timed with CUDA events on the stream the
+    kernels run on; returns (microseconds per step, TFLOP/s algorithmic)."""
+    import torch
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(seed)
+    G = torch.tensor(rng.uniform(0.0, 3.0, (batch, 32)).astype(np.float32), device=dev).to(torch.bfloat16)
+    y = torch.tensor(rng.uniform(0.0, 0.5, batch).astype(np.float32), device=dev)
+    prm = W.config("vacancy2k", apip.apip_ace_basis_size, scale=6)["prm"]
+    holder = apip.Apip(prm, 8, precision="fp32", lam_mode="const0")
+    p = torch.tensor(apip.mlp_flat(W.mlp_params(7)), device=dev)
+    m, v, grad = torch.zeros_like(p), torch.zeros_like(p), torch.empty_like(p)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()   # the kernels' stream (the bindings' default)
+    t = 0
+    for _ in range(warmup):
+        t += 1
+        apip.apip_mlp_loss_grad(holder.ctx, G, y, batch, p, grad, loss)
+        apip.apip_mlp_adam(holder.ctx, p, grad, m, v, t, 1e-4)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        t += 1
+        apip.apip_mlp_loss_grad(holder.ctx, G, y, batch, p, grad, loss)
+        apip.apip_mlp_adam(holder.ctx, p, grad, m, v, t, 1e-4)
+    b.record(stream)
+    torch.cuda.synchronize()
+    holder.sync()
+    holder.close()
+    us = a.elapsed_time(b) * 1e3 / steps
+    return us, FLOP_PER_SAMPLE * batch / (us * 1e-6) / 1e12
+
+
 def _energies(prm, s, lam_mode, params=None):
     """Per-atom energies, lam, E^EAM and d of one configuration (float32 path)."""
     import torch
@@ -151,8 +192,15 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default="mlp_weights.npy")
     ap.add_argument("--held-out", type=int, default=8, help="configurations for the switch comparison")
+    ap.add_argument("--step-bench", action="store_true",
+                    help="only time the training step on synthetic descriptors (--batch, --steps)")
+    ap.add_argument("--steps", type=int, default=50)
     args = ap.parse_args()
     build.build()
+    if args.step_bench:
+        us, tf = step_time(args.batch, args.steps)
+        print(json.dumps({"batch": args.batch, "steps": args.steps, "us_per_step": us, "tflops": tf}))
+        return
     prm = W.config("vacancy2k", apip.apip_ace_basis_size)["prm"]
     torch.cuda.synchronize()
     t0 = time.time()
