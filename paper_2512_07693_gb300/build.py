@@ -16,7 +16,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["apip.cu", "kernels_atoms.cu", "kernels_ace_f32.cu", "kernels_ace_f64.cu", "kernels_ace3_f32.cu",
            "kernels_ace3_f64.cu", "ace_tables.cpp", "apip_static.cu", "kernels_mlp.cu", "peak_probe.cu", "kernels_train_tc.cu"]
 HEADERS = ["apip_internal.h", "device_common.cuh", "kernels.h", "ace_device.cuh", "ace_pool.cuh", "ace_stream.cuh",
-           "gaunt_layout.h"]
+           "gaunt_layout.h", "tc_common.cuh"]
 
 
 def _flags():

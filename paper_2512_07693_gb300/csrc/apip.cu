@@ -77,7 +77,7 @@ void free_all(apip_ctx* c) {
   void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nnb_e, c->posg, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->clist, c->counts, c->flags, c->status, c->partials, c->thermo_part,
-                  c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_frag, c->mlp_ws};
+                  c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_img, c->mlp_ws};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -257,7 +257,8 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.force = force;
   a.e_atom = e_atom;
   a.mlp_w = as<T>(c->mlp_w);
-  a.mlp_frag = static_cast<const uint2*>(c->mlp_frag);
+  a.mlp_img = static_cast<const uint4*>(c->mlp_img);
+  a.learned_grid = c->learned_slots;
   a.ace_rc = T(p.ace_rc);
   a.ace_rc_lo = T(p.ace_rc - p.ace_rc_width);
   return a;
@@ -579,7 +580,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->ind_acc, sizeof(double) * 3);
   APIP_ALLOC(ctx->mlp_w, es * APIP_MLP_NPARAM);
   if (p->precision == APIP_FP32) {
-    APIP_ALLOC(ctx->mlp_frag, mlp_frag_bytes());
+    APIP_ALLOC(ctx->mlp_img, mlp_img_bytes());
     ctx->learned_slots = learned_tc_slots();
     cudaGetLastError();
     if (ctx->learned_slots < 1 && p->lam_mode == APIP_LAM_LEARNED) return fail_create(cudaErrorInvalidConfiguration);
@@ -813,7 +814,7 @@ apip_status apip_sync(apip_ctx* ctx, void* stream) {
   if (st[ST_CELL_OVERFLOW])
     return fail(ctx, APIP_ERR_NB_OVERFLOW, "cell overflow: a cell holds " + std::to_string(st[ST_MAX_CELL]) +
                                               " atoms, cell_cap = " + std::to_string(ctx->p.cell_cap));
-  if (st[ST_TIMEOUT]) return fail(ctx, APIP_ERR_TIMEOUT, "a bounded device wait gave up (the tensor-core training kernel's wait for its matrix products)");
+  if (st[ST_TIMEOUT]) return fail(ctx, APIP_ERR_TIMEOUT, "a bounded device wait gave up (a tensor-core kernel's wait for its matrix products: training or the learned switch)");
   if (st[ST_BAD_INPUT]) return fail(ctx, APIP_ERR_BAD_INPUT, "non-finite position or atom id out of range");
   if (st[ST_BAD_PARTNER]) return fail(ctx, APIP_ERR_BAD_INPUT, "a CSP partner id is not present");
   return APIP_OK;
@@ -825,7 +826,7 @@ apip_status apip_set_mlp(apip_ctx* ctx, const float* params, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (ctx->p.precision == APIP_FP32) {
     launch_cast_params<float>(params, as<float>(ctx->mlp_w), s);
-    launch_mlp_frags(as<float>(ctx->mlp_w), ctx->mlp_frag, s);
+    launch_mlp_images(as<float>(ctx->mlp_w), ctx->mlp_img, s);
   }
   else launch_cast_params<double>(params, as<double>(ctx->mlp_w), s);
   const apip_status st = launch_status(ctx);

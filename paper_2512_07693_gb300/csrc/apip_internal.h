@@ -187,8 +187,8 @@ struct apip_ctx {
 
   // learned indicator
   void* mlp_w = nullptr;       // APIP_MLP_NPARAM weights (element size = precision)
-  void* mlp_frag = nullptr;    // FP32: split bfloat16 fragments of the hidden layers
-  int learned_slots = 0;       // FP32: resident blocks of the tensor-core learned pass 1
+  void* mlp_img = nullptr;     // FP32: the weights as split bfloat16 tensor-core operand images
+  int learned_slots = 0;       // FP32: resident CTAs of the tensor-core learned kernels
   bool mlp_ready = false;
   float* mlp_ws = nullptr;     // training workspace
   size_t mlp_ws_cap = 0;       // floats

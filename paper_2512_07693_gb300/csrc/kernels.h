@@ -66,7 +66,8 @@ struct Args {
   double* force;          // caller force [n][3]
   double* e_atom;         // caller per-atom energy [n] or null
   const T* mlp_w;         // learned indicator weights (APIP_MLP_NPARAM, layout of apip.h)
-  const uint2* mlp_frag;  // FP32 path: the hidden layers' weights as split bfloat16 mma fragments
+  const uint4* mlp_img;   // FP32 path: the weights as split bfloat16 tensor-core operand images
+  int learned_grid;       // FP32 path: persistent CTAs of the tensor-core learned kernels
   T ace_rc, ace_rc_lo;    // cutoff of the radial descriptors (the ACE cutoff)
 };
 
@@ -211,8 +212,8 @@ template <typename T> void launch_cast_params(const float* src, T* dst, cudaStre
 // for n atoms, the weight fragments (from the float32 weights) and their size
 int learned_tc_slots();
 int learned_tc_blocks(int n, int slots);
-void launch_mlp_frags(const float* w, void* frag, cudaStream_t s);
-size_t mlp_frag_bytes();
+void launch_mlp_images(const float* w, void* img, cudaStream_t s);
+size_t mlp_img_bytes();
 // training on the tensor cores (kernels_train_tc.cu); a bounded wait that gives up
 // sets status[ST_TIMEOUT].  False (nothing launched) when desc is not 16-byte
 // aligned or its TMA descriptor cannot be made.

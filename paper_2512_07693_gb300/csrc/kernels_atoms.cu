@@ -18,13 +18,17 @@ __device__ __forceinline__ double wrap1(double x, double L, double invL) {
   return w;
 }
 
+// The rare branch of wrap_near, kept out of line so that the compiler cannot
+// turn it into predicated float64 instructions issued for every atom.
+__device__ __noinline__ double wrap1_slow(double x, double L, double invL) { return wrap1(x, L, invL); }
+
 // wrap1 for a position that is normally already in [0, L) (the drift of one
 // step): the range test is made on the bit patterns (non-negative doubles order
 // as integers), which keeps it off the float64 pipe.
 __device__ __forceinline__ double wrap_near(double x, double L, double invL) {
   const long long b = __double_as_longlong(x), bl = __double_as_longlong(L);
   if (b >= 0 && b < bl) return x;
-  return wrap1(x, L, invL);
+  return wrap1_slow(x, L, invL);
 }
 
 // isfinite from the exponent bits.
@@ -515,19 +519,33 @@ __global__ void k_csp_force(Args<T> a) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.n) return;
   const double c = a.cvec[j];
-  if (c == 0.0) return;
+  if ((__double_as_longlong(c) << 1) == 0) return;   // c == +-0, tested on the bits (off the float64 pipe)
   a.cvec[j] = 0.0;
   const auto sj = a.pv.self(j);
   const int idj = a.id[j];
   if (idj < 0 || idj >= a.nmax) return;   // reported by prep (ST_BAD_INPUT)
-  const int* pr = a.csp + (size_t)idj * kCspCap;
-  double fj[3] = {0.0, 0.0, 0.0};
-  for (int k = 0; 2 * k + 1 < a.csp_nnb; ++k) {
-    const int ia_id = pr[2 * k], ib_id = pr[2 * k + 1];
-    if (ia_id < 0 || ib_id < 0 || ia_id >= a.nmax || ib_id >= a.nmax) continue;
-    const int ia = a.id2idx[ia_id], ib = a.id2idx[ib_id];
+  // the partners' ids, then all their indices, then the checks and positions:
+  // three rounds of independent loads instead of a dependent chain per pair
+  static_assert(kCspCap == 8, "two int4 rows of partner ids");
+  const int4* pr4 = reinterpret_cast<const int4*>(a.csp + (size_t)idj * kCspCap);
+  const int4 q0 = pr4[0], q1 = pr4[1];
+  const int pid[kCspCap] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+  int idx[kCspCap];
+#pragma unroll
+  for (int k = 0; k < kCspCap; ++k)
+    idx[k] = (k >= a.csp_nnb || pid[k] < 0 || pid[k] >= a.nmax) ? -1 : a.id2idx[pid[k]];
+  bool ok[kCspCap / 2];
+#pragma unroll
+  for (int k = 0; k < kCspCap / 2; ++k) {
+    const int ia = idx[2 * k], ib = idx[2 * k + 1];
     // stale map entries (ids no longer present) are reported by pass 1
-    if (ia < 0 || ib < 0 || ia >= a.n || ib >= a.n || a.id[ia] != ia_id || a.id[ib] != ib_id) continue;
+    ok[k] = ia >= 0 && ib >= 0 && ia < a.n && ib < a.n && a.id[ia] == pid[2 * k] && a.id[ib] == pid[2 * k + 1];
+  }
+  double fj[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < kCspCap / 2; ++k) {
+    if (!ok[k]) continue;
+    const int ia = idx[2 * k], ib = idx[2 * k + 1];
     const V3<T> uv = csp_vec(a.pv, sj, ia, ib);
     const double u[3] = {(double)uv.x, (double)uv.y, (double)uv.z};
 #pragma unroll
@@ -584,25 +602,32 @@ __global__ void k_thermo_final(const double* thermo_part, int n_tb, double* ther
 }
 
 // ----------------------------------------------------------------- Verlet
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* pos, double* vel,
-                                                   const double* force, const double* inv_mass,
-                                                   double dt, double half_dt, double* thermo_part) {
+// MODE 0: kick + drift (the first half step of a call); MODE 1: kick + kick +
+// drift (the second half of step s fused with the first half of step s + 1);
+// MODE 2: the final kick.  THERMO: the kinetic-energy and momentum partials of
+// the step that the first kick ends (MODE 1, 2).  Both are template parameters:
+// float64 arithmetic is slow on this GPU, and a run-time test would leave the
+// compiler free to issue the float64 work of the other modes as predicated-off
+// instructions on every atom.
+template <typename T, int MODE, bool THERMO>
+__global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, double* pos, double* vel, const double* force,
+                                                   const double* inv_mass, double dt, double half_dt,
+                                                   double* thermo_part) {
   pdl_begin();
+  static_assert(!(THERMO && MODE == 0), "no thermo output before the first force");
   __shared__ double sh4[4 * 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0 && mode != 2) a.counts[0] = a.counts[1] = 0;
-  // the kinetic energy and momentum partials of the step that the first kick ends,
-  // only when the caller asked for thermo output (float64 work, slow on this GPU)
-  const bool thermo = mode != 0 && thermo_part != nullptr;
+  if (MODE != 2 && i == 0) a.counts[0] = a.counts[1] = 0;
   double ke = 0.0, p[3] = {0.0, 0.0, 0.0};   // ke: 2 E_kin of the atom (v . p; halved after the sums)
   if (i < a.n) {
     const double im = inv_mass[i];
     const double h = half_dt * im;
-    double v[3], x[3];
+    double f[3], v[3], x[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) v[q] = vel[3 * i + q] + h * force[3 * i + q];
-    if (thermo) {
+    for (int q = 0; q < 3; ++q) f[q] = force[3 * i + q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v[q] = vel[3 * i + q] + h * f[q];
+    if constexpr (THERMO) {
       // mass = 1/inv_mass: exact in the float64 path; a float reciprocal (relative
       // error ~1e-7 on each atom's E_kin and momentum) in the float32 path, where
       // a float64 division per atom would cost more than the rest of the kernel
@@ -611,13 +636,13 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* 
       for (int q = 0; q < 3; ++q) p[q] = v[q] * mass;
       ke = v[0] * p[0] + v[1] * p[1] + v[2] * p[2];
     }
-    if (mode == 1) {
+    if constexpr (MODE == 1) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) v[q] += h * force[3 * i + q];
+      for (int q = 0; q < 3; ++q) v[q] += h * f[q];
     }
 #pragma unroll
     for (int q = 0; q < 3; ++q) vel[3 * i + q] = v[q];
-    if (mode != 2) {
+    if constexpr (MODE != 2) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         x[q] = wrap_near(pos[3 * i + q] + dt * v[q], a.geo.L[q], a.geo.invL[q]);
@@ -626,7 +651,7 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, int mode, double* 
       prep_atom(a, i, x[0], x[1], x[2], true);
     }
   }
-  if (thermo) {
+  if constexpr (THERMO) {
     const double vals[4] = {ke, p[0], p[1], p[2]};
     double tot[4];
     block_sum4(vals, sh4, tot);
@@ -749,7 +774,11 @@ void launch_thermo_final(const double* thermo_part, int n_tblocks, double* therm
 template <typename T> void launch_verlet(const Args<T>& a, int mode, double* pos, double* vel,
                                          const double* force, const double* inv_mass, double dt,
                                          double* thermo_part, cudaStream_t s) {
-  launch_pdl(k_verlet<T>, nblocks(a.n), kBlock, 0, s, a, mode, pos, vel, force, inv_mass, dt, 0.5 * dt, thermo_part);
+  const bool th = mode != 0 && thermo_part != nullptr;
+  auto k = mode == 0 ? k_verlet<T, 0, false>
+                     : (mode == 1 ? (th ? k_verlet<T, 1, true> : k_verlet<T, 1, false>)
+                                  : (th ? k_verlet<T, 2, true> : k_verlet<T, 2, false>));
+  launch_pdl(k, nblocks(a.n), kBlock, 0, s, a, pos, vel, force, inv_mass, dt, 0.5 * dt, thermo_part);
 }
 
 template <typename T> void launch_get_field(const Args<T>& a, int field, void* dst, cudaStream_t s) {

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace apip {
 namespace {
@@ -199,25 +200,6 @@ __global__ void __launch_bounds__(kLearnedBlock) k_pass1_learned(Args<T> a) {
   if (threadIdx.x == 0) a.partials[blockIdx.x] = tot;
 }
 
-// ------------------------------------------------ pass 1, learned, float32
-// The network on the tensor cores: mma.sync m16n8k16 with bfloat16 operands and
-// float32 accumulation, a warp per tile of 32 atoms (two 16-row tiles).  Float32
-// accuracy from bfloat16 products: every operand x is split as
-// x = x_hi + x_mid + x_lo (each part the bfloat16 rounding of what the previous
-// parts leave, 8 significant bits each, so 24 in all), and a product is the sum of
-// the six part products whose orders add to at most 2 (hi hi, hi mid, mid hi,
-// hi lo, mid mid, lo hi); the three dropped ones are below 2^-24 of the product.
-// Part products are exact in float32 and accumulate in float32.
-//
-// Fragment layouts (PTX ISA, mma.m16n8k16 .bf16): with g = lane / 4, t = lane % 4,
-// A (16 x 16, row-major) regs a0 = A[g][2t, 2t+1], a1 = A[g+8][2t, 2t+1],
-// a2 = A[g][2t+8, 2t+9], a3 = A[g+8][2t+8, 2t+9]; B (16 x 8, k x n) regs
-// b0 = B[2t, 2t+1][g], b1 = B[2t+8, 2t+9][g]; C (16 x 8) c0 = C[g][2t],
-// c1 = C[g][2t+1], c2 = C[g+8][2t], c3 = C[g+8][2t+1]; the lower column sits in
-// the low 16 bits of a pair.  The C fragments of n-tiles 2kb and 2kb+1 of one
-// layer are the A fragment of k-block kb of the next: activations stay in
-// registers from layer to layer.
-
 // Compensated float32 dot product (the Dot2 scheme of Ogita, Rump and Oishi): s
 // is the running sum, c the sum of the exact rounding errors of every product
 // (from an FMA) and every addition (TwoSum); the value s + c is as accurate as a
@@ -241,15 +223,6 @@ struct Dot2 {
   __device__ __forceinline__ float value() const { return s + c; }
 };
 
-// uint2 offsets of the layers within a split: layer 1 (2 k-blocks), 2 and 3 (4 each)
-constexpr int kTcOff1 = 0, kTcOff2 = 2 * 8 * 32, kTcOff3 = kTcOff2 + 4 * 8 * 32;
-constexpr int kTcSplit = kTcOff3 + 4 * 8 * 32;                              // 2560 uint2 per split
-constexpr int kTcFrag = 3 * kTcSplit;                                       // hi, mid, lo
-constexpr int kTcWarps = 8;
-constexpr int kTcXs = 33;        // staging row stride (floats) of the layer-1 input: odd, so that
-                                 // lanes adding at nearby Gaussian indices hit different banks
-constexpr int kTcBias = 3 * kW + kW + 4;   // b1, b2, b3, w4, b4 (+ pad)
-
 __device__ __forceinline__ uint32_t bf2(float lo_col, float hi_col) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo_col, hi_col);
   return *reinterpret_cast<const uint32_t*>(&v);
@@ -265,76 +238,6 @@ __device__ __forceinline__ void split3(float x, float y, uint32_t& hi, uint32_t&
   hi = *reinterpret_cast<const uint32_t*>(&h);
   mid = *reinterpret_cast<const uint32_t*>(&m);
   lo = bf2(rx - mf.x, ry - mf.y);
-}
-
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint2 b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
-}
-
-// One k-block of a layer for all 8 n-tiles: acc[nt] += A_kb W^T, A given as its
-// three parts (4 regs each), the weights' fragments from shared memory (layer
-// offset lo_off, k-block kb); small part products first.  Product-major order:
-// consecutive mma instructions update different n-tiles, so they overlap
-// instead of waiting on one accumulator.
-__device__ __forceinline__ void tc_kblock(float (*acc)[4], const uint32_t* ah, const uint32_t* am, const uint32_t* al,
-                                          const uint2* sf, int lo_off, int kb, int lane) {
-  const uint2* f = sf + lo_off + kb * 8 * 32 + lane;
-  const uint32_t* const as[6] = {am, ah, al, ah, am, ah};
-  constexpr int ws[6] = {1, 2, 0, 1, 0, 0};   // weight part: 0 hi, 1 mid, 2 lo
-#pragma unroll
-  for (int p = 0; p < 6; ++p)
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) mma_bf16(acc[nt], as[p], f[ws[p] * kTcSplit + nt * 32]);
-}
-
-// acc (layer output, 8 n-tiles) -> bias + SiLU in place.
-__device__ __forceinline__ void tc_bias_silu(float (*acc)[4], const float* b, int t) {
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[nt][q] = silu(acc[nt][q] + b[8 * nt + 2 * t + (q & 1)]);
-}
-
-// A 64-wide hidden layer: out = in W^T (in holds the previous activations).
-__device__ __forceinline__ void tc_hidden(float (*in)[4], float (*out)[4], const uint2* sf, int lo_off, int lane) {
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) out[nt][q] = 0.f;
-#pragma unroll
-  for (int kb = 0; kb < 4; ++kb) {
-    uint32_t ah[4], am[4], al[4];
-    split3(in[2 * kb][0], in[2 * kb][1], ah[0], am[0], al[0]);
-    split3(in[2 * kb][2], in[2 * kb][3], ah[1], am[1], al[1]);
-    split3(in[2 * kb + 1][0], in[2 * kb + 1][1], ah[2], am[2], al[2]);
-    split3(in[2 * kb + 1][2], in[2 * kb + 1][3], ah[3], am[3], al[3]);
-    tc_kblock(out, ah, am, al, sf, lo_off, kb, lane);
-  }
-}
-
-// The fragments of the split weights: thread f of kTcFrag writes uint2 f
-// (split, layer, k-block, n-tile, lane) from the float32 weights.
-__global__ void k_mlp_frags(const float* __restrict__ w, uint2* __restrict__ frag) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= kTcFrag) return;
-  const int sp = f / kTcSplit, r = f % kTcSplit;
-  const int layer = r < kTcOff2 ? 0 : (r < kTcOff3 ? 1 : 2);
-  const int q = r - (layer == 0 ? kTcOff1 : (layer == 1 ? kTcOff2 : kTcOff3));
-  const int lane = q % 32, nt = (q / 32) % 8, kb = q / 256;
-  const int K = layer == 0 ? kIn : kW;
-  const float* W = w + (layer == 0 ? oW1 : (layer == 1 ? oW2 : oW3));
-  const int n = 8 * nt + lane / 4, k0 = 16 * kb + 2 * (lane % 4);
-  uint32_t v[2];
-  for (int h = 0; h < 2; ++h) {
-    uint32_t p[3];
-    split3(W[n * K + k0 + 8 * h], W[n * K + k0 + 8 * h + 1], p[0], p[1], p[2]);
-    v[h] = p[sp];
-  }
-  frag[f] = make_uint2(v[0], v[1]);
 }
 
 // Adds phi_m(r) (fc folded in) to row[m] for the Gaussians within kWin spacings
@@ -362,137 +265,423 @@ __device__ __forceinline__ void add_features_window(float r, float fc, float kap
   }
 }
 
-// Pass 1 with the learned switch, float32: as k_pass1_learned (EAM density,
-// energy, xi'; descriptors; g = MLP(G)) with the network on the tensor cores.
-// Persistent blocks of 8 warps; warp w of block b takes the tiles of 32 atoms
-// b * 8 + w, + 8 gridDim, ...; one energy partial per block.
-__global__ void __launch_bounds__(kTcWarps * 32) k_pass1_learned_tc(Args<float> a, const uint2* __restrict__ frag) {
-  pdl_begin();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint2* sf = reinterpret_cast<uint2*>(smem_raw);
-  float* sb = reinterpret_cast<float*>(sf + kTcFrag);
-  float* sx = sb + kTcBias;
-  __shared__ double sh[32];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
-  for (int k = tid; k < kTcFrag / 2; k += blockDim.x)
-    reinterpret_cast<uint4*>(sf)[k] = reinterpret_cast<const uint4*>(frag)[k];
-  for (int k = tid; k < kW; k += blockDim.x) {
-    sb[k] = a.mlp_w[oB1 + k];
-    sb[kW + k] = a.mlp_w[oB2 + k];
-    sb[2 * kW + k] = a.mlp_w[oB3 + k];
-    sb[3 * kW + k] = a.mlp_w[oW4 + k];
+// ------------------------------------- learned switch, float32, tensor cores
+// The network on the fifth-generation tensor cores (tcgen05.mma, bfloat16
+// operands, float32 accumulation in tensor memory), one kernel for both uses:
+//   pass 1 (FORCE = false): for every atom the EAM density, energy and xi'
+//     (as k_pass1) and g = MLP(G) (also into posg);
+//   the grad-lambda force (FORCE = true): for the atoms with c_k != 0 (the list
+//     k_cvec_compact builds), dG_k = c_k dg/dG by back-propagation through the
+//     same network, then F_j -= v e_kj, F_k += v e_kj per neighbour with
+//     v = sum_m dG_km phi_m'(r_kj) (Eq. 6 with a general g: -grad sum_k c_k g_k).
+// Float32 accuracy from bfloat16 products: every operand x (activation or
+// weight) is split as x = x_hi + x_mid + x_lo, each part the bfloat16 rounding of
+// what the previous parts leave (8 significant bits each, 24 in all), and a
+// product is the sum of the six part products whose orders add to at most 2
+// (mid mid, hi lo, lo hi, hi mid, mid hi, hi hi, small ones first); the three
+// dropped ones are below 2^-24 of the product.  Part products are exact in
+// float32 and accumulate in float32 in tensor memory.
+//
+// A persistent CTA of 512 threads per SM loops over tiles of 128 atoms: atom row
+// r of a tile is tensor-memory lane r; thread (warp w, lane l) owns row
+// r = 32 (w % 4) + l and quarter cg = w / 4 of the work of that row: neighbour
+// entries cg, cg + 4, ... of the atom's list, descriptor columns 8 cg .. + 7 and
+// columns 16 cg .. + 15 of each 64-wide layer.  Per tile, with D = A B^T:
+//   z1 = x0 W1^T, z2 = h1 W2^T, z3 = h2 W3^T                (forward)
+//   dh2 = dz3 W3, dh1 = dz2 W2, dG = dz1 W1                 (FORCE: back-propagation;
+//                                                            the weights read MN-major)
+// The forward epilogues keep silu'(z) in the tensor-memory columns of z for the
+// back-propagation.  The output layer g = b4 + sum_j w4_j silu(z3_j + b3_j) is a
+// compensated dot product on the CUDA cores.  The weight images (three parts,
+// chunk-major with 64 rows; tc_common.cuh) are built once per apip_set_mlp by
+// k_mlp_images and copied into shared memory by each CTA.
+//
+// Every tensor-memory load and store is executed by whole warps on their own
+// quarter of the lanes, never under a branch that splits a warp.  One thread
+// issues the MMAs, committed to an mbarrier that every thread waits on; every
+// wait is bounded (two seconds): on time-out the kernel records ST_TIMEOUT, stops
+// issuing, leaves the tile loop, waits once more for the MMAs in flight, frees
+// its tensor memory and returns.
+namespace lt {
+using namespace tc;
+constexpr int kT = 512;                    // threads per CTA: four per atom
+constexpr int kRows = 128;                 // atoms per tile = tensor-memory lanes
+constexpr int kImgW1 = kW * kIn * 2, kImgW2 = kW * kW * 2;   // bytes of a weight image part
+constexpr int kImgPart = kImgW1 + 2 * kImgW2;                // W1 | W2 | W3 of one part
+constexpr int kImg = 3 * kImgPart;                           // hi, mid, lo
+constexpr int kXPart = kRows * kIn * 2, kHPart = kRows * kW * 2;
+constexpr int kPs = kIn + 1;               // stride (floats) of a descriptor partial row
+// shared memory (byte offsets)
+constexpr int sW = 0;                      // weight images
+constexpr int sX = sW + kImg;              // x0 = G / 4, three parts
+constexpr int sH = sX + 3 * kXPart;        // a 64-wide activation or gradient, three parts
+constexpr int sP = sH + 3 * kHPart;        // descriptor partials [4][128][33]; FORCE: dG rows [128][33]
+constexpr int sF = sP + 4 * kRows * kPs * 4;   // float32 b1, b2, b3, w4, b4 (+ pad)
+constexpr int kNF = 4 * kW + 4;
+constexpr int sE = sF + kNF * 4;           // pass 1: EAM partials [4][128][4]; FORCE: c of each row
+constexpr int sG = sE + 4 * kRows * 4 * 4; // output-layer partials [4][128][2]
+constexpr int kSmem = sG + 4 * kRows * 2 * 4;
+static_assert(kSmem <= 227 * 1024, "shared memory");
+static_assert(kImgPart % 1024 == 0 && sX % 1024 == 0 && sH % 1024 == 0 && sP % 16 == 0, "alignment");
+// tensor-memory columns
+constexpr uint32_t cZ1 = 0, cZ2 = 64, cZ3 = 128, cDH = 192, cDG = 256;
+}  // namespace lt
+
+// Weight images for the tensor-core kernel: part p of W1, W2, W3 (bfloat16,
+// chunk-major with 64 rows) at p * kImgPart; thread e converts the pair of
+// elements (row, 2c), (row, 2c + 1) of one matrix.
+__global__ void k_mlp_images(const float* __restrict__ w, unsigned char* __restrict__ img) {
+  using namespace lt;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int n1 = kW * kIn / 2, n2 = kW * kW / 2;
+  if (e >= n1 + 2 * n2) return;
+  int m, q;   // matrix (0: W1, 1: W2, 2: W3), pair index within it
+  if (e < n1) { m = 0; q = e; } else if (e < n1 + n2) { m = 1; q = e - n1; } else { m = 2; q = e - n1 - n2; }
+  const int K = m == 0 ? kIn : kW;
+  const int row = (2 * q) / K, col = (2 * q) % K;
+  const float* W = w + (m == 0 ? oW1 : (m == 1 ? oW2 : oW3));
+  uint32_t part[3];
+  split3(W[row * K + col], W[row * K + col + 1], part[0], part[1], part[2]);
+  const int off = (m == 0 ? 0 : (m == 1 ? kImgW1 : kImgW1 + kImgW2)) + tc::chunk_off(row, col, kW);
+#pragma unroll
+  for (int p = 0; p < 3; ++p) *reinterpret_cast<uint32_t*>(img + p * kImgPart + off) = part[p];
+}
+
+// Sixteen float32 values, split in three, into row r of the three parts of a
+// 128-row chunk-major operand at column c0 (a multiple of 8): two 16-byte stores
+// per part.
+__device__ __forceinline__ void put16_split(unsigned char* base, int part_bytes, int r, int c0, const float* v) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint4 w[3];
+    uint32_t* u0 = reinterpret_cast<uint32_t*>(&w[0]);
+    uint32_t* u1 = reinterpret_cast<uint32_t*>(&w[1]);
+    uint32_t* u2 = reinterpret_cast<uint32_t*>(&w[2]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) split3(v[8 * h + 2 * q], v[8 * h + 2 * q + 1], u0[q], u1[q], u2[q]);
+    const int off = tc::chunk_off(r, c0 + 8 * h, lt::kRows);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) *reinterpret_cast<uint4*>(base + p * part_bytes + off) = w[p];
   }
-  if (tid == 0) sb[4 * kW] = a.mlp_w[oB4];
-  __syncthreads();
-  float* xs = sx + warp * (32 * kTcXs + 32);   // [32][kTcXs] layer-1 input, then g of the 32 atoms
-  float* gs = xs + 32 * kTcXs;
+}
+
+// D (column d) = A B^T with both operands given as three parts (addresses of
+// part 0; parts pa_bytes / pb_bytes apart): the six part products, small first.
+__device__ __forceinline__ void mma_split(uint32_t tmem, uint32_t d, tc::Opnd A, int pa_bytes, tc::Opnd B,
+                                          int pb_bytes, int K, uint32_t id) {
+  constexpr int ap[6] = {1, 0, 2, 0, 1, 0}, bp[6] = {1, 2, 0, 1, 0, 0};
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    tc::Opnd a = A, b = B;
+    a.addr += ap[q] * pa_bytes;
+    b.addr += bp[q] * pb_bytes;
+    tc::mma(tmem, d, a, b, K, id, q > 0);
+  }
+}
+
+// phi_m(r) (fc folded in) for the Gaussians within kWin spacings of the nearest
+// one, as add_features_window, and their derivatives contracted with dG:
+// returns v = sum_m dG[m] d phi_m / dr (the other Gaussians are below 1.3e-9 of
+// the largest).
+__device__ __forceinline__ float dfeatures_window(float r, float fc, float dfc, float kappa, const float* dG) {
+  const float dmu = float(kDmu), eta = float(kEta);
+  int m0 = __float2int_rn((r - float(kMu0)) / dmu);
+  m0 = m0 < 0 ? 0 : (m0 > kIn - 1 ? kIn - 1 : m0);
+  const float x0 = r - (float(kMu0) + float(m0) * dmu);
+  const float base = -eta * dmu * dmu, slope = 2.f * eta * dmu * x0;
+  const float e0 = __expf(-eta * x0 * x0);
+  float rho = __expf(base + slope), sig = __expf(base - slope), up = e0, dn = e0;
+  const float a2 = -2.f * eta * fc;
+  float v = dG[m0] * e0 * (a2 * x0 + dfc);
+#pragma unroll
+  for (int k = 1; k <= kWin; ++k) {
+    up *= rho;
+    rho *= kappa;
+    dn *= sig;
+    sig *= kappa;
+    if (m0 + k < kIn) v += dG[m0 + k] * up * (a2 * (x0 - float(k) * dmu) + dfc);
+    if (m0 - k >= 0) v += dG[m0 - k] * dn * (a2 * (x0 + float(k) * dmu) + dfc);
+  }
+  return v;
+}
+
+template <bool FORCE>
+__global__ void __launch_bounds__(lt::kT, 1) k_learned_tc(Args<float> a, const uint4* __restrict__ img) {
+  using namespace lt;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_holder;
+  __shared__ int failed;
+  __shared__ double shred[32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quarter = warp & 3, cg = warp >> 2;
+  const int r = 32 * quarter + lane;    // this thread's atom row (tensor-memory lane)
+  const int c0 = 16 * cg;               // its columns of a 64-wide layer
+  // everything below may read what the previous kernel wrote
+  pdl_begin();
+  const int count = FORCE ? a.counts[1] : a.n;
+  const int ntiles = (count + kRows - 1) / kRows;
+  if ((int)blockIdx.x >= ntiles) {   // no tile for this CTA (uniform): nothing allocated
+    if (!FORCE && tid == 0) a.partials[blockIdx.x] = 0.0;
+    return;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    failed = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  for (int k = tid; k < kImg / 16; k += kT) reinterpret_cast<uint4*>(sm + sW)[k] = img[k];
+  float* fb = reinterpret_cast<float*>(sm + sF);
+  if (tid < kNF) {
+    const int q = tid / kW, c = tid % kW;
+    const int src = q == 0 ? oB1 : q == 1 ? oB2 : q == 2 ? oB3 : oW4;
+    fb[tid] = tid < 4 * kW ? a.mlp_w[src + c] : (tid == 4 * kW ? a.mlp_w[oB4] : 0.f);
+  }
+  to_mma();
+  const uint32_t tm = tmem_holder;
+  const uint32_t lane_addr = tm + ((uint32_t)(32 * quarter) << 16);
+  float* P = reinterpret_cast<float*>(sm + sP);           // [cg][row][kPs]
+  float* prow = P + (cg * kRows + r) * kPs;
+  float* E4 = reinterpret_cast<float*>(sm + sE);          // pass 1: [cg][row][4]; FORCE: c[row]
+  float* G2 = reinterpret_cast<float*>(sm + sG);          // [cg][row][2]
+  const uint32_t id64 = idesc(kW, false, false), id_b64 = idesc(kW, false, true), id_b32 = idesc(kIn, false, true);
   const float rcE2 = a.k.eam_rc2;
   const float rc2 = a.ace_rc * a.ace_rc, inv_w = 1.f / (a.ace_rc - a.ace_rc_lo);
   const float kappa = __expf(-2.f * float(kEta) * float(kDmu) * float(kDmu));
-  float* xrow = xs + lane * kTcXs;   // this lane's atom: descriptors accumulate here
+  uint32_t phase = 0;
+  int fail_par = -1;
   double e_out = 0.0;
-  const int ntiles = (a.n + 31) / 32;
-  for (int tile = blockIdx.x * kTcWarps + warp; tile < ntiles; tile += gridDim.x * kTcWarps) {
-    const int i = tile * 32 + lane;
-    const bool act = i < a.n;
+  auto run = [&](auto&& issue) {
+    if (!failed) {
+      if (tid == 0) {
+        issue();
+        commit(&bar);
+      }
+      if (!wait_phase(&bar, phase)) {
+        failed = 1;
+        fail_par = (int)phase;
+      }
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  };
+  // forward epilogue of one layer: h = silu(z + b) (split) into sH; FORCE keeps
+  // silu'(z + b) in the tensor-memory columns of z
+  auto forward = [&](uint32_t col, const float* bias) {
+    float z[16], d[16];
+    tld16(lane_addr + col + c0, z);
 #pragma unroll
-    for (int m = 0; m < kIn; ++m) xrow[m] = 0.f;
-    if (act) {
+    for (int q = 0; q < 16; ++q) {
+      const float u = z[q] + bias[c0 + q];
+      const float sg = 1.f / (1.f + __expf(-u));
+      d[q] = sg * (1.f + u * (1.f - sg));
+      z[q] = u * sg;
+    }
+    put16_split(sm + sH, kHPart, r, c0, z);
+    if (FORCE) tst16(lane_addr + col + c0, d);
+  };
+  // backward epilogue: dz = dh silu'(z) (split) into sH
+  auto backward = [&](uint32_t zcol) {
+    float dh[16], d[16];
+    tld16(lane_addr + cDH + c0, dh);
+    tld16(lane_addr + zcol + c0, d);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) dh[q] *= d[q];
+    put16_split(sm + sH, kHPart, r, c0, dh);
+  };
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int q = tile * kRows + r;
+    const bool valid = q < count;
+    const int i = valid ? (FORCE ? a.clist[q] : q) : -1;
+    // ---- descriptors (and, in pass 1, the EAM terms) over this thread's entries
+#pragma unroll
+    for (int m = 0; m < kIn; ++m) prow[m] = 0.f;
+    Acc<float> zeta, pair;
+    if (valid) {
       const auto si = a.pv.self(i);
-      Acc<float> zeta, pair;
-      walk_list(a.nbl + i, a.nmax, 0, a.nnb[i], [&](int j) { return a.pv.fetch(j); },
-                [&](int, const uint4& o) {
-                  const auto d = a.pv.vec_of(si, o);
-                  const float r2 = dot3(d, d);
-                  if (!(r2 < rc2) && !(r2 < rcE2)) return;
-                  const float r = sqrtf(r2);
-                  if (r2 < rcE2) {
-                    float rho, phi;
-                    eam_terms(a.k, r, &rho, &phi);
-                    zeta.add(rho);
-                    pair.add(phi);
-                  }
-                  if (r2 < rc2) {
-                    float dfc;
-                    const float fc = ftrans(r, a.ace_rc_lo, a.ace_rc, inv_w, &dfc);
-                    add_features_window(r, fc, kappa, xrow);
-                  }
-                });
-      const float zz = zeta.value();
+      const int cnt = a.nnb[i];
+      for (int s = cg; s < cnt; s += 4) {
+        const int j = a.nbl[(size_t)s * a.nmax + i];
+        const auto d = a.pv.vec(si, j);
+        const float r2 = dot3(d, d);
+        if (!(r2 < rc2) && (FORCE || !(r2 < rcE2))) continue;
+        const float rr = sqrtf(r2);
+        if (!FORCE && r2 < rcE2) {
+          float rho, phi;
+          eam_terms(a.k, rr, &rho, &phi);
+          zeta.add(rho);
+          pair.add(phi);
+        }
+        if (r2 < rc2) {
+          float dfc;
+          const float fc = ftrans(rr, a.ace_rc_lo, a.ace_rc, inv_w, &dfc);
+          add_features_window(rr, fc, kappa, prow);
+        }
+      }
+    }
+    if (!FORCE) {
+      float* e4 = E4 + (cg * kRows + r) * 4;
+      e4[0] = zeta.s; e4[1] = zeta.c; e4[2] = pair.s; e4[3] = pair.c;
+    } else if (cg == 0) {
+      float c = 0.f;
+      if (valid) {
+        c = (float)a.cvec[i];
+        a.cvec[i] = 0.0;
+      }
+      E4[r] = c;
+    }
+    __syncthreads();
+    // G columns 8 cg .. + 7: the four partial rows in a fixed order; x0 = G / 4, split
+    {
+      float x[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int f = 8 * cg + m;
+        const float* pr = P + r * kPs + f;
+        x[m] = kSin * ((pr[0] + pr[kRows * kPs]) + (pr[2 * kRows * kPs] + pr[3 * kRows * kPs]));
+      }
+      uint4 w[3];
+      uint32_t* u0 = reinterpret_cast<uint32_t*>(&w[0]);
+      uint32_t* u1 = reinterpret_cast<uint32_t*>(&w[1]);
+      uint32_t* u2 = reinterpret_cast<uint32_t*>(&w[2]);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) split3(x[2 * m], x[2 * m + 1], u0[m], u1[m], u2[m]);
+      const int off = chunk_off(r, 8 * cg, kRows);
+#pragma unroll
+      for (int p = 0; p < 3; ++p) *reinterpret_cast<uint4*>(sm + sX + p * kXPart + off) = w[p];
+    }
+    if (!FORCE && cg == 0 && valid) {
+      // the EAM density and pair sums of the four quarters (compensated)
+      Acc<float> zs, ps;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float* e4 = E4 + (k * kRows + r) * 4;
+        zs.add(e4[0]); zs.add(-e4[1]); ps.add(e4[2]); ps.add(-e4[3]);
+      }
+      const float zz = zs.value();
       const float sz = zz > 0.f ? sqrtf(zz) : 0.f;
-      const float e = -sz + 0.5f * pair.value();
+      const float e = -sz + 0.5f * ps.value();
       a.zeta[i] = zz;
       a.xi_p[i] = zz > 0.f ? -0.5f / sz : 0.f;
       a.e_eam[i] = e;
       const double e_ind = ind_energy(a, i);   // the external indenter, if any
-      if (a.e_atom) a.e_atom[i] = (double)e + (double)e_ind;
-      e_out += (double)e + (double)e_ind;
+      if (a.e_atom) a.e_atom[i] = (double)e + e_ind;
+      e_out += (double)e + e_ind;
     }
+    // ---- forward
+    to_mma();
+    if (failed) break;
+    run([&] { mma_split(tm, cZ1, act_k(sm + sX), kXPart, wt_k(sm + sW), kImgPart, kIn, id64); });
+    forward(cZ1, fb);
+    to_mma();
+    if (failed) break;
+    run([&] { mma_split(tm, cZ2, act_k(sm + sH), kHPart, wt_k(sm + sW + kImgW1), kImgPart, kW, id64); });
+    forward(cZ2, fb + kW);
+    to_mma();
+    if (failed) break;
+    run([&] { mma_split(tm, cZ3, act_k(sm + sH), kHPart, wt_k(sm + sW + kImgW1 + kImgW2), kImgPart, kW, id64); });
+    {
+      // layer 3 and this quarter's part of the output layer (compensated); FORCE:
+      // dz3 = c w4 silu'(z3 + b3) (split) into sH
+      float z[16];
+      tld16(lane_addr + cZ3 + c0, z);
+      Dot2 dg;
+      float dz[16];
+      const float c = FORCE ? E4[r] : 0.f;
 #pragma unroll
-    for (int m = 0; m < kIn; ++m) xrow[m] *= float(kSin);
-    __syncwarp();
-#pragma unroll 1
-    for (int mt = 0; mt < 2; ++mt) {
-      const int r0 = 16 * mt + gq, r1 = r0 + 8;
-      float h1[8][4], h2[8][4];
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) h1[nt][q] = 0.f;
-#pragma unroll
-      for (int kb = 0; kb < 2; ++kb) {
-        const int c = 16 * kb + 2 * tq;
-        uint32_t ah[4], am[4], al[4];
-        split3(xs[r0 * kTcXs + c], xs[r0 * kTcXs + c + 1], ah[0], am[0], al[0]);
-        split3(xs[r1 * kTcXs + c], xs[r1 * kTcXs + c + 1], ah[1], am[1], al[1]);
-        split3(xs[r0 * kTcXs + c + 8], xs[r0 * kTcXs + c + 9], ah[2], am[2], al[2]);
-        split3(xs[r1 * kTcXs + c + 8], xs[r1 * kTcXs + c + 9], ah[3], am[3], al[3]);
-        tc_kblock(h1, ah, am, al, sf, kTcOff1, kb, lane);
+      for (int k = 0; k < 16; ++k) {
+        const float u = z[k] + fb[2 * kW + c0 + k];
+        const float sg = 1.f / (1.f + __expf(-u));
+        const float w4 = fb[3 * kW + c0 + k];
+        if (FORCE) dz[k] = c * w4 * (sg * (1.f + u * (1.f - sg)));
+        else dg.fma(w4, u * sg);
       }
-      tc_bias_silu(h1, sb, tq);
-      tc_hidden(h1, h2, sf, kTcOff2, lane);
-      tc_bias_silu(h2, sb + kW, tq);
-      tc_hidden(h2, h1, sf, kTcOff3, lane);
-      // output: g = b4 + sum_j w4_j SiLU(z3_j + b3_j), rows r0 (q = 0, 1) and r1 (q = 2, 3),
-      // a compensated dot product: each product split exactly (FMA) and each sum
-      // with its rounding error (TwoSum) carried in a second float, so that the
-      // cancelling terms of the output layer add no rounding of their own
-      Dot2 d0, d1;
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int col = 8 * nt + 2 * tq + (q & 1);
-          const float w = sb[3 * kW + col], h = silu(h1[nt][q] + sb[2 * kW + col]);
-          if (q < 2) d0.fma(w, h); else d1.fma(w, h);
-        }
-#pragma unroll
-      for (int o = 1; o <= 2; o <<= 1) {
-        d0.merge(__shfl_xor_sync(0xffffffffu, d0.s, o), __shfl_xor_sync(0xffffffffu, d0.c, o));
-        d1.merge(__shfl_xor_sync(0xffffffffu, d1.s, o), __shfl_xor_sync(0xffffffffu, d1.c, o));
-      }
-      if (tq == 0) {
-        d0.merge(sb[4 * kW], 0.f);
-        d1.merge(sb[4 * kW], 0.f);
-        gs[r0] = d0.value();
-        gs[r1] = d1.value();
+      if (FORCE) {
+        put16_split(sm + sH, kHPart, r, c0, dz);
+      } else {
+        G2[(cg * kRows + r) * 2] = dg.s;
+        G2[(cg * kRows + r) * 2 + 1] = dg.c;
       }
     }
-    __syncwarp();
-    if (act) {
-      const float g = gs[lane];
-      a.g[i] = g;
-      const uint4 q = a.posq[i];
-      a.posg[i] = make_uint4(q.x, q.y, q.z, __float_as_uint(g));
+    if (!FORCE) {
+      __syncthreads();
+      if (cg == 0 && valid) {
+        Dot2 t;
+        t.merge(fb[4 * kW], 0.f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t.merge(G2[(k * kRows + r) * 2], G2[(k * kRows + r) * 2 + 1]);
+        const float g = t.value();
+        a.g[i] = g;
+        const uint4 pq = a.posq[i];
+        a.posg[i] = make_uint4(pq.x, pq.y, pq.z, __float_as_uint(g));
+      }
+      __syncthreads();   // the next tile rewrites the partial rows
+      continue;
     }
-    __syncwarp();   // xs and gs are rewritten by the next tile
+    // ---- back-propagation (FORCE)
+    to_mma();
+    if (failed) break;
+    run([&] { mma_split(tm, cDH, act_k(sm + sH), kHPart, wt_mn(sm + sW + kImgW1 + kImgW2), kImgPart, kW, id_b64); });
+    backward(cZ2);
+    to_mma();
+    if (failed) break;
+    run([&] { mma_split(tm, cDH, act_k(sm + sH), kHPart, wt_mn(sm + sW + kImgW1), kImgPart, kW, id_b64); });
+    backward(cZ1);
+    to_mma();
+    if (failed) break;
+    run([&] { mma_split(tm, cDG, act_k(sm + sH), kHPart, wt_mn(sm + sW), kImgPart, kW, id_b32); });
+    {
+      // dG columns 8 cg .. + 7 (times the input scale) into row r of the dG rows
+      float v[8];
+      tld8(lane_addr + cDG + 8 * cg, v);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) P[r * kPs + 8 * cg + m] = kSin * v[m];
+    }
+    __syncthreads();
+    if (valid) {
+      // the force of this thread's neighbour entries
+      const float* dG = P + r * kPs;
+      const auto sk = a.pv.self(i);
+      const int cnt = a.nnb[i];
+      double fk[3] = {0.0, 0.0, 0.0};
+      for (int s = cg; s < cnt; s += 4) {
+        const int j = a.nbl[(size_t)s * a.nmax + i];
+        const auto d = a.pv.vec(sk, j);
+        const float r2 = dot3(d, d);
+        if (!(r2 < rc2)) continue;
+        const float rr = sqrtf(r2);
+        float dfc;
+        const float fc = ftrans(rr, a.ace_rc_lo, a.ace_rc, inv_w, &dfc);
+        const float v = dfeatures_window(rr, fc, dfc, kappa, dG) / rr;
+        const double f0 = (double)(v * d.x), f1 = (double)(v * d.y), f2 = (double)(v * d.z);
+        atomicAdd(&a.force[3 * j], -f0);
+        atomicAdd(&a.force[3 * j + 1], -f1);
+        atomicAdd(&a.force[3 * j + 2], -f2);
+        fk[0] += f0; fk[1] += f1; fk[2] += f2;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) atomicAdd(&a.force[3 * i + k], fk[k]);
+    }
+    __syncthreads();   // the next tile rewrites the dG rows (partial rows) and c
   }
-  const double tot = block_sum(e_out, sh);
-  if (tid == 0) a.partials[blockIdx.x] = tot;
-}
-
-size_t tc_smem_bytes() {
-  return sizeof(uint2) * kTcFrag + sizeof(float) * (kTcBias + kTcWarps * (32 * kTcXs + 32));
+  __syncthreads();   // `failed` is uniform from here on
+  if (!FORCE) {
+    const double tot = block_sum(e_out, shred);
+    if (tid == 0) a.partials[blockIdx.x] = tot;
+  }
+  if (failed && tid == 0) {
+    atomicOr(&a.status[ST_TIMEOUT], 1);
+    if (fail_par >= 0) wait_phase(&bar, (uint32_t)fail_par);   // the MMAs in flight, once more (bounded)
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(512));
 }
 
 // -grad sum_k c_k g_k for the atoms with c_k != 0 (learned counterpart of
@@ -549,7 +738,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_cvec_compact(Args<T> a) {
   pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool pred = i < a.n && a.cvec[i] != 0.0;
+  const bool pred = i < a.n && (__double_as_longlong(a.cvec[i]) << 1) != 0;   // c != +-0, on the bits
   const unsigned mask = __ballot_sync(0xffffffffu, pred);
   const int lane = threadIdx.x & 31;
   int base = 0;
@@ -601,12 +790,11 @@ __global__ void k_adam(float* p, const float* g, float* m, float* v, int t, floa
 }  // namespace
 
 // float64: the per-thread network, one 128-atom block per partial; float32: the
-// tensor-core kernel on a.n_part_p1 persistent blocks (learned_tc_grid)
+// tensor-core kernel on a.n_part_p1 persistent CTAs (learned_tc_blocks)
 template <typename T> void launch_pass1_learned(const Args<T>& a, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    const size_t bytes = tc_smem_bytes();
-    cudaFuncSetAttribute(k_pass1_learned_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    launch_pdl(k_pass1_learned_tc, a.n_part_p1, kTcWarps * 32, bytes, s, a, a.mlp_frag);
+    cudaFuncSetAttribute(k_learned_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt::kSmem);
+    launch_pdl(k_learned_tc<false>, a.n_part_p1, lt::kT, lt::kSmem, s, a, a.mlp_img);
   } else {
     const size_t bytes = sizeof(T) * APIP_MLP_NPARAM;
     cudaFuncSetAttribute(k_pass1_learned<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -614,34 +802,49 @@ template <typename T> void launch_pass1_learned(const Args<T>& a, cudaStream_t s
   }
 }
 
+// Resident CTAs of the tensor-core learned kernels on this device (one per SM).
 int learned_tc_slots() {
-  const size_t bytes = tc_smem_bytes();
-  if (cudaFuncSetAttribute(k_pass1_learned_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
-    return 0;
-  int occ = 0, dev = 0, sms = 0;
+  int occ = 1, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass1_learned_tc, kTcWarps * 32, bytes) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_learned_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt::kSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_learned_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt::kSmem) != cudaSuccess)
     return 0;
-  return occ * sms;
+  for (int f = 0; f < 2; ++f) {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f ? k_learned_tc<true> : k_learned_tc<false>, lt::kT,
+                                                      lt::kSmem) != cudaSuccess)
+      return 0;
+    occ = f ? (o < occ ? o : occ) : o;
+  }
+  // one CTA per SM: each holds all 512 tensor-memory columns
+  return occ < 1 ? 0 : sms;
 }
 
 int learned_tc_blocks(int n, int slots) {
-  const int need = (n + kTcWarps * 32 - 1) / (kTcWarps * 32);
+  const int need = (n + lt::kRows - 1) / lt::kRows;
   return need < 1 ? 1 : (need < slots ? need : slots);
 }
 
-void launch_mlp_frags(const float* w, void* frag, cudaStream_t s) {
-  k_mlp_frags<<<(kTcFrag + 255) / 256, 256, 0, s>>>(w, reinterpret_cast<uint2*>(frag));
+void launch_mlp_images(const float* w, void* img, cudaStream_t s) {
+  constexpr int pairs = (kW * kIn + 2 * kW * kW) / 2;
+  k_mlp_images<<<(pairs + 255) / 256, 256, 0, s>>>(w, reinterpret_cast<unsigned char*>(img));
 }
 
-size_t mlp_frag_bytes() { return sizeof(uint2) * kTcFrag; }
+size_t mlp_img_bytes() { return lt::kImg; }
 
 template <typename T> void launch_mlp_force(const Args<T>& a, cudaStream_t s) {
   launch_pdl(k_cvec_compact<T>, (a.n + 255) / 256, 256, 0, s, a);
-  int blocks = (a.n + 127) / 128;   // the list holds at most n atoms; a grid-stride loop covers it
-  if (blocks > 2048) blocks = 2048;
-  launch_pdl(k_mlp_force<T>, blocks, 128, 0, s, a);
+  if constexpr (sizeof(T) == 4) {
+    // persistent CTAs over the tiles of the compacted list (its length is on the device)
+    cudaFuncSetAttribute(k_learned_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt::kSmem);
+    launch_pdl(k_learned_tc<true>, a.learned_grid, lt::kT, lt::kSmem, s, a, a.mlp_img);
+  } else {
+    int blocks = (a.n + 127) / 128;   // the list holds at most n atoms; a grid-stride loop covers it
+    if (blocks > 2048) blocks = 2048;
+    launch_pdl(k_mlp_force<T>, blocks, 128, 0, s, a);
+  }
 }
 
 template <typename T> void launch_descriptors(const Args<T>& a, uint16_t* out, cudaStream_t s) {

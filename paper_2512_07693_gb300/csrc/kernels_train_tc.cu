@@ -58,9 +58,12 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace apip {
 namespace {
+
+using namespace tc;
 
 constexpr int kIn = APIP_MLP_IN, kW = APIP_MLP_WIDTH;
 constexpr int oW1 = 0, oB1 = oW1 + kW * kIn, oW2 = oB1 + kW, oB2 = oW2 + kW * kW, oW3 = oB2 + kW,
@@ -102,79 +105,6 @@ constexpr uint32_t cZ1 = 0, cZ2 = 64, cZ3 = 128, cDH = 192, cW32 = 256, cW1 = 40
 constexpr int kNB = 2 * kW + 16, kNB1 = kIn + 16;
 static_assert(cW32 + kNB <= cW1 && cW1 + kNB1 <= 512, "tensor memory");
 
-// element (row, k) of a chunk-major operand with `rows` rows
-__host__ __device__ constexpr int chunk_off(int row, int k, int rows) {
-  return (k >> 3) * (rows * 16) + row * 16 + (k & 7) * 2;
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// An operand for the tensor cores: its shared-memory start, the leading and
-// stride byte offsets of its descriptor, and the bytes to advance per K = 16.
-struct Opnd {
-  uint32_t addr, lbo, sbo, kstep;
-};
-// 128-sample operands: K-major (samples = M) and MN-major (samples = K)
-__device__ __forceinline__ Opnd act_k(const unsigned char* p) { return {smem_u32(p), 2048u, 128u, 4096u}; }
-__device__ __forceinline__ Opnd act_mn(const unsigned char* p) { return {smem_u32(p), 128u, 2048u, 256u}; }
-// 64-row weights: K-major (forward) and MN-major (the transpose, back-propagation)
-__device__ __forceinline__ Opnd wt_k(const unsigned char* p) { return {smem_u32(p), 1024u, 128u, 2048u}; }
-__device__ __forceinline__ Opnd wt_mn(const unsigned char* p) { return {smem_u32(p), 128u, 1024u, 256u}; }
-
-// Shared-memory matrix descriptor: start address, leading and stride byte
-// offsets, the descriptor version of this tensor-core generation, no swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3fff) | ((uint64_t)((lbo >> 4) & 0x3fff) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3fff) << 32) | ((uint64_t)1 << 46);
-}
-
-// Instruction descriptor, kind::f16: float32 D, bfloat16 A and B, M = 128; bits
-// 15 / 16 select an MN-major A / B.
-__device__ __forceinline__ uint32_t idesc(int N, bool a_mn, bool b_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
-// D (tensor memory, column d) (+)= A B^T over K, in K = 16 steps (one thread).
-__device__ __forceinline__ void mma(uint32_t tmem, uint32_t d, Opnd A, Opnd B, int K, uint32_t id, bool accumulate) {
-  for (int kk = 0; kk < K / 16; ++kk) {
-    const uint64_t ad = sdesc(A.addr + kk * A.kstep, A.lbo, A.sbo), bd = sdesc(B.addr + kk * B.kstep, B.lbo, B.sbo);
-    const uint32_t acc = (accumulate || kk > 0) ? 1u : 0u;
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + d),
-        "l"(ad), "l"(bd), "r"(id), "r"(acc));
-  }
-}
-
-__device__ __forceinline__ void commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ unsigned long long now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait for the barrier phase with the given parity (two seconds).
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
-  const unsigned long long t0 = now_ns();
-  while (true) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (now_ns() - t0 > 2000000000ull) return false;
-  }
-}
-
 // G rows 128 tile .. + 127 into an input buffer: four boxes of 8 features x 128
 // samples (TMA; rows past the batch read as zeros), completing on `bar`.
 __device__ __forceinline__ void load_tile(const CUtensorMap* map, unsigned char* dst, uint64_t* bar, int tile) {
@@ -187,33 +117,6 @@ __device__ __forceinline__ void load_tile(const CUtensorMap* map, unsigned char*
             smem_u32(dst + c * kChunk)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(8 * c), "r"(tile * kS), "r"(smem_u32(bar))
         : "memory");
-}
-
-// 16 consecutive float32 columns of this thread's tensor-memory lane.
-__device__ __forceinline__ void tld16(uint32_t addr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
-}
-
-// ... and the reverse: 16 float32 values into this thread's lane.
-__device__ __forceinline__ void tst16(uint32_t addr, const float* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-          addr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
-      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
-      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
-      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
-      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
-      : "memory");
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // Sixteen float32 values as bfloat16 into row r of a chunk-major operand at
@@ -230,21 +133,6 @@ __device__ __forceinline__ void put16(unsigned char* base, int r, int c0, const 
     }
     *reinterpret_cast<uint4*>(base + chunk_off(r, c0 + 8 * h, kS)) = w;
   }
-}
-
-__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
-// The logistic function (hardware exponential and approximate division: a few
-// ulp, far below the bfloat16 rounding of the GEMM operands it feeds).
-__device__ __forceinline__ float sig(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
-
-// Operands written by the threads are made visible to the tensor cores, and the
-// threads' tensor-memory accesses are ordered before the next MMA.
-__device__ __forceinline__ void to_mma() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
 __global__ void __launch_bounds__(kT, 1)
