@@ -182,35 +182,6 @@ __device__ __forceinline__ void group_setup(const Args<T>& a, int grp, int count
   __syncthreads();
 }
 
-// Float-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2): the
-// error-free sum (Knuth's TwoSum) and product (an FMA gives the rounding error of
-// a product exactly), written with the _rn intrinsics, which the compiler never
-// contracts or reorders.
-struct FF { float hi, lo; };
-__device__ __forceinline__ FF ff_sum(float a, float b) {
-  const float s = __fadd_rn(a, b), bp = __fsub_rn(s, a);
-  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp))};
-}
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-  const FF s = ff_sum(a.hi, b.hi);
-  return ff_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ FF ff_prod(float a, float b) {
-  const float p = __fmul_rn(a, b);
-  return {p, __fmaf_rn(a, b, -p)};
-}
-
-// The separation of two fixed-point coordinates in float-float: the exact
-// integer difference d (split as d_h + d_l, d_h = d with its low 8 bits cleared,
-// both exact in float) times the grid unit u = u_hi + u_lo.
-__device__ __forceinline__ FF ff_coord(int d, float u_hi, float u_lo) {
-  const int dh = d & ~0xff;
-  const float h = (float)dh, l = (float)(d - dh);
-  const FF p = ff_prod(h, u_hi);
-  const float small = __fmaf_rn(h, u_lo, __fmaf_rn(l, u_hi, __fmul_rn(l, u_lo)));
-  return ff_sum(p.hi, __fadd_rn(p.lo, small));
-}
-
 // Float32 path: the switch of the group's transition atoms (dlam != 0 after pass
 // 2), recomputed with accurate pair distances and sums of Eq. 6.  Pass 2 takes
 // w-bar_i and sum_k g_k w(r_ik) in float32 from float32 distances, whose

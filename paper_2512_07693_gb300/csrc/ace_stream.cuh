@@ -123,8 +123,7 @@ __device__ __forceinline__ void coupling(const T* Ak, T* Gk, int a1, int a2, int
     T gC[NM];
 #pragma unroll
     for (int M = 0; M < NM; ++M) gC[M] = T(0);
-    for (int p = pb; p < pe; ++p) {
-      const Rec<T> r = ld(part + p);
+    auto adj_partner = [&](const Rec<T>& r) {
       const T k = r.k1 + dfs * r.k2;
       const T* y = Ak + r.key * NAT;
       T* gy = Gk + r.key * NAT;
@@ -133,7 +132,8 @@ __device__ __forceinline__ void coupling(const T* Ak, T* Gk, int a1, int a2, int
         gC[M] += k * y[M * NAT];
         acc_add<PRIV>(gy + M * NAT, k * C[M]);
       }
-    }
+    };
+    for (int p = pb; p < pe; ++p) adj_partner(ld(part + p));
     T g1[N1], g2[N2];
 #pragma unroll
     for (int i = 0; i < N1; ++i) g1[i] = T(0);
@@ -241,8 +241,13 @@ __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev
         f1.add(rc.k1 * d);
         f2.add(rc.k2 * d);
       }
-      for (int u = slice; u < t.ncpl; u += NS)
-        coupling_dispatch<T, K, LMAX, NAT, false, PRIV>(__ldg(t.cpl + u), Ak, Gk, t.part, T(0), f1, f2);
+      // the next coupling's entry is loaded while this one is evaluated
+      uint4 cn = slice < t.ncpl ? __ldg(t.cpl + slice) : make_uint4(0u, 0u, 0u, 0u);
+      for (int u = slice; u < t.ncpl; u += NS) {
+        const uint4 cp = cn;
+        if (u + NS < t.ncpl) cn = __ldg(t.cpl + u + NS);
+        coupling_dispatch<T, K, LMAX, NAT, false, PRIV>(cp, Ak, Gk, t.part, T(0), f1, f2);
+      }
       T v1 = f1.value(), v2 = f2.value();
 #pragma unroll
       for (int o = NAT; o < 32; o <<= 1) {
@@ -288,8 +293,12 @@ __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev
           }
         }
       }
-      for (int u = slice; u < t.ncpl; u += NS)
-        coupling_dispatch<T, K, LMAX, NAT, true, PRIV>(__ldg(t.cpl + u), Ak, Gk, t.part, dfs, unused1, unused2);
+      uint4 cn = slice < t.ncpl ? __ldg(t.cpl + slice) : make_uint4(0u, 0u, 0u, 0u);
+      for (int u = slice; u < t.ncpl; u += NS) {
+        const uint4 cp = cn;
+        if (u + NS < t.ncpl) cn = __ldg(t.cpl + u + NS);
+        coupling_dispatch<T, K, LMAX, NAT, true, PRIV>(cp, Ak, Gk, t.part, dfs, unused1, unused2);
+      }
     }
     __syncthreads();
     // omega = dE/dA a_scale lam into the A region (A is not read again)

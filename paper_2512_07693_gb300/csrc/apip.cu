@@ -75,7 +75,7 @@ void free_all(apip_ctx* c) {
   c->prof_pending.clear();
   c->prof_pool.clear();
   void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nnb_e, c->posg, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
-                  c->csp, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
+                  c->csp, c->csp_idx, c->csp_owner, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->clist, c->counts, c->flags, c->status, c->partials, c->thermo_part,
                   c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_img, c->mlp_ws};
   for (void* q : ptrs)
@@ -143,9 +143,12 @@ apip_status set_geometry(apip_ctx* ctx, const double* box, cudaStream_t s) {
     ctx->cell_q = nullptr;
     APIP_CK(cudaMalloc(&ctx->cell_count, sizeof(int) * ncell));
     APIP_CK(cudaMemsetAsync(ctx->cell_count, 0, sizeof(int) * ncell, s));
-    APIP_CK(cudaMalloc(&ctx->cell_atoms, sizeof(int) * (size_t)ncell * ctx->p.cell_cap));
+    // members: FP64 path their indices, FP32 path their fixed-point positions with
+    // the index in .w
     if (ctx->p.precision == APIP_FP32)
       APIP_CK(cudaMalloc(&ctx->cell_q, sizeof(uint4) * (size_t)ncell * ctx->p.cell_cap));
+    else
+      APIP_CK(cudaMalloc(&ctx->cell_atoms, sizeof(int) * (size_t)ncell * ctx->p.cell_cap));
     ctx->ncell_alloc = ncell;
   }
   ctx->ncell = ncell;
@@ -241,7 +244,7 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.id = id;
   a.nnb_e = c->nnb_e; a.posg = c->posg;
   a.nnb = c->nnb; a.nbl = c->nbl; a.nbl_tmp = c->nbl_tmp; a.pos_ref = c->pos_ref; a.posq = c->posq; a.posq_ref = c->posq_ref;
-  a.id2idx = c->id2idx; a.csp = c->csp; a.cell_count = c->cell_count; a.cell_atoms = c->cell_atoms;
+  a.id2idx = c->id2idx; a.csp = c->csp; a.csp_idx = c->csp_idx; a.csp_owner = c->csp_owner; a.cell_count = c->cell_count; a.cell_atoms = c->cell_atoms;
   a.ncell = c->ncell;
   a.cell_q = c->cell_q;
   a.zeta = as<T>(c->zeta); a.xi_p = as<T>(c->xi_p); a.e_eam = as<T>(c->e_eam); a.g = as<T>(c->g);
@@ -563,6 +566,8 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   }
   APIP_ALLOC(ctx->id2idx, sizeof(int) * N);
   APIP_ALLOC(ctx->csp, sizeof(int) * N * kCspCap);
+  APIP_ALLOC(ctx->csp_idx, sizeof(int) * N * kCspCap);
+  APIP_ALLOC(ctx->csp_owner, sizeof(int) * N);
   void** per_atom[] = {&ctx->zeta, &ctx->xi_p, &ctx->e_eam, &ctx->g, &ctx->wbar, &ctx->dd, &ctx->lam, &ctx->dlam, &ctx->e_ace};
   for (void** q : per_atom) APIP_ALLOC(*q, es * N);
   APIP_ALLOC(ctx->cvec, sizeof(double) * N);
@@ -676,6 +681,7 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   cudaError_t e = cudaMemcpy(ctx->ace_tab, host.data(), host.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(ctx->id2idx, 0xff, sizeof(int) * N);
   if (e == cudaSuccess) e = cudaMemset(ctx->csp, 0xff, sizeof(int) * N * kCspCap);
+  if (e == cudaSuccess) e = cudaMemset(ctx->csp_owner, 0xff, sizeof(int) * N);
   if (e == cudaSuccess) e = cudaMemset(ctx->cvec, 0, sizeof(double) * N);
   if (e == cudaSuccess) e = cudaMemset(ctx->ind_acc, 0, sizeof(double) * 3);
   if (e == cudaSuccess) e = cudaMemset(ctx->counts, 0, sizeof(int) * 4);
@@ -734,6 +740,8 @@ apip_status apip_init_csp_pairs(apip_ctx* ctx, const double* pos, const double b
   if (n == 0) { ctx->csp_ready = true; return APIP_OK; }
   Args<double> a = make_args<double>(ctx, pos, id, (int)n, nullptr, nullptr);
   launch_csp_init(a, (cudaStream_t)stream);
+  // new partner rows: the cached partner indices are looked up again
+  cudaMemsetAsync(ctx->csp_owner, 0xff, sizeof(int) * ctx->nmax, (cudaStream_t)stream);
   st = launch_status(ctx);
   if (st == APIP_OK) ctx->csp_ready = true;
   return st;
@@ -744,6 +752,7 @@ apip_status apip_set_csp_pairs(apip_ctx* ctx, const int32_t* partner_ids, int64_
   if (n < 0 || n > ctx->nmax) return fail(ctx, APIP_ERR_ARG, "n must be in [0, n_atoms_max]");
   if (n > 0 && !partner_ids) return fail(ctx, APIP_ERR_ARG, "partner_ids must not be NULL");
   if (n > 0) launch_set_csp(partner_ids, ctx->csp, (int)n, ctx->p.csp_nnb, (cudaStream_t)stream);
+  cudaMemsetAsync(ctx->csp_owner, 0xff, sizeof(int) * ctx->nmax, (cudaStream_t)stream);
   const apip_status st = launch_status(ctx);
   if (st == APIP_OK) ctx->csp_ready = true;
   return st;

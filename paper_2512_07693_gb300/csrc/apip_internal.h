@@ -151,6 +151,8 @@ struct apip_ctx {
   uint4* posq_ref = nullptr;   // FP32 path: posq at the last neighbour-list build
   int* id2idx = nullptr;       // [nmax]
   int* csp = nullptr;          // [nmax][kCspCap] partner ids
+  int* csp_idx = nullptr;      // [nmax][kCspCap] partner indices of the atom at each index (cache)
+  int* csp_owner = nullptr;    // [nmax] id of the atom each csp_idx row was built for (-1: none)
 
   // per-atom arrays (element size = precision)
   void* zeta = nullptr; void* xi_p = nullptr; void* e_eam = nullptr; void* g = nullptr;

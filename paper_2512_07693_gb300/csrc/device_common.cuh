@@ -180,6 +180,35 @@ __host__ __device__ __forceinline__ unsigned int fixed_coord(double w, unsigned 
   return (unsigned int)((hi >> sh) & 0xffffffffull);
 }
 
+// Float-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2): the
+// error-free sum (Knuth's TwoSum) and product (an FMA gives the rounding error of
+// a product exactly), written with the _rn intrinsics, which the compiler never
+// contracts or reorders.
+struct FF { float hi, lo; };
+__device__ __forceinline__ FF ff_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bp = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp))};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const FF s = ff_sum(a.hi, b.hi);
+  return ff_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ FF ff_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+// The separation of two fixed-point coordinates in float-float: the exact
+// integer difference d (split as d_h + d_l, d_h = d with its low 8 bits cleared,
+// both exact in float) times the grid unit u = u_hi + u_lo.
+__device__ __forceinline__ FF ff_coord(int d, float u_hi, float u_lo) {
+  const int dh = d & ~0xff;
+  const float h = (float)dh, l = (float)(d - dh);
+  const FF p = ff_prod(h, u_hi);
+  const float small = __fmaf_rn(h, u_lo, __fmaf_rn(l, u_hi, __fmul_rn(l, u_lo)));
+  return ff_sum(p.hi, __fadd_rn(p.lo, small));
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

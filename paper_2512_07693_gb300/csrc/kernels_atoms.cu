@@ -120,20 +120,26 @@ __global__ void k_bin(Args<T> a) {
   const int cell = (c[2] * a.geo.nc[1] + c[1]) * a.geo.nc[0] + c[0];
   const int slot = atomicAdd(&a.cell_count[cell], 1);
   if (slot < a.cell_cap) {
-    a.cell_atoms[cell * a.cell_cap + slot] = i;
-    if constexpr (sizeof(T) == 4) a.cell_q[(size_t)cell * a.cell_cap + slot] = a.posq[i];
+    if constexpr (sizeof(T) == 4) {
+      const uint4 q = a.posq[i];
+      a.cell_q[(size_t)cell * a.cell_cap + slot] = make_uint4(q.x, q.y, q.z, (unsigned)i);
+    } else {
+      a.cell_atoms[cell * a.cell_cap + slot] = i;
+    }
   } else {
     atomicOr(&a.status[ST_CELL_OVERFLOW], 1);
     atomicMax(&a.status[ST_MAX_CELL], slot + 1);
   }
 }
 
-// One thread per atom: the candidates go to the scratch list in cell order,
-// tagged in bits 30-31 by distance class (0: within the EAM cutoff, 1: within
-// the EAM cutoff + skin, 2: beyond); the same thread then writes the final list
-// class by class.  The passes' EAM sums stop at nnb_e: a pair now within the EAM
-// cutoff was within cutoff + skin at the build, since each atom has moved less
-// than skin / 2.
+// One thread per atom.  Each candidate within r_list is classed by its distance:
+// 0 within the EAM cutoff, 1 within the EAM cutoff + skin, 2 beyond.  Class 0
+// goes straight to the list, classes 1 and 2 to the two ends of the atom's
+// column of the scratch list; at the end they are copied behind class 0, so the
+// list holds class 0, then 1, then 2, each in cell order.  The passes' EAM sums
+// stop at nnb_e (classes 0 and 1: a pair now within the EAM cutoff was within
+// cutoff + skin at the build, since each atom has moved less than skin / 2), and
+// the class order keeps the lanes of a warp on the same branch of those sums.
 template <typename T>
 __global__ void k_nbfill(Args<T> a) {
   pdl_begin();
@@ -143,70 +149,69 @@ __global__ void k_nbfill(Args<T> a) {
   int c[3];
   atom_cell(a, i, c);
   const auto si = a.pv.self(i);
-  // calls f(j, r^2) for every atom j != i within r_list, in cell order
-  auto scan = [&](auto&& f) {
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int cz = (c[2] + dz + a.geo.nc[2]) % a.geo.nc[2];
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int cy = (c[1] + dy + a.geo.nc[1]) % a.geo.nc[1];
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int cx = (c[0] + dx + a.geo.nc[0]) % a.geo.nc[0];
-          const int cell = (cz * a.geo.nc[1] + cy) * a.geo.nc[0] + cx;
-          const int m = min(a.cell_count[cell], a.cell_cap);
+  const T rin2 = T(a.r_e_in2), rmid2 = T(a.r_e_mid2);
+  int n0 = 0, n1 = 0, n2 = 0;   // class counts
+  int w1 = 0, w2 = 0;           // class 1, 2 entries written to the scratch ends
+  auto keep = [&](int j, T r2) {
+    if (r2 < rin2) {
+      if (n0 < a.max_nb) a.nbl[(size_t)n0 * a.nmax + i] = j;
+      ++n0;
+    } else if (r2 < rmid2) {
+      if (w1 + w2 < a.max_nb) a.nbl_tmp[(size_t)(w1++) * a.nmax + i] = j;   // the ends meet only on overflow
+      ++n1;
+    } else {
+      if (w1 + w2 < a.max_nb) a.nbl_tmp[(size_t)(a.max_nb - 1 - w2++) * a.nmax + i] = j;
+      ++n2;
+    }
+  };
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int cz = (c[2] + dz + a.geo.nc[2]) % a.geo.nc[2];
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int cy = (c[1] + dy + a.geo.nc[1]) % a.geo.nc[1];
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int cx = (c[0] + dx + a.geo.nc[0]) % a.geo.nc[0];
+        const int cell = (cz * a.geo.nc[1] + cy) * a.geo.nc[0] + cx;
+        const int m = min(a.cell_count[cell], a.cell_cap);
+        if constexpr (sizeof(T) == 4) {
+          // float comparison against r_list^2 rounded up: the list holds every pair
+          // whose float distance is below r_list (and perhaps a few at r_list); the
+          // member's index rides in .w of its fixed-point position
+          const uint4* cq = a.cell_q + (size_t)cell * a.cell_cap;
+          const float rl2 = __double2float_ru(a.r_list2);
+#pragma unroll 2
+          for (int k = 0; k < m; ++k) {
+            const uint4 o = cq[k];
+            const float ex = (float)(int)(o.x - si.q.x) * a.pv.unit[0];
+            const float ey = (float)(int)(o.y - si.q.y) * a.pv.unit[1];
+            const float ez = (float)(int)(o.z - si.q.z) * a.pv.unit[2];
+            const float r2 = ex * ex + ey * ey + ez * ez;
+            if (r2 < rl2 && (int)o.w != i) keep((int)o.w, r2);
+          }
+        } else {
           const int* v = a.cell_atoms + (size_t)cell * a.cell_cap;
-          if constexpr (sizeof(T) == 4) {
-            // float comparison against r_list^2 rounded up: the list holds every pair
-            // whose float distance is below r_list (and perhaps a few at r_list)
-            const uint4* cq = a.cell_q + (size_t)cell * a.cell_cap;
-            const float rl2 = __double2float_ru(a.r_list2);
-            for (int k = 0; k < m; ++k) {
-              const uint4 o = cq[k];
-              const float ex = (float)(int)(o.x - si.q.x) * a.pv.unit[0];
-              const float ey = (float)(int)(o.y - si.q.y) * a.pv.unit[1];
-              const float ez = (float)(int)(o.z - si.q.z) * a.pv.unit[2];
-              const float r2 = ex * ex + ey * ey + ez * ez;
-              if (r2 < rl2) {
-                const int j = v[k];
-                if (j != i) f(j, r2);
-              }
-            }
-          } else {
-            for (int k = 0; k < m; ++k) {
-              const int j = v[k];
-              if (j == i) continue;
-              const auto d = a.pv.vec(si, j);
-              const T r2 = dot3(d, d);
-              if ((double)r2 < a.r_list2) f(j, r2);
-            }
+          for (int k = 0; k < m; ++k) {
+            const int j = v[k];
+            if (j == i) continue;
+            const auto d = a.pv.vec(si, j);
+            const T r2 = dot3(d, d);
+            if ((double)r2 < a.r_list2) keep(j, r2);
           }
         }
       }
     }
-  };
-  const T rin2 = T(a.r_e_in2), rmid2 = T(a.r_e_mid2);
-  int cnt = 0;
-  scan([&](int j, T r2) {
-    const unsigned tag = r2 < rin2 ? 0u : (r2 < rmid2 ? 1u : 2u);
-    if (cnt < a.max_nb) a.nbl_tmp[(size_t)cnt * a.nmax + i] = (int)((unsigned)j | (tag << 30));
-    ++cnt;
-  });
+  }
+  const int cnt = n0 + n1 + n2;
   if (cnt > a.max_nb) {
     atomicOr(&a.status[ST_NB_OVERFLOW], 1);
     atomicMax(&a.status[ST_MAX_NNB], cnt);
   }
-  const int kept = min(cnt, a.max_nb);
-  a.nnb[i] = kept;
-  // the final list, by build-time distance class: the entries within the EAM
-  // cutoff first, then those within the EAM cutoff + skin (nnb_e counts the two),
-  // then the rest, each class in cell order (this thread's own scratch entries)
-  int p = 0;
-  for (unsigned tag = 0; tag < 3; ++tag) {
-    for (int s = 0; s < kept; ++s) {
-      const unsigned e = (unsigned)a.nbl_tmp[(size_t)s * a.nmax + i];
-      if ((e >> 30) == tag) a.nbl[(size_t)(p++) * a.nmax + i] = (int)(e & 0x3fffffffu);
-    }
-    if (tag == 1) a.nnb_e[i] = p;
-  }
+  // the kept entries: the first max_nb in class order
+  const int k0 = min(n0, a.max_nb), k1 = min(w1, a.max_nb - k0), k2 = min(w2, a.max_nb - k0 - k1);
+  for (int s = 0; s < k1; ++s) a.nbl[(size_t)(k0 + s) * a.nmax + i] = a.nbl_tmp[(size_t)s * a.nmax + i];
+  for (int s = 0; s < k2; ++s)
+    a.nbl[(size_t)(k0 + k1 + s) * a.nmax + i] = a.nbl_tmp[(size_t)(a.max_nb - 1 - s) * a.nmax + i];
+  a.nnb[i] = k0 + k1 + k2;
+  a.nnb_e[i] = k0 + k1;
   if (sizeof(T) == 4) {
     a.posq_ref[i] = a.posq[i];
   } else {
@@ -307,6 +312,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_pass1(Args<T
     const T rc2 = a.k.eam_rc2, rc = a.k.eam_rc, rlo = a.k.eam_rc_lo, inv_w = a.k.eam_inv_w;
     const T A = a.k.eam_A, beta = a.k.eam_beta, re = a.k.eam_re, D = a.k.eam_D, alpha = a.k.eam_alpha,
             r0 = a.k.eam_r0;
+    const bool paper_g = a.lam_mode == APIP_LAM_PAPER;
     Acc<T> zeta, pair;
     walk_list(a.nbl + i, a.nmax, 0, a.nnb_e[i], [&](int j) { return a.pv.fetch(j); },
               [&](int, const auto& o) {
@@ -332,40 +338,63 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_pass1(Args<T
     if (a.e_atom) a.e_atom[i] = (double)e + e_ind;
     e_out = e + (T)e_ind;
     T g = T(0);
-    if (a.lam_mode == APIP_LAM_PAPER) {
-      // the partner ids and their indices are gathered in two rounds of
-      // independent loads (idx = -1: no partner, -2: id out of range)
-      const int idv = a.id[i];   // the partner row of this atom's id (an invalid id: reported
-      const bool idok = idv >= 0 && idv < a.nmax;   // by prep, no partners here)
+    if (paper_g) {
+      const int idv = a.id[i], own = a.csp_owner[i];
+      const int4* c4 = reinterpret_cast<const int4*>(a.csp_idx + (size_t)i * kCspCap);
+      const int4 cq0 = c4[0], cq1 = c4[1];
+      // g_i = sum over the partner pairs of |r_ia + r_ib|^2 (Eq. B3).  The partner
+      // ids come from the row of this atom's id; their indices from the cache of
+      // the last call (valid while the atom at index i keeps its id and its
+      // partners keep their indices), checked against the ids, else from the
+      // id -> index map, and the cache rewritten (idx = -1: no partner, -2: id
+      // out of range)
+      const bool idok = idv >= 0 && idv < a.nmax;   // an invalid id: reported by prep, no partners
       const int4* pr4 = reinterpret_cast<const int4*>(a.csp + (size_t)(idok ? idv : 0) * kCspCap);
       static_assert(kCspCap == 8, "two int4 rows of partner ids");
-      int idx[kCspCap], pid[kCspCap];
-      {
-        const int4 none = make_int4(-1, -1, -1, -1);
-        const int4 p0 = idok ? pr4[0] : none, p1 = idok ? pr4[1] : none;
-        const int pr[kCspCap] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+      const int4 none = make_int4(-1, -1, -1, -1);
+      const int4 p0 = idok ? pr4[0] : none, p1 = idok ? pr4[1] : none;
+      int pid[kCspCap] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+      int idx[kCspCap] = {cq0.x, cq0.y, cq0.z, cq0.w, cq1.x, cq1.y, cq1.z, cq1.w};
 #pragma unroll
-        for (int k = 0; k < kCspCap; ++k) {
-          pid[k] = pr[k];
-          idx[k] = (k >= a.csp_nnb || pr[k] < 0) ? -1 : (pr[k] >= a.nmax ? -2 : a.id2idx[pr[k]]);
-        }
+      for (int k = 0; k < kCspCap; ++k)
+        if (k >= a.csp_nnb) pid[k] = -1;
+      // a partner entry holds: its index (checked below), -1 for no partner, -2 for
+      // an id out of range
+      auto holds = [&](int k) {
+        if (pid[k] < 0) return idx[k] == -1;
+        if (pid[k] >= a.nmax) return idx[k] == -2;
+        return idx[k] >= 0 && idx[k] < a.n && a.id[idx[k]] == pid[k];
+      };
+      bool hit = own == idv;
+#pragma unroll
+      for (int k = 0; k < kCspCap; ++k) hit = hit && holds(k);
+      if (!hit) {
+#pragma unroll
+        for (int k = 0; k < kCspCap; ++k) idx[k] = pid[k] < 0 ? -1 : (pid[k] >= a.nmax ? -2 : a.id2idx[pid[k]]);
+        int4* c4 = reinterpret_cast<int4*>(a.csp_idx + (size_t)i * kCspCap);
+        c4[0] = make_int4(idx[0], idx[1], idx[2], idx[3]);
+        c4[1] = make_int4(idx[4], idx[5], idx[6], idx[7]);
+        a.csp_owner[i] = idv;
       }
       bool bad = false;
       Acc<T> gs;
 #pragma unroll
       for (int k = 0; k < kCspCap / 2; ++k) {
-        const int ia = idx[2 * k], ib = idx[2 * k + 1];
-        if (ia == -1 || ib == -1) continue;
+        if (pid[2 * k] < 0 || pid[2 * k + 1] < 0) continue;
         // the index must hold that partner now: the id -> index map keeps the
         // entries of ids that are no longer present
-        if (ia < 0 || ib < 0 || ia >= a.n || ib >= a.n || a.id[ia] != pid[2 * k] || a.id[ib] != pid[2 * k + 1]) {
+        const int ia = idx[2 * k], ib = idx[2 * k + 1];
+        if (ia < 0 || ib < 0 || !(hit || (holds(2 * k) && holds(2 * k + 1)))) {
           bad = true;
           continue;
         }
         const V3<T> u = csp_vec(a.pv, si, ia, ib);
         gs.add(dot3(u, u));
       }
-      if (bad) atomicOr(&a.status[ST_BAD_PARTNER], 1);
+      if (bad) {
+        atomicOr(&a.status[ST_BAD_PARTNER], 1);
+        a.csp_owner[i] = -2;   // looked up again next call
+      }
       g = gs.value();
     }
     a.g[i] = g;
@@ -522,24 +551,18 @@ __global__ void k_csp_force(Args<T> a) {
   if ((__double_as_longlong(c) << 1) == 0) return;   // c == +-0, tested on the bits (off the float64 pipe)
   a.cvec[j] = 0.0;
   const auto sj = a.pv.self(j);
-  const int idj = a.id[j];
-  if (idj < 0 || idj >= a.nmax) return;   // reported by prep (ST_BAD_INPUT)
-  // the partners' ids, then all their indices, then the checks and positions:
-  // three rounds of independent loads instead of a dependent chain per pair
-  static_assert(kCspCap == 8, "two int4 rows of partner ids");
-  const int4* pr4 = reinterpret_cast<const int4*>(a.csp + (size_t)idj * kCspCap);
-  const int4 q0 = pr4[0], q1 = pr4[1];
-  const int pid[kCspCap] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-  int idx[kCspCap];
-#pragma unroll
-  for (int k = 0; k < kCspCap; ++k)
-    idx[k] = (k >= a.csp_nnb || pid[k] < 0 || pid[k] >= a.nmax) ? -1 : a.id2idx[pid[k]];
+  // the partners' indices as pass 1 of this call checked them (cached by atom
+  // index); a row pass 1 found bad is skipped (the error is reported)
+  if (a.csp_owner[j] != a.id[j]) return;
+  static_assert(kCspCap == 8, "two int4 rows of partner indices");
+  const int4* c4 = reinterpret_cast<const int4*>(a.csp_idx + (size_t)j * kCspCap);
+  const int4 q0 = c4[0], q1 = c4[1];
+  const int idx[kCspCap] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
   bool ok[kCspCap / 2];
 #pragma unroll
   for (int k = 0; k < kCspCap / 2; ++k) {
     const int ia = idx[2 * k], ib = idx[2 * k + 1];
-    // stale map entries (ids no longer present) are reported by pass 1
-    ok[k] = ia >= 0 && ib >= 0 && ia < a.n && ib < a.n && a.id[ia] == pid[2 * k] && a.id[ib] == pid[2 * k + 1];
+    ok[k] = ia >= 0 && ib >= 0 && ia < a.n && ib < a.n;
   }
   double fj[3] = {0.0, 0.0, 0.0};
 #pragma unroll
