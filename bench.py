@@ -45,11 +45,10 @@ def measured_peaks():
     """The measured peaks of this machine's GPUs (empty if the file is absent)."""
     return json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2, written between timed steps
-# DRAM bytes (read + write) per launch of the step's dominant kernels on this
+# DRAM bytes (read + write) per launch of the step's dominant kernel on this
 # workload from an ncu capture, with the commit of the kernel's source it was
-# taken at; bench.py reports it only while the kernel is unchanged since
-NCU_TRAFFIC = {"pass2": (69.671680e6 + 1.681664e6, "round-1 capture, before the float32 switch sums changed")}
-NCU_TRAFFIC_CURRENT = {}
+# taken at; reported beside the roofline while that kernel is unchanged
+NCU_TRAFFIC_CURRENT = {"pass2": (69.683456e6 + 2.065152e6, "ncu capture of k_pass2 at commit cc18232")}
 
 
 def parse():
@@ -386,7 +385,7 @@ def extra_crack2m(torch, W, apip, flush, steps=3):
             "ace_group": info["group"]}
 
 
-def extra_training(torch, W, apip, configs=400, epochs=20, batch=65536):
+def extra_training(torch, W, apip, configs=4000, epochs=20, batch=65536):
     """C4 on a subsample: labels + descriptors of ``configs`` 2000-site defect
     crystals, then Adam epochs; returns the trained weights for the indentation line."""
     from paper_2512_07693_gb300 import train
@@ -422,31 +421,33 @@ def extra_training(torch, W, apip, configs=400, epochs=20, batch=65536):
 
 def extra_indent4m(torch, W, apip, flush, params, steps=20, ace_steps=3):
     """C5: the 3 993 600-atom indentation slab, three arms on the same GPU: the
-    paper's switch, the learned switch (window placed at the paper's x), all-ACE."""
+    paper's switch, the learned switch (window placed at the paper's x on the
+    starting configuration), all-ACE."""
     import numpy as np
     from paper_2512_07693_gb300 import indent
     s = W.config("indent4m", apip.apip_ace_basis_size)
     n = len(s["pos"])
     arms = {}
-    x_paper = None
+    x_paper_start = None
     for arm in ("paper", "learned", "ace"):
         t = indent._device(torch, s)
         prm = s["prm"]
         if arm == "learned":
             free = ~np.isfinite(s["lam_fixed"])
-            lo, hi = indent.learned_window(torch, s, t, params, x_paper * n / free.sum())
+            lo, hi = indent.learned_window(torch, s, t, params, x_paper_start * n / free.sum())
             prm = dict(s["prm"], switch=dict(s["prm"]["switch"], d_lo=lo, d_hi=hi))
         m, box = indent.model(torch, s, arm, t, prm=prm, mlp_flat=params)
+        x_start = float((m.field("lam", n).cpu().numpy() > 0).mean())
+        if arm == "paper":
+            x_paper_start = x_start
         k = steps if arm != "ace" else ace_steps
         timed_steps(torch, m, t, box, 2, flush)
         per = timed_steps(torch, m, t, box, k, flush)
         lam = m.field("lam", n).cpu().numpy()
         x = float((lam > 0).mean())
-        if arm == "paper":
-            x_paper = x
         m.close()
         arms[arm] = {"steps": k, "ms_per_step": sum(per) / k, "atom_steps_per_s": n * k / (sum(per) * 1e-3),
-                     "x_ace": x}
+                     "x_ace_start": x_start, "x_ace": x}
     for a in arms.values():
         a["speedup_vs_all_ace"] = a["atom_steps_per_s"] / arms["ace"]["atom_steps_per_s"]
     return {"workload": "indent4m", "atoms": n, "precision": "fp32", "arms": arms}
