@@ -77,7 +77,7 @@ void free_all(apip_ctx* c) {
   void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nnb_e, c->posg, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->csp_idx, c->csp_owner, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->clist, c->counts, c->flags, c->status, c->partials, c->thermo_part,
-                  c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_img, c->mlp_ws};
+                  c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_img, c->mlp_x0, c->mlp_ws};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -255,13 +255,15 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.partials = c->partials;
   // one energy partial per pass-1 block, ahead of the ACE blocks' partials
   if (p.lam_mode != APIP_LAM_LEARNED) a.n_part_p1 = nblk(n);
-  else if (sizeof(T) == 4) a.n_part_p1 = learned_tc_blocks(n, c->learned_slots);
+  else if (sizeof(T) == 4) a.n_part_p1 = nblk(n);   // the descriptor kernel's blocks
   else a.n_part_p1 = (int)std::max<int64_t>(1, (n + kLearnedBlock - 1) / kLearnedBlock);
   a.force = force;
   a.e_atom = e_atom;
   a.mlp_w = as<T>(c->mlp_w);
   a.mlp_img = static_cast<const uint4*>(c->mlp_img);
+  a.mlp_x0 = c->mlp_x0;
   a.learned_grid = c->learned_slots;
+  a.learned_grid1 = c->learned_slots1;
   a.ace_rc = T(p.ace_rc);
   a.ace_rc_lo = T(p.ace_rc - p.ace_rc_width);
   return a;
@@ -586,9 +588,11 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->mlp_w, es * APIP_MLP_NPARAM);
   if (p->precision == APIP_FP32) {
     APIP_ALLOC(ctx->mlp_img, mlp_img_bytes());
-    ctx->learned_slots = learned_tc_slots();
+    ctx->learned_slots = learned_tc_slots(&ctx->learned_slots1);
+    if (p->lam_mode == APIP_LAM_LEARNED) APIP_ALLOC(ctx->mlp_x0, sizeof(float) * N * APIP_MLP_IN);
     cudaGetLastError();
-    if (ctx->learned_slots < 1 && p->lam_mode == APIP_LAM_LEARNED) return fail_create(cudaErrorInvalidConfiguration);
+    if ((ctx->learned_slots < 1 || ctx->learned_slots1 < 1) && p->lam_mode == APIP_LAM_LEARNED)
+      return fail_create(cudaErrorInvalidConfiguration);
   }
   // ACE tables: one buffer, sub-arrays 256-byte aligned
   const bool f32 = p->precision == APIP_FP32;

@@ -190,7 +190,9 @@ struct apip_ctx {
   // learned indicator
   void* mlp_w = nullptr;       // APIP_MLP_NPARAM weights (element size = precision)
   void* mlp_img = nullptr;     // FP32: the weights as split bfloat16 tensor-core operand images
-  int learned_slots = 0;       // FP32: resident CTAs of the tensor-core learned kernels
+  int learned_slots = 0;       // FP32: resident CTAs of the tensor-core learned force kernel
+  int learned_slots1 = 0;      // FP32: resident CTAs of the tensor-core network of pass 1
+  float* mlp_x0 = nullptr;     // FP32 learned switch: network inputs [nmax][32]
   bool mlp_ready = false;
   float* mlp_ws = nullptr;     // training workspace
   size_t mlp_ws_cap = 0;       // floats

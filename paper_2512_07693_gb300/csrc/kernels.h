@@ -68,7 +68,9 @@ struct Args {
   double* e_atom;         // caller per-atom energy [n] or null
   const T* mlp_w;         // learned indicator weights (APIP_MLP_NPARAM, layout of apip.h)
   const uint4* mlp_img;   // FP32 path: the weights as split bfloat16 tensor-core operand images
-  int learned_grid;       // FP32 path: persistent CTAs of the tensor-core learned kernels
+  float* mlp_x0;          // FP32 path: the network inputs x0 = G / 4 of every atom [nmax][32]
+  int learned_grid;       // FP32 path: persistent CTAs of the tensor-core learned force kernel
+  int learned_grid1;      // FP32 path: persistent CTAs of the tensor-core network of pass 1
   T ace_rc, ace_rc_lo;    // cutoff of the radial descriptors (the ACE cutoff)
 };
 
@@ -211,8 +213,7 @@ template <typename T> void launch_descriptors(const Args<T>& a, uint16_t* out, c
 template <typename T> void launch_cast_params(const float* src, T* dst, cudaStream_t s);
 // FP32 learned pass 1 on the tensor cores: resident blocks on the device, blocks
 // for n atoms, the weight fragments (from the float32 weights) and their size
-int learned_tc_slots();
-int learned_tc_blocks(int n, int slots);
+int learned_tc_slots(int* grid_pass1);
 void launch_mlp_images(const float* w, void* img, cudaStream_t s);
 size_t mlp_img_bytes();
 // training on the tensor cores (kernels_train_tc.cu); a bounded wait that gives up

@@ -323,6 +323,15 @@ constexpr int sG = sE + 4 * kRows * 4 * 4; // output-layer partials [4][128][2]
 constexpr int kSmem = sG + 4 * kRows * 2 * 4;
 static_assert(kSmem <= 227 * 1024, "shared memory");
 static_assert(kImgPart % 1024 == 0 && sX % 1024 == 0 && sH % 1024 == 0 && sP % 16 == 0, "alignment");
+// pass 1 (network only; the descriptors come from k_learned_desc): weights, one
+// 64-wide activation region (which also holds the split x0 before layer 1 and
+// the output-layer partials after layer 3), the float32 parameters; two CTAs per
+// SM, 256 tensor-memory columns each
+constexpr int sHm = sW + kImg;
+constexpr int sFm = sHm + 3 * kHPart;
+constexpr int kSmemM = sFm + kNF * 4;
+static_assert(2 * (kSmemM + 2048) <= 228 * 1024, "two CTAs per SM");
+static_assert(3 * kXPart <= 3 * kHPart && 4 * kRows * 2 * 4 <= 3 * kHPart, "aliases within the activation region");
 // tensor-memory columns
 constexpr uint32_t cZ1 = 0, cZ2 = 64, cZ3 = 128, cDH = 192, cDG = 256;
 }  // namespace lt
@@ -405,14 +414,76 @@ __device__ __forceinline__ float dfeatures_window(float r, float fc, float dfc, 
   return v;
 }
 
+// Pass 1 of the learned switch, float32, CUDA-core part: one thread per atom
+// walks its list for the EAM density, energy and xi' (as k_pass1) and the radial
+// descriptors, accumulated in the thread's shared-memory row (odd stride: the
+// lanes add at nearby Gaussian indices in different banks), and writes
+// x0 = G / 4 (float32, 32 per atom) for the network (k_learned_tc<false>).
+__global__ void __launch_bounds__(kBlock) k_learned_desc(Args<float> a, float* __restrict__ x0) {
+  pdl_begin();
+  __shared__ float rows[kBlock * (kIn + 1)];
+  __shared__ double sh[32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float* row = rows + threadIdx.x * (kIn + 1);
+#pragma unroll
+  for (int m = 0; m < kIn; ++m) row[m] = 0.f;
+  double e_out = 0.0;
+  if (i < a.n) {
+    const auto si = a.pv.self(i);
+    const float rcE2 = a.k.eam_rc2;
+    const float rc2 = a.ace_rc * a.ace_rc, inv_w = 1.f / (a.ace_rc - a.ace_rc_lo);
+    const float kappa = __expf(-2.f * float(kEta) * float(kDmu) * float(kDmu));
+    Acc<float> zeta, pair;
+    walk_list(a.nbl + i, a.nmax, 0, a.nnb[i], [&](int j) { return a.pv.fetch(j); },
+              [&](int, const uint4& o) {
+                const auto d = a.pv.vec_of(si, o);
+                const float r2 = dot3(d, d);
+                if (!(r2 < rc2) && !(r2 < rcE2)) return;
+                const float r = sqrtf(r2);
+                if (r2 < rcE2) {
+                  float rho, phi;
+                  eam_terms(a.k, r, &rho, &phi);
+                  zeta.add(rho);
+                  pair.add(phi);
+                }
+                if (r2 < rc2) {
+                  float dfc;
+                  const float fc = ftrans(r, a.ace_rc_lo, a.ace_rc, inv_w, &dfc);
+                  add_features_window(r, fc, kappa, row);
+                }
+              });
+    const float zz = zeta.value();
+    const float sz = zz > 0.f ? sqrtf(zz) : 0.f;
+    const float e = -sz + 0.5f * pair.value();
+    a.zeta[i] = zz;
+    a.xi_p[i] = zz > 0.f ? -0.5f / sz : 0.f;
+    a.e_eam[i] = e;
+    const double e_ind = ind_energy(a, i);   // the external indenter, if any
+    if (a.e_atom) a.e_atom[i] = (double)e + e_ind;
+    e_out = (double)e + e_ind;
+    float4* xo = reinterpret_cast<float4*>(x0 + (size_t)i * kIn);
+#pragma unroll
+    for (int m = 0; m < kIn / 4; ++m)
+      xo[m] = make_float4(kSin * row[4 * m], kSin * row[4 * m + 1], kSin * row[4 * m + 2], kSin * row[4 * m + 3]);
+  }
+  const double tot = block_sum(e_out, sh);
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = tot;
+}
+
+// FORCE = false: pass 1's network on x0 from k_learned_desc, two CTAs per SM
+// (256 tensor-memory columns each; the split x0 and the output-layer partials
+// share the activation region); FORCE = true: descriptors, network and
+// back-propagation for the compacted atoms, one CTA per SM (512 columns).
 template <bool FORCE>
-__global__ void __launch_bounds__(lt::kT, 1) k_learned_tc(Args<float> a, const uint4* __restrict__ img) {
+__global__ void __launch_bounds__(lt::kT, FORCE ? 1 : 2)
+    k_learned_tc(Args<float> a, const uint4* __restrict__ img, const float* __restrict__ x0) {
   using namespace lt;
+  constexpr int oX = FORCE ? sX : sHm, oH = FORCE ? sH : sHm, oF = FORCE ? sF : sFm, oG = FORCE ? sG : sHm;
+  constexpr uint32_t kCols = FORCE ? 512u : 256u;
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_holder;
   __shared__ int failed;
-  __shared__ double shred[32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quarter = warp & 3, cg = warp >> 2;
   const int r = 32 * quarter + lane;    // this thread's atom row (tensor-memory lane)
@@ -421,13 +492,10 @@ __global__ void __launch_bounds__(lt::kT, 1) k_learned_tc(Args<float> a, const u
   pdl_begin();
   const int count = FORCE ? a.counts[1] : a.n;
   const int ntiles = (count + kRows - 1) / kRows;
-  if ((int)blockIdx.x >= ntiles) {   // no tile for this CTA (uniform): nothing allocated
-    if (!FORCE && tid == 0) a.partials[blockIdx.x] = 0.0;
-    return;
-  }
+  if ((int)blockIdx.x >= ntiles) return;   // no tile for this CTA (uniform): nothing allocated
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
-                 "r"(512));
+                 "r"(kCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -436,7 +504,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_learned_tc(Args<float> a, const u
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   for (int k = tid; k < kImg / 16; k += kT) reinterpret_cast<uint4*>(sm + sW)[k] = img[k];
-  float* fb = reinterpret_cast<float*>(sm + sF);
+  float* fb = reinterpret_cast<float*>(sm + oF);
   if (tid < kNF) {
     const int q = tid / kW, c = tid % kW;
     const int src = q == 0 ? oB1 : q == 1 ? oB2 : q == 2 ? oB3 : oW4;
@@ -445,17 +513,14 @@ __global__ void __launch_bounds__(lt::kT, 1) k_learned_tc(Args<float> a, const u
   to_mma();
   const uint32_t tm = tmem_holder;
   const uint32_t lane_addr = tm + ((uint32_t)(32 * quarter) << 16);
-  float* P = reinterpret_cast<float*>(sm + sP);           // [cg][row][kPs]
-  float* prow = P + (cg * kRows + r) * kPs;
-  float* E4 = reinterpret_cast<float*>(sm + sE);          // pass 1: [cg][row][4]; FORCE: c[row]
-  float* G2 = reinterpret_cast<float*>(sm + sG);          // [cg][row][2]
+  float* P = reinterpret_cast<float*>(sm + sP);           // FORCE: descriptor partials [cg][row][kPs], then dG rows
+  float* C1 = reinterpret_cast<float*>(sm + sE);          // FORCE: c of each row
+  float* G2 = reinterpret_cast<float*>(sm + oG);          // pass 1: output-layer partials [cg][row][2]
   const uint32_t id64 = idesc(kW, false, false), id_b64 = idesc(kW, false, true), id_b32 = idesc(kIn, false, true);
-  const float rcE2 = a.k.eam_rc2;
   const float rc2 = a.ace_rc * a.ace_rc, inv_w = 1.f / (a.ace_rc - a.ace_rc_lo);
   const float kappa = __expf(-2.f * float(kEta) * float(kDmu) * float(kDmu));
   uint32_t phase = 0;
   int fail_par = -1;
-  double e_out = 0.0;
   auto run = [&](auto&& issue) {
     if (!failed) {
       if (tid == 0) {
@@ -470,8 +535,8 @@ __global__ void __launch_bounds__(lt::kT, 1) k_learned_tc(Args<float> a, const u
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   };
-  // forward epilogue of one layer: h = silu(z + b) (split) into sH; FORCE keeps
-  // silu'(z + b) in the tensor-memory columns of z
+  // forward epilogue of one layer: h = silu(z + b) (split) into the activation
+  // region; FORCE keeps silu'(z + b) in the tensor-memory columns of z
   auto forward = [&](uint32_t col, const float* bias) {
     float z[16], d[16];
     tld16(lane_addr + col + c0, z);
@@ -482,118 +547,100 @@ __global__ void __launch_bounds__(lt::kT, 1) k_learned_tc(Args<float> a, const u
       d[q] = sg * (1.f + u * (1.f - sg));
       z[q] = u * sg;
     }
-    put16_split(sm + sH, kHPart, r, c0, z);
+    put16_split(sm + oH, kHPart, r, c0, z);
     if (FORCE) tst16(lane_addr + col + c0, d);
   };
-  // backward epilogue: dz = dh silu'(z) (split) into sH
+  // backward epilogue: dz = dh silu'(z) (split) into the activation region
   auto backward = [&](uint32_t zcol) {
     float dh[16], d[16];
     tld16(lane_addr + cDH + c0, dh);
     tld16(lane_addr + zcol + c0, d);
 #pragma unroll
     for (int q = 0; q < 16; ++q) dh[q] *= d[q];
-    put16_split(sm + sH, kHPart, r, c0, dh);
+    put16_split(sm + oH, kHPart, r, c0, dh);
+  };
+  // x0 columns 8 cg .. + 7 of row r, split, into the layer-1 operand
+  auto put_x0 = [&](const float* x) {
+    uint4 w[3];
+    uint32_t* u0 = reinterpret_cast<uint32_t*>(&w[0]);
+    uint32_t* u1 = reinterpret_cast<uint32_t*>(&w[1]);
+    uint32_t* u2 = reinterpret_cast<uint32_t*>(&w[2]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) split3(x[2 * m], x[2 * m + 1], u0[m], u1[m], u2[m]);
+    const int off = chunk_off(r, 8 * cg, kRows);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) *reinterpret_cast<uint4*>(sm + oX + p * kXPart + off) = w[p];
   };
 
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int q = tile * kRows + r;
     const bool valid = q < count;
     const int i = valid ? (FORCE ? a.clist[q] : q) : -1;
-    // ---- descriptors (and, in pass 1, the EAM terms) over this thread's entries
+    if constexpr (!FORCE) {
+      // x0 of this row from the descriptor kernel (zero past the atoms)
+      float x[8];
+      const float4* xi = reinterpret_cast<const float4*>(x0 + (size_t)(valid ? i : 0) * kIn + 8 * cg);
+      const float4 v0 = valid ? xi[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 v1 = valid ? xi[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+      x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w; x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+      put_x0(x);
+    } else {
+      // ---- descriptors over this thread's entries
+      float* prow = P + (cg * kRows + r) * kPs;
 #pragma unroll
-    for (int m = 0; m < kIn; ++m) prow[m] = 0.f;
-    Acc<float> zeta, pair;
-    if (valid) {
-      const auto si = a.pv.self(i);
-      const int cnt = a.nnb[i];
-      for (int s = cg; s < cnt; s += 4) {
-        const int j = a.nbl[(size_t)s * a.nmax + i];
-        const auto d = a.pv.vec(si, j);
-        const float r2 = dot3(d, d);
-        if (!(r2 < rc2) && (FORCE || !(r2 < rcE2))) continue;
-        const float rr = sqrtf(r2);
-        if (!FORCE && r2 < rcE2) {
-          float rho, phi;
-          eam_terms(a.k, rr, &rho, &phi);
-          zeta.add(rho);
-          pair.add(phi);
-        }
-        if (r2 < rc2) {
+      for (int m = 0; m < kIn; ++m) prow[m] = 0.f;
+      if (valid) {
+        const auto si = a.pv.self(i);
+        const int cnt = a.nnb[i];
+        for (int s = cg; s < cnt; s += 4) {
+          const int j = a.nbl[(size_t)s * a.nmax + i];
+          const auto d = a.pv.vec(si, j);
+          const float r2 = dot3(d, d);
+          if (!(r2 < rc2)) continue;
+          const float rr = sqrtf(r2);
           float dfc;
           const float fc = ftrans(rr, a.ace_rc_lo, a.ace_rc, inv_w, &dfc);
           add_features_window(rr, fc, kappa, prow);
         }
       }
-    }
-    if (!FORCE) {
-      float* e4 = E4 + (cg * kRows + r) * 4;
-      e4[0] = zeta.s; e4[1] = zeta.c; e4[2] = pair.s; e4[3] = pair.c;
-    } else if (cg == 0) {
-      float c = 0.f;
-      if (valid) {
-        c = (float)a.cvec[i];
-        a.cvec[i] = 0.0;
+      if (cg == 0) {
+        float c = 0.f;
+        if (valid) {
+          c = (float)a.cvec[i];
+          a.cvec[i] = 0.0;
+        }
+        C1[r] = c;
       }
-      E4[r] = c;
-    }
-    __syncthreads();
-    // G columns 8 cg .. + 7: the four partial rows in a fixed order; x0 = G / 4, split
-    {
+      __syncthreads();
+      // G columns 8 cg .. + 7: the four partial rows in a fixed order; x0 = G / 4
       float x[8];
 #pragma unroll
       for (int m = 0; m < 8; ++m) {
-        const int f = 8 * cg + m;
-        const float* pr = P + r * kPs + f;
+        const float* pr = P + r * kPs + 8 * cg + m;
         x[m] = kSin * ((pr[0] + pr[kRows * kPs]) + (pr[2 * kRows * kPs] + pr[3 * kRows * kPs]));
       }
-      uint4 w[3];
-      uint32_t* u0 = reinterpret_cast<uint32_t*>(&w[0]);
-      uint32_t* u1 = reinterpret_cast<uint32_t*>(&w[1]);
-      uint32_t* u2 = reinterpret_cast<uint32_t*>(&w[2]);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) split3(x[2 * m], x[2 * m + 1], u0[m], u1[m], u2[m]);
-      const int off = chunk_off(r, 8 * cg, kRows);
-#pragma unroll
-      for (int p = 0; p < 3; ++p) *reinterpret_cast<uint4*>(sm + sX + p * kXPart + off) = w[p];
-    }
-    if (!FORCE && cg == 0 && valid) {
-      // the EAM density and pair sums of the four quarters (compensated)
-      Acc<float> zs, ps;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float* e4 = E4 + (k * kRows + r) * 4;
-        zs.add(e4[0]); zs.add(-e4[1]); ps.add(e4[2]); ps.add(-e4[3]);
-      }
-      const float zz = zs.value();
-      const float sz = zz > 0.f ? sqrtf(zz) : 0.f;
-      const float e = -sz + 0.5f * ps.value();
-      a.zeta[i] = zz;
-      a.xi_p[i] = zz > 0.f ? -0.5f / sz : 0.f;
-      a.e_eam[i] = e;
-      const double e_ind = ind_energy(a, i);   // the external indenter, if any
-      if (a.e_atom) a.e_atom[i] = (double)e + e_ind;
-      e_out += (double)e + e_ind;
+      put_x0(x);
     }
     // ---- forward
     to_mma();
     if (failed) break;
-    run([&] { mma_split(tm, cZ1, act_k(sm + sX), kXPart, wt_k(sm + sW), kImgPart, kIn, id64); });
+    run([&] { mma_split(tm, cZ1, act_k(sm + oX), kXPart, wt_k(sm + sW), kImgPart, kIn, id64); });
     forward(cZ1, fb);
     to_mma();
     if (failed) break;
-    run([&] { mma_split(tm, cZ2, act_k(sm + sH), kHPart, wt_k(sm + sW + kImgW1), kImgPart, kW, id64); });
+    run([&] { mma_split(tm, cZ2, act_k(sm + oH), kHPart, wt_k(sm + sW + kImgW1), kImgPart, kW, id64); });
     forward(cZ2, fb + kW);
     to_mma();
     if (failed) break;
-    run([&] { mma_split(tm, cZ3, act_k(sm + sH), kHPart, wt_k(sm + sW + kImgW1 + kImgW2), kImgPart, kW, id64); });
+    run([&] { mma_split(tm, cZ3, act_k(sm + oH), kHPart, wt_k(sm + sW + kImgW1 + kImgW2), kImgPart, kW, id64); });
     {
       // layer 3 and this quarter's part of the output layer (compensated); FORCE:
-      // dz3 = c w4 silu'(z3 + b3) (split) into sH
+      // dz3 = c w4 silu'(z3 + b3) (split) into the activation region
       float z[16];
       tld16(lane_addr + cZ3 + c0, z);
       Dot2 dg;
       float dz[16];
-      const float c = FORCE ? E4[r] : 0.f;
+      const float c = FORCE ? C1[r] : 0.f;
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const float u = z[k] + fb[2 * kW + c0 + k];
@@ -603,13 +650,13 @@ __global__ void __launch_bounds__(lt::kT, 1) k_learned_tc(Args<float> a, const u
         else dg.fma(w4, u * sg);
       }
       if (FORCE) {
-        put16_split(sm + sH, kHPart, r, c0, dz);
+        put16_split(sm + oH, kHPart, r, c0, dz);
       } else {
         G2[(cg * kRows + r) * 2] = dg.s;
         G2[(cg * kRows + r) * 2 + 1] = dg.c;
       }
     }
-    if (!FORCE) {
+    if constexpr (!FORCE) {
       __syncthreads();
       if (cg == 0 && valid) {
         Dot2 t;
@@ -621,21 +668,21 @@ __global__ void __launch_bounds__(lt::kT, 1) k_learned_tc(Args<float> a, const u
         const uint4 pq = a.posq[i];
         a.posg[i] = make_uint4(pq.x, pq.y, pq.z, __float_as_uint(g));
       }
-      __syncthreads();   // the next tile rewrites the partial rows
+      __syncthreads();   // the next tile rewrites the partials' region (its x0)
       continue;
     }
     // ---- back-propagation (FORCE)
     to_mma();
     if (failed) break;
-    run([&] { mma_split(tm, cDH, act_k(sm + sH), kHPart, wt_mn(sm + sW + kImgW1 + kImgW2), kImgPart, kW, id_b64); });
+    run([&] { mma_split(tm, cDH, act_k(sm + oH), kHPart, wt_mn(sm + sW + kImgW1 + kImgW2), kImgPart, kW, id_b64); });
     backward(cZ2);
     to_mma();
     if (failed) break;
-    run([&] { mma_split(tm, cDH, act_k(sm + sH), kHPart, wt_mn(sm + sW + kImgW1), kImgPart, kW, id_b64); });
+    run([&] { mma_split(tm, cDH, act_k(sm + oH), kHPart, wt_mn(sm + sW + kImgW1), kImgPart, kW, id_b64); });
     backward(cZ1);
     to_mma();
     if (failed) break;
-    run([&] { mma_split(tm, cDG, act_k(sm + sH), kHPart, wt_mn(sm + sW), kImgPart, kW, id_b32); });
+    run([&] { mma_split(tm, cDG, act_k(sm + oH), kHPart, wt_mn(sm + sW), kImgPart, kW, id_b32); });
     {
       // dG columns 8 cg .. + 7 (times the input scale) into row r of the dG rows
       float v[8];
@@ -671,17 +718,13 @@ __global__ void __launch_bounds__(lt::kT, 1) k_learned_tc(Args<float> a, const u
     __syncthreads();   // the next tile rewrites the dG rows (partial rows) and c
   }
   __syncthreads();   // `failed` is uniform from here on
-  if (!FORCE) {
-    const double tot = block_sum(e_out, shred);
-    if (tid == 0) a.partials[blockIdx.x] = tot;
-  }
   if (failed && tid == 0) {
     atomicOr(&a.status[ST_TIMEOUT], 1);
     if (fail_par >= 0) wait_phase(&bar, (uint32_t)fail_par);   // the MMAs in flight, once more (bounded)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(512));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kCols));
 }
 
 // -grad sum_k c_k g_k for the atoms with c_k != 0 (learned counterpart of
@@ -790,11 +833,14 @@ __global__ void k_adam(float* p, const float* g, float* m, float* v, int t, floa
 }  // namespace
 
 // float64: the per-thread network, one 128-atom block per partial; float32: the
-// tensor-core kernel on a.n_part_p1 persistent CTAs (learned_tc_blocks)
+// descriptor kernel (one thread per atom, one partial per block), then the
+// tensor-core network on persistent CTAs (two per SM)
 template <typename T> void launch_pass1_learned(const Args<T>& a, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    cudaFuncSetAttribute(k_learned_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt::kSmem);
-    launch_pdl(k_learned_tc<false>, a.n_part_p1, lt::kT, lt::kSmem, s, a, a.mlp_img);
+    launch_pdl(k_learned_desc, (a.n + kBlock - 1) / kBlock > 0 ? (a.n + kBlock - 1) / kBlock : 1, kBlock, 0, s, a,
+               a.mlp_x0);
+    cudaFuncSetAttribute(k_learned_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt::kSmemM);
+    launch_pdl(k_learned_tc<false>, a.learned_grid1, lt::kT, lt::kSmemM, s, a, a.mlp_img, (const float*)a.mlp_x0);
   } else {
     const size_t bytes = sizeof(T) * APIP_MLP_NPARAM;
     cudaFuncSetAttribute(k_pass1_learned<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -802,29 +848,24 @@ template <typename T> void launch_pass1_learned(const Args<T>& a, cudaStream_t s
   }
 }
 
-// Resident CTAs of the tensor-core learned kernels on this device (one per SM).
-int learned_tc_slots() {
-  int occ = 1, dev = 0, sms = 0;
+// Resident CTAs of the tensor-core learned kernels on this device: the force
+// kernel one per SM (512 tensor-memory columns), pass 1's network (into
+// *grid_pass1) two per SM (256 columns each); 0 if they do not fit.
+int learned_tc_slots(int* grid_pass1) {
+  int dev = 0, sms = 0, o1 = 0, o0 = 0;
+  *grid_pass1 = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaFuncSetAttribute(k_learned_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt::kSmem) !=
+  if (cudaFuncSetAttribute(k_learned_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt::kSmemM) !=
           cudaSuccess ||
       cudaFuncSetAttribute(k_learned_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt::kSmem) != cudaSuccess)
     return 0;
-  for (int f = 0; f < 2; ++f) {
-    int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f ? k_learned_tc<true> : k_learned_tc<false>, lt::kT,
-                                                      lt::kSmem) != cudaSuccess)
-      return 0;
-    occ = f ? (o < occ ? o : occ) : o;
-  }
-  // one CTA per SM: each holds all 512 tensor-memory columns
-  return occ < 1 ? 0 : sms;
-}
-
-int learned_tc_blocks(int n, int slots) {
-  const int need = (n + lt::kRows - 1) / lt::kRows;
-  return need < 1 ? 1 : (need < slots ? need : slots);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_learned_tc<true>, lt::kT, lt::kSmem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k_learned_tc<false>, lt::kT, lt::kSmemM) != cudaSuccess)
+    return 0;
+  if (o1 < 1 || o0 < 1) return 0;
+  *grid_pass1 = sms * (o0 < 2 ? o0 : 2);   // tensor memory holds two of them
+  return sms;
 }
 
 void launch_mlp_images(const float* w, void* img, cudaStream_t s) {
@@ -839,7 +880,7 @@ template <typename T> void launch_mlp_force(const Args<T>& a, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
     // persistent CTAs over the tiles of the compacted list (its length is on the device)
     cudaFuncSetAttribute(k_learned_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt::kSmem);
-    launch_pdl(k_learned_tc<true>, a.learned_grid, lt::kT, lt::kSmem, s, a, a.mlp_img);
+    launch_pdl(k_learned_tc<true>, a.learned_grid, lt::kT, lt::kSmem, s, a, a.mlp_img, (const float*)nullptr);
   } else {
     int blocks = (a.n + 127) / 128;   // the list holds at most n atoms; a grid-stride loop covers it
     if (blocks > 2048) blocks = 2048;
