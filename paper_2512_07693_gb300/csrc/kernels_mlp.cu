@@ -856,15 +856,19 @@ int learned_tc_slots(int* grid_pass1) {
   *grid_pass1 = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // the whole unified memory of an SM as shared memory: two pass-1 CTAs need 2 x 111 KB
   if (cudaFuncSetAttribute(k_learned_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt::kSmemM) !=
           cudaSuccess ||
+      cudaFuncSetAttribute(k_learned_tc<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess ||
       cudaFuncSetAttribute(k_learned_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt::kSmem) != cudaSuccess)
     return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_learned_tc<true>, lt::kT, lt::kSmem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k_learned_tc<false>, lt::kT, lt::kSmemM) != cudaSuccess)
     return 0;
   if (o1 < 1 || o0 < 1) return 0;
-  *grid_pass1 = sms * (o0 < 2 ? o0 : 2);   // tensor memory holds two of them
+  // two per SM (their shared memory and registers fit twice, tensor memory holds
+  // two); the tile loop is persistent, so a CTA that finds no room waits its turn
+  *grid_pass1 = 2 * sms;
   return sms;
 }
 
