@@ -421,34 +421,33 @@ def extra_training(torch, W, apip, configs=4000, epochs=20, batch=65536):
 
 def extra_indent4m(torch, W, apip, flush, params, steps=20, ace_steps=3):
     """C5: the 3 993 600-atom indentation slab, three arms on the same GPU: the
-    paper's switch, the learned switch, all-ACE.  The learned switch's window is
-    placed at the paper switch's x on the configuration the paper arm reached at
-    the end of its timed steps (the slab heats up from its start-up state within
-    these steps, which shifts the descriptors), so that both adaptive arms are
-    timed at about the same x."""
+    paper's switch, the learned switch (window placed at the paper's x on the
+    starting configuration, the rule of the full-size indentation run), all-ACE.
+    The network here is trained on 4 000 of the 50 000 configurations; its x rises
+    while the slab heats up from its start-up state (x_ace_start, x_ace at the end
+    of the timed steps)."""
     import numpy as np
     from paper_2512_07693_gb300 import indent
     s = W.config("indent4m", apip.apip_ace_basis_size)
     n = len(s["pos"])
     arms = {}
-    x_paper_end, t_paper_end = None, None
+    x_paper_start = None
     for arm in ("paper", "learned", "ace"):
         t = indent._device(torch, s)
         prm = s["prm"]
         if arm == "learned":
             free = ~np.isfinite(s["lam_fixed"])
-            lo, hi = indent.learned_window(torch, s, t_paper_end, params, x_paper_end * n / free.sum())
+            lo, hi = indent.learned_window(torch, s, t, params, x_paper_start * n / free.sum())
             prm = dict(s["prm"], switch=dict(s["prm"]["switch"], d_lo=lo, d_hi=hi))
-            del t_paper_end
         m, box = indent.model(torch, s, arm, t, prm=prm, mlp_flat=params)
         x_start = float((m.field("lam", n).cpu().numpy() > 0).mean())
+        if arm == "paper":
+            x_paper_start = x_start
         k = steps if arm != "ace" else ace_steps
         timed_steps(torch, m, t, box, 2, flush)
         per = timed_steps(torch, m, t, box, k, flush)
         lam = m.field("lam", n).cpu().numpy()
         x = float((lam > 0).mean())
-        if arm == "paper":
-            x_paper_end, t_paper_end = x, t
         m.close()
         arms[arm] = {"steps": k, "ms_per_step": sum(per) / k, "atom_steps_per_s": n * k / (sum(per) * 1e-3),
                      "x_ace_start": x_start, "x_ace": x}
