@@ -74,7 +74,7 @@ void free_all(apip_ctx* c) {
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   c->prof_pending.clear();
   c->prof_pool.clear();
-  void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nnb_e, c->posg, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
+  void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nnb_e, c->nnb_0, c->mind1, c->posg, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->csp_idx, c->csp_owner, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->clist, c->counts, c->flags, c->status, c->partials, c->thermo_part,
                   c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_img, c->mlp_x0, c->mlp_ws};
@@ -242,7 +242,7 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.csp_rcut2 = p.csp_rcut * p.csp_rcut;
   a.pos = pos;
   a.id = id;
-  a.nnb_e = c->nnb_e; a.posg = c->posg;
+  a.nnb_e = c->nnb_e; a.nnb_0 = c->nnb_0; a.mind1 = c->mind1; a.posg = c->posg;
   a.nnb = c->nnb; a.nbl = c->nbl; a.nbl_tmp = c->nbl_tmp; a.pos_ref = c->pos_ref; a.posq = c->posq; a.posq_ref = c->posq_ref;
   a.id2idx = c->id2idx; a.csp = c->csp; a.csp_idx = c->csp_idx; a.csp_owner = c->csp_owner; a.cell_count = c->cell_count; a.cell_atoms = c->cell_atoms;
   a.ncell = c->ncell;
@@ -562,6 +562,8 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->nbl_tmp, sizeof(int) * N * p->max_nb);
   APIP_ALLOC(ctx->pos_ref, sizeof(double) * 3 * N);
   if (p->precision == APIP_FP32) {
+    APIP_ALLOC(ctx->nnb_0, sizeof(int) * N);
+    APIP_ALLOC(ctx->mind1, sizeof(float) * N);
     APIP_ALLOC(ctx->posq, sizeof(uint4) * N);
     APIP_ALLOC(ctx->posq_ref, sizeof(uint4) * N);
     APIP_ALLOC(ctx->posg, sizeof(uint4) * N);

@@ -143,6 +143,8 @@ struct apip_ctx {
   int* cell_atoms = nullptr;
   int* nnb = nullptr;
   int* nnb_e = nullptr;        // entries within eam_rc + skin at build time (they come first)
+  int* nnb_0 = nullptr;        // FP32 path: entries within eam_rc at build time (they come first)
+  float* mind1 = nullptr;      // FP32 path: least squared build distance of the entries in [eam_rc, eam_rc + skin)
   uint4* posg = nullptr;       // FP32 path: posq with g in .w (pass 1 -> pass 2)
   int* nbl = nullptr;          // column-major [max_nb][nmax]
   int* nbl_tmp = nullptr;      // list build scratch, same layout
@@ -162,7 +164,7 @@ struct apip_ctx {
   int* ace_list = nullptr;     // [nmax]
   int* clist = nullptr;        // [nmax] learned switch: atoms with a grad-lambda coefficient
   int* counts = nullptr;       // [4]: |P|, scratch
-  int* flags = nullptr;        // [4]: need_rebuild
+  int* flags = nullptr;        // [4]: need_rebuild, largest squared displacement since the build (float bits)
   int* status = nullptr;       // [ST_COUNT]
   double* partials = nullptr;  // energy partials: P1 blocks then ACE warps
   double* thermo_part = nullptr;  // [blocks][4] KE, px, py, pz

@@ -56,6 +56,8 @@ struct Args {
   int* nnb; int* nbl; int* nbl_tmp; double* pos_ref; uint4* posq; uint4* posq_ref; int* id2idx; int* csp;
   int* csp_idx; int* csp_owner;   // CSP^list partner indices by atom index (cache), the id each row is for
   int* nnb_e;             // entries of the list whose build-time distance is below eam_rc + skin
+  int* nnb_0;             // FP32 path: entries whose build-time distance is below eam_rc
+  float* mind1;           // FP32 path: least squared build-time distance of the entries in [eam_rc, eam_rc + skin)
   uint4* posg;            // FP32 path: (posq.x, posq.y, posq.z, bits of g), written by pass 1
   int* cell_count; int* cell_atoms;   // binning counts (zero outside a build) and members
   int ncell;

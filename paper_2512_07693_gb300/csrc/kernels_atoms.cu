@@ -49,8 +49,8 @@ __device__ __forceinline__ int cell_of(double xw, double L, int nc) {
 // which keeps float64 arithmetic out of this per-atom work; ``wrapped`` says that
 // (x, y, z) already lie in [0, L).
 template <typename T>
-__device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, double y, double z,
-                                          bool wrapped = false) {
+__device__ __forceinline__ float prep_atom(const Args<T>& a, int i, double x, double y, double z,
+                                           bool wrapped = false) {
   if (!finite_bits(x) || !finite_bits(y) || !finite_bits(z)) atomicOr(&a.status[ST_BAD_INPUT], 1);
   const int idv = a.id[i];
   if (idv < 0 || idv >= a.nmax) atomicOr(&a.status[ST_BAD_INPUT], 1);
@@ -65,14 +65,34 @@ __device__ __forceinline__ void prep_atom(const Args<T>& a, int i, double x, dou
     const uint4 r = a.posq_ref[i];
     const float ex = (float)(int)(q[0] - r.x) * a.geo.unit[0], ey = (float)(int)(q[1] - r.y) * a.geo.unit[1],
                 ez = (float)(int)(q[2] - r.z) * a.geo.unit[2];
-    if (ex * ex + ey * ey + ez * ez > a.skin_half2_f) atomicOr(&a.flags[0], 1);
-    return;
+    const float e2 = ex * ex + ey * ey + ez * ez;
+    if (e2 > a.skin_half2_f) atomicOr(&a.flags[0], 1);
+    return e2;
   }
   double dx = x - a.pos_ref[3 * i], dy = y - a.pos_ref[3 * i + 1], dz = z - a.pos_ref[3 * i + 2];
   dx -= a.geo.L[0] * rint(dx * a.geo.invL[0]);
   dy -= a.geo.L[1] * rint(dy * a.geo.invL[1]);
   dz -= a.geo.L[2] * rint(dz * a.geo.invL[2]);
   if (dx * dx + dy * dy + dz * dz > a.skin_half2) atomicOr(&a.flags[0], 1);
+  return 0.f;
+}
+
+// FP32 path: the block's largest squared displacement since the list build into
+// the running maximum flags[1] (float bits; non-negative floats order as
+// integers), one atomic per block.  Called by every thread of the block.
+template <typename T>
+__device__ __forceinline__ void note_displacement(const Args<T>& a, float e2) {
+  if constexpr (sizeof(T) == 4) {
+    __shared__ int wmax[kBlock / 32];
+    const int m = __reduce_max_sync(0xffffffffu, __float_as_int(e2));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int b = wmax[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = max(b, wmax[w]);
+      atomicMax(&a.flags[1], b);
+    }
+  }
 }
 
 template <typename T>
@@ -80,8 +100,9 @@ __global__ void k_prep(Args<T> a) {
   pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) a.counts[0] = a.counts[1] = 0;
-  if (i >= a.n) return;
-  prep_atom(a, i, a.pos[3 * i], a.pos[3 * i + 1], a.pos[3 * i + 2]);
+  float e2 = 0.f;
+  if (i < a.n) e2 = prep_atom(a, i, a.pos[3 * i], a.pos[3 * i + 1], a.pos[3 * i + 2]);
+  note_displacement(a, e2);
 }
 
 // ------------------------------------------------------------ neighbour list
@@ -144,6 +165,8 @@ template <typename T>
 __global__ void k_nbfill(Args<T> a) {
   pdl_begin();
   if (!a.flags[0]) return;
+  // the new list's reference positions are the current ones: no displacement yet
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[1] = 0;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   int c[3];
@@ -152,12 +175,14 @@ __global__ void k_nbfill(Args<T> a) {
   const T rin2 = T(a.r_e_in2), rmid2 = T(a.r_e_mid2);
   int n0 = 0, n1 = 0, n2 = 0;   // class counts
   int w1 = 0, w2 = 0;           // class 1, 2 entries written to the scratch ends
+  T min1 = T(INFINITY);         // least squared distance in class 1
   auto keep = [&](int j, T r2) {
     if (r2 < rin2) {
       if (n0 < a.max_nb) a.nbl[(size_t)n0 * a.nmax + i] = j;
       ++n0;
     } else if (r2 < rmid2) {
       if (w1 + w2 < a.max_nb) a.nbl_tmp[(size_t)(w1++) * a.nmax + i] = j;   // the ends meet only on overflow
+      min1 = r2 < min1 ? r2 : min1;
       ++n1;
     } else {
       if (w1 + w2 < a.max_nb) a.nbl_tmp[(size_t)(a.max_nb - 1 - w2++) * a.nmax + i] = j;
@@ -212,6 +237,10 @@ __global__ void k_nbfill(Args<T> a) {
     a.nbl[(size_t)(k0 + k1 + s) * a.nmax + i] = a.nbl_tmp[(size_t)(a.max_nb - 1 - s) * a.nmax + i];
   a.nnb[i] = k0 + k1 + k2;
   a.nnb_e[i] = k0 + k1;
+  if constexpr (sizeof(T) == 4) {
+    a.nnb_0[i] = k0;
+    a.mind1[i] = k1 < n1 ? 0.f : min1;   // a class-1 entry dropped on overflow: never skip class 1
+  }
   if (sizeof(T) == 4) {
     a.posq_ref[i] = a.posq[i];
   } else {
@@ -313,8 +342,22 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_pass1(Args<T
     const T A = a.k.eam_A, beta = a.k.eam_beta, re = a.k.eam_re, D = a.k.eam_D, alpha = a.k.eam_alpha,
             r0 = a.k.eam_r0;
     const bool paper_g = a.lam_mode == APIP_LAM_PAPER;
+    // FP32 path: a class-1 entry (build distance r_b in [rc, rc + skin)) is now at
+    // r >= r_b - d_i - d_j, where d_i is this atom's displacement since the build
+    // and d_j <= the largest one (flags[1]); when the least r_b of the atom's
+    // class-1 entries is at least rc + d_i + d_max (+ a rounding margin), none of
+    // them is within the cutoff and the sums stop after class 0
+    int end = a.nnb_e[i];
+    if constexpr (sizeof(T) == 4) {
+      const float dmax2 = __int_as_float(a.flags[1]);   // NaN (-1) before the first build: no skip
+      const uint4 r = a.posq_ref[i];
+      const float ex = (float)(int)(si.q.x - r.x) * a.pv.unit[0], ey = (float)(int)(si.q.y - r.y) * a.pv.unit[1],
+                  ez = (float)(int)(si.q.z - r.z) * a.pv.unit[2];
+      const float lim = a.k.eam_rc + sqrtf(ex * ex + ey * ey + ez * ez) + sqrtf(dmax2) + 1e-3f;
+      if (a.mind1[i] >= lim * lim) end = a.nnb_0[i];
+    }
     Acc<T> zeta, pair;
-    walk_list(a.nbl + i, a.nmax, 0, a.nnb_e[i], [&](int j) { return a.pv.fetch(j); },
+    walk_list(a.nbl + i, a.nmax, 0, end, [&](int j) { return a.pv.fetch(j); },
               [&](int, const auto& o) {
                 const auto d = a.pv.vec_of(si, o);
                 const T r2 = dot3(d, d);
@@ -642,6 +685,7 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, double* pos, doubl
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (MODE != 2 && i == 0) a.counts[0] = a.counts[1] = 0;
   double ke = 0.0, p[3] = {0.0, 0.0, 0.0};   // ke: 2 E_kin of the atom (v . p; halved after the sums)
+  float e2 = 0.f;                            // squared displacement since the list build (FP32 path)
   if (i < a.n) {
     const double im = inv_mass[i];
     const double h = half_dt * im;
@@ -671,9 +715,10 @@ __global__ void __launch_bounds__(kBlock) k_verlet(Args<T> a, double* pos, doubl
         x[q] = wrap_near(pos[3 * i + q] + dt * v[q], a.geo.L[q], a.geo.invL[q]);
         pos[3 * i + q] = x[q];
       }
-      prep_atom(a, i, x[0], x[1], x[2], true);
+      e2 = prep_atom(a, i, x[0], x[1], x[2], true);
     }
   }
+  if constexpr (MODE != 2) note_displacement(a, e2);
   if constexpr (THERMO) {
     const double vals[4] = {ke, p[0], p[1], p[2]};
     double tot[4];
