@@ -60,16 +60,11 @@ __host__ __device__ inline size_t ace_stream_smem(int nA) {
 // Ak, Gk point at the atom's column of A and dE/dA (stride NAT).
 template <typename T, typename K, int L1, int L2, int LL, int NAT, bool ADJ, bool PRIV>
 __device__ __forceinline__ void coupling(const T* Ak, T* Gk, int a1, int a2, int pb, int pe, const Rec<T>* part,
-                                         T dfs, Acc<T>& f1, Acc<T>& f2) {
+                                         const Rec<T>& first, T dfs, Acc<T>& f1, Acc<T>& f2) {
   constexpr int N1 = 2 * L1 + 1, N2 = 2 * L2 + 1, NM = 2 * LL + 1;
   constexpr int G0 = gaunt_offset(L1, L2, LL);
-  constexpr int PF = 1;   // forward: partner records loaded ahead of the coupling arithmetic
-  Rec<T> pr[PF];
-  if constexpr (!ADJ) {
-#pragma unroll
-    for (int q = 0; q < PF; ++q)
-      if (pb + q < pe) pr[q] = ld(part + pb + q);
-  }
+  constexpr int PF = 1;   // the first partner's record arrives with the coupling's entry
+  const Rec<T> pr[PF] = {first};
   T x1[N1], x2[N2], C[NM];
 #pragma unroll
   for (int i = 0; i < N1; ++i) x1[i] = Ak[(a1 + i) * NAT];
@@ -133,7 +128,8 @@ __device__ __forceinline__ void coupling(const T* Ak, T* Gk, int a1, int a2, int
         acc_add<PRIV>(gy + M * NAT, k * C[M]);
       }
     };
-    for (int p = pb; p < pe; ++p) adj_partner(ld(part + p));
+    adj_partner(first);   // every coupling has at least one partner
+    for (int p = pb + 1; p < pe; ++p) adj_partner(ld(part + p));
     T g1[N1], g2[N2];
 #pragma unroll
     for (int i = 0; i < N1; ++i) g1[i] = T(0);
@@ -164,15 +160,15 @@ __device__ __forceinline__ void coupling(const T* Ak, T* Gk, int a1, int a2, int
 }
 
 template <typename T, typename K, int LMAX, int NAT, bool ADJ, bool PRIV>
-__device__ __forceinline__ void coupling_dispatch(const uint4& cp, const T* Ak, T* Gk, const Rec<T>* part, T dfs,
-                                                  Acc<T>& f1, Acc<T>& f2) {
+__device__ __forceinline__ void coupling_dispatch(const uint4& cp, const Rec<T>& first, const T* Ak, T* Gk,
+                                                  const Rec<T>* part, T dfs, Acc<T>& f1, Acc<T>& f2) {
   const int a1 = (int)(cp.x & 255u), a2 = (int)((cp.x >> 8) & 255u), type = (int)(cp.x >> 16);
   const int pb = (int)cp.y, pe = (int)cp.z;
   switch (type) {
 #define X(l1, l2, L)                                                                          \
   case gaunt_type(l1, l2, L):                                                                 \
     if constexpr (l2 <= LMAX && L <= LMAX)                                                    \
-      coupling<T, K, l1, l2, L, NAT, ADJ, PRIV>(Ak, Gk, a1, a2, pb, pe, part, dfs, f1, f2);   \
+      coupling<T, K, l1, l2, L, NAT, ADJ, PRIV>(Ak, Gk, a1, a2, pb, pe, part, first, dfs, f1, f2);   \
     break;
     APIP_GAUNT_TYPES
 #undef X
@@ -214,6 +210,7 @@ __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev
         asm volatile("prefetch.global.L1 [%0];" ::"l"(c + o));
     };
     prefetch(t.cpl, sizeof(uint4) * (size_t)t.ncpl);
+    prefetch(t.cfirst, sizeof(Rec<T>) * (size_t)t.ncpl);
     prefetch(t.part, sizeof(Rec<T>) * (size_t)t.npart);
     prefetch(t.prec, sizeof(Rec<T>) * (size_t)t.npr);
   }
@@ -241,12 +238,15 @@ __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev
         f1.add(rc.k1 * d);
         f2.add(rc.k2 * d);
       }
-      // the next coupling's entry is loaded while this one is evaluated
-      uint4 cn = slice < t.ncpl ? __ldg(t.cpl + slice) : make_uint4(0u, 0u, 0u, 0u);
+      // the next coupling's entry and first partner are loaded while this one is evaluated
+      uint4 cn = make_uint4(0u, 0u, 0u, 0u);
+      Rec<T> rn{};
+      if (slice < t.ncpl) { cn = __ldg(t.cpl + slice); rn = ld(t.cfirst + slice); }
       for (int u = slice; u < t.ncpl; u += NS) {
         const uint4 cp = cn;
-        if (u + NS < t.ncpl) cn = __ldg(t.cpl + u + NS);
-        coupling_dispatch<T, K, LMAX, NAT, false, PRIV>(cp, Ak, Gk, t.part, T(0), f1, f2);
+        const Rec<T> rp = rn;
+        if (u + NS < t.ncpl) { cn = __ldg(t.cpl + u + NS); rn = ld(t.cfirst + u + NS); }
+        coupling_dispatch<T, K, LMAX, NAT, false, PRIV>(cp, rp, Ak, Gk, t.part, T(0), f1, f2);
       }
       T v1 = f1.value(), v2 = f2.value();
 #pragma unroll
@@ -293,11 +293,14 @@ __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev
           }
         }
       }
-      uint4 cn = slice < t.ncpl ? __ldg(t.cpl + slice) : make_uint4(0u, 0u, 0u, 0u);
+      uint4 cn = make_uint4(0u, 0u, 0u, 0u);
+      Rec<T> rn{};
+      if (slice < t.ncpl) { cn = __ldg(t.cpl + slice); rn = ld(t.cfirst + slice); }
       for (int u = slice; u < t.ncpl; u += NS) {
         const uint4 cp = cn;
-        if (u + NS < t.ncpl) cn = __ldg(t.cpl + u + NS);
-        coupling_dispatch<T, K, LMAX, NAT, true, PRIV>(cp, Ak, Gk, t.part, dfs, unused1, unused2);
+        const Rec<T> rp = rn;
+        if (u + NS < t.ncpl) { cn = __ldg(t.cpl + u + NS); rn = ld(t.cfirst + u + NS); }
+        coupling_dispatch<T, K, LMAX, NAT, true, PRIV>(cp, rp, Ak, Gk, t.part, dfs, unused1, unused2);
       }
     }
     __syncthreads();

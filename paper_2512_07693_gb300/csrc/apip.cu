@@ -308,6 +308,7 @@ AceDev<T> ace_dev(apip_ctx* c) {
     t.ncpl = c->ace_ncpl;
     t.part = reinterpret_cast<const Rec<T>*>(b + c->ace_off[2]);
     t.npart = c->ace_npart;
+    t.cfirst = reinterpret_cast<const Rec<T>*>(b + c->ace_off[3]);
     t.group = c->ace_group;
     return t;
   }
@@ -632,6 +633,19 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
     put_rec(0, st.pkey, &st.plen, st.p1, st.p2);
     put(1, st.cpl.data(), sizeof(uint32_t) * st.cpl.size());
     put_rec(2, st.tkey, nullptr, st.t1, st.t2);
+    {
+      // the first partner record of every coupling again, indexed by the coupling,
+      // so that it can be loaded together with the coupling's entry
+      std::vector<uint32_t> fk;
+      std::vector<double> f1, f2;
+      for (size_t u = 0; u < st.cpl.size() / 4; ++u) {
+        const uint32_t q = st.cpl[4 * u + 1];
+        fk.push_back(st.tkey[q]);
+        f1.push_back(st.t1[q]);
+        f2.push_back(st.t2[q]);
+      }
+      put_rec(3, fk, nullptr, f1, f2);
+    }
     ctx->ace_npr = (int)st.pkey.size();
     ctx->ace_ncpl = (int)(st.cpl.size() / 4);
     ctx->ace_npart = (int)st.tkey.size();

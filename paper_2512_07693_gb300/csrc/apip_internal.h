@@ -82,6 +82,7 @@ struct AceDev {
   const Rec<T>* prec; int npr;  // nu 1, 2: key a1 | a2 << 16 (A indices; a2 = 0xffff: the constant 1), len
   const uint4* cpl; int ncpl;   // couplings: (a1 | a2 << 8 | type << 16, partner begin, partner end, 0)
   const Rec<T>* part; int npart;  // nu = 3 partners: key = A index of A_{p3, m = -l3}
+  const Rec<T>* cfirst;         // the first partner record of each coupling (a copy, loaded with the coupling)
   int group;                    // compacted atoms per thread block
 };
 
