@@ -207,9 +207,8 @@ __device__ __forceinline__ void refine_switch(const Args<T>& a, const AceGroup<T
         const uint4 qi = a.pv.q[i];
         const int cnt = a.nnb[i];
         FF wsum{0.f, 0.f}, gsum{0.f, 0.f};
-        for (int s = lane; s < cnt; s += 32) {
-          const int j = a.nbl[(size_t)s * a.nmax + i];
-          const uint4 qj = a.pv.q[j];
+        // one neighbour record (fixed-point position, g in .w: pass 1's posg)
+        auto add = [&](const uint4& qj) {
           const FF x = ff_coord((int)(qj.x - qi.x), sw.u_hi[0], sw.u_lo[0]);
           const FF y = ff_coord((int)(qj.y - qi.y), sw.u_hi[1], sw.u_lo[1]);
           const FF z = ff_coord((int)(qj.z - qi.z), sw.u_hi[2], sw.u_lo[2]);
@@ -222,7 +221,7 @@ __device__ __forceinline__ void refine_switch(const Args<T>& a, const AceGroup<T
           t2 = ff_prod(z.hi, z.hi);
           t2.lo = __fmaf_rn(2.f * z.hi, z.lo, t2.lo);
           r2 = ff_add(r2, t2);
-          if (!(r2.hi < sw.rw2)) continue;
+          if (!(r2.hi < sw.rw2)) return;
           float w = 1.f;
           if (r2.hi > sw.rw_lo2) {
             // r = sqrt(r2): the rounded root r_h leaves r2 - r_h^2 exact (FMA)
@@ -237,7 +236,16 @@ __device__ __forceinline__ void refine_switch(const Args<T>& a, const AceGroup<T
             w = 0.0625f * p * p * p * (8.f + t * (-9.f + 3.f * t));
           }
           wsum = ff_add(wsum, FF{w, 0.f});
-          gsum = ff_add(gsum, ff_prod(a.g[j], w));
+          gsum = ff_add(gsum, ff_prod(__uint_as_float(qj.w), w));
+        };
+        // two list entries per lane and round, their loads issued before the arithmetic
+        for (int s = lane; s < cnt; s += 64) {
+          const bool two = s + 32 < cnt;
+          const int j0 = a.nbl[(size_t)s * a.nmax + i];
+          const int j1 = two ? a.nbl[(size_t)(s + 32) * a.nmax + i] : j0;
+          const uint4 q0 = a.posg[j0], q1 = a.posg[j1];
+          add(q0);
+          if (two) add(q1);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
