@@ -51,9 +51,14 @@ typedef enum {
   APIP_ERR_STATE = 5,        /* call order: apip_init_csp_pairs must precede calls that use
                                 the paper's switch */
   APIP_ERR_SIZE = 6,         /* input larger than a fixed-capacity entry point can hold */
-  APIP_ERR_TIMEOUT = 7       /* reserved: a device-side wait exceeded its iteration limit.
-                                No kernel of this version waits on another, so no call
-                                returns it */
+  APIP_ERR_TIMEOUT = 7,      /* a bounded device wait gave up: the tensor-core kernels of
+                                training and of the learned switch wait for their matrix
+                                products with a 2 s limit; no kernel waits on another */
+  APIP_ERR_BOUNDS = 8        /* only in a library compiled with APIP_CHECK_BOUNDS: an index
+                                read from a device list or table fell outside its array;
+                                the access went to index 0 instead and the call's results
+                                are invalid.  apip_last_error names the first site, the
+                                index and the limit */
 } apip_status;
 
 enum { APIP_FP64 = 0, APIP_FP32 = 1 };
@@ -130,7 +135,17 @@ typedef struct apip_params {
   int32_t max_nb;            /* neighbour capacity per atom (1 .. 1024) */
   int32_t cell_cap;          /* atom capacity per cell (1 .. 1024) */
   int32_t mixing;            /* APIP_MIX_ENERGY or APIP_MIX_FORCE */
-  int32_t pad2;
+  int32_t deterministic;     /* 1: results that do not depend on the order in which the
+                                device's threads run.  Each cell's members are sorted by
+                                index after binning, the compacted list is written in index
+                                order, and every scattered force, c-vector and indenter-work
+                                contribution is rounded to a multiple of 2^-40 and summed as a
+                                64-bit integer.  Repeated runs from the same state then give
+                                the same bits, and a run resumed from a checkpoint that holds
+                                APIP_FIELD_BUILD_POS continues the trajectory bit for bit.
+                                Costs three small kernels per call and one per list build.
+                                Not with APIP_MIX_FORCE (APIP_ERR_ARG).  0: float64 atomics,
+                                results reproducible to rounding */
   double prec_shift;         /* energy zero of the precise model: E^prec_i is lowered by this
                                 constant (eV per atom).  0 keeps E^prec as defined above.  Set
                                 to the models' difference per atom in the perfect lattice, it
@@ -246,11 +261,16 @@ const char* apip_last_error(apip_ctx* ctx);
  *   APIP_FIELD_NNB      : int64 dst, neighbours per atom (within cutoff + skin)
  *   APIP_FIELD_NBLIST   : int64 dst [n][max_nb], neighbour indices (-1 padded)
  *   APIP_FIELD_CSP      : int64 dst [n][csp_nnb], partner IDs (-1 = none); row k holds
- *                         the partners of the atom whose id is k */
+ *                         the partners of the atom whose id is k
+ *   APIP_FIELD_BUILD_POS: float64 dst [n][3], the positions (as the caller passed them)
+ *                         from which the current neighbour list was built.  A checkpoint
+ *                         that stores them rebuilds the same list with
+ *                         apip_build_neighbors on resume */
 enum {
   APIP_FIELD_G = 0, APIP_FIELD_D = 1, APIP_FIELD_WBAR = 2, APIP_FIELD_LAM = 3,
   APIP_FIELD_DLAM = 4, APIP_FIELD_E_EAM = 5, APIP_FIELD_E_ACE = 6, APIP_FIELD_ZETA = 7,
-  APIP_FIELD_ACE_LIST = 8, APIP_FIELD_NNB = 9, APIP_FIELD_NBLIST = 10, APIP_FIELD_CSP = 11
+  APIP_FIELD_ACE_LIST = 8, APIP_FIELD_NNB = 9, APIP_FIELD_NBLIST = 10, APIP_FIELD_CSP = 11,
+  APIP_FIELD_BUILD_POS = 12
 };
 apip_status apip_get_field(apip_ctx* ctx, int32_t field, void* dst, int64_t n, void* stream);
 
@@ -260,13 +280,37 @@ apip_status apip_get_field(apip_ctx* ctx, int32_t field, void* dst, int64_t n, v
  * the last read into the host arrays ms[APIP_PHASE_COUNT] and
  * launches[APIP_PHASE_COUNT], and resets them.  Phases: PREP (position
  * preparation or Verlet kernels), NEIGHBOR (the two conditional neighbour-list
- * kernels), PASS1, PASS2, ACE, CSP (CSP part of grad-lambda), REDUCE. */
+ * kernels; three in the deterministic mode), PASS1, PASS2 (with the deterministic
+ * mode's ordered compaction), ACE, CSP (CSP or learned part of grad-lambda, and
+ * the deterministic mode's fixed-point to float64 conversion), REDUCE.
+ * Independently of apip_profile, every call is an NVTX range named after it
+ * ("apip_energy_forces", "apip_verlet_step", "apip_switch",
+ * "apip_build_neighbors") holding one range per phase ("apip/prep",
+ * "apip/neighbor", "apip/pass1", "apip/pass2", "apip/ace", "apip/csp"), which a
+ * profiler attached to the process shows and by which ncu --nvtx selects
+ * kernels; without an attached tool they cost a few nanoseconds per call. */
 enum {
   APIP_PHASE_PREP = 0, APIP_PHASE_NEIGHBOR = 1, APIP_PHASE_PASS1 = 2, APIP_PHASE_PASS2 = 3,
   APIP_PHASE_ACE = 4, APIP_PHASE_CSP = 5, APIP_PHASE_REDUCE = 6, APIP_PHASE_COUNT = 7
 };
 apip_status apip_profile(apip_ctx* ctx, int32_t enable);
 apip_status apip_profile_read(apip_ctx* ctx, double* ms, int64_t* launches);
+
+/* Bounds-checked build.  Compiled with -DAPIP_CHECK_BOUNDS (the package's build
+ * with checked=True writes libapip_checked.so), every index the kernels read from
+ * a device list or table (neighbour entries and list lengths, cell indices and
+ * members, compacted-list entries, the streamed ACE tables' keys and ranges) is
+ * tested against its array before use; the first index out of range is
+ * recorded, the access goes to index 0 instead, and apip_sync returns
+ * APIP_ERR_BOUNDS naming the site, the index and the limit.  CSP partner indices
+ * are checked against the ids in every build.  Every build checks all ACE tables
+ * (streamed and pool) on the host when apip_create builds them.
+ * apip_check_bounds_selftest records one violation through the device check
+ * without touching memory, so that the next apip_sync reports it (a test of the
+ * reporting path).  Errors: APIP_ERR_ARG (NULL ctx). */
+#ifdef APIP_CHECK_BOUNDS
+apip_status apip_check_bounds_selftest(apip_ctx* ctx, void* stream);
+#endif
 
 /* Sizes of the ACE evaluation that apip_create built, for work accounting
  * (host call, no device work).  Body order <= 3 uses the streamed evaluation

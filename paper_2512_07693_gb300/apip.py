@@ -12,11 +12,15 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libapip.so")
+# APIP_LIBRARY may name another build of the same ABI (the bounds-checked
+# libapip_checked.so); the default is the in-tree libapip.so
+LIB_PATH = os.environ.get("APIP_LIBRARY") or os.path.join(_PKG, "libapip.so")
 
-APIP_OK, APIP_ERR_ARG, APIP_ERR_CUDA, APIP_ERR_NB_OVERFLOW, APIP_ERR_BAD_INPUT, APIP_ERR_STATE, APIP_ERR_SIZE = range(7)
+(APIP_OK, APIP_ERR_ARG, APIP_ERR_CUDA, APIP_ERR_NB_OVERFLOW, APIP_ERR_BAD_INPUT, APIP_ERR_STATE, APIP_ERR_SIZE,
+ APIP_ERR_TIMEOUT, APIP_ERR_BOUNDS) = range(9)
 STATUS_NAMES = {0: "APIP_OK", 1: "APIP_ERR_ARG", 2: "APIP_ERR_CUDA", 3: "APIP_ERR_NB_OVERFLOW",
-                4: "APIP_ERR_BAD_INPUT", 5: "APIP_ERR_STATE", 6: "APIP_ERR_SIZE"}
+                4: "APIP_ERR_BAD_INPUT", 5: "APIP_ERR_STATE", 6: "APIP_ERR_SIZE", 7: "APIP_ERR_TIMEOUT",
+                8: "APIP_ERR_BOUNDS"}
 APIP_STATIC_MAX_ATOMS = 4096 * 4096
 APIP_FP64, APIP_FP32 = 0, 1
 APIP_LAM_PAPER, APIP_LAM_CONST0, APIP_LAM_CONST1, APIP_LAM_LEARNED = 0, 1, 2, 3
@@ -28,7 +32,8 @@ APIP_MLP_NPARAM = 10497
 MLP_LAYOUT = (("W1", (64, 32)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (64, 64)), ("b3", (64,)),
               ("w4", (64,)), ("b4", ()))
 PHASES = ("prep", "neighbor", "pass1", "pass2", "ace", "csp", "reduce")
-FIELDS = dict(g=0, d=1, wbar=2, lam=3, dlam=4, e_eam=5, e_ace=6, zeta=7, ace_list=8, nnb=9, nblist=10, csp=11)
+FIELDS = dict(g=0, d=1, wbar=2, lam=3, dlam=4, e_eam=5, e_ace=6, zeta=7, ace_list=8, nnb=9, nblist=10, csp=11,
+              build_pos=12)
 MVV2E = 1.0364269e-4   # amu A^2 / ps^2 -> eV
 
 _c_int32, _c_int64, _c_double, _vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
@@ -47,7 +52,7 @@ class ApipParams(ctypes.Structure):
         ("sw_d0", _c_double),
         ("csp_rcut", _c_double), ("csp_nnb", _c_int32), ("nb_pad", _c_int32),
         ("skin", _c_double), ("max_nb", _c_int32), ("cell_cap", _c_int32), ("mixing", _c_int32),
-        ("pad2", _c_int32), ("prec_shift", _c_double),
+        ("deterministic", _c_int32), ("prec_shift", _c_double),
     ]
 
 
@@ -87,6 +92,9 @@ def _load():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
+    if hasattr(lib, "apip_check_bounds_selftest"):   # the bounds-checked build only
+        lib.apip_check_bounds_selftest.restype = ctypes.c_int
+        lib.apip_check_bounds_selftest.argtypes = [_vp, _vp]
     return lib
 
 
@@ -279,7 +287,7 @@ def mlp_unflat(flat):
 
 # ---------------------------------------------------------------- helpers
 def make_params(prm, precision="fp64", lam_mode="paper", grad_lambda=True, skin=0.5, max_nb=96, cell_cap=64,
-                ace_group=0, mixing="energy"):
+                ace_group=0, mixing="energy", deterministic=False):
     """apip_params from a parameter dict (keys eam, ace, switch, csp,
     precise_adds_eam, optional prec_shift).  The returned structure keeps the coefficient arrays
     alive through its ``_keep`` attribute."""
@@ -308,6 +316,7 @@ def make_params(prm, precision="fp64", lam_mode="paper", grad_lambda=True, skin=
     p.csp_rcut, p.csp_nnb = c["rcut"], c["nnb"]
     p.skin, p.max_nb, p.cell_cap = skin, max_nb, cell_cap
     p.mixing = MIXING[mixing]
+    p.deterministic = int(bool(deterministic))
     p.prec_shift = float(prm.get("prec_shift", 0.0))
     p._keep = (c1, c2)
     return p
@@ -384,6 +393,8 @@ class Apip:
             out = torch.empty((n, self.csp_nnb), dtype=torch.int64, device=dev)
         elif name in ("ace_list", "nnb"):
             out = torch.empty(n, dtype=torch.int64, device=dev)
+        elif name == "build_pos":
+            out = torch.empty((n, 3), dtype=torch.float64, device=dev)
         else:
             out = torch.empty(n, dtype=torch.float64, device=dev)
         apip_get_field(self.ctx, name, out, n)

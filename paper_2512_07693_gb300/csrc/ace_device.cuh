@@ -165,8 +165,8 @@ __device__ __forceinline__ void group_setup(const Args<T>& a, int grp, int count
   const int tid = threadIdx.x;
   if (tid < 32) {
     const int idx = grp * NAT + tid;
-    const int i = (tid < NAT && idx < count) ? a.ace_list[idx] : -1;
-    const int nn = i >= 0 ? a.nnb[i] : 0;
+    const int i = (tid < NAT && idx < count) ? APIP_CHK(a.status, BND_COMPACT, a.ace_list[idx], a.n) : -1;
+    const int nn = i >= 0 ? APIP_CHK(a.status, BND_LIST_LEN, a.nnb[i], a.max_nb + 1) : 0;
     int inc = nn;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -205,7 +205,7 @@ __device__ __forceinline__ void refine_switch(const Args<T>& a, const AceGroup<T
         const int i = g.atom[k];
         if (i < 0 || a.dlam[i] == T(0)) continue;   // not transitional (constant-lam atoms: dlam = 0)
         const uint4 qi = a.pv.q[i];
-        const int cnt = a.nnb[i];
+        const int cnt = APIP_CHK(a.status, BND_LIST_LEN, a.nnb[i], a.max_nb + 1);
         FF wsum{0.f, 0.f}, gsum{0.f, 0.f};
         // one neighbour record (fixed-point position, g in .w: pass 1's posg)
         auto add = [&](const uint4& qj) {
@@ -241,8 +241,8 @@ __device__ __forceinline__ void refine_switch(const Args<T>& a, const AceGroup<T
         // two list entries per lane and round, their loads issued before the arithmetic
         for (int s = lane; s < cnt; s += 64) {
           const bool two = s + 32 < cnt;
-          const int j0 = a.nbl[(size_t)s * a.nmax + i];
-          const int j1 = two ? a.nbl[(size_t)(s + 32) * a.nmax + i] : j0;
+          const int j0 = APIP_CHK(a.status, BND_NEIGHBOUR, a.nbl[(size_t)s * a.nmax + i], a.n);
+          const int j1 = two ? APIP_CHK(a.status, BND_NEIGHBOUR, a.nbl[(size_t)(s + 32) * a.nmax + i], a.n) : j0;
           const uint4 q0 = a.posg[j0], q1 = a.posg[j1];
           add(q0);
           if (two) add(q1);
@@ -292,7 +292,7 @@ __device__ __forceinline__ void densities(const Args<T>& a, const AceDev<T>& t, 
     if (p < total) {
       const int k = atom_of_pair<NAT>(p, g.off);
       const int i = g.atom[k];
-      const int j = a.nbl[(size_t)(p - g.off[k]) * a.nmax + i];
+      const int j = APIP_CHK(a.status, BND_NEIGHBOUR, a.nbl[(size_t)(p - g.off[k]) * a.nmax + i], a.n);
       d = a.pv.vec(a.pv.self(i), j);
       r2 = dot3(d, d);
       in = r2 < rc2;
@@ -374,7 +374,7 @@ __device__ __forceinline__ double pair_forces(const Args<T>& a, const AceDev<T>&
     if (p >= total) continue;
     const int k = atom_of_pair<NAT>(p, g.off);
     const int i = g.atom[k];
-    const int j = a.nbl[(size_t)(p - g.off[k]) * a.nmax + i];
+    const int j = APIP_CHK(a.status, BND_NEIGHBOUR, a.nbl[(size_t)(p - g.off[k]) * a.nmax + i], a.n);
     const V3<T> d = a.pv.vec(a.pv.self(i), j);
     const T r2 = dot3(d, d);
     const bool trans = g.trans[k] != 0;
@@ -424,18 +424,18 @@ __device__ __forceinline__ double pair_forces(const Args<T>& a, const AceDev<T>&
       T dw;
       const T w = ftrans(r, rw_lo, rw, rw_inv, &dw);
       sr += g.et[k] * (a.g[j] - g.D[k]) * dw;
-      atomicAdd(&a.cvec[j], (double)(g.et[k] * w));
+      scatter_add(&a.cvec[j], (double)(g.et[k] * w), a.det);
     }
     const T fx = sr * ex + gx, fy = sr * ey + gy, fz = sr * ez + gz;
     if (!a.force_mix) {
       // AP (Eq. 5): omega already carries lam_i, and the pair term is antisymmetric
       const double f0 = (double)fx, f1 = (double)fy, f2 = (double)fz;
-      atomicAdd(&a.force[3 * j], -f0);
-      atomicAdd(&a.force[3 * j + 1], -f1);
-      atomicAdd(&a.force[3 * j + 2], -f2);
-      atomicAdd(&a.force[3 * i], f0);
-      atomicAdd(&a.force[3 * i + 1], f1);
-      atomicAdd(&a.force[3 * i + 2], f2);
+      scatter_add(&a.force[3 * j], -f0, a.det);
+      scatter_add(&a.force[3 * j + 1], -f1, a.det);
+      scatter_add(&a.force[3 * j + 2], -f2, a.det);
+      scatter_add(&a.force[3 * i], f0, a.det);
+      scatter_add(&a.force[3 * i + 1], f1, a.det);
+      scatter_add(&a.force[3 * i + 2], f2, a.det);
     } else {
       // force mixing (Eq. 3): each receiving atom takes its own lam of the precise
       // model's force (omega without lam)
@@ -456,7 +456,7 @@ __device__ __forceinline__ double pair_forces(const Args<T>& a, const AceDev<T>&
   if (tid < NAT) {
     const int i = g.atom[tid];
     if (i >= 0) {
-      if (g.trans[tid]) atomicAdd(&a.cvec[i], (double)g.et[tid]);
+      if (g.trans[tid]) scatter_add(&a.cvec[i], (double)g.et[tid], a.det);
       a.e_ace[i] = g.e[tid];
       const double ed = (double)g.lam[tid] * (double)g.delta[tid];
       e_part = ed;

@@ -176,6 +176,30 @@ __device__ __forceinline__ void coupling_dispatch(const uint4& cp, const Rec<T>&
   }
 }
 
+#ifdef APIP_CHECK_BOUNDS
+// Bounds-checked build: a coupling entry whose operand offsets, partner range or
+// first partner key fall outside the tables is recorded and dispatched to no
+// coupling type; a nu <= 2 record whose segments do not fit in A is recorded and
+// skipped.
+template <typename T>
+__device__ __forceinline__ void check_coupling(int* status, uint4& cp, const Rec<T>& first, const AceDev<T>& t) {
+  const int a1 = (int)(cp.x & 255u), a2 = (int)((cp.x >> 8) & 255u), pb = (int)cp.y, pe = (int)cp.z;
+  bool ok = APIP_CHK(status, BND_ACE_TABLE, a1, t.nA) == a1;
+  ok = APIP_CHK(status, BND_ACE_TABLE, a2, t.nA) == a2 && ok;
+  ok = APIP_CHK(status, BND_ACE_TABLE, pb, pe) == pb && ok;
+  ok = APIP_CHK(status, BND_ACE_TABLE, pe - 1, t.npart) == pe - 1 && ok;
+  ok = APIP_CHK(status, BND_ACE_TABLE, (int)first.key, t.nA) == (int)first.key && ok;
+  if (!ok) cp.x = 0xffff0000u;
+}
+template <typename T>
+__device__ __forceinline__ bool record_ok(int* status, const Rec<T>& rc, int nA) {
+  const int a1 = (int)(rc.key & 0xffffu), a2 = (int)(rc.key >> 16), len = (int)rc.len;
+  bool ok = APIP_CHK(status, BND_ACE_TABLE, a1 + len - 1, nA) == a1 + len - 1;
+  if ((uint32_t)a2 != kConstOne) ok = APIP_CHK(status, BND_ACE_TABLE, a2 + len - 1, nA) == a2 + len - 1 && ok;
+  return ok;
+}
+#endif
+
 template <typename T, typename K, int LMAX, int NAT>
 __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev<T> t) {
   pdl_begin();
@@ -227,6 +251,9 @@ __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev
       Acc<T> f1, f2;
       for (int r = slice; r < t.npr; r += NS) {
         const Rec<T> rc = ld(t.prec + r);
+#ifdef APIP_CHECK_BOUNDS
+        if (!record_ok(a.status, rc, nA)) continue;
+#endif
         const int a1 = (int)(rc.key & 0xffffu);
         const uint32_t a2 = rc.key >> 16;
         T d = T(0);
@@ -243,8 +270,11 @@ __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev
       Rec<T> rn{};
       if (slice < t.ncpl) { cn = __ldg(t.cpl + slice); rn = ld(t.cfirst + slice); }
       for (int u = slice; u < t.ncpl; u += NS) {
-        const uint4 cp = cn;
+        uint4 cp = cn;
         const Rec<T> rp = rn;
+#ifdef APIP_CHECK_BOUNDS
+        check_coupling(a.status, cp, rp, t);
+#endif
         if (u + NS < t.ncpl) { cn = __ldg(t.cpl + u + NS); rn = ld(t.cfirst + u + NS); }
         coupling_dispatch<T, K, LMAX, NAT, false, PRIV>(cp, rp, Ak, Gk, t.part, T(0), f1, f2);
       }
@@ -281,6 +311,9 @@ __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev
       Acc<T> unused1, unused2;
       for (int r = slice; r < t.npr; r += NS) {
         const Rec<T> rc = ld(t.prec + r);
+#ifdef APIP_CHECK_BOUNDS
+        if (!record_ok(a.status, rc, nA)) continue;
+#endif
         const int a1 = (int)(rc.key & 0xffffu);
         const uint32_t a2 = rc.key >> 16;
         const T k = rc.k1 + dfs * rc.k2;
@@ -297,8 +330,11 @@ __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev
       Rec<T> rn{};
       if (slice < t.ncpl) { cn = __ldg(t.cpl + slice); rn = ld(t.cfirst + slice); }
       for (int u = slice; u < t.ncpl; u += NS) {
-        const uint4 cp = cn;
+        uint4 cp = cn;
         const Rec<T> rp = rn;
+#ifdef APIP_CHECK_BOUNDS
+        check_coupling(a.status, cp, rp, t);
+#endif
         if (u + NS < t.ncpl) { cn = __ldg(t.cpl + u + NS); rn = ld(t.cfirst + u + NS); }
         coupling_dispatch<T, K, LMAX, NAT, true, PRIV>(cp, rp, Ak, Gk, t.part, dfs, unused1, unused2);
       }

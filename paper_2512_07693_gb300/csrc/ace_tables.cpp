@@ -412,4 +412,68 @@ bool build_streamed(int n_max, int l_max, int nu_max, const double* c1, const do
   return true;
 }
 
+// Host check of every key and range of the tables against the arrays they
+// index, run by apip_create after building them (in every build): each segment a
+// record, coupling, partner, Gaunt, reverse-row or C -> A entry names lies inside
+// A (or the pool) and each range inside its entry array.  The device's
+// bounds-checked build tests the streamed tables again as it reads them.
+bool validate_streamed(const HostStream& h, int nA, std::string* err) {
+  auto bad = [&](const std::string& what) { *err = "internal: ACE table check failed: " + what; return false; };
+  for (size_t r = 0; r < h.pkey.size(); ++r) {
+    const int a1 = (int)(h.pkey[r] & 0xffffu), a2 = (int)(h.pkey[r] >> 16), len = (int)h.plen[r];
+    if (len < 1 || a1 + len > nA) return bad("nu <= 2 record " + std::to_string(r));
+    if ((uint32_t)a2 != 0xffffu && a2 + len > nA) return bad("nu = 2 record " + std::to_string(r));
+  }
+  if (h.cpl.size() % 4) return bad("coupling array length");
+  for (size_t u = 0; u < h.cpl.size() / 4; ++u) {
+    const uint32_t w = h.cpl[4 * u];
+    const int a1 = (int)(w & 255u), a2 = (int)((w >> 8) & 255u), type = (int)(w >> 16);
+    const int l1 = type / 25, l2 = (type / 5) % 5, L = type % 5;
+    if (type >= 125 || !gaunt_type_valid(l1, l2, L)) return bad("coupling type " + std::to_string(u));
+    if (a1 + 2 * l1 + 1 > nA || a2 + 2 * l2 + 1 > nA) return bad("coupling operands " + std::to_string(u));
+    const uint32_t pb = h.cpl[4 * u + 1], pe = h.cpl[4 * u + 2];
+    if (!(pb < pe) || pe > h.tkey.size()) return bad("coupling partner range " + std::to_string(u));
+    for (uint32_t q = pb; q < pe; ++q)
+      if ((int)h.tkey[q] + 2 * L + 1 > nA) return bad("partner " + std::to_string(q));
+  }
+  return true;
+}
+
+bool validate_coupled(const HostAce& h, std::string* err) {
+  auto bad = [&](const std::string& what) { *err = "internal: ACE table check failed: " + what; return false; };
+  const int nA = h.nA, npool = h.npool;
+  if (npool != 1 + nA + h.nC || h.comp.size() != (size_t)2 * h.nC) return bad("pool sizes");
+  for (int c = 0; c < h.nC; ++c) {
+    const int a1 = (int)(h.comp[2 * c] & 0xffffu), a2 = (int)(h.comp[2 * c] >> 16);
+    const int gofs = (int)(h.comp[2 * c + 1] >> 8), gcnt = (int)(h.comp[2 * c + 1] & 255u);
+    if (a1 < 1 || a2 < 1 || gofs + gcnt > (int)h.gkey.size()) return bad("C component " + std::to_string(c));
+    for (int e = gofs; e < gofs + gcnt; ++e)
+      if (a1 + (int)(h.gkey[e] & 255u) > nA || a2 + (int)(h.gkey[e] >> 8) > nA)
+        return bad("Gaunt entry " + std::to_string(e));
+  }
+  for (size_t r = 0; r < h.fkey.size(); ++r) {
+    const int o1 = (int)(h.fkey[r] & 0xffffu), o2 = (int)(h.fkey[r] >> 16), len = (int)h.flen[r];
+    if (len < 1 || o1 + len > npool || o2 + len > npool) return bad("record " + std::to_string(r));
+  }
+  if (h.qrow.size() != (size_t)4 * npool) return bad("reverse row table length");
+  for (int q = 1; q < npool; ++q) {
+    const int b = h.qrow[4 * q], e = h.qrow[4 * q + 1], m = h.qrow[4 * q + 2];
+    if (b < 0 || b > e || e > (int)h.rkey.size() || m < 0 || m > q) return bad("reverse row " + std::to_string(q));
+    for (int k = b; k < e; ++k)
+      if ((int)h.rkey[k] + m >= npool) return bad("reverse entry " + std::to_string(k));
+  }
+  for (size_t k = 0; k < h.bkey.size(); ++k) {
+    const int qc = (int)(h.bkey[k] & 0xffffu), qa = (int)(h.bkey[k] >> 16);
+    if (qc < 1 + nA || qc >= npool || qa < 1 || qa > nA) return bad("C -> A entry " + std::to_string(k));
+  }
+  if (h.poff.empty() || h.poff[0] != 0 || h.poff.back() != (int)h.bkey.size()) return bad("piece offsets");
+  for (size_t k = 1; k < h.poff.size(); ++k)
+    if (h.poff[k] < h.poff[k - 1]) return bad("piece offsets");
+  const int npc = (int)h.poff.size() - 1;
+  if (npc > h.nC || h.tpiece.size() != (size_t)nA + 1) return bad("pieces per target");
+  for (size_t k = 0; k < h.tpiece.size(); ++k)
+    if (h.tpiece[k] < 0 || h.tpiece[k] > npc || (k && h.tpiece[k] < h.tpiece[k - 1])) return bad("pieces per target");
+  return true;
+}
+
 }  // namespace apip

@@ -13,12 +13,29 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gaunt_layout.h"
 #include "kernels.h"
 
 using namespace apip;
 
 namespace {
+
+// An NVTX range: a named span of host time that a profiler attached to the
+// process shows on its timeline and by which ncu's --nvtx filters select the
+// kernels launched inside it.  Each call is one range ("apip_energy_forces", ...)
+// with one nested range per phase ("apip/pass2", ...).  Without an attached
+// tool a push or pop costs a few nanoseconds.
+struct NvtxRange {
+  bool open = true;
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  void end() {
+    if (open) nvtxRangePop();
+    open = false;
+  }
+  ~NvtxRange() { end(); }
+};
 
 apip_status fail(apip_ctx* c, apip_status s, const std::string& msg) {
   if (c) c->err = msg;
@@ -77,7 +94,7 @@ void free_all(apip_ctx* c) {
   void* ptrs[] = {c->cell_count, c->cell_atoms, c->cell_q, c->nnb, c->nnb_e, c->nnb_0, c->mind1, c->posg, c->nbl, c->nbl_tmp, c->pos_ref, c->posq, c->posq_ref, c->id2idx,
                   c->csp, c->csp_idx, c->csp_owner, c->zeta, c->xi_p, c->e_eam, c->g, c->wbar, c->dd, c->lam, c->dlam, c->e_ace,
                   c->cvec, c->ace_list, c->clist, c->counts, c->flags, c->status, c->partials, c->thermo_part,
-                  c->e_scratch, c->ind_acc, c->ace_tab, c->mlp_w, c->mlp_img, c->mlp_x0, c->mlp_ws};
+                  c->e_scratch, c->ind_acc, c->blk_cnt, c->ace_tab, c->mlp_w, c->mlp_img, c->mlp_x0, c->mlp_ws};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -95,6 +112,8 @@ apip_status check_params(const apip_params* p, std::string* why) {
     return bad("ace_group must be 0, 1, 2, 4, 8 or 32");
   if (!p->ace_c1 || !p->ace_c2) return bad("ace_c1 / ace_c2 must not be NULL");
   if (p->mixing != APIP_MIX_ENERGY && p->mixing != APIP_MIX_FORCE) return bad("unknown mixing");
+  if (p->deterministic != 0 && p->deterministic != 1) return bad("deterministic must be 0 or 1");
+  if (p->deterministic && p->mixing == APIP_MIX_FORCE) return bad("the deterministic mode does not support force mixing");
   if (!(p->ace_rc > 0 && p->ace_rc_width > 0 && p->ace_rc_width <= p->ace_rc)) return bad("bad ACE cutoff");
   if (!(p->ace_eps > 0)) return bad("ace_eps must be > 0");
   if (!std::isfinite(p->prec_shift)) return bad("prec_shift must be finite");
@@ -252,6 +271,7 @@ Args<T> make_args(apip_ctx* c, const double* pos, const int* id, int n, double* 
   a.e_ace = as<T>(c->e_ace);
   a.cvec = c->cvec; a.ace_list = c->ace_list; a.clist = c->clist; a.counts = c->counts;
   a.flags = c->flags; a.status = c->status;
+  a.det = c->det ? 1 : 0; a.blk_cnt = c->blk_cnt;
   a.partials = c->partials;
   // one energy partial per pass-1 block, ahead of the ACE blocks' partials
   if (p.lam_mode != APIP_LAM_LEARNED) a.n_part_p1 = nblk(n);
@@ -360,41 +380,51 @@ void pass1(const Args<T>& a, cudaStream_t s) {
 // The force pipeline after prep (or after the drift of a Verlet step).
 template <typename T>
 void force_pipeline(apip_ctx* c, Args<T>& a, cudaStream_t s) {
-  { Phase ph(c, APIP_PHASE_NEIGHBOR, 2, s); launch_neighbors<T>(a, c->ncell, s); }
-  { Phase ph(c, APIP_PHASE_PASS1, 1, s); pass1<T>(a, s); }
-  { Phase ph(c, APIP_PHASE_PASS2, 1, s); launch_pass2<T>(a, s); if (a.force_mix) launch_fm_buffer<T>(a, s); }
-  { Phase ph(c, APIP_PHASE_ACE, 1, s); const AceDev<T> t = ace_dev<T>(c);
+  { NvtxRange nv("apip/neighbor"); Phase ph(c, APIP_PHASE_NEIGHBOR, a.det ? 3 : 2, s); launch_neighbors<T>(a, c->ncell, s); }
+  { NvtxRange nv("apip/pass1"); Phase ph(c, APIP_PHASE_PASS1, 1, s); pass1<T>(a, s); }
+  { NvtxRange nv("apip/pass2"); Phase ph(c, APIP_PHASE_PASS2, a.det ? 3 : 1, s); launch_pass2<T>(a, s);
+    if (a.force_mix) launch_fm_buffer<T>(a, s); }
+  { NvtxRange nv("apip/ace"); Phase ph(c, APIP_PHASE_ACE, 1, s); const AceDev<T> t = ace_dev<T>(c);
     if (t.kind == kAceStreamed) launch_ace_stream<T>(a, t, c->ace_blocks, s);
     else launch_ace_pool<T>(a, t, c->ace_blocks, s); }
   if (a.lam_mode == APIP_LAM_PAPER && a.grad_lambda) {
+    NvtxRange nv("apip/csp");
     Phase ph(c, APIP_PHASE_CSP, 1, s);
     launch_csp_force<T>(a, s);
   } else if (a.lam_mode == APIP_LAM_LEARNED && a.grad_lambda) {
+    NvtxRange nv("apip/csp");
     Phase ph(c, APIP_PHASE_CSP, 1, s);
     launch_mlp_force<T>(a, s);
+  }
+  if (a.det && a.force) {   // the fixed-point force sums back to float64
+    NvtxRange nv("apip/csp");
+    Phase ph(c, APIP_PHASE_CSP, 1, s);
+    launch_fix_finish(a.force, a.n, s);
   }
 }
 
 template <typename T>
 apip_status energy_forces_t(apip_ctx* c, const double* pos, const int32_t* id, int n, double* force,
                             double* e_atom, double* e_total, cudaStream_t s) {
+  NvtxRange nv_call("apip_energy_forces");
   Args<T> a = make_args<T>(c, pos, id, n, force, e_atom);
   set_view<T>(a, c);
   mark_atom_count(c, n, s);
-  { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_prep<T>(a, s); }
+  { NvtxRange nv("apip/prep"); Phase ph(c, APIP_PHASE_PREP, 1, s); launch_prep<T>(a, s); }
   force_pipeline<T>(c, a, s);
   if (e_total) {
     Phase ph(c, APIP_PHASE_REDUCE, 1, s);
     launch_final(c->partials, a.n_part_p1 + c->ace_blocks, e_total, nullptr, nullptr, 0, nullptr,
                  c->flags, c->counts, nullptr, c->cell_count, c->ncell, s);
   }
-  if (a.ind_on) launch_ind_work(c->ind_acc, 0.0, s);
+  if (a.ind_on) launch_ind_work(c->ind_acc, 0.0, a.det, s);
   return launch_status(c);
 }
 
 template <typename T>
 apip_status switch_t(apip_ctx* c, const double* pos, const int32_t* id, int n, double* lam_out,
                      double* dlam_out, int64_t* n_ace_out, cudaStream_t s) {
+  NvtxRange nv_call("apip_switch");
   Args<T> a = make_args<T>(c, pos, id, n, nullptr, nullptr);
   set_view<T>(a, c);
   a.eam_force = 0;
@@ -412,6 +442,7 @@ apip_status switch_t(apip_ctx* c, const double* pos, const int32_t* id, int n, d
 
 template <typename T>
 apip_status neighbors_t(apip_ctx* c, const double* pos, const int32_t* id, int n, cudaStream_t s) {
+  NvtxRange nv_call("apip_build_neighbors");
   Args<T> a = make_args<T>(c, pos, id, n, nullptr, nullptr);
   set_view<T>(a, c);
   launch_prep<T>(a, s);
@@ -426,6 +457,7 @@ apip_status neighbors_t(apip_ctx* c, const double* pos, const int32_t* id, int n
 template <typename T>
 apip_status verlet_t(apip_ctx* c, double* pos, double* vel, double* force, const double* inv_mass,
                      const int32_t* id, int n, double dt, int steps, double* thermo, cudaStream_t s) {
+  NvtxRange nv_call("apip_verlet_step");
   Args<T> a = make_args<T>(c, pos, id, n, force, nullptr);
   set_view<T>(a, c);
   mark_atom_count(c, n, s);
@@ -435,20 +467,20 @@ apip_status verlet_t(apip_ctx* c, double* pos, double* vel, double* force, const
   // are left unread and the ACE kernel clears the rebuild flag
   double* tp = thermo ? c->thermo_part : nullptr;
   for (int k = 0; k < steps; ++k) {
-    { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, k == 0 ? 0 : 1, pos, vel, force, inv_mass, dt, k > 0 ? tp : nullptr, s); }
+    { NvtxRange nv("apip/prep"); Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, k == 0 ? 0 : 1, pos, vel, force, inv_mass, dt, k > 0 ? tp : nullptr, s); }
     if (a.ind_on) {   // the indenter centre moves with the drift
       for (int q = 0; q < 3; ++q) c->ind_c[q] += dt * c->ind_v[q];
       set_ind_center(a, c->geo, c->ind_c);
     }
     force_pipeline<T>(c, a, s);
-    if (a.ind_on) launch_ind_work(c->ind_acc, dt, s);
+    if (a.ind_on) launch_ind_work(c->ind_acc, dt, a.det, s);
     if (thermo) {
       Phase ph(c, APIP_PHASE_REDUCE, 1, s);
       launch_final(c->partials, n_part, nullptr, thermo + 5 * k, k > 0 ? tp : nullptr, ntb,
                    k > 0 ? thermo + 5 * (k - 1) : nullptr, c->flags, c->counts, nullptr, c->cell_count, c->ncell, s);
     }
   }
-  { Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, 2, pos, vel, force, inv_mass, dt, tp, s); }
+  { NvtxRange nv("apip/prep"); Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, 2, pos, vel, force, inv_mass, dt, tp, s); }
   if (thermo) {
     Phase ph(c, APIP_PHASE_REDUCE, 1, s);
     launch_thermo_final(c->thermo_part, ntb, thermo + 5 * (steps - 1), s);
@@ -491,6 +523,11 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
                                  nb, &st, &why)
                : !build_coupled(p->ace_n_max, p->ace_l_max, p->ace_nu_max, ctx->ace_c1.data(), ctx->ace_c2.data(),
                                 nb, &tab, &why)) {
+    delete ctx;
+    return APIP_ERR_ARG;
+  }
+  if (streamed ? !validate_streamed(st, p->ace_n_max * (p->ace_l_max + 1) * (p->ace_l_max + 1), &why)
+               : !validate_coupled(tab, &why)) {
     delete ctx;
     return APIP_ERR_ARG;
   }
@@ -579,6 +616,8 @@ apip_status apip_create(const apip_params* p, int64_t n_atoms_max, apip_ctx** ou
   APIP_ALLOC(ctx->ace_list, sizeof(int) * N);
   if (p->lam_mode == APIP_LAM_LEARNED) APIP_ALLOC(ctx->clist, sizeof(int) * N);
   APIP_ALLOC(ctx->counts, sizeof(int) * 4);
+  ctx->det = p->deterministic != 0;
+  if (ctx->det) APIP_ALLOC(ctx->blk_cnt, sizeof(int) * nblk(N));
   APIP_ALLOC(ctx->flags, sizeof(int) * 4);
   APIP_ALLOC(ctx->status, sizeof(int) * ST_COUNT);
   // pass-1 partials: the most blocks either pass 1 launches (the learned one has
@@ -837,13 +876,23 @@ apip_status apip_sync(apip_ctx* ctx, void* stream) {
   int st[ST_COUNT];
   APIP_CK(cudaMemcpy(st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost));
   APIP_CK(cudaMemset(ctx->status, 0, sizeof(st)));
+  if (st[ST_BOUNDS]) {
+    static const char* const site[] = {"?", "neighbour-list entry", "neighbour-list length", "cell index or member",
+                                       "compacted-list entry", "ACE table key or range", "self-test"};
+    const int k = st[ST_BOUNDS] >= 1 && st[ST_BOUNDS] <= BND_SELFTEST ? st[ST_BOUNDS] : 0;
+    return fail(ctx, APIP_ERR_BOUNDS, std::string("bounds check: ") + site[k] + " " + std::to_string(st[ST_BOUNDS_VAL]) +
+                                          " outside [0, " + std::to_string(st[ST_BOUNDS_LIM]) + ")");
+  }
   if (st[ST_NB_OVERFLOW])
     return fail(ctx, APIP_ERR_NB_OVERFLOW, "neighbour list overflow: an atom has " + std::to_string(st[ST_MAX_NNB]) +
                                               " neighbours, max_nb = " + std::to_string(ctx->p.max_nb));
   if (st[ST_CELL_OVERFLOW])
     return fail(ctx, APIP_ERR_NB_OVERFLOW, "cell overflow: a cell holds " + std::to_string(st[ST_MAX_CELL]) +
                                               " atoms, cell_cap = " + std::to_string(ctx->p.cell_cap));
-  if (st[ST_TIMEOUT]) return fail(ctx, APIP_ERR_TIMEOUT, "a bounded device wait gave up (a tensor-core kernel's wait for its matrix products: training or the learned switch)");
+  if (st[ST_TIMEOUT])
+    return fail(ctx, APIP_ERR_TIMEOUT,
+                "a bounded device wait gave up (a tensor-core kernel's wait for its matrix products: training or the "
+                "learned switch)");
   if (st[ST_BAD_INPUT]) return fail(ctx, APIP_ERR_BAD_INPUT, "non-finite position or atom id out of range");
   if (st[ST_BAD_PARTNER]) return fail(ctx, APIP_ERR_BAD_INPUT, "a CSP partner id is not present");
   return APIP_OK;
@@ -992,7 +1041,7 @@ apip_status apip_ace_info(apip_ctx* ctx, int64_t* out) {
 apip_status apip_get_field(apip_ctx* ctx, int32_t field, void* dst, int64_t n, void* stream) {
   if (!ctx) return APIP_ERR_ARG;
   if (!dst || n < 0 || n > ctx->nmax) return fail(ctx, APIP_ERR_ARG, "bad dst or n");
-  if (field < APIP_FIELD_G || field > APIP_FIELD_CSP) return fail(ctx, APIP_ERR_ARG, "unknown field");
+  if (field < APIP_FIELD_G || field > APIP_FIELD_BUILD_POS) return fail(ctx, APIP_ERR_ARG, "unknown field");
   if (n == 0) return APIP_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (ctx->p.precision == APIP_FP32) {
@@ -1004,5 +1053,23 @@ apip_status apip_get_field(apip_ctx* ctx, int32_t field, void* dst, int64_t n, v
   }
   return launch_status(ctx);
 }
+
+#ifdef APIP_CHECK_BOUNDS
+namespace {
+__global__ void k_bounds_selftest(int* status) {
+  // an out-of-range index that touches no memory: 7 against the limit 5
+  if (threadIdx.x == 0) (void)APIP_CHK(status, BND_SELFTEST, 7, 5);
+}
+}  // namespace
+
+// Exported only by the bounds-checked build: records a violation through the
+// device check (no memory is accessed with the bad index), so that the next
+// apip_sync reports APIP_ERR_BOUNDS.
+apip_status apip_check_bounds_selftest(apip_ctx* ctx, void* stream) {
+  if (!ctx) return APIP_ERR_ARG;
+  k_bounds_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(ctx->status);
+  return launch_status(ctx);
+}
+#endif
 
 }  // extern "C"

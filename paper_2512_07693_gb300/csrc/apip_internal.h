@@ -29,7 +29,20 @@ enum {
   ST_MAX_NNB = 4,       // largest neighbour count seen (for the error text)
   ST_MAX_CELL = 5,      // largest cell occupancy seen
   ST_TIMEOUT = 6,       // a bounded device wait gave up
-  ST_COUNT = 8
+  ST_BOUNDS = 7,        // bounds-checked build: site of the first out-of-range index (0: none)
+  ST_BOUNDS_VAL = 8,    // that index
+  ST_BOUNDS_LIM = 9,    // and the limit it broke
+  ST_COUNT = 10
+};
+
+// Sites of the bounds-checked build (APIP_CHECK_BOUNDS), reported by apip_sync.
+enum {
+  BND_NEIGHBOUR = 1,    // an atom index read from the neighbour list
+  BND_LIST_LEN = 2,     // a neighbour-list length above max_nb
+  BND_CELL = 3,         // a cell index or a cell member's atom index
+  BND_COMPACT = 4,      // an entry of the compacted lists
+  BND_ACE_TABLE = 5,    // an ACE table key or partner range
+  BND_SELFTEST = 6      // apip_check_bounds_selftest
 };
 
 // Derived scalar parameters, passed by value to kernels.
@@ -110,6 +123,8 @@ bool build_coupled(int n_max, int l_max, int nu_max, const double* c1, const dou
                    HostAce* out, std::string* err);
 bool build_streamed(int n_max, int l_max, int nu_max, const double* c1, const double* c2, int64_t n_basis,
                     HostStream* out, std::string* err);
+bool validate_streamed(const HostStream& h, int nA, std::string* err);
+bool validate_coupled(const HostAce& h, std::string* err);
 // real Gaunt values in the canonical layout of gaunt_layout.h (kGauntTotal entries)
 void gaunt_fill(double* out);
 // real Y_lm normalisation N_lm (times sqrt 2 for m != 0), index l^2 + l + m
@@ -164,7 +179,9 @@ struct apip_ctx {
   double* cvec = nullptr;      // [nmax] grad-lambda CSP coefficients (kept zero between calls)
   int* ace_list = nullptr;     // [nmax]
   int* clist = nullptr;        // [nmax] learned switch: atoms with a grad-lambda coefficient
-  int* counts = nullptr;       // [4]: |P|, scratch
+  int* counts = nullptr;       // [4]: |P|, learned c-vector count, scratch
+  int* blk_cnt = nullptr;      // deterministic mode: pass 2's per-block counts of lam > 0, then their offsets
+  bool det = false;            // apip_params.deterministic
   int* flags = nullptr;        // [4]: need_rebuild, largest squared displacement since the build (float bits)
   int* status = nullptr;       // [ST_COUNT]
   double* partials = nullptr;  // energy partials: P1 blocks then ACE warps

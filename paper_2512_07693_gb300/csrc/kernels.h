@@ -64,6 +64,8 @@ struct Args {
   uint4* cell_q;          // FP32 path: fixed-point positions of the cell members, cell order
   T* zeta; T* xi_p; T* e_eam; T* g; T* wbar; T* dd; T* lam; T* dlam; T* e_ace;
   double* cvec; int* ace_list; int* counts; int* flags; int* status;
+  int det;                // deterministic mode: fixed-point scatter sums, index-ordered compaction
+  int* blk_cnt;           // deterministic mode: pass 2's per-block counts, then offsets
   int* clist;             // learned switch: the atoms with cvec != 0 (counts[1] of them)
   double* partials; int n_part_p1;
   double* force;          // caller force [n][3]
@@ -75,6 +77,47 @@ struct Args {
   int learned_grid1;      // FP32 path: persistent CTAs of the tensor-core network of pass 1
   T ace_rc, ace_rc_lo;    // cutoff of the radial descriptors (the ACE cutoff)
 };
+
+// Scattered sums (forces, the grad-lambda c-vector, the indenter work).  In
+// deterministic mode a contribution v is rounded to a multiple of 2^-40 and added
+// as a 64-bit integer into the same 8 bytes: integer addition is associative, so
+// the sum does not depend on the order in which the atomics arrive.  fix_get
+// reads such a slot back as float64, fix_put gives the bits of a plain value in
+// that form.  Otherwise the slot holds a float64 and takes float64 atomic adds.
+constexpr double kFixOne = 1099511627776.0;          // 2^40
+constexpr double kFixUnit = 1.0 / 1099511627776.0;   // 2^-40
+__device__ __forceinline__ void scatter_add(double* p, double v, int det) {
+  if (det) atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)__double2ll_rn(v * kFixOne));
+  else atomicAdd(p, v);
+}
+__device__ __forceinline__ double fix_get(const double* p, int det) {
+  const double v = *p;
+  return det ? (double)__double_as_longlong(v) * kFixUnit : v;
+}
+__device__ __forceinline__ double fix_put(double v, int det) {
+  return det ? __longlong_as_double(__double2ll_rn(v * kFixOne)) : v;
+}
+
+// Bounds-checked build (APIP_CHECK_BOUNDS): an index v outside [0, lim) is
+// recorded (the first violation's site, index and limit go to the status words,
+// reported by apip_sync as APIP_ERR_BOUNDS) and replaced by 0, so that no access
+// leaves its array.  In the normal build the check is the index itself.
+#ifdef APIP_CHECK_BOUNDS
+static __device__ __noinline__ void bounds_violation(int* status, int site, int v, int lim) {
+  if (atomicCAS(&status[ST_BOUNDS], 0, site) == 0) {
+    status[ST_BOUNDS_VAL] = v;
+    status[ST_BOUNDS_LIM] = lim;
+  }
+}
+__device__ __forceinline__ int bounds_check(int* status, int site, int v, int lim) {
+  if ((unsigned)v < (unsigned)lim) return v;
+  bounds_violation(status, site, v, lim);
+  return 0;
+}
+#define APIP_CHK(status, site, v, lim) ::apip::bounds_check((status), (site), (v), (lim))
+#else
+#define APIP_CHK(status, site, v, lim) (v)
+#endif
 
 // Ends a call's use of the list-build trigger, by one whole block, after every
 // kernel that reads the trigger or the binning counts has completed: after a
@@ -92,18 +135,22 @@ __device__ __forceinline__ void end_list_build(int* flags, int* cell_count, int 
 // the index fetched two entries and the neighbour's record (load(j)) one entry
 // ahead of the arithmetic f(j, record), so that the gathers of the next entries
 // are in flight while the current one is evaluated.
+// (status, n: the bounds-checked build's check of each index against [0, n).)
 template <typename L, typename F>
-__device__ __forceinline__ void walk_list(const int* nb, int nmax, int s0, int s1, L&& load, F&& f) {
+__device__ __forceinline__ void walk_list(const int* nb, int nmax, int s0, int s1, int* status, int n, L&& load,
+                                          F&& f) {
+  (void)status;
+  (void)n;
   if (s0 >= s1) return;
-  int j = nb[(size_t)s0 * nmax];
+  int j = APIP_CHK(status, BND_NEIGHBOUR, nb[(size_t)s0 * nmax], n);
   auto r = load(j);
-  int jn = s0 + 1 < s1 ? nb[(size_t)(s0 + 1) * nmax] : j;
+  int jn = s0 + 1 < s1 ? APIP_CHK(status, BND_NEIGHBOUR, nb[(size_t)(s0 + 1) * nmax], n) : j;
   for (int s = s0; s < s1; ++s) {
     const int jc = j;
     const auto rc = r;
     j = jn;
     r = load(j);
-    jn = s + 2 < s1 ? nb[(size_t)(s + 2) * nmax] : j;
+    jn = s + 2 < s1 ? APIP_CHK(status, BND_NEIGHBOUR, nb[(size_t)(s + 2) * nmax], n) : j;
     f(jc, rc);
   }
 }
@@ -193,7 +240,8 @@ template <typename T> void launch_pass2(const Args<T>& a, cudaStream_t s);
 // neighbour within the ACE cutoff with lam > 0 (the precise model's buffer)
 template <typename T> void launch_fm_buffer(const Args<T>& a, cudaStream_t s);
 // indenter work: W += dt/2 ((sum F).v old + new) when dt > 0; then old = new, new = 0
-void launch_ind_work(double* acc, double dt, cudaStream_t s);
+void launch_ind_work(double* acc, double dt, int det, cudaStream_t s);
+void launch_fix_finish(double* force, int n, cudaStream_t s);
 template <typename T> void launch_csp_force(const Args<T>& a, cudaStream_t s);
 void launch_final(double* partials, int n_part, double* e_total, double* e_pot_slot,
                   const double* thermo_part, int n_tblocks, double* thermo_slot, int* flags,

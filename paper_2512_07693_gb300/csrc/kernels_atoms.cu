@@ -127,9 +127,10 @@ __device__ __forceinline__ void atom_cell(const Args<T>& a, int i, int c[3]) {
 }
 
 // Binning: each atom takes a slot of its cell (the order of the slots follows
-// the atomics, so neighbour order within a cell is not fixed; every sum over
-// neighbours is order-independent up to rounding); FP32 path: the member's
-// fixed-point position is copied into cell order for the fill.
+// the atomics, so neighbour order within a cell is not fixed and every sum over
+// neighbours is order-independent up to rounding, unless the deterministic mode
+// sorts the cells); FP32 path: the member's fixed-point position is copied into
+// cell order for the fill.
 template <typename T>
 __global__ void k_bin(Args<T> a) {
   pdl_begin();
@@ -150,6 +151,36 @@ __global__ void k_bin(Args<T> a) {
   } else {
     atomicOr(&a.status[ST_CELL_OVERFLOW], 1);
     atomicMax(&a.status[ST_MAX_CELL], slot + 1);
+  }
+}
+
+// Deterministic mode, on a build: each cell's members sorted by atom index (one
+// thread per cell, insertion sort: a cell holds a few atoms), so that the list's
+// order, and with it every sum over neighbours, does not depend on the order of
+// the binning atomics.
+template <typename T>
+__global__ void k_cell_sort(Args<T> a) {
+  pdl_begin();
+  if (!a.flags[0]) return;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= a.ncell) return;
+  const int m = min(a.cell_count[cell], a.cell_cap);
+  if constexpr (sizeof(T) == 4) {
+    uint4* v = a.cell_q + (size_t)cell * a.cell_cap;
+    for (int k = 1; k < m; ++k) {
+      const uint4 x = v[k];
+      int p = k;
+      for (; p > 0 && v[p - 1].w > x.w; --p) v[p] = v[p - 1];
+      v[p] = x;
+    }
+  } else {
+    int* v = a.cell_atoms + (size_t)cell * a.cell_cap;
+    for (int k = 1; k < m; ++k) {
+      const int x = v[k];
+      int p = k;
+      for (; p > 0 && v[p - 1] > x; --p) v[p] = v[p - 1];
+      v[p] = x;
+    }
   }
 }
 
@@ -195,7 +226,7 @@ __global__ void k_nbfill(Args<T> a) {
       const int cy = (c[1] + dy + a.geo.nc[1]) % a.geo.nc[1];
       for (int dx = -1; dx <= 1; ++dx) {
         const int cx = (c[0] + dx + a.geo.nc[0]) % a.geo.nc[0];
-        const int cell = (cz * a.geo.nc[1] + cy) * a.geo.nc[0] + cx;
+        const int cell = APIP_CHK(a.status, BND_CELL, (cz * a.geo.nc[1] + cy) * a.geo.nc[0] + cx, a.ncell);
         const int m = min(a.cell_count[cell], a.cell_cap);
         if constexpr (sizeof(T) == 4) {
           // float comparison against r_list^2 rounded up: the list holds every pair
@@ -210,12 +241,12 @@ __global__ void k_nbfill(Args<T> a) {
             const float ey = (float)(int)(o.y - si.q.y) * a.pv.unit[1];
             const float ez = (float)(int)(o.z - si.q.z) * a.pv.unit[2];
             const float r2 = ex * ex + ey * ey + ez * ez;
-            if (r2 < rl2 && (int)o.w != i) keep((int)o.w, r2);
+            if (r2 < rl2 && (int)o.w != i) keep(APIP_CHK(a.status, BND_CELL, (int)o.w, a.n), r2);
           }
         } else {
           const int* v = a.cell_atoms + (size_t)cell * a.cell_cap;
           for (int k = 0; k < m; ++k) {
-            const int j = v[k];
+            const int j = APIP_CHK(a.status, BND_CELL, v[k], a.n);
             if (j == i) continue;
             const auto d = a.pv.vec(si, j);
             const T r2 = dot3(d, d);
@@ -241,13 +272,12 @@ __global__ void k_nbfill(Args<T> a) {
     a.nnb_0[i] = k0;
     a.mind1[i] = k1 < n1 ? 0.f : min1;   // a class-1 entry dropped on overflow: never skip class 1
   }
-  if (sizeof(T) == 4) {
-    a.posq_ref[i] = a.posq[i];
-  } else {
-    a.pos_ref[3 * i] = a.pos[3 * i];
-    a.pos_ref[3 * i + 1] = a.pos[3 * i + 1];
-    a.pos_ref[3 * i + 2] = a.pos[3 * i + 2];
-  }
+  // the positions of this build: the FP64 path's displacement reference, and in
+  // both paths what a checkpoint keeps to rebuild the same list on resume
+  if (sizeof(T) == 4) a.posq_ref[i] = a.posq[i];
+  a.pos_ref[3 * i] = a.pos[3 * i];
+  a.pos_ref[3 * i + 1] = a.pos[3 * i + 1];
+  a.pos_ref[3 * i + 2] = a.pos[3 * i + 2];
 }
 
 // -------------------------------------------------------------- CSP pairs
@@ -271,9 +301,9 @@ __global__ void k_csp_init(Args<double> a) {
   int m = 0;
   const int K = a.csp_nnb;
   const double xi = a.pos[3 * i], yi = a.pos[3 * i + 1], zi = a.pos[3 * i + 2];
-  const int cnt = a.nnb[i];
+  const int cnt = APIP_CHK(a.status, BND_LIST_LEN, a.nnb[i], a.max_nb + 1);
   for (int s = 0; s < cnt; ++s) {
-    const int j = a.nbl[(size_t)s * a.nmax + i];
+    const int j = APIP_CHK(a.status, BND_NEIGHBOUR, a.nbl[(size_t)s * a.nmax + i], a.n);
     const double dx = minimg_rn(__dsub_rn(a.pos[3 * j], xi), a.geo.L[0]);
     const double dy = minimg_rn(__dsub_rn(a.pos[3 * j + 1], yi), a.geo.L[1]);
     const double dz = minimg_rn(__dsub_rn(a.pos[3 * j + 2], zi), a.geo.L[2]);
@@ -347,17 +377,17 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_pass1(Args<T
     // and d_j <= the largest one (flags[1]); when the least r_b of the atom's
     // class-1 entries is at least rc + d_i + d_max (+ a rounding margin), none of
     // them is within the cutoff and the sums stop after class 0
-    int end = a.nnb_e[i];
+    int end = APIP_CHK(a.status, BND_LIST_LEN, a.nnb_e[i], a.max_nb + 1);
     if constexpr (sizeof(T) == 4) {
       const float dmax2 = __int_as_float(a.flags[1]);   // NaN (-1) before the first build: no skip
       const uint4 r = a.posq_ref[i];
       const float ex = (float)(int)(si.q.x - r.x) * a.pv.unit[0], ey = (float)(int)(si.q.y - r.y) * a.pv.unit[1],
                   ez = (float)(int)(si.q.z - r.z) * a.pv.unit[2];
       const float lim = a.k.eam_rc + sqrtf(ex * ex + ey * ey + ez * ez) + sqrtf(dmax2) + 1e-3f;
-      if (a.mind1[i] >= lim * lim) end = a.nnb_0[i];
+      if (a.mind1[i] >= lim * lim) end = APIP_CHK(a.status, BND_LIST_LEN, a.nnb_0[i], a.max_nb + 1);
     }
     Acc<T> zeta, pair;
-    walk_list(a.nbl + i, a.nmax, 0, end, [&](int j) { return a.pv.fetch(j); },
+    walk_list(a.nbl + i, a.nmax, 0, end, a.status, a.n, [&](int j) { return a.pv.fetch(j); },
               [&](int, const auto& o) {
                 const auto d = a.pv.vec_of(si, o);
                 const T r2 = dot3(d, d);
@@ -505,19 +535,20 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
     };
     // neighbour records, fetched one entry ahead: FP32 the posg entry (fixed-point
     // position, g in .w) and, within nnb_e, xi'_j; FP64 the position
-    const int cnt = a.nnb[i], cnt_e = a.nnb_e[i];
+    const int cnt = APIP_CHK(a.status, BND_LIST_LEN, a.nnb[i], a.max_nb + 1);
+    const int cnt_e = APIP_CHK(a.status, BND_LIST_LEN, a.nnb_e[i], cnt + 1);
     if constexpr (sizeof(T) == 4) {
       struct RecE { uint4 o; float xi; };
-      walk_list(a.nbl + i, a.nmax, 0, cnt_e, [&](int j) { return RecE{a.posg[j], a.xi_p[j]}; },
+      walk_list(a.nbl + i, a.nmax, 0, cnt_e, a.status, a.n, [&](int j) { return RecE{a.posg[j], a.xi_p[j]}; },
                 [&](int j, const RecE& e) { term(j, a.pv.vec_of(si, e.o), __uint_as_float(e.o.w), e.xi, true); });
       if (paper)
-        walk_list(a.nbl + i, a.nmax, cnt_e, cnt, [&](int j) { return a.posg[j]; },
+        walk_list(a.nbl + i, a.nmax, cnt_e, cnt, a.status, a.n, [&](int j) { return a.posg[j]; },
                   [&](int j, const uint4& o) { term(j, a.pv.vec_of(si, o), __uint_as_float(o.w), T(0), false); });
     } else {
-      walk_list(a.nbl + i, a.nmax, 0, cnt_e, [&](int j) { return a.pv.fetch(j); },
+      walk_list(a.nbl + i, a.nmax, 0, cnt_e, a.status, a.n, [&](int j) { return a.pv.fetch(j); },
                 [&](int j, const auto& o) { term(j, a.pv.vec_of(si, o), paper ? a.g[j] : T(0), a.xi_p[j], true); });
       if (paper)
-        walk_list(a.nbl + i, a.nmax, cnt_e, cnt, [&](int j) { return a.pv.fetch(j); },
+        walk_list(a.nbl + i, a.nmax, cnt_e, cnt, a.status, a.n, [&](int j) { return a.pv.fetch(j); },
                   [&](int j, const auto& o) { term(j, a.pv.vec_of(si, o), a.g[j], T(0), false); });
     }
     T dv = T(0), dl = T(0), wb = T(1);
@@ -551,17 +582,25 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
         gz += fi[2];
         ind_fv = fi[0] * a.ind_v[0] + fi[1] * a.ind_v[1] + fi[2] * a.ind_v[2];
       }
-      a.force[3 * i] = gx;
-      a.force[3 * i + 1] = gy;
-      a.force[3 * i + 2] = gz;
+      a.force[3 * i] = fix_put(gx, a.det);
+      a.force[3 * i + 1] = fix_put(gy, a.det);
+      a.force[3 * i + 2] = fix_put(gz, a.det);
     }
   }
   if (a.ind_on && __syncthreads_or(ind_fv != 0.0)) {
     __shared__ double shw[32];
     const double t = block_sum(ind_fv, shw);
-    if (threadIdx.x == 0) atomicAdd(&a.ind_acc[2], t);
+    if (threadIdx.x == 0) scatter_add(&a.ind_acc[2], t, a.det);
   }
   const bool pred = active && lam > T(0);
+  if (a.det) {   // the block's count (k_blk_scan and k_compact_det write the list in index order)
+    const int cnt = __syncthreads_count(pred);
+    if (threadIdx.x == 0) {
+      a.blk_cnt[blockIdx.x] = cnt;
+      if (cnt) atomicAdd(&a.counts[0], cnt);
+    }
+    return;
+  }
   const unsigned mask = __ballot_sync(0xffffffffu, pred);
   const int lane = threadIdx.x & 31;
   int base = 0;
@@ -570,12 +609,65 @@ __global__ void __launch_bounds__(kBlock) k_pass2(Args<T> a) {
   if (pred) a.ace_list[base + __popc(mask & ((1u << lane) - 1u))] = i;
 }
 
-// Indenter work by the midpoint rule over one step (dt > 0), or just the shift of
-// the last (sum F).v (dt = 0, a plain force evaluation).
-__global__ void k_ind_work(double* acc, double dt) {
+// Deterministic mode: pass 2's per-block counts turned into exclusive offsets, in
+// place (one block; each thread a contiguous run of counts, then a scan of the
+// run totals).
+__global__ void __launch_bounds__(1024) k_blk_scan(int* cnt, int nb) {
   pdl_begin();
-  acc[0] += 0.5 * dt * (acc[1] + acc[2]);
-  acc[1] = acc[2];
+  __shared__ int sc[1024];
+  const int per = (nb + blockDim.x - 1) / blockDim.x;
+  const int b0 = min((int)threadIdx.x * per, nb), b1 = min(b0 + per, nb);
+  int run = 0;
+  for (int b = b0; b < b1; ++b) run += cnt[b];
+  sc[threadIdx.x] = run;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {   // inclusive scan of the run totals
+    const int v = (int)threadIdx.x >= o ? sc[threadIdx.x - o] : 0;
+    __syncthreads();
+    sc[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int off = sc[threadIdx.x] - run;
+  for (int b = b0; b < b1; ++b) {
+    const int v = cnt[b];
+    cnt[b] = off;
+    off += v;
+  }
+}
+
+// Deterministic mode: the compacted list {i : lam_i > 0} in index order, each
+// block at the offset k_blk_scan computed for it.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_compact_det(Args<T> a) {
+  pdl_begin();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool pred = i < a.n && a.lam[i] > T(0);
+  const unsigned mask = __ballot_sync(0xffffffffu, pred);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ int wc[kBlock / 32];
+  if (lane == 0) wc[warp] = __popc(mask);
+  __syncthreads();
+  int off = a.blk_cnt[blockIdx.x];
+  for (int w = 0; w < warp; ++w) off += wc[w];
+  if (pred) a.ace_list[APIP_CHK(a.status, BND_COMPACT, off + __popc(mask & ((1u << lane) - 1u)), a.n)] = i;
+}
+
+// Deterministic mode: the force array, summed as 64-bit fixed point by pass 2 and
+// the scattering kernels, back to float64.
+__global__ void k_fix_finish(double* force, int n3) {
+  pdl_begin();
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n3) force[k] = fix_get(force + k, 1);
+}
+
+// Indenter work by the midpoint rule over one step (dt > 0), or just the shift of
+// the last (sum F).v (dt = 0, a plain force evaluation).  acc[2] holds fixed point
+// in deterministic mode.
+__global__ void k_ind_work(double* acc, double dt, int det) {
+  pdl_begin();
+  const double f = fix_get(acc + 2, det);
+  acc[0] += 0.5 * dt * (acc[1] + f);
+  acc[1] = f;
   acc[2] = 0.0;
 }
 
@@ -590,7 +682,7 @@ __global__ void k_csp_force(Args<T> a) {
   pdl_begin();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.n) return;
-  const double c = a.cvec[j];
+  const double c = fix_get(&a.cvec[j], a.det);
   if ((__double_as_longlong(c) << 1) == 0) return;   // c == +-0, tested on the bits (off the float64 pipe)
   a.cvec[j] = 0.0;
   const auto sj = a.pv.self(j);
@@ -616,13 +708,13 @@ __global__ void k_csp_force(Args<T> a) {
     const double u[3] = {(double)uv.x, (double)uv.y, (double)uv.z};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      atomicAdd(&a.force[3 * ia + q], -2.0 * c * u[q]);
-      atomicAdd(&a.force[3 * ib + q], -2.0 * c * u[q]);
+      scatter_add(&a.force[3 * ia + q], -2.0 * c * u[q], a.det);
+      scatter_add(&a.force[3 * ib + q], -2.0 * c * u[q], a.det);
       fj[q] += 4.0 * c * u[q];
     }
   }
 #pragma unroll
-  for (int q = 0; q < 3; ++q) atomicAdd(&a.force[3 * j + q], fj[q]);
+  for (int q = 0; q < 3; ++q) scatter_add(&a.force[3 * j + q], fj[q], a.det);
 }
 
 // ------------------------------------------------------------- reductions
@@ -754,6 +846,9 @@ __global__ void k_get_field(Args<T> a, int field, void* dst) {
       // row i: the partners of the atom whose id is i (the rows are kept by id)
       for (int s = 0; s < a.csp_nnb; ++s) di[(size_t)i * a.csp_nnb + s] = a.csp[(size_t)i * kCspCap + s];
       break;
+    case APIP_FIELD_BUILD_POS:
+      for (int q = 0; q < 3; ++q) dd[3 * i + q] = a.pos_ref[3 * i + q];
+      break;
     default: break;
   }
 }
@@ -770,6 +865,7 @@ template <typename T> void launch_prep(const Args<T>& a, cudaStream_t s) {
 template <typename T> void launch_neighbors(const Args<T>& a, int ncell, cudaStream_t s) {
   (void)ncell;
   launch_pdl(k_bin<T>, nblocks(a.n), kBlock, 0, s, a);
+  if (a.det) launch_pdl(k_cell_sort<T>, nblocks(a.ncell), kBlock, 0, s, a);
   launch_pdl(k_nbfill<T>, nblocks(a.n), kBlock, 0, s, a);
 }
 
@@ -796,10 +892,10 @@ __global__ void __launch_bounds__(kBlock) k_fm_buffer(Args<T> a) {
   if (i < a.n && a.lam[i] == T(0)) {
     const auto si = a.pv.self(i);
     const T rc2 = a.ace_rc * a.ace_rc;
-    const int cnt = a.nnb[i];
+    const int cnt = APIP_CHK(a.status, BND_LIST_LEN, a.nnb[i], a.max_nb + 1);
     const int* nb = a.nbl + i;
     for (int s = 0; s < cnt && !pred; ++s, nb += a.nmax) {
-      const int j = *nb;
+      const int j = APIP_CHK(a.status, BND_NEIGHBOUR, *nb, a.n);
       if (a.lam[j] > T(0)) {
         const auto d = a.pv.vec(si, j);
         pred = dot3(d, d) < rc2;
@@ -814,7 +910,13 @@ __global__ void __launch_bounds__(kBlock) k_fm_buffer(Args<T> a) {
   if (pred) a.ace_list[base + __popc(mask & ((1u << lane) - 1u))] = i;
 }
 
-void launch_ind_work(double* acc, double dt, cudaStream_t s) { launch_pdl(k_ind_work, 1, 1, 0, s, acc, dt); }
+void launch_ind_work(double* acc, double dt, int det, cudaStream_t s) {
+  launch_pdl(k_ind_work, 1, 1, 0, s, acc, dt, det);
+}
+
+void launch_fix_finish(double* force, int n, cudaStream_t s) {
+  launch_pdl(k_fix_finish, nblocks(3 * n), kBlock, 0, s, force, 3 * n);
+}
 
 template <typename T> void launch_fm_buffer(const Args<T>& a, cudaStream_t s) {
   launch_pdl(k_fm_buffer<T>, nblocks(a.n), kBlock, 0, s, a);
@@ -822,6 +924,10 @@ template <typename T> void launch_fm_buffer(const Args<T>& a, cudaStream_t s) {
 
 template <typename T> void launch_pass2(const Args<T>& a, cudaStream_t s) {
   launch_pdl(k_pass2<T>, nblocks(a.n), kBlock, 0, s, a);
+  if (a.det) {
+    launch_pdl(k_blk_scan, 1, 1024, 0, s, a.blk_cnt, nblocks(a.n));
+    launch_pdl(k_compact_det<T>, nblocks(a.n), kBlock, 0, s, a);
+  }
 }
 
 template <typename T> void launch_csp_force(const Args<T>& a, cudaStream_t s) {

@@ -70,9 +70,9 @@ __device__ __forceinline__ void descriptors_of(const Args<T>& a, int i, T* G) {
   for (int m = 0; m < kIn; ++m) G[m] = T(0);
   const auto si = a.pv.self(i);
   const T rc2 = a.ace_rc * a.ace_rc, inv_w = T(1) / (a.ace_rc - a.ace_rc_lo);
-  const int cnt = a.nnb[i];
+  const int cnt = APIP_CHK(a.status, BND_LIST_LEN, a.nnb[i], a.max_nb + 1);
   for (int s = 0; s < cnt; ++s) {
-    const int j = a.nbl[(size_t)s * a.nmax + i];
+    const int j = APIP_CHK(a.status, BND_NEIGHBOUR, a.nbl[(size_t)s * a.nmax + i], a.n);
     const auto d = a.pv.vec(si, j);
     const T r2 = dot3(d, d);
     if (!(r2 < rc2)) continue;
@@ -161,9 +161,9 @@ __global__ void __launch_bounds__(kLearnedBlock) k_pass1_learned(Args<T> a) {
     T G[kIn];
 #pragma unroll
     for (int m = 0; m < kIn; ++m) G[m] = T(0);
-    const int cnt = a.nnb[i];
+    const int cnt = APIP_CHK(a.status, BND_LIST_LEN, a.nnb[i], a.max_nb + 1);
     for (int s = 0; s < cnt; ++s) {
-      const int j = a.nbl[(size_t)s * a.nmax + i];
+      const int j = APIP_CHK(a.status, BND_NEIGHBOUR, a.nbl[(size_t)s * a.nmax + i], a.n);
       const auto d = a.pv.vec(si, j);
       const T r2 = dot3(d, d);
       if (!(r2 < rc2) && !(r2 < rcE2)) continue;
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kBlock) k_learned_desc(Args<float> a, float* _
     const float rc2 = a.ace_rc * a.ace_rc, inv_w = 1.f / (a.ace_rc - a.ace_rc_lo);
     const float kappa = __expf(-2.f * float(kEta) * float(kDmu) * float(kDmu));
     Acc<float> zeta, pair;
-    walk_list(a.nbl + i, a.nmax, 0, a.nnb[i], [&](int j) { return a.pv.fetch(j); },
+    walk_list(a.nbl + i, a.nmax, 0, APIP_CHK(a.status, BND_LIST_LEN, a.nnb[i], a.max_nb + 1), a.status, a.n, [&](int j) { return a.pv.fetch(j); },
               [&](int, const uint4& o) {
                 const auto d = a.pv.vec_of(si, o);
                 const float r2 = dot3(d, d);
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(lt::kT, FORCE ? 1 : 2)
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int q = tile * kRows + r;
     const bool valid = q < count;
-    const int i = valid ? (FORCE ? a.clist[q] : q) : -1;
+    const int i = valid ? (FORCE ? APIP_CHK(a.status, BND_COMPACT, a.clist[q], a.n) : q) : -1;
     if constexpr (!FORCE) {
       // x0 of this row from the descriptor kernel (zero past the atoms)
       float x[8];
@@ -591,9 +591,9 @@ __global__ void __launch_bounds__(lt::kT, FORCE ? 1 : 2)
       for (int m = 0; m < kIn; ++m) prow[m] = 0.f;
       if (valid) {
         const auto si = a.pv.self(i);
-        const int cnt = a.nnb[i];
+        const int cnt = APIP_CHK(a.status, BND_LIST_LEN, a.nnb[i], a.max_nb + 1);
         for (int s = cg; s < cnt; s += 4) {
-          const int j = a.nbl[(size_t)s * a.nmax + i];
+          const int j = APIP_CHK(a.status, BND_NEIGHBOUR, a.nbl[(size_t)s * a.nmax + i], a.n);
           const auto d = a.pv.vec(si, j);
           const float r2 = dot3(d, d);
           if (!(r2 < rc2)) continue;
@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(lt::kT, FORCE ? 1 : 2)
       if (cg == 0) {
         float c = 0.f;
         if (valid) {
-          c = (float)a.cvec[i];
+          c = (float)fix_get(&a.cvec[i], a.det);
           a.cvec[i] = 0.0;
         }
         C1[r] = c;
@@ -695,10 +695,10 @@ __global__ void __launch_bounds__(lt::kT, FORCE ? 1 : 2)
       // the force of this thread's neighbour entries
       const float* dG = P + r * kPs;
       const auto sk = a.pv.self(i);
-      const int cnt = a.nnb[i];
+      const int cnt = APIP_CHK(a.status, BND_LIST_LEN, a.nnb[i], a.max_nb + 1);
       double fk[3] = {0.0, 0.0, 0.0};
       for (int s = cg; s < cnt; s += 4) {
-        const int j = a.nbl[(size_t)s * a.nmax + i];
+        const int j = APIP_CHK(a.status, BND_NEIGHBOUR, a.nbl[(size_t)s * a.nmax + i], a.n);
         const auto d = a.pv.vec(sk, j);
         const float r2 = dot3(d, d);
         if (!(r2 < rc2)) continue;
@@ -707,13 +707,13 @@ __global__ void __launch_bounds__(lt::kT, FORCE ? 1 : 2)
         const float fc = ftrans(rr, a.ace_rc_lo, a.ace_rc, inv_w, &dfc);
         const float v = dfeatures_window(rr, fc, dfc, kappa, dG) / rr;
         const double f0 = (double)(v * d.x), f1 = (double)(v * d.y), f2 = (double)(v * d.z);
-        atomicAdd(&a.force[3 * j], -f0);
-        atomicAdd(&a.force[3 * j + 1], -f1);
-        atomicAdd(&a.force[3 * j + 2], -f2);
+        scatter_add(&a.force[3 * j], -f0, a.det);
+        scatter_add(&a.force[3 * j + 1], -f1, a.det);
+        scatter_add(&a.force[3 * j + 2], -f2, a.det);
         fk[0] += f0; fk[1] += f1; fk[2] += f2;
       }
 #pragma unroll
-      for (int k = 0; k < 3; ++k) atomicAdd(&a.force[3 * i + k], fk[k]);
+      for (int k = 0; k < 3; ++k) scatter_add(&a.force[3 * i + k], fk[k], a.det);
     }
     __syncthreads();   // the next tile rewrites the dG rows (partial rows) and c
   }
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(lt::kT, FORCE ? 1 : 2)
 // Here for one atom k of the compacted list; resets c_k.
 template <typename T>
 __device__ __forceinline__ void mlp_force_atom(const Args<T>& a, int k) {
-  const double c = a.cvec[k];
+  const double c = fix_get(&a.cvec[k], a.det);
   a.cvec[k] = 0.0;
   T G[kIn];
   descriptors_of(a, k, G);
@@ -749,10 +749,10 @@ __device__ __forceinline__ void mlp_force_atom(const Args<T>& a, int k) {
   }
   const auto sk = a.pv.self(k);
   const T rc2 = a.ace_rc * a.ace_rc, inv_w = T(1) / (a.ace_rc - a.ace_rc_lo);
-  const int cnt = a.nnb[k];
+  const int cnt = APIP_CHK(a.status, BND_LIST_LEN, a.nnb[k], a.max_nb + 1);
   double fk[3] = {0.0, 0.0, 0.0};
   for (int s = 0; s < cnt; ++s) {
-    const int j = a.nbl[(size_t)s * a.nmax + k];
+    const int j = APIP_CHK(a.status, BND_NEIGHBOUR, a.nbl[(size_t)s * a.nmax + k], a.n);
     const auto dv = a.pv.vec(sk, j);
     const T r2 = dot3(dv, dv);
     if (!(r2 < rc2)) continue;
@@ -766,13 +766,13 @@ __device__ __forceinline__ void mlp_force_atom(const Args<T>& a, int k) {
     for (int m = 0; m < kIn; ++m) v += dG[m] * dphi[m];
     const T ir = T(1) / r;
     const double f0 = (double)(v * dv.x * ir), f1 = (double)(v * dv.y * ir), f2 = (double)(v * dv.z * ir);
-    atomicAdd(&a.force[3 * j], -f0);
-    atomicAdd(&a.force[3 * j + 1], -f1);
-    atomicAdd(&a.force[3 * j + 2], -f2);
+    scatter_add(&a.force[3 * j], -f0, a.det);
+    scatter_add(&a.force[3 * j + 1], -f1, a.det);
+    scatter_add(&a.force[3 * j + 2], -f2, a.det);
     fk[0] += f0; fk[1] += f1; fk[2] += f2;
   }
 #pragma unroll
-  for (int q = 0; q < 3; ++q) atomicAdd(&a.force[3 * k + q], fk[q]);
+  for (int q = 0; q < 3; ++q) scatter_add(&a.force[3 * k + q], fk[q], a.det);
 }
 
 // The atoms with c_k != 0 in warp-ballot order (counts[1] of them), so that the
@@ -795,7 +795,7 @@ __global__ void __launch_bounds__(128) k_mlp_force(Args<T> a) {
   pdl_begin();
   const int count = a.counts[1];
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x)
-    mlp_force_atom(a, a.clist[q]);
+    mlp_force_atom(a, APIP_CHK(a.status, BND_COMPACT, a.clist[q], a.n));
 }
 
 template <typename T>

@@ -20,13 +20,19 @@ def lib():
     return apip
 
 
-def _declared():
+def _declared(checked=False):
+    """Function names the header declares; the declarations inside
+    #ifdef APIP_CHECK_BOUNDS only with checked=True (the bounds-checked build)."""
     text = open(os.path.join(ROOT, "include", "apip.h")).read()
+    if not checked:
+        text = re.sub(r"#ifdef APIP_CHECK_BOUNDS.*?#endif", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(apip_[a-z_]+)\s*\(", text)))
 
 
 def test_header_declares_the_boundary():
     names = _declared()
+    assert "apip_check_bounds_selftest" not in names
+    assert "apip_check_bounds_selftest" in _declared(checked=True)
     for n in ("apip_create", "apip_destroy", "apip_build_neighbors", "apip_init_csp_pairs", "apip_switch",
               "apip_energy_forces", "apip_verlet_step", "apip_sync", "apip_last_error", "apip_get_field",
               "apip_ace_basis_size"):
@@ -59,9 +65,11 @@ def test_create_rejects_bad_parameters_before_touching_the_device(lib):
     from paper_2512_07693_gb300 import workloads as W
     s = W.config("vacancy2k", lib.apip_ace_basis_size)
     cases = [("csp_nnb", 3), ("precision", 7), ("lam_mode", 9), ("ace_n_max", 0), ("ace_l_max", 5),
-             ("sw_d_hi", -1.0), ("max_nb", 0), ("ace_n_basis", 5), ("skin", -0.1), ("csp_rcut", 99.0)]
+             ("sw_d_hi", -1.0), ("max_nb", 0), ("ace_n_basis", 5), ("skin", -0.1), ("csp_rcut", 99.0),
+             ("deterministic", 2), ("mixing", lib.APIP_MIX_FORCE)]
     for field, val in cases:
-        p = lib.make_params(s["prm"])
+        # (force mixing is rejected only together with the deterministic mode)
+        p = lib.make_params(s["prm"], deterministic=field == "mixing")
         setattr(p, field, val)
         ctx = ctypes.c_void_p()
         assert lib.lib.apip_create(ctypes.byref(p), 100, ctypes.byref(ctx)) == lib.APIP_ERR_ARG, field
@@ -74,3 +82,4 @@ def test_create_rejects_bad_parameters_before_touching_the_device(lib):
     assert lib.lib.apip_sync(None, None) == lib.APIP_ERR_ARG
     assert lib.lib.apip_destroy(None) == lib.APIP_OK
     assert lib.lib.apip_last_error(None) == b""
+
