@@ -21,13 +21,13 @@ def to_dev(torch, s):
 
 
 def run_gpu(s, precision="fp64", lam_mode="paper", grad_lambda=True, max_nb=96, fields=True, prm=None, ace_group=0,
-            mixing="energy", lam_fixed=None):
+            mixing="energy", lam_fixed=None, deterministic=False):
     torch = torch_cuda()
     from paper_2512_07693_gb300 import apip
     prm = prm or s["prm"]
     n = len(s["pos"])
     m = apip.Apip(prm, n, precision=precision, lam_mode=lam_mode, grad_lambda=grad_lambda, max_nb=max_nb,
-                  ace_group=ace_group, mixing=mixing)
+                  ace_group=ace_group, mixing=mixing, deterministic=deterministic)
     t = to_dev(torch, s)
     if lam_fixed is not None:
         m.set_lam_fixed(torch.tensor(lam_fixed, dtype=torch.float64, device="cuda"))
