@@ -144,7 +144,9 @@ typedef struct apip_params {
                                 the same bits, and a run resumed from a checkpoint that holds
                                 APIP_FIELD_BUILD_POS continues the trajectory bit for bit.
                                 Costs three small kernels per call and one per list build.
-                                Not with APIP_MIX_FORCE (APIP_ERR_ARG).  0: float64 atomics,
+                                Requires APIP_FP32 with ace_nu_max <= 3 and ace_l_max <= 3
+                                (elsewhere dE/dA is summed with shared-memory atomics) and
+                                APIP_MIX_ENERGY; otherwise APIP_ERR_ARG.  0: float64 atomics,
                                 results reproducible to rounding */
   double prec_shift;         /* energy zero of the precise model: E^prec_i is lowered by this
                                 constant (eV per atom).  0 keeps E^prec as defined above.  Set

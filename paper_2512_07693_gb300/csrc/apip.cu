@@ -114,6 +114,10 @@ apip_status check_params(const apip_params* p, std::string* why) {
   if (p->mixing != APIP_MIX_ENERGY && p->mixing != APIP_MIX_FORCE) return bad("unknown mixing");
   if (p->deterministic != 0 && p->deterministic != 1) return bad("deterministic must be 0 or 1");
   if (p->deterministic && p->mixing == APIP_MIX_FORCE) return bad("the deterministic mode does not support force mixing");
+  // the float64 path and the evaluations with l_max = 4 or body order 4 sum dE/dA
+  // with shared-memory atomics, whose order is not fixed
+  if (p->deterministic && !(p->precision == APIP_FP32 && p->ace_nu_max <= 3 && p->ace_l_max <= 3))
+    return bad("the deterministic mode needs the float32 path with ACE body order <= 3 and l_max <= 3");
   if (!(p->ace_rc > 0 && p->ace_rc_width > 0 && p->ace_rc_width <= p->ace_rc)) return bad("bad ACE cutoff");
   if (!(p->ace_eps > 0)) return bad("ace_eps must be > 0");
   if (!std::isfinite(p->prec_shift)) return bad("prec_shift must be finite");

@@ -66,10 +66,11 @@ def test_create_rejects_bad_parameters_before_touching_the_device(lib):
     s = W.config("vacancy2k", lib.apip_ace_basis_size)
     cases = [("csp_nnb", 3), ("precision", 7), ("lam_mode", 9), ("ace_n_max", 0), ("ace_l_max", 5),
              ("sw_d_hi", -1.0), ("max_nb", 0), ("ace_n_basis", 5), ("skin", -0.1), ("csp_rcut", 99.0),
-             ("deterministic", 2), ("mixing", lib.APIP_MIX_FORCE)]
-    for field, val in cases:
-        # (force mixing is rejected only together with the deterministic mode)
-        p = lib.make_params(s["prm"], deterministic=field == "mixing")
+             ("deterministic", 2), ("mixing", lib.APIP_MIX_FORCE), ("precision", lib.APIP_FP64)]
+    for k, (field, val) in enumerate(cases):
+        # (the last two are rejected only together with the deterministic mode,
+        # which needs the float32 path and energy mixing)
+        p = lib.make_params(s["prm"], precision="fp32", deterministic=k >= len(cases) - 2)
         setattr(p, field, val)
         ctx = ctypes.c_void_p()
         assert lib.lib.apip_create(ctypes.byref(p), 100, ctypes.byref(ctx)) == lib.APIP_ERR_ARG, field
