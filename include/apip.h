@@ -287,8 +287,8 @@ apip_status apip_get_field(apip_ctx* ctx, int32_t field, void* dst, int64_t n, v
  * the deterministic mode's fixed-point to float64 conversion), REDUCE.
  * Independently of apip_profile, every call is an NVTX range named after it
  * ("apip_energy_forces", "apip_verlet_step", "apip_switch",
- * "apip_build_neighbors") holding one range per phase ("apip/prep",
- * "apip/neighbor", "apip/pass1", "apip/pass2", "apip/ace", "apip/csp"), which a
+ * "apip_build_neighbors") holding one range per phase ("apip.prep",
+ * "apip.neighbor", "apip.pass1", "apip.pass2", "apip.ace", "apip.csp"), which a
  * profiler attached to the process shows and by which ncu --nvtx selects
  * kernels; without an attached tool they cost a few nanoseconds per call. */
 enum {

@@ -25,7 +25,7 @@ namespace {
 // An NVTX range: a named span of host time that a profiler attached to the
 // process shows on its timeline and by which ncu's --nvtx filters select the
 // kernels launched inside it.  Each call is one range ("apip_energy_forces", ...)
-// with one nested range per phase ("apip/pass2", ...).  Without an attached
+// with one nested range per phase ("apip.pass2", ...).  Without an attached
 // tool a push or pop costs a few nanoseconds.
 struct NvtxRange {
   bool open = true;
@@ -384,24 +384,24 @@ void pass1(const Args<T>& a, cudaStream_t s) {
 // The force pipeline after prep (or after the drift of a Verlet step).
 template <typename T>
 void force_pipeline(apip_ctx* c, Args<T>& a, cudaStream_t s) {
-  { NvtxRange nv("apip/neighbor"); Phase ph(c, APIP_PHASE_NEIGHBOR, a.det ? 3 : 2, s); launch_neighbors<T>(a, c->ncell, s); }
-  { NvtxRange nv("apip/pass1"); Phase ph(c, APIP_PHASE_PASS1, 1, s); pass1<T>(a, s); }
-  { NvtxRange nv("apip/pass2"); Phase ph(c, APIP_PHASE_PASS2, a.det ? 3 : 1, s); launch_pass2<T>(a, s);
+  { NvtxRange nv("apip.neighbor"); Phase ph(c, APIP_PHASE_NEIGHBOR, a.det ? 3 : 2, s); launch_neighbors<T>(a, c->ncell, s); }
+  { NvtxRange nv("apip.pass1"); Phase ph(c, APIP_PHASE_PASS1, 1, s); pass1<T>(a, s); }
+  { NvtxRange nv("apip.pass2"); Phase ph(c, APIP_PHASE_PASS2, a.det ? 3 : 1, s); launch_pass2<T>(a, s);
     if (a.force_mix) launch_fm_buffer<T>(a, s); }
-  { NvtxRange nv("apip/ace"); Phase ph(c, APIP_PHASE_ACE, 1, s); const AceDev<T> t = ace_dev<T>(c);
+  { NvtxRange nv("apip.ace"); Phase ph(c, APIP_PHASE_ACE, 1, s); const AceDev<T> t = ace_dev<T>(c);
     if (t.kind == kAceStreamed) launch_ace_stream<T>(a, t, c->ace_blocks, s);
     else launch_ace_pool<T>(a, t, c->ace_blocks, s); }
   if (a.lam_mode == APIP_LAM_PAPER && a.grad_lambda) {
-    NvtxRange nv("apip/csp");
+    NvtxRange nv("apip.csp");
     Phase ph(c, APIP_PHASE_CSP, 1, s);
     launch_csp_force<T>(a, s);
   } else if (a.lam_mode == APIP_LAM_LEARNED && a.grad_lambda) {
-    NvtxRange nv("apip/csp");
+    NvtxRange nv("apip.csp");
     Phase ph(c, APIP_PHASE_CSP, 1, s);
     launch_mlp_force<T>(a, s);
   }
   if (a.det && a.force) {   // the fixed-point force sums back to float64
-    NvtxRange nv("apip/csp");
+    NvtxRange nv("apip.csp");
     Phase ph(c, APIP_PHASE_CSP, 1, s);
     launch_fix_finish(a.force, a.n, s);
   }
@@ -414,7 +414,7 @@ apip_status energy_forces_t(apip_ctx* c, const double* pos, const int32_t* id, i
   Args<T> a = make_args<T>(c, pos, id, n, force, e_atom);
   set_view<T>(a, c);
   mark_atom_count(c, n, s);
-  { NvtxRange nv("apip/prep"); Phase ph(c, APIP_PHASE_PREP, 1, s); launch_prep<T>(a, s); }
+  { NvtxRange nv("apip.prep"); Phase ph(c, APIP_PHASE_PREP, 1, s); launch_prep<T>(a, s); }
   force_pipeline<T>(c, a, s);
   if (e_total) {
     Phase ph(c, APIP_PHASE_REDUCE, 1, s);
@@ -471,7 +471,7 @@ apip_status verlet_t(apip_ctx* c, double* pos, double* vel, double* force, const
   // are left unread and the ACE kernel clears the rebuild flag
   double* tp = thermo ? c->thermo_part : nullptr;
   for (int k = 0; k < steps; ++k) {
-    { NvtxRange nv("apip/prep"); Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, k == 0 ? 0 : 1, pos, vel, force, inv_mass, dt, k > 0 ? tp : nullptr, s); }
+    { NvtxRange nv("apip.prep"); Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, k == 0 ? 0 : 1, pos, vel, force, inv_mass, dt, k > 0 ? tp : nullptr, s); }
     if (a.ind_on) {   // the indenter centre moves with the drift
       for (int q = 0; q < 3; ++q) c->ind_c[q] += dt * c->ind_v[q];
       set_ind_center(a, c->geo, c->ind_c);
@@ -484,7 +484,7 @@ apip_status verlet_t(apip_ctx* c, double* pos, double* vel, double* force, const
                    k > 0 ? thermo + 5 * (k - 1) : nullptr, c->flags, c->counts, nullptr, c->cell_count, c->ncell, s);
     }
   }
-  { NvtxRange nv("apip/prep"); Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, 2, pos, vel, force, inv_mass, dt, tp, s); }
+  { NvtxRange nv("apip.prep"); Phase ph(c, APIP_PHASE_PREP, 1, s); launch_verlet<T>(a, 2, pos, vel, force, inv_mass, dt, tp, s); }
   if (thermo) {
     Phase ph(c, APIP_PHASE_REDUCE, 1, s);
     launch_thermo_final(c->thermo_part, ntb, thermo + 5 * (steps - 1), s);
