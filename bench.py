@@ -48,7 +48,7 @@ L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2, written between timed steps
 # DRAM bytes (read + write) per launch of the step's dominant kernel on this
 # workload from an ncu capture, with the commit of the kernel's source it was
 # taken at; reported beside the roofline while that kernel is unchanged
-NCU_TRAFFIC_CURRENT = {"pass2": (69.683456e6 + 2.065152e6, "ncu capture of k_pass2 at commit cc18232")}
+NCU_TRAFFIC_CURRENT = {"pass2": (69.683968e6 + 0.957696e6, "ncu capture of k_pass2 at commit 513b48c")}
 
 
 def parse():

@@ -682,8 +682,11 @@ __global__ void k_csp_force(Args<T> a) {
   pdl_begin();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.n) return;
-  const double c = fix_get(&a.cvec[j], a.det);
-  if ((__double_as_longlong(c) << 1) == 0) return;   // c == +-0, tested on the bits (off the float64 pipe)
+  // c == +-0 tested on the bits (off the float64 pipe; a zero fixed-point slot has
+  // the bits of +0), so that only the few atoms with c != 0 convert it
+  const double raw = a.cvec[j];
+  if ((__double_as_longlong(raw) << 1) == 0) return;
+  const double c = a.det ? fix_get(&raw, 1) : raw;
   a.cvec[j] = 0.0;
   const auto sj = a.pv.self(j);
   // the partners' indices as pass 1 of this call checked them (cached by atom
