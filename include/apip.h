@@ -259,7 +259,8 @@ const char* apip_last_error(apip_ctx* ctx);
  * testing.  Copies n entries as float64 into dst (device) unless stated:
  *   APIP_FIELD_G, _D, _WBAR, _LAM, _DLAM, _E_EAM, _E_ACE (0 unless lam > 0), _ZETA
  *   APIP_FIELD_ACE_LIST : int64 dst, the compacted atom indices with lam > 0
- *                         (unordered; only the first count entries are defined)
+ *                         (unordered, in index order in the deterministic mode; only the
+ *                         first count entries are defined)
  *   APIP_FIELD_NNB      : int64 dst, neighbours per atom (within cutoff + skin)
  *   APIP_FIELD_NBLIST   : int64 dst [n][max_nb], neighbour indices (-1 padded)
  *   APIP_FIELD_CSP      : int64 dst [n][csp_nnb], partner IDs (-1 = none); row k holds
