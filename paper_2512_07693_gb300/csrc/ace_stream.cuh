@@ -103,6 +103,9 @@ __device__ __forceinline__ void coupling(const T* Ak, T* Gk, int a1, int a2, int
         s2 += r.k2 * d;
       }
     }
+    // the remaining partners (a few per coupling): a plain loop, not unrolled, so
+    // that the per-type coupling bodies stay small enough for the instruction cache
+#pragma unroll 1
     for (int p = pb + PF; p < pe; ++p) {
       const Rec<T> r = ld(part + p);
       const T* y = Ak + r.key * NAT;
@@ -129,6 +132,7 @@ __device__ __forceinline__ void coupling(const T* Ak, T* Gk, int a1, int a2, int
       }
     };
     adj_partner(first);   // every coupling has at least one partner
+#pragma unroll 1
     for (int p = pb + 1; p < pe; ++p) adj_partner(ld(part + p));
     T g1[N1], g2[N2];
 #pragma unroll
