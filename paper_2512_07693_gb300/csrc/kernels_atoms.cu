@@ -220,11 +220,37 @@ __global__ void k_nbfill(Args<T> a) {
       ++n2;
     }
   };
+  // FP32 path: the squared distance from the atom to the nearest face of the
+  // neighbour cell at offset -1, 0, +1 along each axis, from the atom's fraction
+  // within its own cell (the low 32 bits of q * nc, exact); a cell whose nearest
+  // point is beyond r_list (with a 1e-5 relative margin, far above the rounding of
+  // these gaps) holds no candidate and is skipped.  Only with at least 5 cells per
+  // axis, where no member of a neighbour cell is nearer through the other side of
+  // the box.
+  float lo2[3] = {0.f, 0.f, 0.f}, hi2[3] = {0.f, 0.f, 0.f};
+  float prune2 = INFINITY;
+  if constexpr (sizeof(T) == 4) {
+    if (a.geo.nc[0] >= 5 && a.geo.nc[1] >= 5 && a.geo.nc[2] >= 5) {
+      const unsigned qq[3] = {si.q.x, si.q.y, si.q.z};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const unsigned frac = (unsigned)((unsigned long long)qq[k] * (unsigned)a.geo.nc[k]);
+        const float w = a.pv.unit[k] / (float)a.geo.nc[k];
+        const float lo = (float)frac * w, hi = (4294967296.0f - (float)frac) * w;
+        lo2[k] = lo * lo;
+        hi2[k] = hi * hi;
+      }
+      prune2 = (float)(a.r_list2 * (1.0 + 1e-5));
+    }
+  }
+  auto gap = [&](int k, int d) { return d < 0 ? lo2[k] : (d > 0 ? hi2[k] : 0.f); };
   for (int dz = -1; dz <= 1; ++dz) {
     const int cz = (c[2] + dz + a.geo.nc[2]) % a.geo.nc[2];
     for (int dy = -1; dy <= 1; ++dy) {
       const int cy = (c[1] + dy + a.geo.nc[1]) % a.geo.nc[1];
+      const float gzy = gap(2, dz) + gap(1, dy);
       for (int dx = -1; dx <= 1; ++dx) {
+        if (gzy + gap(0, dx) > prune2) continue;
         const int cx = (c[0] + dx + a.geo.nc[0]) % a.geo.nc[0];
         const int cell = APIP_CHK(a.status, BND_CELL, (cz * a.geo.nc[1] + cy) * a.geo.nc[0] + cx, a.ncell);
         const int m = min(a.cell_count[cell], a.cell_cap);
