@@ -140,7 +140,8 @@ typedef struct apip_params {
                                 index after binning, the compacted list is written in index
                                 order, and every scattered force, c-vector and indenter-work
                                 contribution is rounded to a multiple of 2^-40 and summed as a
-                                64-bit integer.  Repeated runs from the same state then give
+                                64-bit integer (each sum must stay below 2^23 = 8.4e6 in
+                                magnitude: eV/A for forces).  Repeated runs from the same state then give
                                 the same bits, and a run resumed from a checkpoint that holds
                                 APIP_FIELD_BUILD_POS continues the trajectory bit for bit.
                                 Costs three small kernels per call and one per list build.
