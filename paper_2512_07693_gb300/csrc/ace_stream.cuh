@@ -253,8 +253,12 @@ __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev
     // 2. embedding channels
     {
       Acc<T> f1, f2;
+      // the next record is loaded while this one is evaluated
+      Rec<T> rnext{};
+      if (slice < t.npr) rnext = ld(t.prec + slice);
       for (int r = slice; r < t.npr; r += NS) {
-        const Rec<T> rc = ld(t.prec + r);
+        const Rec<T> rc = rnext;
+        if (r + NS < t.npr) rnext = ld(t.prec + r + NS);
 #ifdef APIP_CHECK_BOUNDS
         if (!record_ok(a.status, rc, nA)) continue;
 #endif
@@ -313,8 +317,12 @@ __global__ void __launch_bounds__(kAceThreads, 2) k_ace_stream(Args<T> a, AceDev
     {
       const T dfs = g.dfs[ka];
       Acc<T> unused1, unused2;
+      // the next record is loaded while this one is evaluated
+      Rec<T> rnext{};
+      if (slice < t.npr) rnext = ld(t.prec + slice);
       for (int r = slice; r < t.npr; r += NS) {
-        const Rec<T> rc = ld(t.prec + r);
+        const Rec<T> rc = rnext;
+        if (r + NS < t.npr) rnext = ld(t.prec + r + NS);
 #ifdef APIP_CHECK_BOUNDS
         if (!record_ok(a.status, rc, nA)) continue;
 #endif
